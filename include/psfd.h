@@ -1,0 +1,212 @@
+/*
+ * psfd.h - C ABI of the B300 library for the background-decomposed,
+ * preconditioned pseudo-spectral frequency-domain (PSFD) solve of the
+ * scattered field of a 3-D EUV mask, with a factorised-FNO warm start
+ * (Kim & Gillijns, "Physics-Informed Neural Operator for Warm-Starting
+ * Background-Decomposed and Preconditioned PSFD").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Complex numbers are complex64, stored as interleaved (re, im) float pairs
+ *   (psfd_c64).  Fields are arrays [nrhs][3][nz][ny][nx] (x fastest) holding
+ *   the Bloch envelopes of (Ex, Ey, Ez): physical field = envelope *
+ *   exp(i (kx_inc x + ky_inc y)).  Grid points sit at x = i dx, y = j dy,
+ *   z = k dz.  Time dependence exp(-i w t); illumination comes from +z.
+ * - "Real-space" arrays use that layout directly.  Arrays marked HYBRID hold
+ *   the same field after the unitary lateral DFT (1/sqrt(nx ny) scaling),
+ *   indexed [nrhs][3][nz][ky][kx] with kx, ky in FFT order.  Norms and inner
+ *   products are the same in both domains.
+ * - Every array pointer is caller-owned DEVICE memory unless the argument is
+ *   documented as host memory.  Calls are asynchronous on the plan's stream
+ *   unless stated otherwise; the library allocates only inside
+ *   psfd_plan_create / psfd_background (plan-owned tables and scratch), inside
+ *   psfd_solve when the caller passes no workspace (see
+ *   psfd_solve_workspace_size) and, temporarily, inside psfd_spectral_upsample.
+ * - Return codes: PSFD_OK (0) or one of the PSFD_ERR_* / PSFD_NOT_CONVERGED
+ *   values; psfd_last_error() returns a message for the last failing call on
+ *   the calling thread.  Argument errors are detected before any launch.
+ */
+#ifndef PSFD_H
+#define PSFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSFD_API __attribute__((visibility("default")))
+#else
+#define PSFD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } psfd_c64;
+typedef struct psfd_plan_s* psfd_plan;
+
+enum {
+  PSFD_OK = 0,
+  PSFD_ERR_ARG = 1,          /* invalid argument or unsupported size            */
+  PSFD_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  PSFD_NOT_CONVERGED = 3,    /* maxit reached before the tolerance (solve)      */
+  PSFD_ERR_BREAKDOWN = 4,    /* Krylov breakdown (rho or <rhat,v> vanished)     */
+  PSFD_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up              */
+  PSFD_ERR_STATE = 6         /* call order violated (e.g. apply before background) */
+};
+
+enum { PSFD_TE = 0, PSFD_TM = 1 };
+
+/* psfd_apply / psfd_precond flags */
+enum {
+  PSFD_PRECOND = 1,          /* apply A M instead of A                          */
+  PSFD_HYBRID = 2,           /* x and y are in the HYBRID (kx, ky, z) domain    */
+  PSFD_ADJOINT = 4           /* apply A^H (or (A M)^H = M A^H with PSFD_PRECOND) */
+};
+
+enum { PSFD_BICGSTAB = 0, PSFD_GMRES = 1 };
+
+/* Problem description (lengths in nm).  Sec. 2.2 of the paper states the
+ * operator; the discretisation constants it leaves to the companion PSFD
+ * paper are explicit fields here. */
+typedef struct {
+  int nx, ny, nz;            /* grid; nx, ny, nz in {16,32,48,64,96,128,256,512}-type sizes, see psfd_supported */
+  int nrhs;                  /* right-hand sides sharing this operator (e.g. TE + TM)      */
+  double dx, dy, dz;         /* grid spacing                                                */
+  double lambda;             /* vacuum wavelength (13.5 nm for EUV)                         */
+  double theta_deg, phi_deg; /* incidence polar / azimuth angle; sets the Bloch shift       */
+  int pml_planes;            /* PML thickness in planes at each z end (0 = periodic)        */
+  double pml_R0;             /* nominal normal-incidence PML reflection (sets the strength) */
+  int z_ml;                  /* plane index of the multilayer interface z_ml                */
+  double eps_abs_re, eps_abs_im;  /* absorber permittivity; deps = fill * (eps_abs - 1)     */
+  double m_min, k_ref, gamma, damp_eps_rel;  /* spectral damping (Eq. spectral_damping_mask);
+                                                k_ref <= 0 means k0; eps = damp_eps_rel * k0^2 */
+  double sigma_px;           /* lateral Gaussian smoothing width of the mask (pixels)       */
+  void* stream;              /* cudaStream_t for every call on this plan (NULL = legacy)    */
+} psfd_params_t;
+
+/* Multilayer below z_ml, top to bottom, host memory (Sec. 3: 40 Mo/Si pairs). */
+typedef struct {
+  int n_layers;
+  const double* n_re;        /* [n_layers] refractive index, real part  */
+  const double* n_im;        /* [n_layers] imaginary part (absorbing > 0) */
+  const double* d;           /* [n_layers] thickness, nm                 */
+  double sub_re, sub_im;     /* substrate index                          */
+} psfd_stack_t;
+
+typedef struct {
+  int iters;                 /* Krylov iterations (operator applications for GMRES)      */
+  int status;                /* PSFD_OK / PSFD_NOT_CONVERGED / PSFD_ERR_BREAKDOWN          */
+  double r_rel;              /* true relative residual ||b - A E|| / ||b|| (FP64), Eq. relative_residual */
+  double r_rel_recursive;    /* the solver's recursive estimate at exit                   */
+  double r_rel_initial;      /* ||b - A E_base|| / ||b|| before the first iteration       */
+} psfd_info_t;
+
+/* ---------------------------------------------------------------- plan */
+
+/* Create a plan: validates sizes, builds the PML profile s(z), the Bloch-shifted
+ * wavenumbers, the FFT twiddle tables, and allocates plan-owned scratch.  Blocks
+ * until the tables are on the device.  The multilayer reflection is computed by
+ * psfd_background.  Returns PSFD_ERR_ARG for unsupported sizes. */
+PSFD_API int psfd_plan_create(psfd_plan* plan, const psfd_params_t* params);
+PSFD_API int psfd_plan_destroy(psfd_plan plan);
+
+/* 1 if (n along a lateral axis, nz) is supported by the FFT kernels, else 0. */
+PSFD_API int psfd_supported(int nx, int ny, int nz);
+
+/* ---------------------------------------------------------------- geometry (Sec. 2.1 / Sec. 3)
+ * a_bin: device uint8 [ny][nx], binary indicator of the absorber layout.
+ * zprof: HOST float [nz], fraction of each z cell covered by the absorber.
+ * fill:  device float [nz][ny][nx] (output): Gaussian-smoothed indicator
+ *        (spectral, periodic, width sigma_px) times zprof[z].
+ */
+PSFD_API int psfd_mask_fill(psfd_plan plan, const uint8_t* a_bin, const float* zprof, float* fill);
+
+/* ---------------------------------------------------------------- background (Eq. bg_source)
+ * Computes in FP64 on the device the reflection coefficients r_s, r_p (ratios of
+ * reflected to incident tangential E) of the stack for every lateral Bloch mode
+ * (transfer-matrix method), registers `fill` (device [nz][ny][nx], kept by
+ * pointer: it must stay alive while the plan is used), and writes the source
+ *   b = k0^2 deps (E_inc + R E_inc)
+ * for each right-hand side r with polarisation pol[r] (HOST int array [nrhs],
+ * PSFD_TE = E along s, PSFD_TM).  b: device [nrhs][3][nz][ny][nx], real space. */
+PSFD_API int psfd_background(psfd_plan plan, const psfd_stack_t* stack, const float* fill,
+                    const int* pol, psfd_c64* b);
+
+/* Copy the FP64 reflection tables to host: rs, rp, kz0 as [ny][nx] complex
+ * double pairs (re, im), each array 2*nx*ny doubles.  Synchronous. */
+PSFD_API int psfd_reflection_tables(psfd_plan plan, double* rs, double* rp, double* kz0);
+
+/* ---------------------------------------------------------------- operator (Sec. 2.2)
+ * y = A x with
+ *   A E = curl_s curl_s E - k0^2 E - k0^2 deps (E + R E)    (Eqs. bg_source,
+ *         vector_helmholtz_operator; derivatives pseudo-spectral, PML in z)
+ * flags: PSFD_PRECOND -> y = A M x (Eq. right_preconditioned);
+ *        PSFD_ADJOINT -> y = A^H x (with PRECOND: M A^H x);
+ *        PSFD_HYBRID  -> x, y in the HYBRID domain (no lateral transforms of x, y).
+ * x, y: device [nrhs][3][nz][ny][nx]; x and y must not overlap. */
+PSFD_API int psfd_apply(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int flags);
+
+/* y = M x, spectral damping (Eq. spectral_damping_action): componentwise 3-D
+ * Fourier multiplier m(k).  flags: PSFD_HYBRID.  In-place (x == y) allowed. */
+PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int flags);
+
+/* ---------------------------------------------------------------- solve (Sec. 3, warm start)
+ * Solves A E = b for every right-hand side with right preconditioning and an
+ * affine warm start: E = E_base + M y with A M y = b - A E_base
+ * (Eqs. right_correction_solution, right_preconditioned_system); x0 = NULL is
+ * the null initialisation (Eq. right_preconditioned).  With use_precond = 0, M
+ * is the identity (the paper's "null preconditioner").  Convergence: recursive
+ * relative residual <= tol with ||b|| of the original b (Eq. relative_residual);
+ * the true residual is recomputed in FP64 at exit.
+ *   b, x0 (nullable), E: device [nrhs][3][nz][ny][nx], real space.
+ *   method: PSFD_BICGSTAB (the paper's solver) or PSFD_GMRES (restart m).
+ *   info: HOST array [nrhs].  Blocks until the solve has finished.
+ *   workspace: device scratch of psfd_solve_workspace_size() bytes, or NULL to
+ *   let the library allocate (and free) it inside the call.
+ * Returns PSFD_OK when every right-hand side converged, else the worst status. */
+PSFD_API int psfd_solve(psfd_plan plan, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E,
+               double tol, int maxit, int method, int restart, int use_precond,
+               psfd_info_t* info, void* workspace, size_t workspace_bytes);
+PSFD_API size_t psfd_solve_workspace_size(psfd_plan plan, int method, int restart);
+
+/* Optional residual history: if set, psfd_solve writes ||r_k|| / ||b|| for every
+ * iteration k < capacity and right-hand side r to hist[r * capacity + k] (HOST). */
+PSFD_API int psfd_set_history(psfd_plan plan, double* hist, int capacity);
+
+/* ---------------------------------------------------------------- factorised FNO (Sec. 2.1, Eqs. 1-5)
+ * Device pointers to float32 parameters; complex kernels as psfd_c64.
+ *   lift_w [dv][4], lift_b [dv]                         (inputs: a, x/Lx, y/Ly, z/Lz)
+ *   kxy [L][my][mx][dv][dv]  (modes k = -m/2..m/2-1, centred order; [out][in])
+ *   kz  [L][mz][dv][dv]
+ *   w1 [L][dh][dv], b1 [L][dh], w2 [L][dv][dh], b2 [L][dv]
+ *   q1 [dq][dv], qb1 [dq], q2 [6][dq], qb2 [6]           (6 = Re/Im of Ex, Ey, Ez)
+ * Mode mixing rounds both operands to bfloat16 and accumulates in float32. */
+typedef struct {
+  int dv, dh, layers, mx, my, mz, dq;
+  const float* lift_w; const float* lift_b;
+  const psfd_c64* kxy; const psfd_c64* kz;
+  const float* w1; const float* b1; const float* w2; const float* b2;
+  const float* q1; const float* qb1; const float* q2; const float* qb2;
+} fno_weights_t;
+
+/* E_out = G_theta(a): a device float [B][nz][ny][nx] (smoothed indicator),
+ * E_out device [B][3][nz][ny][nx] complex64.  workspace of
+ * fno_workspace_size() bytes (device).  stream: cudaStream_t or NULL. */
+PSFD_API size_t fno_workspace_size(const fno_weights_t* w, int B, int nx, int ny, int nz);
+PSFD_API int fno_forward(const fno_weights_t* w, const float* a, int B, int nx, int ny, int nz,
+                psfd_c64* E_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Zero-pad the 3-D spectrum of src [nb][nz0][ny0][nx0] to dst [nb][nz][ny][nx]
+ * (spectral interpolation of a coarse prediction, amplitude preserving). */
+PSFD_API int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,
+                           psfd_c64* dst, int nx, int ny, int nz, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+PSFD_API const char* psfd_last_error(void);
+PSFD_API const char* psfd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSFD_H */

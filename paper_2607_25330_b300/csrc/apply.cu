@@ -1,0 +1,641 @@
+// The PSFD operator apply (Sec. 2.2) on the device.
+//
+// Krylov vectors live in the HYBRID domain (kx, ky, z) (unitary lateral DFT).
+// In that domain every term except the contrast is local to one (kx, ky)
+// column: the spectral-damping preconditioner M (a 3-D Fourier multiplier:
+// FFT_z, x m(k), IFFT_z), the stretched-coordinate curl-curl (i kx, i ky and
+// D_z = s^-1 F_z^-1 i kz F_z), -k0^2 E and the multilayer reflection R
+// (tangential field at z_ml -> r_s/r_p -> upgoing profile).  One fused kernel
+// ("axial") does all of that per column and emits
+//   W = curl_s curl_s q - k0^2 q           for every plane, into y
+//   G = q + R q                            for the absorber planes, into scratch
+// with q = M x (or x).  The contrast term is then added on the absorber planes
+// only by three lateral passes: IFFT_x (rows), IFFT_y * k0^2 deps / N * FFT_y
+// (columns), FFT_x with y -= result (rows).
+#include <cstdio>
+
+#include "fft.cuh"
+#include "internal.h"
+
+// ======================================================================= axial kernel
+struct AxialArgs {
+  const cf* x;
+  cf* y;
+  cf* G;
+  const float* kx;
+  const float* ky;
+  const float* kz;
+  const cf* sinv;
+  const cf* tw;
+  const float4* refl;
+  const cf* kz0;
+  const int* done;
+  int nx;
+  long ncols, vstride, gstride;
+  int z_ml, za0, za1;
+  float dz, k02;
+  float m_min, kref2, gamma, damp_eps;
+};
+
+enum { AX_AM = 0, AX_A = 1, AX_M = 2 };
+
+template <int NZ, int T, int MODE>
+__global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
+  constexpr int P = 32 / T;
+  constexpr int R = NZ / T;
+  using PZ = Pencil<NZ, T, P>;
+  extern __shared__ cf smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = lane / P, p = lane - t * P;
+  const int rhs = blockIdx.y;
+  if (a.done && a.done[rhs]) return;
+  const long col = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  const bool act = col < a.ncols;
+  const long cc = act ? col : 0;
+  const long nc = a.ncols;
+  const cf* __restrict__ x = a.x + rhs * a.vstride;
+  cf* __restrict__ y = a.y + rhs * a.vstride;
+  const float kx = __ldg(a.kx + cc % a.nx), ky = __ldg(a.ky + cc / a.nx);
+  const float inv_n = 1.0f / (float)NZ;
+
+  auto load = [&](int c, cf* v) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? __ldg(x + (long)(c * NZ + t + T * m) * nc + col) : czero();
+  };
+  auto store = [&](int c, int m, cf v) {
+    if (act) y[(long)(c * NZ + t + T * m) * nc + col] = v;
+  };
+
+  float mv[R];
+  if constexpr (MODE != AX_A) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
+      const float k2 = fmaf(kx, kx, fmaf(ky, ky, kzv * kzv));
+      float d = 1.0f;
+      if (k2 > a.kref2) {
+        const float ratio = a.kref2 / (k2 + a.damp_eps);
+        d = (a.gamma == 1.0f) ? ratio : powf(ratio, a.gamma);
+      }
+      mv[s] = (a.m_min + (1.0f - a.m_min) * d) * inv_n;
+    }
+  }
+
+  if constexpr (MODE == AX_M) {
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cf v[R];
+      load(c, v);
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) v[s] = cscale(v[s], mv[s]);
+      PZ::template to_time<true>(v, t, a.tw);
+#pragma unroll
+      for (int m = 0; m < R; ++m) store(c, m, v[m]);
+    }
+    return;
+  } else {
+    cf* st = smem + (size_t)warp * 4 * R * 32;
+    auto stash = [&](int s, const cf* v) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) st[(s * R + m) * 32 + lane] = v[m];
+    };
+    auto unst = [&](int s, int m) -> cf { return st[(s * R + m) * 32 + lane]; };
+    const cf ikx = make_float2(0.f, kx), iky = make_float2(0.f, ky);
+
+    // ---- q_z -> slot 0
+    {
+      cf v[R];
+      load(2, v);
+      if constexpr (MODE == AX_AM) {
+        PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+        for (int s = 0; s < R; ++s) v[s] = cscale(v[s], mv[s]);
+        PZ::template to_time<true>(v, t, a.tw);
+      }
+      stash(0, v);
+    }
+    // ---- q_y -> slot 1, c_x = i ky q_z - D_z q_y -> slot 2
+    {
+      cf v[R], w[R];
+      load(1, v);
+      cf q[R];
+      if constexpr (MODE == AX_A) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) q[m] = v[m];
+      }
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
+        if constexpr (MODE == AX_AM) v[s] = cscale(v[s], mv[s]);
+        else v[s] = cscale(v[s], inv_n);
+        w[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
+      }
+      if constexpr (MODE == AX_AM) {
+        PZ::template to_time<true>(v, t, a.tw);
+#pragma unroll
+        for (int m = 0; m < R; ++m) q[m] = v[m];
+      }
+      PZ::template to_time<true>(w, t, a.tw);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf dq = cmul(w[m], __ldg(a.sinv + z));
+        w[m] = csub(cmul(iky, unst(0, m)), dq);
+      }
+      stash(1, q);
+      stash(2, w);
+    }
+    // ---- q_x -> slot 3, c_y = D_z q_x - i kx q_z (registers), emit W_z and G
+    {
+      cf v[R], w[R];
+      load(0, v);
+      cf q[R];
+      if constexpr (MODE == AX_A) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) q[m] = v[m];
+      }
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
+        if constexpr (MODE == AX_AM) v[s] = cscale(v[s], mv[s]);
+        else v[s] = cscale(v[s], inv_n);
+        w[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
+      }
+      if constexpr (MODE == AX_AM) {
+        PZ::template to_time<true>(v, t, a.tw);
+#pragma unroll
+        for (int m = 0; m < R; ++m) q[m] = v[m];
+      }
+      PZ::template to_time<true>(w, t, a.tw);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf dq = cmul(w[m], __ldg(a.sinv + z));
+        w[m] = csub(dq, cmul(ikx, unst(0, m)));
+      }
+      stash(3, q);
+      __syncwarp();
+      // reflected vector of this column from the tangential q at z_ml (Sec. 2.2, R_ml)
+      const int tml = a.z_ml % T, mml = a.z_ml / T;
+      const cf exm = st[(3 * R + mml) * 32 + tml * P + p];
+      const cf eym = st[(1 * R + mml) * 32 + tml * P + p];
+      const float4 rr = __ldg(a.refl + cc);
+      const cf rs = make_float2(rr.x, rr.y), rp = make_float2(rr.z, rr.w);
+      const cf kz0 = __ldg(a.kz0 + cc);
+      const float kp = sqrtf(kx * kx + ky * ky);
+      float sx, sy, tx, ty;
+      if (kp > 0.f) { sx = -ky / kp; sy = kx / kp; tx = kx / kp; ty = ky / kp; }
+      else { sx = 0.f; sy = 1.f; tx = 1.f; ty = 0.f; }
+      const cf as = make_float2(sx * exm.x + sy * eym.x, sx * exm.y + sy * eym.y);
+      const cf at = make_float2(tx * exm.x + ty * eym.x, tx * exm.y + ty * eym.y);
+      const cf ras = cmul(rs, as), rat = cmul(rp, at);
+      const cf r0 = make_float2(ras.x * sx + rat.x * tx, ras.y * sx + rat.y * tx);
+      const cf r1 = make_float2(ras.x * sy + rat.x * ty, ras.y * sy + rat.y * ty);
+      const cf num = make_float2(-(kx * r0.x + ky * r1.x), -(kx * r0.y + ky * r1.y));
+      const float kd = kz0.x * kz0.x + kz0.y * kz0.y;
+      const cf r2 = make_float2((num.x * kz0.x + num.y * kz0.y) / kd, (num.y * kz0.x - num.x * kz0.y) / kd);
+      const int nab = a.za1 - a.za0;
+      cf* __restrict__ G = a.G + rhs * a.gstride;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf qz = unst(0, m), cx = unst(2, m), cy = w[m];
+        const cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
+        store(2, m, Wz);
+        if (z >= a.za0 && z < a.za1 && act) {
+          cf prof = czero();
+          if (z >= a.z_ml) {
+            const float zr = (float)(z - a.z_ml) * a.dz;
+            float sn, cs;
+            sincosf(kz0.x * zr, &sn, &cs);
+            const float mag = expf(-kz0.y * zr);
+            prof = make_float2(mag * cs, mag * sn);
+          }
+          const long o = (long)(z - a.za0) * nc + col;
+          G[o] = cfma(r0, prof, q[m]);
+          G[(long)nab * nc + o] = cfma(r1, prof, unst(1, m));
+          G[2L * nab * nc + o] = cfma(r2, prof, qz);
+        }
+      }
+      stash(0, w);  // c_y replaces q_z (lane-private entries)
+    }
+    // ---- W_y = D_z c_x - i kx c_z - k0^2 q_y
+    {
+      cf v[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = unst(2, m);
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const float kzv = __ldg(a.kz + PZ::freq_index(t, s)) * inv_n;
+        v[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
+      }
+      PZ::template to_time<true>(v, t, a.tw);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf dcx = cmul(v[m], __ldg(a.sinv + z));
+        const cf qx = unst(3, m), qy = unst(1, m);
+        const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
+        store(1, m, csub(csub(dcx, cmul(ikx, cz)), cscale(qy, a.k02)));
+      }
+    }
+    // ---- W_x = i ky c_z - D_z c_y - k0^2 q_x
+    {
+      cf v[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = unst(0, m);
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const float kzv = __ldg(a.kz + PZ::freq_index(t, s)) * inv_n;
+        v[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
+      }
+      PZ::template to_time<true>(v, t, a.tw);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf dcy = cmul(v[m], __ldg(a.sinv + z));
+        const cf qx = unst(3, m), qy = unst(1, m);
+        const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
+        store(0, m, csub(csub(cmul(iky, cz), dcy), cscale(qx, a.k02)));
+      }
+    }
+  }
+}
+
+template <int NZ, int T, int MODE>
+static int run_axial(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
+  constexpr int P_ = 32 / T, R = NZ / T;
+  AxialArgs a;
+  a.x = x; a.y = y; a.G = P->G;
+  a.kx = P->kx; a.ky = P->ky; a.kz = P->kz; a.sinv = P->sinv; a.tw = P->tw_z;
+  a.refl = P->R.refl; a.kz0 = P->R.kz0; a.done = done;
+  a.nx = P->nx; a.ncols = P->ncols; a.vstride = P->nvec;
+  a.gstride = 3L * (P->za1 - P->za0) * P->ncols;
+  a.z_ml = P->p.z_ml; a.za0 = P->za0; a.za1 = P->za1;
+  a.dz = (float)P->p.dz; a.k02 = (float)(P->k0 * P->k0);
+  a.m_min = P->m_min; a.kref2 = P->kref2; a.gamma = P->gamma; a.damp_eps = P->damp_eps;
+  const int warps = 4;
+  const long cols_per_block = warps * P_;
+  dim3 grid((unsigned)((P->ncols + cols_per_block - 1) / cols_per_block), (unsigned)P->nrhs);
+  size_t smem = (MODE == AX_M) ? 0 : (size_t)warps * 4 * R * 32 * sizeof(cf);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_axial<NZ, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  k_axial<NZ, T, MODE><<<grid, warps * 32, smem, P->stream>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <int NZ, int T>
+static int run_axial_mode(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done) {
+  switch (mode) {
+    case AX_AM: return run_axial<NZ, T, AX_AM>(P, x, y, done);
+    case AX_A: return run_axial<NZ, T, AX_A>(P, x, y, done);
+    default: return run_axial<NZ, T, AX_M>(P, x, y, done);
+  }
+}
+
+int axial_supported(int nz) {
+  switch (nz) {
+    case 16: case 32: case 48: case 64: case 96: case 128: return 1;
+    default: return 0;
+  }
+}
+
+int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int) {
+  const int T = P->axial_T;
+  switch (P->nz) {
+    case 16: return run_axial_mode<16, 2>(P, x, y, mode, done);
+    case 32: return run_axial_mode<32, 4>(P, x, y, mode, done);
+    case 48: return run_axial_mode<48, 4>(P, x, y, mode, done);
+    case 64: return (T == 4) ? run_axial_mode<64, 4>(P, x, y, mode, done)
+                             : run_axial_mode<64, 8>(P, x, y, mode, done);
+    case 96: return run_axial_mode<96, 4>(P, x, y, mode, done);
+    case 128: return run_axial_mode<128, 8>(P, x, y, mode, done);
+  }
+  psfd_set_error("axial: unsupported nz %d", P->nz);
+  return PSFD_ERR_ARG;
+}
+
+// ======================================================================= lateral passes
+// Rows (x axis, contiguous): lane = p*T + t, P = 32/T rows per warp.
+enum { ROW_FWD = 0, ROW_INV = 1, ROW_FWD_SUB = 2 };
+
+struct RowArgs {
+  cf* buf;
+  long nrows;
+  float scale;
+  const cf* tw;
+  // ROW_FWD_SUB: y[row'] -= scale * FFT_x(buf[row])
+  cf* y;
+  int ny, nz, nab, za0;
+  const int* done;
+  long rows_per_rhs;
+};
+
+template <int NX, int T, int OP>
+__global__ void __launch_bounds__(128) k_rows(RowArgs a) {
+  constexpr int P = 32 / T, R = NX / T;
+  using PX = Pencil<NX, T, 1>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane / T, t = lane - p * T;
+  const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  bool act = row < a.nrows;
+  if (act && a.done && a.done[row / a.rows_per_rhs]) act = false;
+  cf* __restrict__ src = a.buf + (act ? row : 0) * NX;
+  cf v[R];
+  if constexpr (OP == ROW_INV) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? src[PX::freq_index(t, s)] : czero();
+    PX::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+      if (act) src[t + T * m] = cscale(v[m], a.scale);
+  } else {
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : czero();
+    PX::template to_freq<false>(v, t, a.tw);
+    if constexpr (OP == ROW_FWD) {
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
+    } else {
+      // map the G row (rhs, c, zz, iy) to the y row (rhs, c, za0 + zz, iy)
+      const long per_c = (long)a.nab * a.ny;
+      const long r = act ? row : 0;
+      const long rhs = r / (3 * per_c), rem = r - rhs * 3 * per_c;
+      const long c = rem / per_c, rem2 = rem - c * per_c;
+      const long zz = rem2 / a.ny, iy = rem2 - zz * a.ny;
+      cf* __restrict__ dst = a.y + (((rhs * 3 + c) * a.nz + a.za0 + zz) * a.ny + iy) * NX;
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        if (act) {
+          const int k = PX::freq_index(t, s);
+          const cf o = dst[k];
+          dst[k] = make_float2(fmaf(-a.scale, v[s].x, o.x), fmaf(-a.scale, v[s].y, o.y));
+        }
+      }
+    }
+  }
+}
+
+// Columns (y axis, stride nx): lane = t*P + p, P = 32/T consecutive x per warp.
+enum { COL_FWD = 0, COL_INV = 1, COL_CONTRAST = 2, COL_GAUSS = 3 };
+
+struct ColArgs {
+  cf* buf;
+  long ncolumns;   // nplanes * nx
+  int nx;
+  float scale;
+  const cf* tw;
+  // COL_CONTRAST
+  const float* fill;
+  float dre, dim;  // scale * deps (complex)
+  int nab, za0;
+  long plane_elems;  // nx * ny
+  const int* done;
+  long planes_per_rhs;
+  // COL_GAUSS
+  float sigma;
+};
+
+template <int NY, int T, int OP>
+__global__ void __launch_bounds__(128) k_cols(ColArgs a) {
+  constexpr int P = 32 / T, R = NY / T;
+  using PY = Pencil<NY, T, P>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = lane / P, p = lane - t * P;
+  const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  bool act = colid < a.ncolumns;
+  const long cid = act ? colid : 0;
+  const long plane = cid / a.nx;
+  const int ix = (int)(cid - plane * a.nx);
+  if (act && a.done && a.done[plane / a.planes_per_rhs]) act = false;
+  cf* __restrict__ base = a.buf + plane * a.plane_elems + ix;
+  const long sx = a.nx;
+  cf v[R];
+  if constexpr (OP == COL_FWD) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : czero();
+    PY::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (act) base[(long)PY::freq_index(t, s) * sx] = cscale(v[s], a.scale);
+  } else if constexpr (OP == COL_INV) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : czero();
+    PY::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+      if (act) base[(long)(t + T * m) * sx] = cscale(v[m], a.scale);
+  } else if constexpr (OP == COL_CONTRAST) {
+    // IFFT_y -> * scale * deps * fill(x, y, z) -> FFT_y
+    const long zz = plane % a.nab;
+    const float* __restrict__ f = a.fill + (a.za0 + zz) * a.plane_elems + ix;
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : czero();
+    PY::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const float fv = act ? __ldg(f + (long)(t + T * m) * sx) : 0.f;
+      v[m] = cmul(v[m], make_float2(a.dre * fv, a.dim * fv));
+    }
+    PY::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (act) base[(long)PY::freq_index(t, s) * sx] = v[s];
+  } else {
+    // Gaussian smoothing of a single plane: FFT_y -> * exp(-sigma^2 |kappa|^2 / 2) -> IFFT_y
+    const float kxp = 6.283185307179586f * (float)fft_signed(ix, a.nx) / (float)a.nx;
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : czero();
+    PY::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const float kyp = 6.283185307179586f * (float)fft_signed(PY::freq_index(t, s), NY) / (float)NY;
+      const float g = expf(-0.5f * a.sigma * a.sigma * (kxp * kxp + kyp * kyp));
+      v[s] = cscale(v[s], g);
+    }
+    PY::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+      if (act) base[(long)(t + T * m) * sx] = v[m];
+  }
+}
+
+int lateral_supported(int n) {
+  switch (n) {
+    case 16: case 32: case 64: case 96: case 128: case 256: case 512: return 1;
+    default: return 0;
+  }
+}
+
+template <int NX, int T>
+static int rows_op(const RowArgs& a, int op, cudaStream_t s) {
+  constexpr int P = 32 / T;
+  const int warps = 4;
+  const long per_block = warps * P;
+  dim3 grid((unsigned)((a.nrows + per_block - 1) / per_block));
+  if (grid.x == 0) return PSFD_OK;
+  switch (op) {
+    case ROW_FWD: k_rows<NX, T, ROW_FWD><<<grid, warps * 32, 0, s>>>(a); break;
+    case ROW_INV: k_rows<NX, T, ROW_INV><<<grid, warps * 32, 0, s>>>(a); break;
+    default: k_rows<NX, T, ROW_FWD_SUB><<<grid, warps * 32, 0, s>>>(a); break;
+  }
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+static int rows_dispatch(int nx, const RowArgs& a, int op, cudaStream_t s) {
+  switch (nx) {
+    case 16: return rows_op<16, 4>(a, op, s);
+    case 32: return rows_op<32, 4>(a, op, s);
+    case 64: return rows_op<64, 8>(a, op, s);
+    case 96: return rows_op<96, 4>(a, op, s);
+    case 128: return rows_op<128, 8>(a, op, s);
+    case 256: return rows_op<256, 16>(a, op, s);
+    case 512: return rows_op<512, 16>(a, op, s);
+  }
+  psfd_set_error("rows: unsupported n %d", nx);
+  return PSFD_ERR_ARG;
+}
+
+template <int NY, int T>
+static int cols_op(const ColArgs& a, int op, cudaStream_t s) {
+  constexpr int P = 32 / T;
+  if (a.nx % P != 0) {
+    psfd_set_error("cols: nx %d not a multiple of %d", a.nx, P);
+    return PSFD_ERR_ARG;
+  }
+  const int warps = 4;
+  const long per_block = warps * P;
+  dim3 grid((unsigned)((a.ncolumns + per_block - 1) / per_block));
+  if (grid.x == 0) return PSFD_OK;
+  switch (op) {
+    case COL_FWD: k_cols<NY, T, COL_FWD><<<grid, warps * 32, 0, s>>>(a); break;
+    case COL_INV: k_cols<NY, T, COL_INV><<<grid, warps * 32, 0, s>>>(a); break;
+    case COL_CONTRAST: k_cols<NY, T, COL_CONTRAST><<<grid, warps * 32, 0, s>>>(a); break;
+    default: k_cols<NY, T, COL_GAUSS><<<grid, warps * 32, 0, s>>>(a); break;
+  }
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+static int cols_dispatch(int ny, const ColArgs& a, int op, cudaStream_t s) {
+  switch (ny) {
+    case 16: return cols_op<16, 2>(a, op, s);
+    case 32: return cols_op<32, 4>(a, op, s);
+    case 48: return cols_op<48, 4>(a, op, s);
+    case 64: return cols_op<64, 4>(a, op, s);
+    case 96: return cols_op<96, 4>(a, op, s);
+    case 128: return cols_op<128, 8>(a, op, s);
+    case 256: return cols_op<256, 8>(a, op, s);
+    case 512: return cols_op<512, 16>(a, op, s);
+  }
+  psfd_set_error("cols: unsupported n %d", ny);
+  return PSFD_ERR_ARG;
+}
+
+int launch_rows(int n, cf* buf, long nrows, bool forward, float scale, const cf* tw, cudaStream_t s) {
+  RowArgs a{};
+  a.buf = buf; a.nrows = nrows; a.scale = scale; a.tw = tw; a.rows_per_rhs = 1;
+  return rows_dispatch(n, a, forward ? ROW_FWD : ROW_INV, s);
+}
+
+int launch_cols(int n, int nx, cf* buf, long ncols_total, bool forward, float scale, const cf* tw,
+                cudaStream_t s) {
+  ColArgs a{};
+  a.buf = buf; a.ncolumns = ncols_total; a.nx = nx; a.scale = scale; a.tw = tw;
+  a.plane_elems = (long)n * nx; a.planes_per_rhs = 1;
+  return cols_dispatch(n, a, forward ? COL_FWD : COL_INV, s);
+}
+
+int launch_cols_gauss(int ny, int nx, cf* buf, float sigma, const cf* tw, cudaStream_t s) {
+  ColArgs a{};
+  a.buf = buf; a.ncolumns = nx; a.nx = nx; a.scale = 1.f; a.tw = tw; a.sigma = sigma;
+  a.plane_elems = (long)nx * ny; a.planes_per_rhs = 1;
+  return cols_dispatch(ny, a, COL_GAUSS, s);
+}
+
+// real space <-> HYBRID over nplanes planes: forward = rows then columns (unitary scale)
+int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward, float scale) {
+  int rc;
+  const long rows = nplanes * P->ny, cols = nplanes * P->nx;
+  if (forward) {
+    if ((rc = launch_rows(P->nx, buf, rows, true, 1.f, P->tw_x, P->stream))) return rc;
+    return launch_cols(P->ny, P->nx, buf, cols, true, scale, P->tw_y, P->stream);
+  }
+  if ((rc = launch_cols(P->ny, P->nx, buf, cols, false, 1.f, P->tw_y, P->stream))) return rc;
+  return launch_rows(P->nx, buf, rows, false, scale, P->tw_x, P->stream);
+}
+
+// y (absorber planes) -= k0^2 F_xy[deps F_xy^-1 G] / (nx ny): G is consumed.
+int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint) {
+  const int nab = P->za1 - P->za0;
+  if (nab <= 0) return PSFD_OK;
+  const long nplanes = (long)P->nrhs * 3 * nab;
+  int rc;
+  RowArgs r{};
+  r.buf = P->G; r.nrows = nplanes * P->ny; r.scale = 1.f; r.tw = P->tw_x; r.done = done;
+  r.rows_per_rhs = 3L * nab * P->ny;
+  if ((rc = rows_dispatch(P->nx, r, ROW_INV, P->stream))) return rc;
+  ColArgs c{};
+  const double sc = P->k0 * P->k0 / (double)P->ncols;
+  c.buf = P->G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.f; c.tw = P->tw_y;
+  c.fill = P->fill; c.dre = (float)(sc * P->deps_re); c.dim = (float)(sc * (adjoint ? -P->deps_im : P->deps_im));
+  c.nab = nab; c.za0 = P->za0; c.plane_elems = P->ncols; c.done = done; c.planes_per_rhs = 3L * nab;
+  if ((rc = cols_dispatch(P->ny, c, COL_CONTRAST, P->stream))) return rc;
+  RowArgs w{};
+  w.buf = P->G; w.nrows = nplanes * P->ny; w.scale = 1.f; w.tw = P->tw_x; w.y = y;
+  w.ny = P->ny; w.nz = P->nz; w.nab = nab; w.za0 = P->za0; w.done = done; w.rows_per_rhs = 3L * nab * P->ny;
+  return rows_dispatch(P->nx, w, ROW_FWD_SUB, P->stream);
+}
+
+// y = A x or A M x, both in the HYBRID domain
+int apply_hybrid(psfd_plan_s* P, const cf* x, cf* y, int flags, const int* done) {
+  int rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) ? AX_AM : AX_A, done, P->nrhs);
+  if (rc) return rc;
+  return launch_lateral_contrast(P, y, done, false);
+}
+
+extern "C" int psfd_apply(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags) {
+  if (!P || !x || !y) { psfd_set_error("psfd_apply: null argument"); return PSFD_ERR_ARG; }
+  if (!P->have_background) { psfd_set_error("psfd_apply: call psfd_background first"); return PSFD_ERR_STATE; }
+  if (x == y) { psfd_set_error("psfd_apply: x and y must not overlap"); return PSFD_ERR_ARG; }
+  if (flags & PSFD_ADJOINT) { psfd_set_error("psfd_apply: adjoint not available in this build"); return PSFD_ERR_ARG; }
+  const cf* xi = (const cf*)x;
+  cf* yo = (cf*)y;
+  const long bytes = (long)P->nrhs * P->nvec * sizeof(cf);
+  if (flags & PSFD_HYBRID) return apply_hybrid(P, xi, yo, flags, nullptr);
+  const float us = 1.0f / sqrtf((float)P->ncols);
+  const long nplanes = (long)P->nrhs * 3 * P->nz;
+  PSFD_CUDA_TRY(cudaMemcpyAsync(P->tmpA, xi, bytes, cudaMemcpyDeviceToDevice, P->stream));
+  int rc;
+  if ((rc = launch_lateral_transform(P, P->tmpA, nplanes, true, us))) return rc;
+  if ((rc = apply_hybrid(P, P->tmpA, yo, flags, nullptr))) return rc;
+  return launch_lateral_transform(P, yo, nplanes, false, us);
+}
+
+extern "C" int psfd_precond(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags) {
+  if (!P || !x || !y) { psfd_set_error("psfd_precond: null argument"); return PSFD_ERR_ARG; }
+  const long bytes = (long)P->nrhs * P->nvec * sizeof(cf);
+  if (flags & PSFD_HYBRID) {
+    if ((const void*)x == (void*)y) {
+      PSFD_CUDA_TRY(cudaMemcpyAsync(P->tmpA, x, bytes, cudaMemcpyDeviceToDevice, P->stream));
+      return launch_axial(P, P->tmpA, (cf*)y, AX_M, nullptr, P->nrhs);
+    }
+    return launch_axial(P, (const cf*)x, (cf*)y, AX_M, nullptr, P->nrhs);
+  }
+  const float us = 1.0f / sqrtf((float)P->ncols);
+  const long nplanes = (long)P->nrhs * 3 * P->nz;
+  PSFD_CUDA_TRY(cudaMemcpyAsync(P->tmpA, x, bytes, cudaMemcpyDeviceToDevice, P->stream));
+  int rc;
+  if ((rc = launch_lateral_transform(P, P->tmpA, nplanes, true, us))) return rc;
+  if ((rc = launch_axial(P, P->tmpA, (cf*)y, AX_M, nullptr, P->nrhs))) return rc;
+  return launch_lateral_transform(P, (cf*)y, nplanes, false, us);
+}

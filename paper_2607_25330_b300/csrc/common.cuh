@@ -1,0 +1,116 @@
+// Common device helpers: complex64 arithmetic, compile-time trigonometry,
+// compile-time loops and error reporting.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <type_traits>
+
+typedef float2 cf;
+
+__host__ __device__ __forceinline__ cf mk(float re, float im) { return make_float2(re, im); }
+__device__ __forceinline__ cf cadd(cf a, cf b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cf csub(cf a, cf b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cf cmul(cf a, cf b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ cf cmulc(cf a, cf b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ cf cconj(cf a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ cf cscale(cf a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ cf ctimesi(cf a) { return make_float2(-a.y, a.x); }     // i a
+__device__ __forceinline__ cf ctimesmi(cf a) { return make_float2(a.y, -a.x); }    // -i a
+__device__ __forceinline__ cf cfma(cf a, cf b, cf c) {                                 // a*b + c
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ cf czero() { return make_float2(0.f, 0.f); }
+
+// ------------------------------------------------------------ compile-time loops
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// ------------------------------------------------------------ compile-time trigonometry
+// sin / cos of 2*pi*J/N evaluated at compile time: exact integer reduction to
+// [0, pi/4] followed by a Taylor series (error far below float rounding).
+namespace ct {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double sin_small(double x) {
+  double t = x, s = x;
+  for (int n = 1; n < 16; ++n) { t *= -x * x / double((2 * n) * (2 * n + 1)); s += t; }
+  return s;
+}
+constexpr double cos_small(double x) {
+  double t = 1.0, s = 1.0;
+  for (int n = 1; n < 16; ++n) { t *= -x * x / double((2 * n - 1) * (2 * n)); s += t; }
+  return s;
+}
+struct SinCos { double s, c; };
+constexpr SinCos sincos2pi(long J, long N) {
+  long j = ((J % N) + N) % N;
+  long q = (4 * j) / N;
+  long rem = 4 * j - q * N;  // angle = q*pi/2 + (pi/2) * rem / N
+  double s = 0, c = 0;
+  if (2 * rem <= N) {
+    double x = (kPi / 2) * double(rem) / double(N);
+    s = sin_small(x); c = cos_small(x);
+  } else {
+    double x = (kPi / 2) * double(N - rem) / double(N);
+    s = cos_small(x); c = sin_small(x);
+  }
+  switch (q & 3) {
+    case 0: return {s, c};
+    case 1: return {c, -s};
+    case 2: return {-s, -c};
+    default: return {-c, s};
+  }
+}
+}  // namespace ct
+
+// a * exp(sign * 2 pi i J / N) with sign = -1 (forward) or +1 (INV); the
+// special angles become sign flips and swaps.
+template <int N, int J, bool INV>
+__device__ __forceinline__ cf twmul(cf a) {
+  constexpr int j = ((J % N) + N) % N;
+  if constexpr (j == 0) {
+    return a;
+  } else if constexpr (2 * j == N) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (4 * j == N) {
+    return INV ? ctimesi(a) : ctimesmi(a);
+  } else if constexpr (4 * j == 3 * N) {
+    return INV ? ctimesmi(a) : ctimesi(a);
+  } else {
+    constexpr ct::SinCos sc = ct::sincos2pi(j, N);
+    constexpr float c = (float)sc.c;
+    constexpr float s = INV ? (float)sc.s : (float)(-sc.s);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+// ------------------------------------------------------------ host error helpers
+#define PSFD_CUDA_TRY(expr)                                                  \
+  do {                                                                       \
+    cudaError_t err__ = (expr);                                              \
+    if (err__ != cudaSuccess) {                                              \
+      psfd_set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,             \
+                     cudaGetErrorString(err__));                             \
+      return PSFD_ERR_CUDA;                                                  \
+    }                                                                        \
+  } while (0)
+
+#define PSFD_CHECK_LAUNCH()                                                  \
+  do {                                                                       \
+    cudaError_t err__ = cudaGetLastError();                                  \
+    if (err__ != cudaSuccess) {                                              \
+      psfd_set_error("%s:%d: launch: %s", __FILE__, __LINE__,                \
+                     cudaGetErrorString(err__));                             \
+      return PSFD_ERR_CUDA;                                                  \
+    }                                                                        \
+  } while (0)
+
+void psfd_set_error(const char* fmt, ...);

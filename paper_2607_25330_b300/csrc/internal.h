@@ -1,0 +1,65 @@
+// Host-side plan structure and internal launch interfaces shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include "../../include/psfd.h"
+#include "common.cuh"
+
+struct ReflTables {
+  double2* rs64 = nullptr;   // [ny*nx]
+  double2* rp64 = nullptr;
+  double2* kz064 = nullptr;
+  float4* refl = nullptr;    // (rs.re, rs.im, rp.re, rp.im) per mode
+  cf* kz0 = nullptr;         // kz0 per mode (float)
+};
+
+struct psfd_plan_s {
+  psfd_params_t p{};
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 0, nrhs = 0;
+  long ncols = 0;            // nx * ny
+  long nvec = 0;             // 3 * nz * ncols (complex entries per right-hand side)
+  double k0 = 0, kx_inc = 0, ky_inc = 0, kz_inc = 0;
+  double deps_re = 0, deps_im = 0;
+  // device tables
+  float* kx = nullptr;       // [nx] Bloch-shifted lateral wavenumbers
+  float* ky = nullptr;       // [ny]
+  float* kz = nullptr;       // [nz] axial wavenumbers (FFT order)
+  cf* sinv = nullptr;        // [nz] 1 / s(z)
+  cf* tw_x = nullptr;        // [nx] exp(-2 pi i m / nx)
+  cf* tw_y = nullptr;
+  cf* tw_z = nullptr;
+  ReflTables R;
+  // geometry
+  const float* fill = nullptr;
+  int za0 = 0, za1 = 0;      // planes with nonzero fill: [za0, za1)
+  bool have_background = false;
+  // damping
+  float m_min = 0, kref2 = 0, gamma = 1, damp_eps = 0;
+  // scratch (plan-owned)
+  cf* G = nullptr;           // [nrhs][3][nab][ny][nx]
+  size_t G_elems = 0;
+  cf* tmpA = nullptr;        // [nrhs][3][nz][ny][nx]
+  cf* tmpB = nullptr;        // [nrhs][3][nz][ny][nx]
+  // history (host)
+  double* hist = nullptr;
+  int hist_cap = 0;
+  // launch choices (set by the tuner)
+  int axial_T = 0;
+};
+
+// apply.cu
+int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int nrhs_active);
+int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint);
+int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward, float scale);
+int apply_hybrid(psfd_plan_s* P, const cf* x, cf* y, int flags, const int* done);
+int launch_rows(int n, cf* buf, long nrows, bool forward, float scale, const cf* tw, cudaStream_t s);
+int launch_cols(int n, int nx, cf* buf, long ncols_total, bool forward, float scale, const cf* tw,
+                cudaStream_t s);
+int launch_cols_gauss(int ny, int nx, cf* buf, float sigma, const cf* tw, cudaStream_t s);
+int axial_supported(int nz);
+int lateral_supported(int n);
+
+// plan.cu
+void psfd_set_error(const char* fmt, ...);

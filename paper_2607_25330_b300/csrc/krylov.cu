@@ -1,0 +1,494 @@
+// Right-preconditioned Krylov solves with the affine warm start (Sec. 3:
+// Eqs. right_preconditioned, right_correction_solution,
+// right_preconditioned_system, relative_residual).
+//
+// All vectors are complex64 in the HYBRID domain, batched over the plan's
+// right-hand sides; every scalar is FP64 and stays on the device.  Inner
+// products use error-free transformations: each thread accumulates exact
+// float products (TwoProduct via fma) with a compensated float sum (TwoSum),
+// which gives twice-float accuracy per thread; the per-thread results are then
+// summed in FP64 in a fixed order (warp tree, block tree, blocks in index
+// order by the last block to finish), so results are reproducible run to run.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxQ = 4;  // reals reduced per kernel
+
+struct KScal {
+  double2 rho, rho_old, alpha, omega, rv, ts;
+  double tt, rr, bnorm2, rr0, res0, res1;
+  int status, iters, maxit, pad;
+  double tol2;
+};
+
+struct Acc2 {
+  float s, c;
+};
+
+__device__ __forceinline__ void acc_add(Acc2& A, float p, float ep) {
+  const float s = __fadd_rn(A.s, p);
+  const float bb = __fsub_rn(s, A.s);
+  const float e = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  A.s = s;
+  A.c = __fadd_rn(A.c, __fadd_rn(e, ep));
+}
+__device__ __forceinline__ void acc_prod(Acc2& A, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float ep = fmaf(a, b, -p);
+  acc_add(A, p, ep);
+}
+// re/im of conj(a) * b
+__device__ __forceinline__ void acc_cdot(Acc2& re, Acc2& im, cf a, cf b) {
+  acc_prod(re, a.x, b.x);
+  acc_prod(re, a.y, b.y);
+  acc_prod(im, a.x, b.y);
+  acc_prod(im, -a.y, b.x);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce NQ doubles; write partials; the last block of this rhs sums the
+// partials in index order and returns true with the totals in out[].
+template <int NQ>
+__device__ bool reduce_finish(double (&val)[NQ], double* partials, unsigned* counters, double* out) {
+  __shared__ double sh[kThreads / 32][kMaxQ];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rhs = blockIdx.y;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double v = warp_sum(val[q]);
+    if (lane == 0) sh[warp][q] = v;
+  }
+  __syncthreads();
+  double* part = partials + ((long)rhs * gridDim.x + blockIdx.x) * kMaxQ;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0;
+      for (int w = 0; w < kThreads / 32; ++w) s += sh[w][q];
+      part[q] = s;
+    }
+    __threadfence();
+    unsigned prev = atomicAdd(counters + rhs, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    const double* base = partials + (long)rhs * gridDim.x * kMaxQ;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0;
+      for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile const double*)base)[b * kMaxQ + q];
+      out[q] = s;
+    }
+    counters[rhs] = 0;  // ready for the next reduction
+  }
+  return true;
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ cf zf(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+enum {
+  OK_INIT = 0,   // rhat = r, p = v = y = 0; <r, r> -> rho, rr, rr0
+  OK_P = 1,      // p = r + beta (p - omega v)
+  OK_RV = 2,     // <rhat, v> -> alpha
+  OK_S = 3,      // s = r - alpha v
+  OK_TS = 4,     // <t, s>, <t, t> -> omega
+  OK_XR = 5,     // y += alpha p + omega s ; r = s - omega t ; <rhat, r>, <r, r>
+  OK_NORM = 6,   // <a, a> -> res0
+  OK_SUB = 7,    // c = a - b ; <c, c> -> res1
+  OK_AXPY = 8    // c = a + b
+};
+
+struct VArgs {
+  cf* v0;  // meaning depends on the op
+  cf* v1;
+  cf* v2;
+  cf* v3;
+  cf* v4;
+  cf* v5;
+  long n;  // complex entries per rhs
+  KScal* sc;
+  int* done;
+  double* partials;
+  unsigned* counters;
+  double* hist;
+  int hist_cap;
+  bool use_done;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
+  const int rhs = blockIdx.y;
+  KScal* S = a.sc + rhs;
+  if (a.use_done && a.done[rhs]) return;
+  const long off = (long)rhs * a.n;
+  const long n2 = a.n / 2;  // float4 = 2 complex
+  const long stride = (long)gridDim.x * blockDim.x;
+  Acc2 acc[kMaxQ];
+#pragma unroll
+  for (int q = 0; q < kMaxQ; ++q) acc[q] = {0.f, 0.f};
+
+  cf beta = czero(), omg = czero(), alp = czero();
+  if constexpr (OP == OK_P) {
+    // beta = (rho / rho_old) (alpha / omega)
+    const double2 b = zmul(zdiv(S->rho, S->rho_old), zdiv(S->alpha, S->omega));
+    beta = zf(b);
+    omg = zf(S->omega);
+  }
+  if constexpr (OP == OK_S || OP == OK_XR) alp = zf(S->alpha);
+  if constexpr (OP == OK_XR) omg = zf(S->omega);
+
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const long e = off / 2 + i;
+    if constexpr (OP == OK_INIT) {
+      // v0 = r, v1 = rhat, v2 = p, v3 = v, v4 = y
+      const float4 r = reinterpret_cast<const float4*>(a.v0)[e];
+      reinterpret_cast<float4*>(a.v1)[e] = r;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(a.v2)[e] = z;
+      reinterpret_cast<float4*>(a.v3)[e] = z;
+      reinterpret_cast<float4*>(a.v4)[e] = z;
+      acc_cdot(acc[0], acc[1], make_float2(r.x, r.y), make_float2(r.x, r.y));
+      acc_cdot(acc[0], acc[1], make_float2(r.z, r.w), make_float2(r.z, r.w));
+    } else if constexpr (OP == OK_P) {
+      // v0 = p (in/out), v1 = r, v2 = v
+      const float4 pp = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 rr = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 vv = reinterpret_cast<const float4*>(a.v2)[e];
+      cf p0 = make_float2(pp.x, pp.y), p1 = make_float2(pp.z, pp.w);
+      cf t0 = csub(p0, cmul(omg, make_float2(vv.x, vv.y)));
+      cf t1 = csub(p1, cmul(omg, make_float2(vv.z, vv.w)));
+      cf o0 = cfma(beta, t0, make_float2(rr.x, rr.y));
+      cf o1 = cfma(beta, t1, make_float2(rr.z, rr.w));
+      reinterpret_cast<float4*>(a.v0)[e] = make_float4(o0.x, o0.y, o1.x, o1.y);
+    } else if constexpr (OP == OK_RV) {
+      // v0 = rhat, v1 = v
+      const float4 h = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 v = reinterpret_cast<const float4*>(a.v1)[e];
+      acc_cdot(acc[0], acc[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
+      acc_cdot(acc[0], acc[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
+    } else if constexpr (OP == OK_S) {
+      // v0 = s (out), v1 = r, v2 = v
+      const float4 rr = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 vv = reinterpret_cast<const float4*>(a.v2)[e];
+      cf s0 = csub(make_float2(rr.x, rr.y), cmul(alp, make_float2(vv.x, vv.y)));
+      cf s1 = csub(make_float2(rr.z, rr.w), cmul(alp, make_float2(vv.z, vv.w)));
+      reinterpret_cast<float4*>(a.v0)[e] = make_float4(s0.x, s0.y, s1.x, s1.y);
+    } else if constexpr (OP == OK_TS) {
+      // v0 = t, v1 = s
+      const float4 tt = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 ss = reinterpret_cast<const float4*>(a.v1)[e];
+      cf t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
+      acc_cdot(acc[0], acc[1], t0, make_float2(ss.x, ss.y));
+      acc_cdot(acc[0], acc[1], t1, make_float2(ss.z, ss.w));
+      acc_cdot(acc[2], acc[3], t0, t0);
+      acc_cdot(acc[2], acc[3], t1, t1);
+    } else if constexpr (OP == OK_XR) {
+      // v0 = y, v1 = r (out), v2 = p, v3 = s, v4 = t, v5 = rhat
+      const float4 yy = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 pp = reinterpret_cast<const float4*>(a.v2)[e];
+      const float4 ss = reinterpret_cast<const float4*>(a.v3)[e];
+      const float4 tt = reinterpret_cast<const float4*>(a.v4)[e];
+      const float4 hh = reinterpret_cast<const float4*>(a.v5)[e];
+      cf s0 = make_float2(ss.x, ss.y), s1 = make_float2(ss.z, ss.w);
+      cf y0 = cfma(alp, make_float2(pp.x, pp.y), make_float2(yy.x, yy.y));
+      cf y1 = cfma(alp, make_float2(pp.z, pp.w), make_float2(yy.z, yy.w));
+      y0 = cfma(omg, s0, y0);
+      y1 = cfma(omg, s1, y1);
+      cf r0 = csub(s0, cmul(omg, make_float2(tt.x, tt.y)));
+      cf r1 = csub(s1, cmul(omg, make_float2(tt.z, tt.w)));
+      reinterpret_cast<float4*>(a.v0)[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
+      reinterpret_cast<float4*>(a.v1)[e] = make_float4(r0.x, r0.y, r1.x, r1.y);
+      acc_cdot(acc[0], acc[1], make_float2(hh.x, hh.y), r0);
+      acc_cdot(acc[0], acc[1], make_float2(hh.z, hh.w), r1);
+      acc_cdot(acc[2], acc[3], r0, r0);
+      acc_cdot(acc[2], acc[3], r1, r1);
+    } else if constexpr (OP == OK_NORM) {
+      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
+      acc_cdot(acc[0], acc[1], make_float2(x.x, x.y), make_float2(x.x, x.y));
+      acc_cdot(acc[0], acc[1], make_float2(x.z, x.w), make_float2(x.z, x.w));
+    } else if constexpr (OP == OK_SUB) {
+      // v2 = v0 - v1
+      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 c = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+      reinterpret_cast<float4*>(a.v2)[e] = c;
+      acc_cdot(acc[0], acc[1], make_float2(c.x, c.y), make_float2(c.x, c.y));
+      acc_cdot(acc[0], acc[1], make_float2(c.z, c.w), make_float2(c.z, c.w));
+    } else if constexpr (OP == OK_AXPY) {
+      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
+      reinterpret_cast<float4*>(a.v2)[e] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+    }
+  }
+
+  constexpr int NQ = (OP == OK_TS || OP == OK_XR) ? 4 : ((OP == OK_INIT || OP == OK_RV || OP == OK_NORM || OP == OK_SUB) ? 2 : 0);
+  if constexpr (NQ > 0) {
+    double val[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) val[q] = (double)acc[q].s + (double)acc[q].c;
+    double tot[NQ];
+    if (!reduce_finish<NQ>(val, a.partials, a.counters, tot)) return;
+    if (threadIdx.x != 0) return;
+    // ---- scalar updates (one thread per rhs)
+    if constexpr (OP == OK_INIT) {
+      S->rho = make_double2(tot[0], 0.0);
+      S->rho_old = make_double2(1.0, 0.0);
+      S->alpha = make_double2(1.0, 0.0);
+      S->omega = make_double2(1.0, 0.0);
+      S->rr = tot[0];
+      S->rr0 = tot[0];
+      S->iters = 0;
+      S->status = PSFD_NOT_CONVERGED;
+      int d = 0;
+      if (tot[0] <= S->tol2 * S->bnorm2) { d = 1; S->status = PSFD_OK; }
+      if (S->maxit <= 0) d = 1;
+      a.done[rhs] = d;
+    } else if constexpr (OP == OK_RV) {
+      S->rv = make_double2(tot[0], tot[1]);
+      const double arv = zabs(S->rv);
+      if (!(arv > 1e-300) || !isfinite(arv)) {
+        S->status = PSFD_ERR_BREAKDOWN;
+        S->alpha = make_double2(0.0, 0.0);
+        a.done[rhs] = 1;
+      } else {
+        S->alpha = zdiv(S->rho, S->rv);
+      }
+    } else if constexpr (OP == OK_TS) {
+      S->ts = make_double2(tot[0], tot[1]);
+      S->tt = tot[2];
+      S->omega = (tot[2] > 0.0) ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
+    } else if constexpr (OP == OK_XR) {
+      S->rho_old = S->rho;
+      S->rho = make_double2(tot[0], tot[1]);
+      S->rr = tot[2];
+      const int it = ++S->iters;
+      const double rel = sqrt(tot[2] / S->bnorm2);
+      if (a.hist && it - 1 < a.hist_cap) a.hist[(long)rhs * a.hist_cap + it - 1] = rel;
+      int d = 0;
+      if (!isfinite(tot[2])) { S->status = PSFD_ERR_BREAKDOWN; d = 1; }
+      else if (tot[2] <= S->tol2 * S->bnorm2) { S->status = PSFD_OK; d = 1; }
+      else if (!(zabs(S->rho) > 1e-300) || !(zabs(S->omega) > 0.0)) { S->status = PSFD_ERR_BREAKDOWN; d = 1; }
+      else if (it >= S->maxit) { S->status = PSFD_NOT_CONVERGED; d = 1; }
+      a.done[rhs] = d;
+    } else if constexpr (OP == OK_NORM) {
+      S->res0 = tot[0];
+    } else if constexpr (OP == OK_SUB) {
+      S->res1 = tot[0];
+    }
+  }
+}
+
+template <int OP>
+int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
+  dim3 grid((unsigned)nblocks, (unsigned)nrhs);
+  k_vec<OP><<<grid, kThreads, 0, s>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+__global__ void k_set_scalars(KScal* sc, int nrhs, double tol2, int maxit) {
+  int r = threadIdx.x;
+  if (r < nrhs) {
+    KScal z{};
+    z.tol2 = tol2;
+    z.maxit = maxit;
+    z.status = PSFD_NOT_CONVERGED;
+    sc[r] = z;
+  }
+}
+__global__ void k_copy_bnorm(KScal* sc, int nrhs) {
+  int r = threadIdx.x;
+  if (r < nrhs) sc[r].bnorm2 = sc[r].res0;
+}
+
+}  // namespace
+
+struct SolveWs {
+  cf *bH, *r, *rhat, *p, *v, *s, *t, *y, *Eb;
+  KScal* sc;
+  int* done;
+  double* partials;
+  unsigned* counters;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int nblocks_for(long n) {
+  long per = (n / 2 + kThreads - 1) / kThreads;
+  long nb = per < 4 * 148 ? per : 4 * 148;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+static size_t ws_layout(psfd_plan_s* P, SolveWs* w, char* base) {
+  const size_t vb = align256((size_t)P->nrhs * P->nvec * sizeof(cf));
+  const int nb = nblocks_for(P->nvec);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* { char* q = base ? base + off : nullptr; off += align256(bytes); return q; };
+  cf** vecs[] = {&w->bH, &w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->y, &w->Eb};
+  for (cf** q : vecs) *q = (cf*)take(vb);
+  w->sc = (KScal*)take(sizeof(KScal) * P->nrhs);
+  w->done = (int*)take(sizeof(int) * P->nrhs);
+  w->partials = (double*)take(sizeof(double) * kMaxQ * nb * P->nrhs);
+  w->counters = (unsigned*)take(sizeof(unsigned) * P->nrhs);
+  return off;
+}
+
+extern "C" size_t psfd_solve_workspace_size(psfd_plan P, int method, int restart) {
+  (void)method; (void)restart;
+  if (!P) return 0;
+  SolveWs w;
+  return ws_layout(P, &w, nullptr);
+}
+
+extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E, double tol, int maxit,
+                          int method, int restart, int use_precond, psfd_info_t* info, void* workspace,
+                          size_t workspace_bytes) {
+  if (!P || !b || !E || !info) { psfd_set_error("psfd_solve: null argument"); return PSFD_ERR_ARG; }
+  if (!P->have_background) { psfd_set_error("psfd_solve: call psfd_background first"); return PSFD_ERR_STATE; }
+  if (!(tol > 0) || maxit < 0) { psfd_set_error("psfd_solve: bad tol / maxit"); return PSFD_ERR_ARG; }
+  if (method != PSFD_BICGSTAB) { psfd_set_error("psfd_solve: only BiCGSTAB in this build"); return PSFD_ERR_ARG; }
+  (void)restart;
+  cudaStream_t st = P->stream;
+  SolveWs w;
+  const size_t need = ws_layout(P, &w, nullptr);
+  char* base = (char*)workspace;
+  bool own = false;
+  if (!base) {
+    PSFD_CUDA_TRY(cudaMallocAsync((void**)&base, need, st));
+    own = true;
+  } else if (workspace_bytes < need) {
+    psfd_set_error("psfd_solve: workspace too small (%zu < %zu)", workspace_bytes, need);
+    return PSFD_ERR_ARG;
+  }
+  ws_layout(P, &w, base);
+  const int nr = P->nrhs;
+  const long n = P->nvec;
+  const size_t vbytes = (size_t)nr * n * sizeof(cf);
+  const int nb = nblocks_for(n);
+  const float us = 1.0f / sqrtf((float)P->ncols);
+  const long nplanes = (long)nr * 3 * P->nz;
+  int rc = PSFD_OK;
+  auto fail = [&](int code) { if (own) cudaFreeAsync(base, st); return code; };
+
+  PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr, st));
+  k_set_scalars<<<1, 32 * ((nr + 31) / 32), 0, st>>>(w.sc, nr, tol * tol, maxit);
+  PSFD_CHECK_LAUNCH();
+  VArgs va{};
+  va.n = n; va.sc = w.sc; va.done = w.done; va.partials = w.partials; va.counters = w.counters;
+  va.hist = nullptr; va.hist_cap = 0; va.use_done = false;
+  // b -> HYBRID, ||b||^2
+  PSFD_CUDA_TRY(cudaMemcpyAsync(w.bH, b, vbytes, cudaMemcpyDeviceToDevice, st));
+  if ((rc = launch_lateral_transform(P, w.bH, nplanes, true, us))) return fail(rc);
+  va.v0 = w.bH;
+  if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return fail(rc);
+  k_copy_bnorm<<<1, 32 * ((nr + 31) / 32), 0, st>>>(w.sc, nr);
+  // r0 = b - A E_base
+  if (x0) {
+    PSFD_CUDA_TRY(cudaMemcpyAsync(w.Eb, x0, vbytes, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_lateral_transform(P, w.Eb, nplanes, true, us))) return fail(rc);
+    if ((rc = apply_hybrid(P, w.Eb, w.v, 0, nullptr))) return fail(rc);
+    va.v0 = w.bH; va.v1 = w.v; va.v2 = w.r;
+    if ((rc = launch_vec<OK_SUB>(va, nr, st, nb))) return fail(rc);
+  } else {
+    PSFD_CUDA_TRY(cudaMemcpyAsync(w.r, w.bH, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
+  va.v0 = w.r; va.v1 = w.rhat; va.v2 = w.p; va.v3 = w.v; va.v4 = w.y;
+  if ((rc = launch_vec<OK_INIT>(va, nr, st, nb))) return fail(rc);
+
+  // ---- BiCGSTAB iterations (van der Vorst), on B = A M
+  const int aflags = use_precond ? PSFD_PRECOND : 0;
+  va.use_done = true;
+  va.hist = nullptr;
+  double* dhist = nullptr;
+  if (P->hist && P->hist_cap > 0) {
+    PSFD_CUDA_TRY(cudaMallocAsync((void**)&dhist, sizeof(double) * nr * P->hist_cap, st));
+    PSFD_CUDA_TRY(cudaMemsetAsync(dhist, 0, sizeof(double) * nr * P->hist_cap, st));
+    va.hist = dhist; va.hist_cap = P->hist_cap;
+  }
+  std::vector<int> hdone(nr);
+  const int check_every = 8;
+  for (int it = 0; it < maxit; it += check_every) {
+    for (int k = 0; k < check_every && it + k < maxit; ++k) {
+      va.v0 = w.p; va.v1 = w.r; va.v2 = w.v;
+      if ((rc = launch_vec<OK_P>(va, nr, st, nb))) return fail(rc);
+      if ((rc = apply_hybrid(P, w.p, w.v, aflags, w.done))) return fail(rc);
+      va.v0 = w.rhat; va.v1 = w.v;
+      if ((rc = launch_vec<OK_RV>(va, nr, st, nb))) return fail(rc);
+      va.v0 = w.s; va.v1 = w.r; va.v2 = w.v;
+      if ((rc = launch_vec<OK_S>(va, nr, st, nb))) return fail(rc);
+      if ((rc = apply_hybrid(P, w.s, w.t, aflags, w.done))) return fail(rc);
+      va.v0 = w.t; va.v1 = w.s;
+      if ((rc = launch_vec<OK_TS>(va, nr, st, nb))) return fail(rc);
+      va.v0 = w.y; va.v1 = w.r; va.v2 = w.p; va.v3 = w.s; va.v4 = w.t; va.v5 = w.rhat;
+      if ((rc = launch_vec<OK_XR>(va, nr, st, nb))) return fail(rc);
+    }
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hdone.data(), w.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int r = 0; r < nr; ++r) all = all && hdone[r];
+    if (all) break;
+  }
+  // ---- E = E_base + M y ; true residual
+  cf* My = w.s;
+  if (use_precond) {
+    if ((rc = launch_axial(P, w.y, My, 2, nullptr, nr))) return fail(rc);
+  } else {
+    PSFD_CUDA_TRY(cudaMemcpyAsync(My, w.y, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
+  cf* EH = w.p;
+  va.use_done = false;
+  if (x0) {
+    va.v0 = w.Eb; va.v1 = My; va.v2 = EH;
+    if ((rc = launch_vec<OK_AXPY>(va, nr, st, nb))) return fail(rc);
+  } else {
+    PSFD_CUDA_TRY(cudaMemcpyAsync(EH, My, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
+  if ((rc = apply_hybrid(P, EH, w.v, 0, nullptr))) return fail(rc);
+  va.v0 = w.bH; va.v1 = w.v; va.v2 = w.t;
+  if ((rc = launch_vec<OK_SUB>(va, nr, st, nb))) return fail(rc);
+  PSFD_CUDA_TRY(cudaMemcpyAsync(E, EH, vbytes, cudaMemcpyDeviceToDevice, st));
+  if ((rc = launch_lateral_transform(P, (cf*)E, nplanes, false, us))) return fail(rc);
+  std::vector<KScal> hs(nr);
+  PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+  if (dhist) {
+    PSFD_CUDA_TRY(cudaMemcpyAsync(P->hist, dhist, sizeof(double) * nr * P->hist_cap, cudaMemcpyDeviceToHost, st));
+  }
+  PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+  if (dhist) cudaFree(dhist);
+  int worst = PSFD_OK;
+  for (int r = 0; r < nr; ++r) {
+    const double bn = hs[r].bnorm2;
+    info[r].iters = hs[r].iters;
+    info[r].status = (bn == 0.0) ? PSFD_OK : hs[r].status;
+    info[r].r_rel = bn > 0 ? sqrt(hs[r].res1 / bn) : 0.0;
+    info[r].r_rel_recursive = bn > 0 ? sqrt(hs[r].rr / bn) : 0.0;
+    info[r].r_rel_initial = bn > 0 ? sqrt(hs[r].rr0 / bn) : 0.0;
+    if (info[r].status != PSFD_OK && worst == PSFD_OK) worst = info[r].status;
+  }
+  if (own) PSFD_CUDA_TRY(cudaFreeAsync(base, st));
+  return worst;
+}

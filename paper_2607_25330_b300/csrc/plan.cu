@@ -1,0 +1,445 @@
+// Plan set-up, geometry (mask -> fill), FP64 multilayer reflection and the
+// background source b (Sec. 2.2, Eq. bg_source).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+static thread_local char g_err[1024] = "";
+
+void psfd_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* psfd_last_error(void) { return g_err; }
+extern "C" const char* psfd_version(void) { return "psfd-b300 0.1 (sm_103a)"; }
+
+extern "C" int psfd_supported(int nx, int ny, int nz) {
+  return lateral_supported(nx) && lateral_supported(ny) && axial_supported(nz) ? 1 : 0;
+}
+
+// ------------------------------------------------------------ FP64 complex helpers
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd cd_(double r, double i) { return {r, i}; }
+__device__ __forceinline__ cd operator+(cd a, cd b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cd operator-(cd a, cd b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cd operator*(cd a, cd b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ cd operator*(double s, cd a) { return {s * a.re, s * a.im}; }
+__device__ __forceinline__ cd cdiv(cd a, cd b) {
+  // scaled division
+  if (fabs(b.re) >= fabs(b.im)) {
+    double r = b.im / b.re, den = b.re + b.im * r;
+    return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+  } else {
+    double r = b.re / b.im, den = b.re * r + b.im;
+    return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+  }
+}
+__device__ __forceinline__ double cabs_(cd a) { return hypot(a.re, a.im); }
+// principal square root, then the branch with Im >= 0
+__device__ __forceinline__ cd csqrt_up(cd z) {
+  double r = hypot(z.re, z.im);
+  cd s;
+  if (r == 0.0) return {0.0, 0.0};
+  if (z.re >= 0) {
+    double u = sqrt(0.5 * (r + z.re));
+    s = {u, z.im / (2.0 * u)};
+  } else {
+    double u = sqrt(0.5 * (r - z.re));
+    s = {fabs(z.im) / (2.0 * u), (z.im >= 0 ? u : -u)};
+  }
+  if (s.im < 0) s = {-s.re, -s.im};
+  return s;
+}
+__device__ __forceinline__ cd ccos_(cd z) { return {cos(z.re) * cosh(z.im), -sin(z.re) * sinh(z.im)}; }
+__device__ __forceinline__ cd csin_(cd z) { return {sin(z.re) * cosh(z.im), cos(z.re) * sinh(z.im)}; }
+
+// ------------------------------------------------------------ transfer matrix (FP64)
+// Reflection of the stack below z_ml for every lateral Bloch mode (Sec. 2.2,
+// TMM-based R_ml).  Characteristic matrix of the tangential fields per layer,
+//   [[cos d, i sin d / q], [i q sin d, cos d]],  d = kz_j t_j,
+// q = kz (s) or kz / eps (p); the product is renormalised after each layer
+// (the reflection is a ratio, so scale does not matter).  r = (a + c)/(c - a)
+// with a = P21 - q_s P11, c = q_0 (P22 - q_s P12); r_p (tangential E) = -r.
+struct StackDev {
+  int nl;
+  const double* n_re;
+  const double* n_im;
+  const double* d;
+  double sub_re, sub_im;
+};
+
+__device__ cd tmm_r(double kp2, double k0, const StackDev& st, bool ppol) {
+  cd P11 = {1, 0}, P12 = {0, 0}, P21 = {0, 0}, P22 = {1, 0};
+  for (int j = 0; j < st.nl; ++j) {
+    cd n = {st.n_re[j], st.n_im[j]};
+    cd eps = n * n;
+    cd kzj = csqrt_up(k0 * k0 * eps - cd_(kp2, 0.0));
+    cd q = ppol ? cdiv(kzj, eps) : kzj;
+    cd dl = st.d[j] * kzj;
+    cd c = ccos_(dl), s = csin_(dl);
+    cd is = {-s.im, s.re};                 // i sin
+    cd m12 = cdiv(is, q), m21 = is * q;
+    cd N11 = c * P11 + m12 * P21, N12 = c * P12 + m12 * P22;
+    cd N21 = m21 * P11 + c * P21, N22 = m21 * P12 + c * P22;
+    double mx = fmax(fmax(cabs_(N11), cabs_(N12)), fmax(cabs_(N21), cabs_(N22)));
+    double inv = (mx > 0) ? 1.0 / mx : 1.0;
+    P11 = inv * N11; P12 = inv * N12; P21 = inv * N21; P22 = inv * N22;
+  }
+  cd ns = {st.sub_re, st.sub_im};
+  cd es = ns * ns;
+  cd kzs = csqrt_up(k0 * k0 * es - cd_(kp2, 0.0));
+  cd qs = ppol ? cdiv(kzs, es) : kzs;
+  cd q0 = csqrt_up(cd_(k0 * k0 - kp2, 0.0));
+  cd a = P21 - qs * P11;
+  cd c = q0 * (P22 - qs * P12);
+  cd r = cdiv(a + c, c - a);
+  return ppol ? cd_(-r.re, -r.im) : r;
+}
+
+__global__ void k_tmm(int nx, int ny, double dkx, double dky, double kx_inc, double ky_inc, double k0,
+                      StackDev st, double2* rs64, double2* rp64, double2* kz064, float4* refl, cf* kz0f) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nx * ny) return;
+  int ix = m % nx, iy = m / nx;
+  double kx = dkx * fft_signed(ix, nx) + kx_inc;
+  double ky = dky * fft_signed(iy, ny) + ky_inc;
+  double kp2 = kx * kx + ky * ky;
+  cd rs = tmm_r(kp2, k0, st, false);
+  cd rp = tmm_r(kp2, k0, st, true);
+  cd kz0 = csqrt_up(cd_(k0 * k0 - kp2, 0.0));
+  rs64[m] = make_double2(rs.re, rs.im);
+  rp64[m] = make_double2(rp.re, rp.im);
+  kz064[m] = make_double2(kz0.re, kz0.im);
+  refl[m] = make_float4((float)rs.re, (float)rs.im, (float)rp.re, (float)rp.im);
+  kz0f[m] = make_float2((float)kz0.re, (float)kz0.im);
+}
+
+// ------------------------------------------------------------ source b (Eq. bg_source)
+// b = k0^2 deps (E_inc + R E_inc): the incident plane wave is the lateral mode
+// (0,0); its reflection uses that mode's FP64 r_s, r_p.  Computed in FP64.
+struct SourceArgs {
+  const float* fill;
+  cf* b;
+  int nx, ny, nz, z_ml;
+  long ncols;
+  double dz, k0, theta, phi, deps_re, deps_im;
+  const double2* rs64;
+  const double2* rp64;
+  const double2* kz064;
+  int pol;
+};
+
+__global__ void k_source(SourceArgs a) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long n = a.ncols * a.nz;
+  if (i >= n) return;
+  int z = (int)(i / a.ncols);
+  double f = a.fill[i];
+  double k02 = a.k0 * a.k0;
+  cd de = {f * a.deps_re * k02, f * a.deps_im * k02};
+  // polarisation vector and wave vector of the incident wave
+  double st = sin(a.theta), ctt = cos(a.theta), sp = sin(a.phi), cp = cos(a.phi);
+  double e[3];
+  if (a.pol == 0) { e[0] = -sp; e[1] = cp; e[2] = 0.0; }
+  else { e[0] = ctt * cp; e[1] = ctt * sp; e[2] = st; }
+  double kx = a.k0 * st * cp, ky = a.k0 * st * sp;
+  double kpar = sqrt(kx * kx + ky * ky);
+  double sx, sy, tx, ty;
+  if (kpar < 1e-12 * a.k0) { sx = 0; sy = 1; tx = 1; ty = 0; }
+  else { sx = -ky / kpar; sy = kx / kpar; tx = kx / kpar; ty = ky / kpar; }
+  cd rs = {a.rs64[0].x, a.rs64[0].y}, rp = {a.rp64[0].x, a.rp64[0].y};
+  cd kz0 = {a.kz064[0].x, a.kz064[0].y};
+  double as = sx * e[0] + sy * e[1], at = tx * e[0] + ty * e[1];
+  cd r0 = as * sx * rs + at * tx * rp;
+  cd r1 = as * sy * rs + at * ty * rp;
+  cd r2 = cdiv(cd_(-1, 0) * (kx * r0 + ky * r1), kz0);
+  double zr = (z - a.z_ml) * a.dz;
+  double kzi = a.k0 * ctt;
+  cd einc = {cos(kzi * zr), -sin(kzi * zr)};
+  cd prof = {0, 0};
+  if (zr >= 0) {
+    double mag = exp(-kz0.im * zr);
+    prof = {mag * cos(kz0.re * zr), mag * sin(kz0.re * zr)};
+  }
+  cd tot[3] = {e[0] * einc + r0 * prof, e[1] * einc + r1 * prof, e[2] * einc + r2 * prof};
+  long plane = a.ncols * a.nz;
+  long xy = i % a.ncols;
+  for (int c = 0; c < 3; ++c) {
+    cd v = de * tot[c];
+    a.b[c * plane + (long)z * a.ncols + xy] = make_float2((float)v.re, (float)v.im);
+  }
+}
+
+// ------------------------------------------------------------ geometry kernels
+__global__ void k_u8_to_c(const uint8_t* a, cf* out, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)a[i], 0.f);
+}
+
+__global__ void k_extrude(const cf* plane, const float* zprof, float* fill, long ncols, int nz) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncols * nz) return;
+  int z = (int)(i / ncols);
+  fill[i] = zprof[z] * plane[i % ncols].x;
+}
+
+// planes with any nonzero fill
+__global__ void k_fill_range(const float* fill, long ncols, int nz, int* zr) {
+  int z = blockIdx.x;
+  int any = 0;
+  for (long i = threadIdx.x; i < ncols; i += blockDim.x) any |= (fill[(long)z * ncols + i] != 0.f);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0 && any) {
+    atomicMin(&zr[0], z);
+    atomicMax(&zr[1], z + 1);
+  }
+}
+
+// ------------------------------------------------------------ plan
+static void host_twiddles(int n, std::vector<cf>& out) {
+  out.resize(n);
+  for (int m = 0; m < n; ++m) {
+    double a = -2.0 * M_PI * (double)m / (double)n;
+    out[m] = make_float2((float)cos(a), (float)sin(a));
+  }
+}
+
+static double host_fftk(int i, int n, double d) {
+  int m = (i <= (n - 1) / 2) ? i : i - n;
+  return 2.0 * M_PI * m / (n * d);
+}
+
+static int upload(void** dst, const void* src, size_t bytes) {
+  PSFD_CUDA_TRY(cudaMalloc(dst, bytes));
+  PSFD_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return PSFD_OK;
+}
+
+static void plan_free(psfd_plan_s* P) {
+  void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
+                  P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
+  if (!out || !prm) { psfd_set_error("psfd_plan_create: null argument"); return PSFD_ERR_ARG; }
+  *out = nullptr;
+  const psfd_params_t& p = *prm;
+  if (p.nrhs < 1 || p.dx <= 0 || p.dy <= 0 || p.dz <= 0 || p.lambda <= 0) {
+    psfd_set_error("psfd_plan_create: invalid sizes or spacing");
+    return PSFD_ERR_ARG;
+  }
+  if (!psfd_supported(p.nx, p.ny, p.nz)) {
+    psfd_set_error("psfd_plan_create: unsupported grid %dx%dx%d", p.nx, p.ny, p.nz);
+    return PSFD_ERR_ARG;
+  }
+  if (p.pml_planes < 0 || 2 * p.pml_planes >= p.nz || p.z_ml < 0 || p.z_ml >= p.nz ||
+      (p.pml_planes > 0 && !(p.pml_R0 > 0 && p.pml_R0 < 1))) {
+    psfd_set_error("psfd_plan_create: invalid PML / z_ml");
+    return PSFD_ERR_ARG;
+  }
+  psfd_plan_s* P = new psfd_plan_s();
+  P->p = p;
+  P->stream = (cudaStream_t)p.stream;
+  P->nx = p.nx; P->ny = p.ny; P->nz = p.nz; P->nrhs = p.nrhs;
+  P->ncols = (long)p.nx * p.ny;
+  P->nvec = 3L * p.nz * P->ncols;
+  P->k0 = 2.0 * M_PI / p.lambda;
+  double th = p.theta_deg * M_PI / 180.0, ph = p.phi_deg * M_PI / 180.0;
+  P->kx_inc = P->k0 * sin(th) * cos(ph);
+  P->ky_inc = P->k0 * sin(th) * sin(ph);
+  P->kz_inc = P->k0 * cos(th);
+  P->deps_re = p.eps_abs_re - 1.0;
+  P->deps_im = p.eps_abs_im;
+  // light-cone check (k_z = 0 exactly is not representable)
+  for (int iy = 0; iy < p.ny; ++iy)
+    for (int ix = 0; ix < p.nx; ++ix) {
+      double kx = host_fftk(ix, p.nx, p.dx) + P->kx_inc, ky = host_fftk(iy, p.ny, p.dy) + P->ky_inc;
+      if (fabs(P->k0 * P->k0 - kx * kx - ky * ky) < 1e-18 * P->k0 * P->k0) {
+        psfd_set_error("psfd_plan_create: a lateral mode lies on the light cone");
+        delete P;
+        return PSFD_ERR_ARG;
+      }
+    }
+  std::vector<float> kx(p.nx), ky(p.ny), kz(p.nz);
+  for (int i = 0; i < p.nx; ++i) kx[i] = (float)(host_fftk(i, p.nx, p.dx) + P->kx_inc);
+  for (int i = 0; i < p.ny; ++i) ky[i] = (float)(host_fftk(i, p.ny, p.dy) + P->ky_inc);
+  for (int i = 0; i < p.nz; ++i) kz[i] = (float)host_fftk(i, p.nz, p.dz);
+  // PML: s = 1 + i alpha (d/d_pml)^3, alpha = 4 ln(1/R0) / (2 k0 d_pml)
+  std::vector<cf> sinv(p.nz);
+  int np = p.pml_planes;
+  double dpml = np * p.dz;
+  double alpha = np > 0 ? 4.0 * log(1.0 / p.pml_R0) / (2.0 * P->k0 * dpml) : 0.0;
+  for (int k = 0; k < p.nz; ++k) {
+    double d = 0.0;
+    if (k < np) d = (np - k) * p.dz;
+    else if (k >= p.nz - np) d = (k - (p.nz - np - 1)) * p.dz;
+    double sig = np > 0 ? alpha * pow(d / dpml, 3.0) : 0.0;
+    double den = 1.0 + sig * sig;            // 1/(1 + i sig) = (1 - i sig)/(1 + sig^2)
+    sinv[k] = make_float2((float)(1.0 / den), (float)(-sig / den));
+  }
+  std::vector<cf> twx, twy, twz;
+  host_twiddles(p.nx, twx);
+  host_twiddles(p.ny, twy);
+  host_twiddles(p.nz, twz);
+  int rc = PSFD_OK;
+  if ((rc = upload((void**)&P->kx, kx.data(), kx.size() * 4)) ||
+      (rc = upload((void**)&P->ky, ky.data(), ky.size() * 4)) ||
+      (rc = upload((void**)&P->kz, kz.data(), kz.size() * 4)) ||
+      (rc = upload((void**)&P->sinv, sinv.data(), sinv.size() * 8)) ||
+      (rc = upload((void**)&P->tw_x, twx.data(), twx.size() * 8)) ||
+      (rc = upload((void**)&P->tw_y, twy.data(), twy.size() * 8)) ||
+      (rc = upload((void**)&P->tw_z, twz.data(), twz.size() * 8))) {
+    plan_free(P);
+    delete P;
+    return rc;
+  }
+  // damping
+  double kref = p.k_ref > 0 ? p.k_ref : P->k0;
+  P->m_min = (float)p.m_min;
+  P->kref2 = (float)(kref * kref);
+  P->gamma = (float)p.gamma;
+  P->damp_eps = (float)(p.damp_eps_rel * P->k0 * P->k0);
+  // scratch
+  size_t nm = (size_t)P->ncols;
+  size_t vec_bytes = (size_t)p.nrhs * P->nvec * sizeof(cf);
+  cudaError_t e1 = cudaMalloc((void**)&P->R.rs64, nm * 16);
+  cudaError_t e2 = cudaMalloc((void**)&P->R.rp64, nm * 16);
+  cudaError_t e3 = cudaMalloc((void**)&P->R.kz064, nm * 16);
+  cudaError_t e4 = cudaMalloc((void**)&P->R.refl, nm * 16);
+  cudaError_t e5 = cudaMalloc((void**)&P->R.kz0, nm * 8);
+  cudaError_t e6 = cudaMalloc((void**)&P->tmpA, vec_bytes);
+  cudaError_t e7 = cudaMalloc((void**)&P->tmpB, vec_bytes);
+  if (e1 || e2 || e3 || e4 || e5 || e6 || e7) {
+    psfd_set_error("psfd_plan_create: cudaMalloc failed (%s)", cudaGetErrorString(cudaGetLastError()));
+    plan_free(P);
+    delete P;
+    return PSFD_ERR_CUDA;
+  }
+  *out = P;
+  return PSFD_OK;
+}
+
+extern "C" int psfd_plan_destroy(psfd_plan P) {
+  if (!P) return PSFD_OK;
+  cudaStreamSynchronize(P->stream);
+  plan_free(P);
+  delete P;
+  return PSFD_OK;
+}
+
+extern "C" int psfd_set_history(psfd_plan P, double* hist, int capacity) {
+  if (!P || capacity < 0) { psfd_set_error("psfd_set_history: bad argument"); return PSFD_ERR_ARG; }
+  P->hist = hist;
+  P->hist_cap = hist ? capacity : 0;
+  return PSFD_OK;
+}
+
+extern "C" int psfd_mask_fill(psfd_plan P, const uint8_t* a_bin, const float* zprof, float* fill) {
+  if (!P || !a_bin || !zprof || !fill) { psfd_set_error("psfd_mask_fill: null argument"); return PSFD_ERR_ARG; }
+  cudaStream_t s = P->stream;
+  long n = P->ncols;
+  cf* buf = P->tmpA;  // one plane
+  float* zp = nullptr;
+  PSFD_CUDA_TRY(cudaMallocAsync((void**)&zp, P->nz * sizeof(float), s));
+  PSFD_CUDA_TRY(cudaMemcpyAsync(zp, zprof, P->nz * sizeof(float), cudaMemcpyHostToDevice, s));
+  k_u8_to_c<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a_bin, buf, n);
+  PSFD_CHECK_LAUNCH();
+  int rc;
+  if ((rc = launch_rows(P->nx, buf, P->ny, true, 1.0f, P->tw_x, s))) return rc;
+  if ((rc = launch_cols_gauss(P->ny, P->nx, buf, (float)P->p.sigma_px, P->tw_y, s))) return rc;
+  if ((rc = launch_rows(P->nx, buf, P->ny, false, 1.0f / (float)n, P->tw_x, s))) return rc;
+  k_extrude<<<(unsigned)((n * P->nz + 255) / 256), 256, 0, s>>>(buf, zp, fill, n, P->nz);
+  PSFD_CHECK_LAUNCH();
+  PSFD_CUDA_TRY(cudaFreeAsync(zp, s));
+  return PSFD_OK;
+}
+
+extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const float* fill, const int* pol,
+                               psfd_c64* b) {
+  if (!P || !stack || !fill || !pol || !b) { psfd_set_error("psfd_background: null argument"); return PSFD_ERR_ARG; }
+  if (stack->n_layers < 0 || (stack->n_layers > 0 && (!stack->n_re || !stack->n_im || !stack->d))) {
+    psfd_set_error("psfd_background: bad stack");
+    return PSFD_ERR_ARG;
+  }
+  for (int r = 0; r < P->nrhs; ++r)
+    if (pol[r] != PSFD_TE && pol[r] != PSFD_TM) { psfd_set_error("psfd_background: bad polarisation"); return PSFD_ERR_ARG; }
+  cudaStream_t s = P->stream;
+  int nl = stack->n_layers;
+  double* dstack = nullptr;
+  if (nl > 0) {
+    PSFD_CUDA_TRY(cudaMalloc((void**)&dstack, 3 * nl * sizeof(double)));
+    PSFD_CUDA_TRY(cudaMemcpy(dstack, stack->n_re, nl * 8, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(dstack + nl, stack->n_im, nl * 8, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(dstack + 2 * nl, stack->d, nl * 8, cudaMemcpyHostToDevice));
+  }
+  StackDev st{nl, dstack, dstack ? dstack + nl : nullptr, dstack ? dstack + 2 * nl : nullptr, stack->sub_re,
+              stack->sub_im};
+  double dkx = 2.0 * M_PI / (P->nx * P->p.dx), dky = 2.0 * M_PI / (P->ny * P->p.dy);
+  long nm = P->ncols;
+  k_tmm<<<(unsigned)((nm + 127) / 128), 128, 0, s>>>(P->nx, P->ny, dkx, dky, P->kx_inc, P->ky_inc, P->k0, st,
+                                                     P->R.rs64, P->R.rp64, P->R.kz064, P->R.refl, P->R.kz0);
+  PSFD_CHECK_LAUNCH();
+  // absorber plane range
+  int* zr = nullptr;
+  int hz[2] = {P->nz, 0};
+  PSFD_CUDA_TRY(cudaMallocAsync((void**)&zr, 2 * sizeof(int), s));
+  PSFD_CUDA_TRY(cudaMemcpyAsync(zr, hz, 8, cudaMemcpyHostToDevice, s));
+  k_fill_range<<<P->nz, 256, 0, s>>>(fill, nm, P->nz, zr);
+  PSFD_CHECK_LAUNCH();
+  PSFD_CUDA_TRY(cudaMemcpyAsync(hz, zr, 8, cudaMemcpyDeviceToHost, s));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  PSFD_CUDA_TRY(cudaFreeAsync(zr, s));
+  if (dstack) PSFD_CUDA_TRY(cudaFree(dstack));
+  if (hz[1] <= hz[0]) { hz[0] = 0; hz[1] = 0; }
+  P->za0 = hz[0];
+  P->za1 = hz[1];
+  size_t need = (size_t)P->nrhs * 3 * (size_t)(P->za1 - P->za0) * nm;
+  if (need > P->G_elems) {
+    if (P->G) cudaFree(P->G);
+    P->G = nullptr;
+    P->G_elems = 0;
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->G, need * sizeof(cf)));
+    P->G_elems = need;
+  }
+  P->fill = fill;
+  // sources
+  for (int r = 0; r < P->nrhs; ++r) {
+    SourceArgs a;
+    a.fill = fill; a.b = (cf*)b + (long)r * P->nvec;
+    a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.z_ml = P->p.z_ml; a.ncols = nm;
+    a.dz = P->p.dz; a.k0 = P->k0;
+    a.theta = P->p.theta_deg * M_PI / 180.0; a.phi = P->p.phi_deg * M_PI / 180.0;
+    a.deps_re = P->deps_re; a.deps_im = P->deps_im;
+    a.rs64 = P->R.rs64; a.rp64 = P->R.rp64; a.kz064 = P->R.kz064;
+    a.pol = pol[r];
+    long n = nm * P->nz;
+    k_source<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    PSFD_CHECK_LAUNCH();
+  }
+  P->have_background = true;
+  return PSFD_OK;
+}
+
+extern "C" int psfd_reflection_tables(psfd_plan P, double* rs, double* rp, double* kz0) {
+  if (!P || !P->have_background) { psfd_set_error("psfd_reflection_tables: no background yet"); return PSFD_ERR_STATE; }
+  size_t bytes = (size_t)P->ncols * 16;
+  PSFD_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (rs) PSFD_CUDA_TRY(cudaMemcpy(rs, P->R.rs64, bytes, cudaMemcpyDeviceToHost));
+  if (rp) PSFD_CUDA_TRY(cudaMemcpy(rp, P->R.rp64, bytes, cudaMemcpyDeviceToHost));
+  if (kz0) PSFD_CUDA_TRY(cudaMemcpy(kz0, P->R.kz064, bytes, cudaMemcpyDeviceToHost));
+  return PSFD_OK;
+}

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libpsfd (the C ABI in include/psfd.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  torch provides device memory and the stream.  The binding
+fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpsfd.so")
+
+PSFD_OK, PSFD_ERR_ARG, PSFD_ERR_CUDA, PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN, PSFD_ERR_TIMEOUT, PSFD_ERR_STATE = range(7)
+PSFD_TE, PSFD_TM = 0, 1
+PSFD_PRECOND, PSFD_HYBRID, PSFD_ADJOINT = 1, 2, 4
+PSFD_BICGSTAB, PSFD_GMRES = 0, 1
+
+
+class PsfdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"psfd error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nrhs", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("lam", C.c_double),
+                ("theta_deg", C.c_double), ("phi_deg", C.c_double),
+                ("pml_planes", C.c_int), ("pml_R0", C.c_double), ("z_ml", C.c_int),
+                ("eps_abs_re", C.c_double), ("eps_abs_im", C.c_double),
+                ("m_min", C.c_double), ("k_ref", C.c_double), ("gamma", C.c_double), ("damp_eps_rel", C.c_double),
+                ("sigma_px", C.c_double), ("stream", C.c_void_p)]
+
+
+class Stack(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("n_re", C.POINTER(C.c_double)), ("n_im", C.POINTER(C.c_double)),
+                ("d", C.POINTER(C.c_double)), ("sub_re", C.c_double), ("sub_im", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("r_rel", C.c_double),
+                ("r_rel_recursive", C.c_double), ("r_rel_initial", C.c_double)]
+
+
+class FnoWeights(C.Structure):
+    _fields_ = [("dv", C.c_int), ("dh", C.c_int), ("layers", C.c_int), ("mx", C.c_int), ("my", C.c_int),
+                ("mz", C.c_int), ("dq", C.c_int)] + \
+               [(n, C.c_void_p) for n in ("lift_w", "lift_b", "kxy", "kz", "w1", "b1", "w2", "b2",
+                                          "q1", "qb1", "q2", "qb2")]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpsfd.so (built by paper_2607_25330_b300.build); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpsfd.so not built ({LIB_PATH}); run paper_2607_25330_b300/build.py")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    sig = {
+        "psfd_plan_create": (i, [C.POINTER(vp), C.POINTER(Params)]),
+        "psfd_plan_destroy": (i, [vp]),
+        "psfd_supported": (i, [i, i, i]),
+        "psfd_mask_fill": (i, [vp, vp, C.POINTER(C.c_float), vp]),
+        "psfd_background": (i, [vp, C.POINTER(Stack), vp, C.POINTER(C.c_int), vp]),
+        "psfd_reflection_tables": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "psfd_apply": (i, [vp, vp, vp, i]),
+        "psfd_precond": (i, [vp, vp, vp, i]),
+        "psfd_solve": (i, [vp, vp, vp, vp, d, i, i, i, i, C.POINTER(Info), vp, sz]),
+        "psfd_solve_workspace_size": (sz, [vp, i, i]),
+        "psfd_set_history": (i, [vp, C.POINTER(C.c_double), i]),
+        "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
+        "fno_forward": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, vp]),
+        "psfd_spectral_upsample": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
+        "psfd_last_error": (C.c_char_p, []),
+        "psfd_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols() -> List[str]:
+    """Names of the functions the binding expects the library to export."""
+    return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
+            "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
+            "psfd_set_history", "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
+            "psfd_last_error", "psfd_version"]
+
+
+def _check(code: int, what: str, allow=()):
+    if code != PSFD_OK and code not in allow:
+        raise PsfdError(code, f"{what}: {lib().psfd_last_error().decode()}")
+    return code
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_stack(stack: Dict):
+    n = [complex(v) for v in stack["n"]]
+    nl = len(n)
+    nre = (C.c_double * max(nl, 1))(*[v.real for v in n])
+    nim = (C.c_double * max(nl, 1))(*[v.imag for v in n])
+    d = (C.c_double * max(nl, 1))(*[float(v) for v in stack["d"]])
+    sub = complex(stack["n_sub"])
+    st = Stack(nl, C.cast(nre, C.POINTER(C.c_double)), C.cast(nim, C.POINTER(C.c_double)),
+               C.cast(d, C.POINTER(C.c_double)), sub.real, sub.imag)
+    st._keep = (nre, nim, d)
+    return st
+
+
+class Plan:
+    """One PSFD operator (grid, angle, PML, damping) shared by nrhs right-hand sides."""
+
+    def __init__(self, prob, nrhs: Optional[int] = None, stream: Optional[torch.cuda.Stream] = None):
+        L = lib()
+        self.prob = prob
+        self.nrhs = nrhs if nrhs is not None else len(prob.pols)
+        self.stream = stream
+        eps = prob.eps_abs
+        self.params = Params(prob.nx, prob.ny, prob.nz, self.nrhs, prob.dx, prob.dy, prob.dz, prob.lam,
+                             prob.theta_deg, prob.phi_deg, prob.pml_planes, prob.pml_R0, prob.z_ml,
+                             eps.real, eps.imag, prob.m_min, prob.k_ref, prob.gamma, prob.damp_eps_rel,
+                             prob.sigma_px, _stream_handle(stream))
+        h = C.c_void_p()
+        _check(L.psfd_plan_create(C.byref(h), C.byref(self.params)), "psfd_plan_create")
+        self.h = h
+        self.shape = (self.nrhs, 3, prob.nz, prob.ny, prob.nx)
+        self.fill = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().psfd_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self) -> torch.Tensor:
+        return torch.empty(self.shape, dtype=torch.complex64, device="cuda")
+
+    def mask_fill(self, a_bin: torch.Tensor, zprof: Sequence[float]) -> torch.Tensor:
+        p = self.prob
+        a = a_bin.to(device="cuda", dtype=torch.uint8).contiguous()
+        zp = (C.c_float * p.nz)(*[float(v) for v in zprof])
+        fill = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device="cuda")
+        _check(lib().psfd_mask_fill(self.h, _ptr(a), zp, _ptr(fill)), "psfd_mask_fill")
+        return fill
+
+    def background(self, stack: Dict, fill: torch.Tensor, pols: Sequence[int]) -> torch.Tensor:
+        st = make_stack(stack)
+        pol = (C.c_int * self.nrhs)(*[int(v) for v in pols])
+        b = self.empty()
+        self.fill = fill
+        _check(lib().psfd_background(self.h, C.byref(st), _ptr(fill), pol, _ptr(b)), "psfd_background")
+        return b
+
+    def reflection_tables(self):
+        p = self.prob
+        n = p.nx * p.ny
+        bufs = [np.zeros(2 * n, dtype=np.float64) for _ in range(3)]
+        ptrs = [b.ctypes.data_as(C.POINTER(C.c_double)) for b in bufs]
+        _check(lib().psfd_reflection_tables(self.h, *ptrs), "psfd_reflection_tables")
+        return [(b[0::2] + 1j * b[1::2]).reshape(p.ny, p.nx) for b in bufs]
+
+    def apply(self, x: torch.Tensor, flags: int = 0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        y = self.empty() if out is None else out
+        _check(lib().psfd_apply(self.h, _ptr(x), _ptr(y), flags), "psfd_apply")
+        return y
+
+    def precond(self, x: torch.Tensor, flags: int = 0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        y = self.empty() if out is None else out
+        _check(lib().psfd_precond(self.h, _ptr(x), _ptr(y), flags), "psfd_precond")
+        return y
+
+    def workspace_size(self, method: int = PSFD_BICGSTAB, restart: int = 30) -> int:
+        return int(lib().psfd_solve_workspace_size(self.h, method, restart))
+
+    def solve(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-6, maxit: int = 1000,
+              method: int = PSFD_BICGSTAB, restart: int = 30, precond: bool = True,
+              out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+              history: int = 0):
+        E = self.empty() if out is None else out
+        info = (Info * self.nrhs)()
+        hist = None
+        if history > 0:
+            hist = np.zeros(self.nrhs * history, dtype=np.float64)
+            _check(lib().psfd_set_history(self.h, hist.ctypes.data_as(C.POINTER(C.c_double)), history),
+                   "psfd_set_history")
+        ws, wsb = None, 0
+        if workspace is not None:
+            ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
+        code = lib().psfd_solve(self.h, _ptr(b), _ptr(x0), _ptr(E), tol, maxit, method, restart,
+                                1 if precond else 0, info, ws, wsb)
+        if history > 0:
+            lib().psfd_set_history(self.h, None, 0)
+        _check(code, "psfd_solve", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
+        res = [{"iters": i.iters, "status": i.status, "r_rel": i.r_rel, "r_rel_recursive": i.r_rel_recursive,
+                "r_rel_initial": i.r_rel_initial} for i in info]
+        out_d = {"E": E, "info": res, "code": code}
+        if hist is not None:
+            out_d["history"] = hist.reshape(self.nrhs, history)
+        return out_d
+
+
+def fno_struct(w: Dict[str, torch.Tensor], shape) -> FnoWeights:
+    """Device weights (dict of CUDA tensors, complex kernels as complex64) -> fno_weights_t."""
+    names = ("lift_w", "lift_b", "kxy", "kz", "w1", "b1", "w2", "b2", "q1", "qb1", "q2", "qb2")
+    s = FnoWeights(shape.dv, shape.dh, shape.layers, shape.mx, shape.my, shape.mz, shape.dq,
+                   *[_ptr(w[n]) for n in names])
+    s._keep = w
+    return s
+
+
+def fno_forward(wt: FnoWeights, a: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    B, nz, ny, nx = a.shape
+    E = torch.empty((B, 3, nz, ny, nx), dtype=torch.complex64, device="cuda") if out is None else out
+    L = lib()
+    n = int(L.fno_workspace_size(C.byref(wt), B, nx, ny, nz))
+    ws = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    _check(L.fno_forward(C.byref(wt), _ptr(a.contiguous()), B, nx, ny, nz, _ptr(E), _ptr(ws), n,
+                         _stream_handle(stream)), "fno_forward")
+    return E
+
+
+def spectral_upsample(src: torch.Tensor, nz: int, ny: int, nx: int,
+                      stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    nb = int(np.prod(src.shape[:-3]))
+    nz0, ny0, nx0 = src.shape[-3:]
+    dst = torch.empty(src.shape[:-3] + (nz, ny, nx), dtype=torch.complex64, device="cuda")
+    _check(lib().psfd_spectral_upsample(_ptr(src.contiguous()), nb, nx0, ny0, nz0, _ptr(dst), nx, ny, nz,
+                                        _stream_handle(stream)), "psfd_spectral_upsample")
+    return dst

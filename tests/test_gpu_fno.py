@@ -1,0 +1,65 @@
+"""GPU parity of the factorised FNO forward pass (Sec. 2.1) and the spectral upsampling.
+
+The oracle rounds both operands of the per-mode mixing to bfloat16 exactly as
+the workload prescribes, then accumulates in float64; the GPU accumulates in
+float32 from float32 FFTs, so the only differences are float32 rounding and the
+rare bfloat16 rounding decision flipped by it.  Tolerance: relative L2 2e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fno as F
+from paper_2607_25330_b300 import inputs as I
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL_FNO = 2e-3
+
+
+def device_weights(w):
+    out = {}
+    for k, v in w.items():
+        t = torch.from_numpy(np.ascontiguousarray(v))
+        out[k] = t.cuda().contiguous()
+    return out
+
+
+@pytest.mark.parametrize("dims", [(2, 32, 32, 16), (1, 64, 32, 32), (2, 16, 16, 48), (1, 96, 64, 16)])
+def test_fno_forward_matches_oracle(dims):
+    from paper_2607_25330_b300 import psfd
+    B, nx, ny, nz = dims
+    S = I.FNOShape()
+    w = I.fno_weights(S, 21, spectral_scale=4.0)
+    a = np.random.default_rng(5).random((B, nz, ny, nx)).astype(np.float32)
+    ws = psfd.fno_struct(device_weights(w), S)
+    E = psfd.fno_forward(ws, torch.from_numpy(a).cuda())
+    torch.cuda.synchronize()
+    ref = F.forward(w, torch.from_numpy(a).double(), mix_bf16=True)
+    assert rel_l2(E.cpu(), ref) < TOL_FNO
+    # the bf16 rounding is what separates the GPU from the float64 network
+    ref64 = F.forward(w, torch.from_numpy(a).double(), mix_bf16=False)
+    assert rel_l2(E.cpu(), ref64) < 5e-2
+
+
+def test_fno_forward_128x128x48_training_shape():
+    from paper_2607_25330_b300 import psfd
+    S = I.FNOShape()
+    w = I.fno_weights(S, 22, spectral_scale=4.0)
+    p = I.preset("fno_train_128x128x48")
+    a = I.mask_for(p, 4)
+    from oracle import psfd as O
+    fill = O.fill_fraction(a, p.zprofile(), p.sigma_px).float().numpy()[None]
+    E = psfd.fno_forward(psfd.fno_struct(device_weights(w), S), torch.from_numpy(fill).cuda())
+    ref = F.forward(w, torch.from_numpy(fill).double(), mix_bf16=True)
+    assert rel_l2(E.cpu(), ref) < TOL_FNO
+
+
+@pytest.mark.parametrize("shapes", [((16, 16, 16), (32, 64, 32)), ((32, 32, 16), (128, 128, 64))])
+def test_spectral_upsample_matches_oracle(shapes):
+    from paper_2607_25330_b300 import psfd
+    (nz0, ny0, nx0), (nz, ny, nx) = shapes
+    src = torch.from_numpy(I.random_field((2, 3, nz0, ny0, nx0), 3)).to(torch.complex64)
+    out = psfd.spectral_upsample(src.cuda(), nz, ny, nx).cpu()
+    ref = F.spectral_upsample(src.to(torch.complex128), nz, ny, nx)
+    assert rel_l2(out, ref) < 1e-5

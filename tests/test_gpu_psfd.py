@@ -1,0 +1,167 @@
+"""GPU parity of the CUDA PSFD path against the FP64 oracle, through the C ABI.
+
+Tolerances: complex64 operator outputs within relative L2 1e-4 of the FP64
+oracle; FP64 paths (multilayer reflection) within 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov as K
+from oracle import psfd as O
+from paper_2607_25330_b300 import inputs as I
+from tests.helpers import oracle_setup, problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL_C64 = 1e-4
+
+GRIDS = [  # (nx, ny, nz, theta, phi, nrhs)
+    (32, 32, 16, 6.0, 0.0, 1),
+    (16, 32, 32, 8.0, 30.0, 2),
+    (64, 16, 48, 4.0, 0.0, 1),
+    (96, 96, 64, 6.0, 10.0, 1),
+    (128, 64, 96, 6.0, 0.0, 1),
+    (16, 16, 128, 5.0, 0.0, 3),
+]
+
+
+def gpu_plan(prob, nrhs):
+    from paper_2607_25330_b300 import psfd
+    return psfd.Plan(prob, nrhs=nrhs)
+
+
+def setup(nx, ny, nz, theta, phi, nrhs, seed=1, kind=None):
+    prob = problem(nx, ny, nz, theta=theta, phi=phi, pols=[i % 2 for i in range(nrhs)])
+    a = I.mask_for(prob, seed, kind)
+    g, fill_o = oracle_setup(prob, a)
+    plan = gpu_plan(prob, nrhs)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    return prob, a, g, fill_o, plan, fill, b
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_reflection_tables_fp64(grid):
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
+    rs, rp, kz0 = plan.reflection_tables()
+    assert np.max(np.abs(rs - g.rs.numpy())) < 1e-10
+    assert np.max(np.abs(rp - g.rp.numpy())) < 1e-10
+    assert np.max(np.abs(kz0 - g.kz0.numpy())) < 1e-10 * g.k0
+
+
+@pytest.mark.parametrize("grid", GRIDS[:4])
+def test_mask_fill_and_source(grid):
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
+    assert float((fill.cpu().double() - fill_o).abs().max()) < 1e-5
+    for r, pol in enumerate(prob.pols):
+        bo = O.source_b(g, fill_o, pol)
+        assert rel_l2(b[r].cpu(), bo) < 2e-6
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("flags", [0, 1])
+def test_apply_matches_oracle(grid, flags):
+    """y = A x (flags 0) and y = A M x (flags 1) against the oracle, random complex x."""
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
+    x = torch.from_numpy(I.random_field(plan.shape, 7)).to(torch.complex64)
+    y = plan.apply(x.cuda(), flags=flags).cpu()
+    for r in range(plan.nrhs):
+        xr = x[r].to(torch.complex128)
+        ref = O.apply_A(g, O.apply_M(g, xr) if flags else xr, fill_o)
+        assert rel_l2(y[r], ref) < TOL_C64, (grid, flags, r)
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_precond_matches_oracle(grid):
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
+    x = torch.from_numpy(I.random_field(plan.shape, 8)).to(torch.complex64)
+    y = plan.precond(x.cuda()).cpu()
+    for r in range(plan.nrhs):
+        assert rel_l2(y[r], O.apply_M(g, x[r].to(torch.complex128))) < TOL_C64
+
+
+def test_hybrid_apply_is_the_conjugated_real_space_apply():
+    from paper_2607_25330_b300 import psfd
+    prob, a, g, fill_o, plan, fill, b = setup(64, 32, 32, 6.0, 0.0, 2)
+    x = torch.from_numpy(I.random_field(plan.shape, 9)).to(torch.complex64).cuda()
+    y = plan.apply(x, flags=psfd.PSFD_PRECOND)
+    xh = torch.fft.fft2(x, norm="ortho")
+    yh = plan.apply(xh.contiguous(), flags=psfd.PSFD_PRECOND | psfd.PSFD_HYBRID)
+    assert rel_l2(torch.fft.ifft2(yh, norm="ortho").cpu(), y.cpu()) < 1e-5
+
+
+def test_blank_mask_gives_zero_field():
+    prob, a, g, fill_o, plan, fill, b = setup(32, 32, 16, 6.0, 0.0, 1, kind="blank")
+    assert float(b.abs().max()) == 0.0
+    res = plan.solve(b, tol=1e-6, maxit=50)
+    assert res["info"][0]["iters"] == 0 and float(res["E"].abs().max()) == 0.0
+
+
+def test_solve_line_space_32x32x16_matches_oracle():
+    """32x32x16 line/space, TE at 6 deg: complex64 solve to 1e-6 against the FP64 solution."""
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    g, fill_o = oracle_setup(prob, a)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    bo = O.source_b(g, fill_o, 0)
+    A = lambda E: O.apply_A(g, E, fill_o)
+    ref = K.solve(A, lambda x: O.apply_M(g, x), bo, tol=1e-12, maxit=5000)
+    assert ref["status"] == 0
+    res = plan.solve(b, tol=1e-6, maxit=2000)
+    info = res["info"][0]
+    assert info["status"] == 0
+    assert info["r_rel"] < 3e-6
+    E = res["E"][0].cpu()
+    # the FP64 residual of the GPU field, and its distance to the FP64 solution
+    r_true = O.rel_residual(g, E.to(torch.complex128), fill_o, bo)
+    assert r_true < 3e-6
+    assert rel_l2(E, ref["E"]) < 1e-4
+    # unpreconditioned solve converges to the same field
+    res0 = plan.solve(b, tol=1e-6, maxit=4000, precond=False)
+    assert res0["info"][0]["status"] == 0
+    assert rel_l2(res0["E"][0].cpu(), ref["E"]) < 1e-4
+
+
+def test_warm_start_identities():
+    """Eq. right_correction_solution: x0 = solution needs (almost) no iterations;
+    x0 = 0 reproduces the cold solve (Eq. right_preconditioned)."""
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    cold = plan.solve(b, tol=1e-6, maxit=2000)
+    warm = plan.solve(b, x0=cold["E"], tol=1e-5, maxit=2000)
+    assert warm["info"][0]["iters"] <= 1
+    assert warm["info"][0]["r_rel_initial"] < 1e-5
+    zero = plan.solve(b, x0=torch.zeros_like(b), tol=1e-6, maxit=2000)
+    assert zero["info"][0]["iters"] == cold["info"][0]["iters"]
+    assert rel_l2(zero["E"].cpu(), cold["E"].cpu()) < 1e-6
+
+
+def test_manhattan_128x128x64_full_size_apply_and_solve():
+    """The 128x128x64 TE+TM workload at full size: operator parity and a converged solve
+    whose FP64 residual (oracle) is at the solver tolerance."""
+    prob = I.preset("manhattan_128x128x64")
+    a = I.mask_for(prob, 11)
+    g, fill_o = oracle_setup(prob, a)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    x = torch.from_numpy(I.random_field(plan.shape, 5)).to(torch.complex64)
+    y = plan.apply(x.cuda(), flags=psfd.PSFD_PRECOND).cpu()
+    for r in range(2):
+        ref = O.apply_A(g, O.apply_M(g, x[r].to(torch.complex128)), fill_o)
+        assert rel_l2(y[r], ref) < TOL_C64
+    res = plan.solve(b, tol=1e-6, maxit=3000)
+    for r, pol in enumerate(prob.pols):
+        assert res["info"][r]["status"] == 0
+        bo = O.source_b(g, fill_o, pol)
+        assert O.rel_residual(g, res["E"][r].cpu().to(torch.complex128), fill_o, bo) < 3e-6
