@@ -202,6 +202,18 @@ PSFD_API int fno_forward(const fno_weights_t* w, const float* a, int B, int nx, 
 PSFD_API int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,
                            psfd_c64* dst, int nx, int ny, int nz, void* stream);
 
+/* ---------------------------------------------------------------- observability
+ * psfd_launch_count: number of kernels this library has launched in the process.
+ * psfd_timing_enable(1) starts per-stage timing with CUDA events recorded on each
+ * call's stream around the launches of a stage (0 fused axial operator kernel,
+ * 1 lateral contrast passes, 2 Krylov vector kernels, 3 lateral real<->HYBRID
+ * transforms, 4 FNO forward) and clears the totals; 0 stops it.
+ * psfd_timing_read synchronises on the recorded events and returns the summed
+ * milliseconds and the number of timed launches groups per stage (HOST arrays). */
+PSFD_API long long psfd_launch_count(void);
+PSFD_API int psfd_timing_enable(int on);
+PSFD_API int psfd_timing_read(double* ms, long long* calls, int nstages);
+
 /* ---------------------------------------------------------------- misc */
 PSFD_API const char* psfd_last_error(void);
 PSFD_API const char* psfd_version(void);

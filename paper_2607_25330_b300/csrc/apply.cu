@@ -308,6 +308,7 @@ int axial_supported(int nz) {
 }
 
 int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int) {
+  StageScope sc(P->stream, ST_AXIAL);
   const int T = P->axial_T;
   switch (P->nz) {
     case 16: return run_axial_mode<16, 2>(P, x, y, mode, done);
@@ -564,6 +565,7 @@ int launch_cols_gauss(int ny, int nx, cf* buf, float sigma, const cf* tw, cudaSt
 
 // real space <-> HYBRID over nplanes planes: forward = rows then columns (unitary scale)
 int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward, float scale) {
+  StageScope sc(P->stream, ST_TRANSFORM);
   int rc;
   const long rows = nplanes * P->ny, cols = nplanes * P->nx;
   if (forward) {
@@ -578,6 +580,7 @@ int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward
 int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint) {
   const int nab = P->za1 - P->za0;
   if (nab <= 0) return PSFD_OK;
+  StageScope scope(P->stream, ST_CONTRAST);
   const long nplanes = (long)P->nrhs * 3 * nab;
   int rc;
   RowArgs r{};

@@ -105,6 +105,7 @@ __device__ __forceinline__ cf twmul(cf a) {
 
 #define PSFD_CHECK_LAUNCH()                                                  \
   do {                                                                       \
+    psfd_count_launch();                                                     \
     cudaError_t err__ = cudaGetLastError();                                  \
     if (err__ != cudaSuccess) {                                              \
       psfd_set_error("%s:%d: launch: %s", __FILE__, __LINE__,                \
@@ -114,3 +115,14 @@ __device__ __forceinline__ cf twmul(cf a) {
   } while (0)
 
 void psfd_set_error(const char* fmt, ...);
+void psfd_count_launch();
+
+// Optional per-stage timing with CUDA events on the launching stream.
+enum { ST_AXIAL = 0, ST_CONTRAST = 1, ST_KRYLOV = 2, ST_TRANSFORM = 3, ST_FNO = 4, ST_N = 5 };
+void stage_mark(cudaStream_t s, int stage, bool begin);
+struct StageScope {
+  cudaStream_t s;
+  int st;
+  StageScope(cudaStream_t s_, int st_) : s(s_), st(st_) { stage_mark(s, st, true); }
+  ~StageScope() { stage_mark(s, st, false); }
+};

@@ -420,6 +420,7 @@ extern "C" int fno_forward(const fno_weights_t* w, const float* a, int B, int nx
   if (workspace_bytes < need) { psfd_set_error("fno_forward: workspace too small"); return PSFD_ERR_ARG; }
   fno_ws(w, B, nx, ny, nz, &ws, (char*)workspace);
   cudaStream_t s = (cudaStream_t)stream;
+  StageScope scope(s, ST_FNO);
   {
     std::vector<cf> tx, ty, tz;
     host_tw(nx, tx); host_tw(ny, ty); host_tw(nz, tz);

@@ -60,19 +60,20 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Block-reduce NQ doubles; write partials; the last block of this rhs sums the
 // partials in index order and returns true with the totals in out[].
-template <int NQ>
-__device__ bool reduce_finish(double (&val)[NQ], double* partials, unsigned* counters, double* out) {
-  __shared__ double sh[kThreads / 32][kMaxQ];
+// Generic form: `pbase` holds gridDim.x * QS doubles for this reduction group,
+// `counter` counts finished blocks of the group.
+template <int NQ, int QS>
+__device__ bool reduce_group(double (&val)[NQ], double* pbase, unsigned* counter, double* out) {
+  __shared__ double sh[kThreads / 32][QS];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rhs = blockIdx.y;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     double v = warp_sum(val[q]);
     if (lane == 0) sh[warp][q] = v;
   }
   __syncthreads();
-  double* part = partials + ((long)rhs * gridDim.x + blockIdx.x) * kMaxQ;
+  double* part = pbase + (long)blockIdx.x * QS;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -81,23 +82,39 @@ __device__ bool reduce_finish(double (&val)[NQ], double* partials, unsigned* cou
       part[q] = s;
     }
     __threadfence();
-    unsigned prev = atomicAdd(counters + rhs, 1u);
+    unsigned prev = atomicAdd(counter, 1u);
     last = (prev == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // last block: every thread sums a fixed strided subset of the partials, then the
+  // same fixed tree as above (deterministic for a given grid)
+  const volatile double* base = pbase;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += base[b * QS + q];
+    s = warp_sum(s);
+    if (lane == 0) sh[warp][q] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double* base = partials + (long)rhs * gridDim.x * kMaxQ;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double s = 0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile const double*)base)[b * kMaxQ + q];
+      for (int w = 0; w < kThreads / 32; ++w) s += sh[w][q];
       out[q] = s;
     }
-    counters[rhs] = 0;  // ready for the next reduction
+    *counter = 0;  // ready for the next reduction
   }
   return true;
+}
+
+template <int NQ>
+__device__ bool reduce_finish(double (&val)[NQ], double* partials, unsigned* counters, double* out) {
+  const int rhs = blockIdx.y;
+  return reduce_group<NQ, kMaxQ>(val, partials + (long)rhs * gridDim.x * kMaxQ, counters + rhs, out);
 }
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -304,6 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
 
 template <int OP>
 int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
+  StageScope sc(s, ST_KRYLOV);
   dim3 grid((unsigned)nblocks, (unsigned)nrhs);
   k_vec<OP><<<grid, kThreads, 0, s>>>(a);
   PSFD_CHECK_LAUNCH();
@@ -327,12 +345,228 @@ __global__ void k_copy_bnorm(KScal* sc, int nrhs) {
 
 }  // namespace
 
-struct SolveWs {
-  cf *bH, *r, *rhat, *p, *v, *s, *t, *y, *Eb;
-  KScal* sc;
-  int* done;
+
+// ======================================================================= GMRES(m)
+// Arnoldi with classical Gram-Schmidt applied twice (CGS2); the Hessenberg
+// matrix, the Givens rotations and the small triangular solve are FP64 on the
+// device (one thread per right-hand side).
+namespace {
+
+constexpr int GCH = 8;       // basis vectors per multi-dot block
+constexpr int GMAX = 64;     // largest restart length supported
+
+struct GState {
+  double2 H[(GMAX + 1) * GMAX];  // column-major: H[i + j*(m+1)]
+  double2 cs[GMAX], sn[GMAX], g[GMAX + 1], z[GMAX];
+  double beta, bnorm2, tol2;
+  int jd, iters, maxit, status, m, active, pad0, pad1;
+};
+
+struct GArgs {
+  cf* V;           // basis, V_i at V + i * vs (each [nrhs][n])
+  long vs;
+  long n;
+  int nv;          // vectors used (multi-dot / update)
+  int j;           // Arnoldi column being built
+  GState* gs;
+  const int* mask; // skip rhs with mask != 0 (nullable)
   double* partials;
   unsigned* counters;
+  double2* hout;   // [nrhs][GMAX] results of the multi-dot
+  cf* w;           // target vector (V_{j+1})
+  cf* y;           // solution accumulator
+};
+
+// mask: nonzero = skip this right-hand side (same convention as the operator kernels)
+__device__ __forceinline__ bool skip_rhs(const GArgs& a, int rhs) { return a.mask && a.mask[rhs]; }
+
+// h[i] = <V_i, w>, i in [chunk*GCH, min(nv, chunk*GCH+GCH))
+__global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
+  const int rhs = blockIdx.y, chunk = blockIdx.z;
+  if (skip_rhs(a, rhs)) return;
+  const int i0 = chunk * GCH;
+  const int nq = min(GCH, a.nv - i0);
+  if (nq <= 0) return;
+  Acc2 acc[2 * GCH];
+#pragma unroll
+  for (int q = 0; q < 2 * GCH; ++q) acc[q] = {0.f, 0.f};
+  const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
+  const float4* w4 = reinterpret_cast<const float4*>(a.w);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    const float4 wv = w4[off2 + i];
+    const cf w0 = make_float2(wv.x, wv.y), w1 = make_float2(wv.z, wv.w);
+#pragma unroll
+    for (int q = 0; q < GCH; ++q) {
+      if (q < nq) {
+        const float4 vv = reinterpret_cast<const float4*>(a.V + (i0 + q) * a.vs)[off2 + i];
+        acc_cdot(acc[2 * q], acc[2 * q + 1], make_float2(vv.x, vv.y), w0);
+        acc_cdot(acc[2 * q], acc[2 * q + 1], make_float2(vv.z, vv.w), w1);
+      }
+    }
+  }
+  double val[2 * GCH];
+#pragma unroll
+  for (int q = 0; q < 2 * GCH; ++q) val[q] = (double)acc[q].s + (double)acc[q].c;
+  double tot[2 * GCH];
+  double* pbase = a.partials + ((long)rhs * gridDim.z + chunk) * gridDim.x * (2 * GCH);
+  if (!reduce_group<2 * GCH, 2 * GCH>(val, pbase, a.counters + rhs * gridDim.z + chunk, tot)) return;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nq; ++q) a.hout[rhs * GMAX + i0 + q] = make_double2(tot[2 * q], tot[2 * q + 1]);
+}
+
+// w -= sum_i h[i] V_i  (h from hout)   or   y += sum_i z[i] V_i (ADD, count jd per rhs)
+template <bool ADD>
+__global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
+  const int rhs = blockIdx.y;
+  if (skip_rhs(a, rhs)) return;
+  const int nv = ADD ? a.gs[rhs].jd : a.nv;
+  if (nv <= 0) return;
+  __shared__ cf coef[GMAX];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double2 c = ADD ? a.gs[rhs].z[i] : a.hout[rhs * GMAX + i];
+    coef[i] = ADD ? make_float2((float)c.x, (float)c.y) : make_float2((float)-c.x, (float)-c.y);
+  }
+  __syncthreads();
+  const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
+  float4* t4 = reinterpret_cast<float4*>(ADD ? a.y : a.w);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 acc = t4[off2 + i];
+    cf a0 = make_float2(acc.x, acc.y), a1 = make_float2(acc.z, acc.w);
+    for (int q = 0; q < nv; ++q) {
+      const float4 vv = reinterpret_cast<const float4*>(a.V + q * a.vs)[off2 + i];
+      a0 = cfma(coef[q], make_float2(vv.x, vv.y), a0);
+      a1 = cfma(coef[q], make_float2(vv.z, vv.w), a1);
+    }
+    t4[off2 + i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+}
+
+// V_0 = r / beta, or V_{j+1} = w / H[j+1][j]
+__global__ void k_gscale(GArgs a, bool first) {
+  const int rhs = blockIdx.y;
+  if (skip_rhs(a, rhs)) return;
+  const GState& G = a.gs[rhs];
+  const double b = first ? G.beta : G.H[(a.j + 1) + a.j * (G.m + 1)].x;
+  const float inv = b > 0 ? (float)(1.0 / b) : 0.f;
+  const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
+  float4* t4 = reinterpret_cast<float4*>(a.w);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 v = t4[off2 + i];
+    t4[off2 + i] = make_float4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+  }
+}
+
+__global__ void k_ginit(GState* gs, const KScal* sc, int nrhs, int m, double tol2, int maxit) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  GState& G = gs[r];
+  G.m = m; G.tol2 = tol2; G.maxit = maxit; G.iters = 0; G.status = PSFD_NOT_CONVERGED;
+  G.bnorm2 = sc[r].bnorm2; G.jd = 0; G.active = 0;
+}
+
+// start of a cycle: beta = ||r|| (from res1 of the scalar block); skip[r] = 1 for
+// right-hand sides that are finished
+__global__ void k_gstart(GState* gs, KScal* sc, int* skip, int* done, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  GState& G = gs[r];
+  G.jd = 0;
+  if (done[r]) { skip[r] = 1; G.active = 0; return; }
+  const double rr = sc[r].res1;
+  G.beta = sqrt(rr);
+  sc[r].rr = rr;
+  if (G.iters == 0) sc[r].rr0 = rr;
+  for (int i = 0; i <= G.m; ++i) G.g[i] = make_double2(0.0, 0.0);
+  G.g[0] = make_double2(G.beta, 0.0);
+  int act = 1;
+  if (rr <= G.tol2 * G.bnorm2 || G.bnorm2 == 0.0) { G.status = PSFD_OK; act = 0; done[r] = 1; }
+  else if (G.iters >= G.maxit) { G.status = PSFD_NOT_CONVERGED; act = 0; done[r] = 1; }
+  else if (!isfinite(rr)) { G.status = PSFD_ERR_BREAKDOWN; act = 0; done[r] = 1; }
+  skip[r] = !act;
+  G.active = act;
+}
+
+// Hessenberg column j: h = h1 + h2 (two CGS passes), H[j+1][j] = ||w||, Givens update
+__global__ void k_givens(GState* gs, const double2* h1, const double2* h2, const KScal* sc, int* skip,
+                         double* hist, int hist_cap, int nrhs, int j) {
+  const int r = threadIdx.x;
+  if (r >= nrhs || skip[r]) return;
+  GState& G = gs[r];
+  const int ld = G.m + 1;
+  double2* Hc = G.H + j * ld;
+  for (int i = 0; i <= j; ++i) {
+    const double2 a = h1[r * GMAX + i], b = h2[r * GMAX + i];
+    Hc[i] = make_double2(a.x + b.x, a.y + b.y);
+  }
+  const double beta = sqrt(sc[r].res0);
+  Hc[j + 1] = make_double2(beta, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = Hc[i], b = Hc[i + 1];
+    const double2 c = G.cs[i], s = G.sn[i];
+    // [conj(c) conj(s); -s c] [a; b]
+    Hc[i] = make_double2(c.x * a.x + c.y * a.y + s.x * b.x + s.y * b.y, c.x * a.y - c.y * a.x + s.x * b.y - s.y * b.x);
+    Hc[i + 1] = make_double2(-(s.x * a.x - s.y * a.y) + (c.x * b.x - c.y * b.y),
+                             -(s.x * a.y + s.y * a.x) + (c.x * b.y + c.y * b.x));
+  }
+  const double2 a = Hc[j];
+  const double den = sqrt(a.x * a.x + a.y * a.y + beta * beta);
+  double2 c = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
+  if (den > 0) { c = make_double2(a.x / den, a.y / den); s = make_double2(beta / den, 0.0); }
+  G.cs[j] = c; G.sn[j] = s;
+  Hc[j] = make_double2(den, 0.0);
+  const double2 gj = G.g[j];
+  G.g[j + 1] = make_double2(-(s.x * gj.x - s.y * gj.y), -(s.x * gj.y + s.y * gj.x));
+  G.g[j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
+  G.iters += 1;
+  G.jd = j + 1;
+  const double res2 = G.g[j + 1].x * G.g[j + 1].x + G.g[j + 1].y * G.g[j + 1].y;
+  if (hist && G.iters - 1 < hist_cap) hist[(long)r * hist_cap + G.iters - 1] = sqrt(res2 / G.bnorm2);
+  if (res2 <= G.tol2 * G.bnorm2 || beta == 0.0 || G.iters >= G.maxit || !isfinite(res2) || j + 1 == G.m) {
+    skip[r] = 1;
+    G.active = 0;
+  }
+}
+
+// z = H^-1 g on the leading jd x jd triangle (FP64 back substitution)
+__global__ void k_gtri(GState* gs, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  GState& G = gs[r];
+  const int ld = G.m + 1, n = G.jd;
+  for (int i = n - 1; i >= 0; --i) {
+    double2 acc = G.g[i];
+    for (int k = i + 1; k < n; ++k) {
+      const double2 h = G.H[i + k * ld], zk = G.z[k];
+      acc.x -= h.x * zk.x - h.y * zk.y;
+      acc.y -= h.x * zk.y + h.y * zk.x;
+    }
+    const double2 d = G.H[i + i * ld];
+    const double dd = d.x * d.x + d.y * d.y;
+    G.z[i] = dd > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                    : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void k_gfinish(GState* gs, KScal* sc, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  sc[r].iters = gs[r].iters;
+  sc[r].status = gs[r].status;
+}
+
+}  // namespace
+
+struct SolveWs {
+  cf *bH, *r, *rhat, *p, *v, *s, *t, *y, *Eb;
+  cf* V;            // GMRES basis (m + 1 vectors)
+  KScal* sc;
+  int* done;
+  int* active;
+  double* partials;
+  unsigned* counters;
+  GState* gs;
+  double2* h1;
+  double2* h2;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -343,25 +577,158 @@ static int nblocks_for(long n) {
   return (int)(nb < 1 ? 1 : nb);
 }
 
-static size_t ws_layout(psfd_plan_s* P, SolveWs* w, char* base) {
+static size_t ws_layout(psfd_plan_s* P, int method, int restart, SolveWs* w, char* base) {
   const size_t vb = align256((size_t)P->nrhs * P->nvec * sizeof(cf));
   const int nb = nblocks_for(P->nvec);
+  const int nr = P->nrhs;
+  const int nch = (GMAX + GCH - 1) / GCH;
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* { char* q = base ? base + off : nullptr; off += align256(bytes); return q; };
-  cf** vecs[] = {&w->bH, &w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->y, &w->Eb};
-  for (cf** q : vecs) *q = (cf*)take(vb);
-  w->sc = (KScal*)take(sizeof(KScal) * P->nrhs);
-  w->done = (int*)take(sizeof(int) * P->nrhs);
-  w->partials = (double*)take(sizeof(double) * kMaxQ * nb * P->nrhs);
-  w->counters = (unsigned*)take(sizeof(unsigned) * P->nrhs);
+  const bool gm = method == PSFD_GMRES;
+  cf** common[] = {&w->bH, &w->r, &w->v, &w->t, &w->y, &w->Eb};
+  for (cf** q : common) *q = (cf*)take(vb);
+  if (gm) {
+    w->rhat = w->p = w->s = nullptr;
+    w->V = (cf*)take(vb * (size_t)(restart + 1));
+  } else {
+    cf** bic[] = {&w->rhat, &w->p, &w->s};
+    for (cf** q : bic) *q = (cf*)take(vb);
+    w->V = nullptr;
+  }
+  w->sc = (KScal*)take(sizeof(KScal) * nr);
+  w->done = (int*)take(sizeof(int) * nr);
+  w->active = (int*)take(sizeof(int) * nr);
+  w->partials = (double*)take(sizeof(double) * (size_t)nr * nb * (gm ? nch * 2 * GCH : kMaxQ));
+  w->counters = (unsigned*)take(sizeof(unsigned) * nr * (gm ? nch : 1));
+  w->gs = gm ? (GState*)take(sizeof(GState) * nr) : nullptr;
+  w->h1 = gm ? (double2*)take(sizeof(double2) * nr * GMAX) : nullptr;
+  w->h2 = gm ? (double2*)take(sizeof(double2) * nr * GMAX) : nullptr;
   return off;
 }
 
 extern "C" size_t psfd_solve_workspace_size(psfd_plan P, int method, int restart) {
-  (void)method; (void)restart;
   if (!P) return 0;
   SolveWs w;
-  return ws_layout(P, &w, nullptr);
+  return ws_layout(P, method, restart, &w, nullptr);
+}
+
+static int bicgstab_loop(psfd_plan_s* P, SolveWs& w, VArgs va, int maxit, int aflags, int nb) {
+  const int nr = P->nrhs;
+  cudaStream_t st = P->stream;
+  int rc;
+  va.v0 = w.r; va.v1 = w.rhat; va.v2 = w.p; va.v3 = w.v; va.v4 = w.y;
+  if ((rc = launch_vec<OK_INIT>(va, nr, st, nb))) return rc;
+  va.use_done = true;
+  std::vector<int> hdone(nr);
+  const int check_every = 8;
+  for (int it = 0; it < maxit; it += check_every) {
+    for (int k = 0; k < check_every && it + k < maxit; ++k) {
+      va.v0 = w.p; va.v1 = w.r; va.v2 = w.v;
+      if ((rc = launch_vec<OK_P>(va, nr, st, nb))) return rc;
+      if ((rc = apply_hybrid(P, w.p, w.v, aflags, w.done))) return rc;
+      va.v0 = w.rhat; va.v1 = w.v;
+      if ((rc = launch_vec<OK_RV>(va, nr, st, nb))) return rc;
+      va.v0 = w.s; va.v1 = w.r; va.v2 = w.v;
+      if ((rc = launch_vec<OK_S>(va, nr, st, nb))) return rc;
+      if ((rc = apply_hybrid(P, w.s, w.t, aflags, w.done))) return rc;
+      va.v0 = w.t; va.v1 = w.s;
+      if ((rc = launch_vec<OK_TS>(va, nr, st, nb))) return rc;
+      va.v0 = w.y; va.v1 = w.r; va.v2 = w.p; va.v3 = w.s; va.v4 = w.t; va.v5 = w.rhat;
+      if ((rc = launch_vec<OK_XR>(va, nr, st, nb))) return rc;
+    }
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hdone.data(), w.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int r = 0; r < nr; ++r) all = all && hdone[r];
+    if (all) break;
+  }
+  return PSFD_OK;
+}
+
+static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxit, int m, int aflags, int nb) {
+  const int nr = P->nrhs;
+  cudaStream_t st = P->stream;
+  const long n = P->nvec;
+  const size_t vbytes = (size_t)nr * n * sizeof(cf);
+  const long vs = (long)(align256(vbytes) / sizeof(cf));
+  const int nch_max = (GMAX + GCH - 1) / GCH;
+  int rc;
+  const unsigned tpb = 32 * ((nr + 31) / 32);
+  PSFD_CUDA_TRY(cudaMemsetAsync(w.done, 0, sizeof(int) * nr, st));
+  PSFD_CUDA_TRY(cudaMemsetAsync(w.y, 0, vbytes, st));
+  PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr * nch_max, st));
+  k_ginit<<<1, tpb, 0, st>>>(w.gs, w.sc, nr, m, tol * tol, maxit);
+  PSFD_CHECK_LAUNCH();
+  GArgs g{};
+  g.V = w.V; g.vs = vs; g.n = n; g.gs = w.gs; g.partials = w.partials; g.counters = w.counters; g.y = w.y;
+  std::vector<int> hv(nr);
+  bool first = true;
+  for (int cycle = 0;; ++cycle) {
+    // restart residual r = c - B y (c kept in w.r), written into V_0 with ||r||^2 -> res1
+    va.use_done = false;
+    if (first) {
+      va.v0 = w.r;
+      va.v1 = w.t;  // t = 0
+      PSFD_CUDA_TRY(cudaMemsetAsync(w.t, 0, vbytes, st));
+    } else {
+      if ((rc = apply_hybrid(P, w.y, w.t, aflags, w.done))) return rc;
+      va.v0 = w.r; va.v1 = w.t;
+    }
+    va.v2 = w.V;
+    if ((rc = launch_vec<OK_SUB>(va, nr, st, nb))) return rc;
+    first = false;
+    k_gstart<<<1, tpb, 0, st>>>(w.gs, w.sc, w.active, w.done, nr);
+    PSFD_CHECK_LAUNCH();
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hv.data(), w.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int r = 0; r < nr; ++r) any = any || !hv[r];
+    if (!any) break;
+    g.mask = w.active; g.w = w.V; g.j = 0;
+    k_gscale<<<dim3(nb, nr), kThreads, 0, st>>>(g, true);
+    PSFD_CHECK_LAUNCH();
+    for (int j = 0; j < m; ++j) {
+      cf* Vj = w.V + (long)j * vs;
+      cf* Wn = w.V + (long)(j + 1) * vs;
+      if ((rc = apply_hybrid(P, Vj, Wn, aflags, w.active))) return rc;
+      g.w = Wn; g.nv = j + 1; g.j = j;
+      const int nch = (j + 1 + GCH - 1) / GCH;
+      for (int pass = 0; pass < 2; ++pass) {
+        g.hout = pass == 0 ? w.h1 : w.h2;
+        StageScope sc(st, ST_KRYLOV);
+        k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
+        PSFD_CHECK_LAUNCH();
+        k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+        PSFD_CHECK_LAUNCH();
+      }
+      va.v0 = Wn;
+      va.done = w.active;  // w.active holds the skip flags here
+      va.use_done = true;
+      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;
+      va.done = w.done;
+      va.use_done = false;
+      k_givens<<<1, tpb, 0, st>>>(w.gs, w.h1, w.h2, w.sc, w.active, va.hist, va.hist_cap, nr, j);
+      PSFD_CHECK_LAUNCH();
+      k_gscale<<<dim3(nb, nr), kThreads, 0, st>>>(g, false);
+      PSFD_CHECK_LAUNCH();
+      if ((j & 3) == 3 || j == m - 1) {
+        PSFD_CUDA_TRY(cudaMemcpyAsync(hv.data(), w.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+        PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+        bool a = false;
+        for (int r = 0; r < nr; ++r) a = a || !hv[r];
+        if (!a) break;
+      }
+    }
+    // y += V z for every rhs that ran this cycle
+    k_gtri<<<1, tpb, 0, st>>>(w.gs, nr);
+    PSFD_CHECK_LAUNCH();
+    g.mask = nullptr;  // every rhs with jd > 0 updates y
+    k_gupd<true><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+    PSFD_CHECK_LAUNCH();
+  }
+  k_gfinish<<<1, tpb, 0, st>>>(w.gs, w.sc, nr);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
 }
 
 extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E, double tol, int maxit,
@@ -370,11 +737,14 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
   if (!P || !b || !E || !info) { psfd_set_error("psfd_solve: null argument"); return PSFD_ERR_ARG; }
   if (!P->have_background) { psfd_set_error("psfd_solve: call psfd_background first"); return PSFD_ERR_STATE; }
   if (!(tol > 0) || maxit < 0) { psfd_set_error("psfd_solve: bad tol / maxit"); return PSFD_ERR_ARG; }
-  if (method != PSFD_BICGSTAB) { psfd_set_error("psfd_solve: only BiCGSTAB in this build"); return PSFD_ERR_ARG; }
-  (void)restart;
+  if (method != PSFD_BICGSTAB && method != PSFD_GMRES) { psfd_set_error("psfd_solve: unknown method"); return PSFD_ERR_ARG; }
+  if (method == PSFD_GMRES && (restart < 1 || restart > GMAX)) {
+    psfd_set_error("psfd_solve: GMRES restart must be in [1, %d]", GMAX);
+    return PSFD_ERR_ARG;
+  }
   cudaStream_t st = P->stream;
   SolveWs w;
-  const size_t need = ws_layout(P, &w, nullptr);
+  const size_t need = ws_layout(P, method, restart, &w, nullptr);
   char* base = (char*)workspace;
   bool own = false;
   if (!base) {
@@ -384,29 +754,41 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
     psfd_set_error("psfd_solve: workspace too small (%zu < %zu)", workspace_bytes, need);
     return PSFD_ERR_ARG;
   }
-  ws_layout(P, &w, base);
+  ws_layout(P, method, restart, &w, base);
   const int nr = P->nrhs;
   const long n = P->nvec;
   const size_t vbytes = (size_t)nr * n * sizeof(cf);
   const int nb = nblocks_for(n);
   const float us = 1.0f / sqrtf((float)P->ncols);
   const long nplanes = (long)nr * 3 * P->nz;
+  const unsigned tpb = 32 * ((nr + 31) / 32);
   int rc = PSFD_OK;
-  auto fail = [&](int code) { if (own) cudaFreeAsync(base, st); return code; };
+  double* dhist = nullptr;
+  auto fail = [&](int code) {
+    if (own) cudaFreeAsync(base, st);
+    if (dhist) cudaFreeAsync(dhist, st);
+    return code;
+  };
 
   PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr, st));
-  k_set_scalars<<<1, 32 * ((nr + 31) / 32), 0, st>>>(w.sc, nr, tol * tol, maxit);
+  k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, tol * tol, maxit);
   PSFD_CHECK_LAUNCH();
   VArgs va{};
   va.n = n; va.sc = w.sc; va.done = w.done; va.partials = w.partials; va.counters = w.counters;
   va.hist = nullptr; va.hist_cap = 0; va.use_done = false;
+  if (P->hist && P->hist_cap > 0) {
+    PSFD_CUDA_TRY(cudaMallocAsync((void**)&dhist, sizeof(double) * nr * P->hist_cap, st));
+    PSFD_CUDA_TRY(cudaMemsetAsync(dhist, 0, sizeof(double) * nr * P->hist_cap, st));
+    va.hist = dhist; va.hist_cap = P->hist_cap;
+  }
   // b -> HYBRID, ||b||^2
   PSFD_CUDA_TRY(cudaMemcpyAsync(w.bH, b, vbytes, cudaMemcpyDeviceToDevice, st));
   if ((rc = launch_lateral_transform(P, w.bH, nplanes, true, us))) return fail(rc);
   va.v0 = w.bH;
   if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return fail(rc);
-  k_copy_bnorm<<<1, 32 * ((nr + 31) / 32), 0, st>>>(w.sc, nr);
-  // r0 = b - A E_base
+  k_copy_bnorm<<<1, tpb, 0, st>>>(w.sc, nr);
+  PSFD_CHECK_LAUNCH();
+  // c = b - A E_base (the right-hand side of A M y = c)
   if (x0) {
     PSFD_CUDA_TRY(cudaMemcpyAsync(w.Eb, x0, vbytes, cudaMemcpyDeviceToDevice, st));
     if ((rc = launch_lateral_transform(P, w.Eb, nplanes, true, us))) return fail(rc);
@@ -416,51 +798,19 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
   } else {
     PSFD_CUDA_TRY(cudaMemcpyAsync(w.r, w.bH, vbytes, cudaMemcpyDeviceToDevice, st));
   }
-  va.v0 = w.r; va.v1 = w.rhat; va.v2 = w.p; va.v3 = w.v; va.v4 = w.y;
-  if ((rc = launch_vec<OK_INIT>(va, nr, st, nb))) return fail(rc);
-
-  // ---- BiCGSTAB iterations (van der Vorst), on B = A M
   const int aflags = use_precond ? PSFD_PRECOND : 0;
-  va.use_done = true;
-  va.hist = nullptr;
-  double* dhist = nullptr;
-  if (P->hist && P->hist_cap > 0) {
-    PSFD_CUDA_TRY(cudaMallocAsync((void**)&dhist, sizeof(double) * nr * P->hist_cap, st));
-    PSFD_CUDA_TRY(cudaMemsetAsync(dhist, 0, sizeof(double) * nr * P->hist_cap, st));
-    va.hist = dhist; va.hist_cap = P->hist_cap;
-  }
-  std::vector<int> hdone(nr);
-  const int check_every = 8;
-  for (int it = 0; it < maxit; it += check_every) {
-    for (int k = 0; k < check_every && it + k < maxit; ++k) {
-      va.v0 = w.p; va.v1 = w.r; va.v2 = w.v;
-      if ((rc = launch_vec<OK_P>(va, nr, st, nb))) return fail(rc);
-      if ((rc = apply_hybrid(P, w.p, w.v, aflags, w.done))) return fail(rc);
-      va.v0 = w.rhat; va.v1 = w.v;
-      if ((rc = launch_vec<OK_RV>(va, nr, st, nb))) return fail(rc);
-      va.v0 = w.s; va.v1 = w.r; va.v2 = w.v;
-      if ((rc = launch_vec<OK_S>(va, nr, st, nb))) return fail(rc);
-      if ((rc = apply_hybrid(P, w.s, w.t, aflags, w.done))) return fail(rc);
-      va.v0 = w.t; va.v1 = w.s;
-      if ((rc = launch_vec<OK_TS>(va, nr, st, nb))) return fail(rc);
-      va.v0 = w.y; va.v1 = w.r; va.v2 = w.p; va.v3 = w.s; va.v4 = w.t; va.v5 = w.rhat;
-      if ((rc = launch_vec<OK_XR>(va, nr, st, nb))) return fail(rc);
-    }
-    PSFD_CUDA_TRY(cudaMemcpyAsync(hdone.data(), w.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
-    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
-    bool all = true;
-    for (int r = 0; r < nr; ++r) all = all && hdone[r];
-    if (all) break;
-  }
-  // ---- E = E_base + M y ; true residual
-  cf* My = w.s;
+  if (method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, maxit, aflags, nb);
+  else rc = gmres_loop(P, w, va, tol, maxit, restart, aflags, nb);
+  if (rc) return fail(rc);
+  // ---- E = E_base + M y ; true residual (FP64 norm)
+  va.use_done = false;
+  cf* My = w.t;
   if (use_precond) {
     if ((rc = launch_axial(P, w.y, My, 2, nullptr, nr))) return fail(rc);
   } else {
     PSFD_CUDA_TRY(cudaMemcpyAsync(My, w.y, vbytes, cudaMemcpyDeviceToDevice, st));
   }
-  cf* EH = w.p;
-  va.use_done = false;
+  cf* EH = w.r;
   if (x0) {
     va.v0 = w.Eb; va.v1 = My; va.v2 = EH;
     if ((rc = launch_vec<OK_AXPY>(va, nr, st, nb))) return fail(rc);
@@ -478,7 +828,7 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
     PSFD_CUDA_TRY(cudaMemcpyAsync(P->hist, dhist, sizeof(double) * nr * P->hist_cap, cudaMemcpyDeviceToHost, st));
   }
   PSFD_CUDA_TRY(cudaStreamSynchronize(st));
-  if (dhist) cudaFree(dhist);
+  if (dhist) { cudaFree(dhist); dhist = nullptr; }
   int worst = PSFD_OK;
   for (int r = 0; r < nr; ++r) {
     const double bn = hs[r].bnorm2;

@@ -3,13 +3,93 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fft.cuh"
 #include "internal.h"
 
 static thread_local char g_err[1024] = "";
+static std::atomic<long long> g_launches{0};
+
+void psfd_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" long long psfd_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- stage timing
+namespace {
+struct StageRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<StageRec> g_open[ST_N];   // begun, not yet ended (stack per stage)
+std::vector<StageRec> g_done;
+std::vector<cudaEvent_t> g_pool;
+double g_ms[ST_N];
+long long g_calls[ST_N];
+
+cudaEvent_t ev_get() {
+  if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+void harvest(bool wait) {
+  std::vector<StageRec> keep;
+  for (auto& r : g_done) {
+    if (wait) cudaEventSynchronize(r.b);
+    if (cudaEventQuery(r.b) == cudaSuccess) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      g_ms[r.stage] += ms;
+      g_calls[r.stage] += 1;
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    } else {
+      keep.push_back(r);
+    }
+  }
+  g_done.swap(keep);
+}
+}  // namespace
+
+void stage_mark(cudaStream_t s, int stage, bool begin) {
+  if (!g_timing) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (begin) {
+    StageRec r{stage, ev_get(), nullptr};
+    cudaEventRecord(r.a, s);
+    g_open[stage].push_back(r);
+  } else if (!g_open[stage].empty()) {
+    StageRec r = g_open[stage].back();
+    g_open[stage].pop_back();
+    r.b = ev_get();
+    cudaEventRecord(r.b, s);
+    g_done.push_back(r);
+    if (g_done.size() > 4096) harvest(true);
+  }
+}
+
+extern "C" int psfd_timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  harvest(true);
+  for (int i = 0; i < ST_N; ++i) { g_ms[i] = 0; g_calls[i] = 0; g_open[i].clear(); }
+  g_timing = on != 0;
+  return PSFD_OK;
+}
+
+extern "C" int psfd_timing_read(double* ms, long long* calls, int nstages) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  harvest(true);
+  for (int i = 0; i < nstages && i < ST_N; ++i) {
+    if (ms) ms[i] = g_ms[i];
+    if (calls) calls[i] = g_calls[i];
+  }
+  return PSFD_OK;
+}
 
 void psfd_set_error(const char* fmt, ...) {
   va_list ap;

@@ -83,6 +83,9 @@ def lib() -> C.CDLL:
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
         "fno_forward": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, vp]),
         "psfd_spectral_upsample": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
+        "psfd_launch_count": (C.c_longlong, []),
+        "psfd_timing_enable": (i, [i]),
+        "psfd_timing_read": (i, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]),
         "psfd_last_error": (C.c_char_p, []),
         "psfd_version": (C.c_char_p, []),
     }
@@ -99,7 +102,7 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
-            "psfd_last_error", "psfd_version"]
+            "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_last_error", "psfd_version"]
 
 
 def _check(code: int, what: str, allow=()):
@@ -262,3 +265,21 @@ def spectral_upsample(src: torch.Tensor, nz: int, ny: int, nx: int,
     _check(lib().psfd_spectral_upsample(_ptr(src.contiguous()), nb, nx0, ny0, nz0, _ptr(dst), nx, ny, nz,
                                         _stream_handle(stream)), "psfd_spectral_upsample")
     return dst
+
+
+STAGES = ("axial", "contrast", "krylov", "transform", "fno")
+
+
+def launch_count() -> int:
+    return int(lib().psfd_launch_count())
+
+
+def timing_enable(on: bool = True):
+    lib().psfd_timing_enable(1 if on else 0)
+
+
+def timing_read() -> Dict[str, Dict[str, float]]:
+    ms = (C.c_double * len(STAGES))()
+    calls = (C.c_longlong * len(STAGES))()
+    lib().psfd_timing_read(ms, calls, len(STAGES))
+    return {s: {"ms": ms[i], "calls": int(calls[i])} for i, s in enumerate(STAGES)}

@@ -165,3 +165,36 @@ def test_manhattan_128x128x64_full_size_apply_and_solve():
         assert res["info"][r]["status"] == 0
         bo = O.source_b(g, fill_o, pol)
         assert O.rel_residual(g, res["E"][r].cpu().to(torch.complex128), fill_o, bo) < 3e-6
+
+
+def test_gmres_solve_matches_oracle():
+    """GMRES(30) with CGS2 (the fine-discretisation solver) reaches the same field."""
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    g, fill_o = oracle_setup(prob, a)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    bo = O.source_b(g, fill_o, 0)
+    ref = K.solve(lambda E: O.apply_A(g, E, fill_o), lambda x: O.apply_M(g, x), bo, tol=1e-12, maxit=5000)
+    for restart in (30, 7):
+        res = plan.solve(b, tol=1e-6, maxit=4000, method=psfd.PSFD_GMRES, restart=restart)
+        info = res["info"][0]
+        assert info["status"] == 0, info
+        assert info["r_rel"] < 3e-6
+        assert rel_l2(res["E"][0].cpu(), ref["E"]) < 1e-4
+
+
+def test_solver_history_and_initial_residual():
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    res = plan.solve(b, tol=1e-6, maxit=2000, history=2000)
+    it = res["info"][0]["iters"]
+    h = res["history"][0]
+    assert abs(res["info"][0]["r_rel_initial"] - 1.0) < 1e-6      # null initialisation: r0 = b
+    assert h[it - 1] <= 1e-6 and np.all(h[:it] > 0)
