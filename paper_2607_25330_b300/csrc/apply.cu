@@ -39,6 +39,20 @@ struct AxialArgs {
 
 enum { AX_AM = 0, AX_A = 1, AX_M = 2 };
 
+// The column work is a loop over "jobs"; each job is
+//   source (time layout) -> FFT_z -> one spectral factor -> IFFT_z -> post-op
+// so that each transform direction is instantiated once (the fully inlined
+// 12-transform body overflowed the instruction cache).  Jobs (q = M x):
+//   0: x_z -> m/N          -> q_z                     -> slot 0
+//   1: x_y -> m/N          -> q_y                     -> slot 1
+//   2: x_y -> m i kz / N   -> D q_y  -> c_x = i ky q_z - D q_y       -> slot 2
+//   3: x_x -> m/N          -> q_x                     -> slot 3
+//   4: x_x -> m i kz / N   -> D q_x  -> c_y = D q_x - i kx q_z; emit W_z, G; c_y -> slot 0
+//   5: c_x -> i kz / N     -> D c_x  -> W_y = D c_x - i kx c_z - k0^2 q_y
+//   6: c_y -> i kz / N     -> D c_y  -> W_x = i ky c_z - D c_y - k0^2 q_x
+// with D = s^-1 (.) applied after the inverse transform, c_z = i kx q_y - i ky q_x.
+// Without M (mode A) jobs 0, 1, 3 copy the input.  Mode M runs jobs 0, 1, 3 only
+// and writes q to y.
 template <int NZ, int T, int MODE>
 __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
   constexpr int P = 32 / T;
@@ -57,126 +71,74 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
   cf* __restrict__ y = a.y + rhs * a.vstride;
   const float kx = __ldg(a.kx + cc % a.nx), ky = __ldg(a.ky + cc / a.nx);
   const float inv_n = 1.0f / (float)NZ;
+  const cf ikx = make_float2(0.f, kx), iky = make_float2(0.f, ky);
+  cf* st = smem + (size_t)warp * 4 * R * 32;
+  auto unst = [&](int sl, int m) -> cf { return st[(sl * R + m) * 32 + lane]; };
+  auto stash = [&](int sl, int m, cf v) { st[(sl * R + m) * 32 + lane] = v; };
 
-  auto load = [&](int c, cf* v) {
-#pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = act ? __ldg(x + (long)(c * NZ + t + T * m) * nc + col) : czero();
-  };
-  auto store = [&](int c, int m, cf v) {
-    if (act) y[(long)(c * NZ + t + T * m) * nc + col] = v;
-  };
-
-  float mv[R];
-  if constexpr (MODE != AX_A) {
-#pragma unroll
-    for (int s = 0; s < R; ++s) {
-      const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
-      const float k2 = fmaf(kx, kx, fmaf(ky, ky, kzv * kzv));
-      float d = 1.0f;
-      if (k2 > a.kref2) {
-        const float ratio = a.kref2 / (k2 + a.damp_eps);
-        d = (a.gamma == 1.0f) ? ratio : powf(ratio, a.gamma);
-      }
-      mv[s] = (a.m_min + (1.0f - a.m_min) * d) * inv_n;
-    }
-  }
-
-  if constexpr (MODE == AX_M) {
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      cf v[R];
-      load(c, v);
-      PZ::template to_freq<false>(v, t, a.tw);
+  for (int job = 0; job < 7; ++job) {
+    if (MODE == AX_M && (job == 2 || job >= 4)) continue;
+    const bool copy_only = (MODE == AX_A) && (job == 0 || job == 1 || job == 3);
+    cf v[R];
+    // ---- source
+    if (job < 5) {
+      const int c = (job == 0) ? 2 : (job <= 2 ? 1 : 0);
+      const cf* src = x + (long)(c * NZ + t) * nc + col;
 #pragma unroll
-      for (int s = 0; s < R; ++s) v[s] = cscale(v[s], mv[s]);
+      for (int m = 0; m < R; ++m) v[m] = act ? __ldg(src + (long)(T * m) * nc) : czero();
+    } else {
+      const int sl = (job == 5) ? 2 : 0;
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = unst(sl, m);
+    }
+    // ---- spectral filter along z
+    if (!copy_only) {
+      PZ::template to_freq<false>(v, t, a.tw);
+      const bool with_m = (MODE != AX_A) && job < 5;
+      const bool with_d = (job == 2 || job >= 4);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
+        float f = inv_n;
+        if (with_m) {
+          const float k2 = fmaf(kx, kx, fmaf(ky, ky, kzv * kzv));
+          float d = 1.0f;
+          if (k2 > a.kref2) {
+            const float ratio = a.kref2 / (k2 + a.damp_eps);
+            d = (a.gamma == 1.0f) ? ratio : powf(ratio, a.gamma);
+          }
+          f *= a.m_min + (1.0f - a.m_min) * d;
+        }
+        cf w = cscale(v[s], f);
+        v[s] = with_d ? make_float2(-kzv * w.y, kzv * w.x) : w;
+      }
       PZ::template to_time<true>(v, t, a.tw);
-#pragma unroll
-      for (int m = 0; m < R; ++m) store(c, m, v[m]);
     }
-    return;
-  } else {
-    cf* st = smem + (size_t)warp * 4 * R * 32;
-    auto stash = [&](int s, const cf* v) {
+    // ---- post-op (time layout, z = t + T m)
+    if (MODE == AX_M) {
+      const int c = (job == 0) ? 2 : (job == 1 ? 1 : 0);
 #pragma unroll
-      for (int m = 0; m < R; ++m) st[(s * R + m) * 32 + lane] = v[m];
-    };
-    auto unst = [&](int s, int m) -> cf { return st[(s * R + m) * 32 + lane]; };
-    const cf ikx = make_float2(0.f, kx), iky = make_float2(0.f, ky);
-
-    // ---- q_z -> slot 0
-    {
-      cf v[R];
-      load(2, v);
-      if constexpr (MODE == AX_AM) {
-        PZ::template to_freq<false>(v, t, a.tw);
-#pragma unroll
-        for (int s = 0; s < R; ++s) v[s] = cscale(v[s], mv[s]);
-        PZ::template to_time<true>(v, t, a.tw);
-      }
-      stash(0, v);
+      for (int m = 0; m < R; ++m)
+        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = v[m];
+      continue;
     }
-    // ---- q_y -> slot 1, c_x = i ky q_z - D_z q_y -> slot 2
-    {
-      cf v[R], w[R];
-      load(1, v);
-      cf q[R];
-      if constexpr (MODE == AX_A) {
+    if (job == 0 || job == 1 || job == 3) {
+      const int sl = (job == 0) ? 0 : (job == 1 ? 1 : 3);
 #pragma unroll
-        for (int m = 0; m < R; ++m) q[m] = v[m];
-      }
-      PZ::template to_freq<false>(v, t, a.tw);
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
-        if constexpr (MODE == AX_AM) v[s] = cscale(v[s], mv[s]);
-        else v[s] = cscale(v[s], inv_n);
-        w[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
-      }
-      if constexpr (MODE == AX_AM) {
-        PZ::template to_time<true>(v, t, a.tw);
-#pragma unroll
-        for (int m = 0; m < R; ++m) q[m] = v[m];
-      }
-      PZ::template to_time<true>(w, t, a.tw);
+      for (int m = 0; m < R; ++m) stash(sl, m, v[m]);
+    } else if (job == 2) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const int z = t + T * m;
-        const cf dq = cmul(w[m], __ldg(a.sinv + z));
-        w[m] = csub(cmul(iky, unst(0, m)), dq);
+        const cf dq = cmul(v[m], __ldg(a.sinv + t + T * m));
+        stash(2, m, csub(cmul(iky, unst(0, m)), dq));
       }
-      stash(1, q);
-      stash(2, w);
-    }
-    // ---- q_x -> slot 3, c_y = D_z q_x - i kx q_z (registers), emit W_z and G
-    {
-      cf v[R], w[R];
-      load(0, v);
-      cf q[R];
-      if constexpr (MODE == AX_A) {
-#pragma unroll
-        for (int m = 0; m < R; ++m) q[m] = v[m];
-      }
-      PZ::template to_freq<false>(v, t, a.tw);
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const float kzv = __ldg(a.kz + PZ::freq_index(t, s));
-        if constexpr (MODE == AX_AM) v[s] = cscale(v[s], mv[s]);
-        else v[s] = cscale(v[s], inv_n);
-        w[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
-      }
-      if constexpr (MODE == AX_AM) {
-        PZ::template to_time<true>(v, t, a.tw);
-#pragma unroll
-        for (int m = 0; m < R; ++m) q[m] = v[m];
-      }
-      PZ::template to_time<true>(w, t, a.tw);
+    } else if (job == 4) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const int z = t + T * m;
-        const cf dq = cmul(w[m], __ldg(a.sinv + z));
-        w[m] = csub(dq, cmul(ikx, unst(0, m)));
+        const cf dq = cmul(v[m], __ldg(a.sinv + t + T * m));
+        v[m] = csub(dq, cmul(ikx, unst(0, m)));   // c_y
       }
-      stash(3, q);
       __syncwarp();
       // reflected vector of this column from the tangential q at z_ml (Sec. 2.2, R_ml)
       const int tml = a.z_ml % T, mml = a.z_ml / T;
@@ -202,9 +164,9 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int z = t + T * m;
-        const cf qz = unst(0, m), cx = unst(2, m), cy = w[m];
+        const cf qz = unst(0, m), cx = unst(2, m), cy = v[m];
         const cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
-        store(2, m, Wz);
+        if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
         if (z >= a.za0 && z < a.za1 && act) {
           cf prof = czero();
           if (z >= a.z_ml) {
@@ -215,53 +177,23 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
             prof = make_float2(mag * cs, mag * sn);
           }
           const long o = (long)(z - a.za0) * nc + col;
-          G[o] = cfma(r0, prof, q[m]);
+          G[o] = cfma(r0, prof, unst(3, m));
           G[(long)nab * nc + o] = cfma(r1, prof, unst(1, m));
           G[2L * nab * nc + o] = cfma(r2, prof, qz);
         }
       }
-      stash(0, w);  // c_y replaces q_z (lane-private entries)
-    }
-    // ---- W_y = D_z c_x - i kx c_z - k0^2 q_y
-    {
-      cf v[R];
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = unst(2, m);
-      PZ::template to_freq<false>(v, t, a.tw);
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const float kzv = __ldg(a.kz + PZ::freq_index(t, s)) * inv_n;
-        v[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
-      }
-      PZ::template to_time<true>(v, t, a.tw);
+      for (int m = 0; m < R; ++m) stash(0, m, v[m]);   // c_y replaces q_z (lane-private entries)
+    } else {
+      const int c = (job == 5) ? 1 : 0;
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const int z = t + T * m;
-        const cf dcx = cmul(v[m], __ldg(a.sinv + z));
+        const cf d = cmul(v[m], __ldg(a.sinv + t + T * m));
         const cf qx = unst(3, m), qy = unst(1, m);
         const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        store(1, m, csub(csub(dcx, cmul(ikx, cz)), cscale(qy, a.k02)));
-      }
-    }
-    // ---- W_x = i ky c_z - D_z c_y - k0^2 q_x
-    {
-      cf v[R];
-#pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = unst(0, m);
-      PZ::template to_freq<false>(v, t, a.tw);
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const float kzv = __ldg(a.kz + PZ::freq_index(t, s)) * inv_n;
-        v[s] = make_float2(-kzv * v[s].y, kzv * v[s].x);
-      }
-      PZ::template to_time<true>(v, t, a.tw);
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int z = t + T * m;
-        const cf dcy = cmul(v[m], __ldg(a.sinv + z));
-        const cf qx = unst(3, m), qy = unst(1, m);
-        const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        store(0, m, csub(csub(cmul(iky, cz), dcy), cscale(qx, a.k02)));
+        const cf W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
+                                : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
+        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = W;
       }
     }
   }
@@ -283,6 +215,7 @@ static int run_axial(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   const long cols_per_block = warps * P_;
   dim3 grid((unsigned)((P->ncols + cols_per_block - 1) / cols_per_block), (unsigned)P->nrhs);
   size_t smem = (MODE == AX_M) ? 0 : (size_t)warps * 4 * R * 32 * sizeof(cf);
+  static_assert(R > 0, "");
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_axial<NZ, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
