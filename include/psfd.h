@@ -202,6 +202,23 @@ PSFD_API int fno_forward(const fno_weights_t* w, const float* a, int B, int nx, 
 PSFD_API int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,
                            psfd_c64* dst, int nx, int ny, int nz, void* stream);
 
+/* Allocation-free variant of psfd_spectral_upsample (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory inside
+ * a call, e.g. while a caching allocator holds the free memory or in loops that
+ * must not enter the driver's allocator).  Same arguments and result as
+ * psfd_spectral_upsample.  Its scratch is one fixed device array of 2^21
+ * complex64 entries (16 MiB) inside the library, held by every GPU that loads
+ * the library until the process exits: requests with
+ * nb*nx0*ny0*nz0 + nx0+ny0+nz0+nx+ny+nz > 2^21 return PSFD_ERR_ARG.  The call
+ * allocates nothing (no cudaMalloc, no host allocation); it launches kernels
+ * and issues asynchronous copies / memsets on `stream`.  All calls share the
+ * scratch, so calls that may overlap on the GPU race and must be serialised.
+ * The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture. */
+PSFD_API int psfd_spectral_upsample_static(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,
+                                           psfd_c64* dst, int nx, int ny, int nz, void* stream);
+
 /* ---------------------------------------------------------------- observability
  * psfd_launch_count: number of kernels this library has launched in the process.
  * psfd_timing_enable(1) starts per-stage timing with CUDA events recorded on each

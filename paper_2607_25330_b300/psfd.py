@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
         "fno_forward": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, vp]),
         "psfd_spectral_upsample": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
+        "psfd_spectral_upsample_static": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
         "psfd_launch_count": (C.c_longlong, []),
         "psfd_timing_enable": (i, [i]),
         "psfd_timing_read": (i, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]),
@@ -102,7 +103,7 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
-            "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_last_error", "psfd_version"]
+            "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_last_error", "psfd_version"]
 
 
 def _check(code: int, what: str, allow=()):
@@ -264,6 +265,19 @@ def spectral_upsample(src: torch.Tensor, nz: int, ny: int, nx: int,
     dst = torch.empty(src.shape[:-3] + (nz, ny, nx), dtype=torch.complex64, device="cuda")
     _check(lib().psfd_spectral_upsample(_ptr(src.contiguous()), nb, nx0, ny0, nz0, _ptr(dst), nx, ny, nz,
                                         _stream_handle(stream)), "psfd_spectral_upsample")
+    return dst
+
+
+def spectral_upsample_static(src: torch.Tensor, nz: int, ny: int, nx: int,
+                             stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Same result as spectral_upsample; the library call allocates no device memory (its scratch
+    is a fixed 16 MiB array inside the library; overlapping calls race).  The output tensor is
+    allocated here, by the caller, as for every other call."""
+    nb = int(np.prod(src.shape[:-3]))
+    nz0, ny0, nx0 = src.shape[-3:]
+    dst = torch.empty(src.shape[:-3] + (nz, ny, nx), dtype=torch.complex64, device="cuda")
+    _check(lib().psfd_spectral_upsample_static(_ptr(src.contiguous()), nb, nx0, ny0, nz0, _ptr(dst), nx, ny, nz,
+                                               _stream_handle(stream)), "psfd_spectral_upsample_static")
     return dst
 
 
