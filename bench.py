@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 
 WORKLOAD = "manhattan_128x128x64"
 TOL = 1e-6
-MAXIT = 20000
+PRACTICAL_TOL = 5e-2      # the paper's practical criterion (Sec. 3, Fig. 5a discussion)
+MAXIT = 4000
 BYTES_PER_POINT = 52.0   # algorithmic bytes of one A M apply per grid point and rhs
 
 
@@ -47,7 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "gmres"])
+    ap.add_argument("--method", default="gmres", choices=["bicgstab", "gmres"])
+    ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--maxit", type=int, default=MAXIT,
                     help="iteration cap per solve (lower it only for profiling runs)")
     ap.add_argument("--profile-apply", type=int, default=0,
@@ -133,6 +135,7 @@ def run_ours(args, rank, world):
     zprof = prob.zprofile()
     method = psfd.PSFD_GMRES if args.method == "gmres" else psfd.PSFD_BICGSTAB
     nsteps = args.warmup + args.steps
+    tol_run = TOL
     # one seeded mask per step (rank-dependent seeds: independent problems per GPU)
     masks_host = [I.mask_for(prob, 1000 * rank + s) for s in range(nsteps)]
     masks = [torch.from_numpy(m).cuda() for m in masks_host]
@@ -144,7 +147,7 @@ def run_ours(args, rank, world):
         wd = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in w.items()}
         models.append(psfd.fno_struct(wd, shape))
     plan = psfd.Plan(prob, nrhs=nrhs)
-    ws = torch.empty(plan.workspace_size(method), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(plan.workspace_size_ex(method, args.restart, True), dtype=torch.uint8, device="cuda")
     E = plan.empty()
     x0 = plan.empty()
     E_host = torch.empty(plan.shape, dtype=torch.complex64).pin_memory()
@@ -157,7 +160,8 @@ def run_ours(args, rank, world):
             a = fill.unsqueeze(0).contiguous()
             for r, m in enumerate(models):
                 psfd.fno_forward(m, a, out=x0[r:r + 1])
-        res = plan.solve(b, x0=x0 if warm else None, tol=TOL, maxit=args.maxit, method=method, out=E, workspace=ws)
+        res = plan.solve_ex(b, x0=x0 if warm else None, tol=tol_run, maxit=args.maxit, method=method,
+                            restart=args.restart, refine=True, inner_tol=1e-2, out=E, workspace=ws)
         return res
 
     # warm-up (also exercises every kernel once)
@@ -190,15 +194,21 @@ def run_ours(args, rank, world):
     ms_warm, info_warm, launches = timed(True)
     clocks = clk.stop()
     ms_cold, info_cold, _ = timed(False)
+    # the same steps to the paper's practical criterion r_rel <= 5e-2
+    tol_run = PRACTICAL_TOL
+    ms_pw, info_pw, _ = timed(True)
+    ms_pc, info_pc, _ = timed(False)
+    tol_run = TOL
 
     # end to end through the public API: host mask in, host field out, copies inside the region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    info_e2e = []
     for i in range(args.warmup, nsteps):
         dm = pinned[i].to("cuda", non_blocking=True)
-        step(i, True, mask=dm)
+        info_e2e.append(step(i, True, mask=dm)["info"])
         E_host.copy_(E, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -234,16 +244,32 @@ def run_ours(args, rank, world):
 
     npts = prob.nx * prob.ny * prob.nz * nrhs
     peak, peak_kind = measured_peaks()
-    axial_ms = stages["axial"]["ms"] / max(1, stages["axial"]["calls"])
-    # axial kernel algorithmic bytes: read x (24 B/pt), write W (24 B/pt), write G on absorber planes
-    nab_frac = float((prob.zprofile() > 0).sum()) / prob.nz
-    axial_bytes = npts * (48.0 + 24.0 * nab_frac)
     apply_bytes = npts * BYTES_PER_POINT
-    solves_per_step = nrhs
+    # roofline of each stage inside the solve step: algorithmic bytes / CUDA-event time
+    kernels = {"axial": "k_axial (fused M + stretched curl-curl + R column kernel)",
+               "contrast": "k_rows/k_cols contrast passes (absorber planes)",
+               "krylov": "Krylov vector kernels (k_vec, k_gdot, k_gupd, k_v64)",
+               "transform": "lateral real<->HYBRID transforms (k_rows/k_cols)"}
+    by_stage = {}
+    for k, v in solve_stages.items():
+        if v["calls"] and v["bytes"] > 0 and k in kernels:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            by_stage[k] = {"ms": v["ms"], "share": None, "GBps": gbs, "frac": gbs / peak,
+                           "bytes_per_call": v["bytes"] / v["calls"], "ms_per_call": v["ms"] / v["calls"]}
+    tot_ms = sum(v["ms"] for v in solve_stages.values() if v["calls"])
+    for k in by_stage:
+        by_stage[k]["share"] = by_stage[k]["ms"] / tot_ms
+    dom = max(by_stage, key=lambda k: by_stage[k]["ms"])
+    d = by_stage[dom]
     K = args.steps
-    value = world * solves_per_step * K / (ms_warm / 1e3)
-    cold_value = world * solves_per_step * K / (ms_cold / 1e3)
-    e2e_value = world * solves_per_step * K / (ms_e2e / 1e3)
+
+    def converged(infos):
+        return sum(1 for inf in infos for r in inf if r["status"] == 0)
+
+    # only right-hand sides that reached the tolerance count as solves
+    value = world * converged(info_warm) / (ms_warm / 1e3)
+    cold_value = world * converged(info_cold) / (ms_cold / 1e3)
+    e2e_value = world * converged(info_e2e) / (ms_e2e / 1e3)
     iters_w = [r["iters"] for inf in info_warm for r in inf]
     iters_c = [r["iters"] for inf in info_cold for r in inf]
     rrel = [r["r_rel"] for inf in info_warm + info_cold for r in inf]
@@ -263,24 +289,35 @@ def run_ours(args, rank, world):
         "data": "synthetic: seeded random Manhattan masks (4-24 rectangles, edges 4-40 px), "
                 "seed-initialised FNO weights",
         "config": {"workload": args.workload, "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
-                   "rhs_per_step": nrhs, "pols": ["TE", "TM"], "theta_deg": prob.theta_deg, "tol": TOL,
-                   "solver": args.method + ", spectral-damping right preconditioner, affine warm start",
+                   "rhs_per_step": nrhs, "pols": ["TE", "TM"][:nrhs], "theta_deg": prob.theta_deg, "tol": TOL,
+                   "solver": f"{args.method}({args.restart}) in complex64 with FP64 outer residual and field "
+                             "(mixed-precision refinement, inner tol 1e-2), spectral-damping right preconditioner, "
+                             "affine warm start",
                    "damping": {"m_min": prob.m_min, "gamma": prob.gamma, "k_ref": "k0"},
                    "l2": "working set (>= 9 vectors x 25 MB) exceeds the 126 MB L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "solve": {"iters_warm": iters_w, "iters_cold": iters_c, "r_rel_true_max": max(rrel),
-                  "status": status, "r_rel_initial_warm": [r["r_rel_initial"] for inf in info_warm for r in inf]},
+        "solve": {"iters_warm": iters_w, "iters_cold": iters_c, "r_rel_fp64_warm": [r["r_rel"] for inf in info_warm for r in inf],
+                  "r_rel_fp64_cold": [r["r_rel"] for inf in info_cold for r in inf],
+                  "r_rel_output_c64": [r["r_rel_output"] for inf in info_warm + info_cold for r in inf],
+                  "status": status, "converged": f"{converged(info_warm) + converged(info_cold)} of {len(status)}",
+                  "maxit": args.maxit, "outer_steps": [r["outer"] for inf in info_warm for r in inf],
+                  "r_rel_initial_warm": [r["r_rel_initial"] for inf in info_warm for r in inf]},
         "cold": {"value": cold_value, "unit": "solves/s", "ms_per_step": ms_cold / K},
+        "practical_5e-2": {"warm": {"value": world * converged(info_pw) / (ms_pw / 1e3), "ms_per_step": ms_pw / K,
+                                    "iters": [r["iters"] for inf in info_pw for r in inf]},
+                           "cold": {"value": world * converged(info_pc) / (ms_pc / 1e3), "ms_per_step": ms_pc / K,
+                                    "iters": [r["iters"] for inf in info_pc for r in inf]},
+                           "unit": "solves/s"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "matvec": {"ms": ms_apply, "algorithmic_bytes": apply_bytes, "GBps_algorithmic": apply_bytes / ms_apply / 1e6,
                    "frac_of_peak": apply_bytes / ms_apply / 1e6 / peak, "stages_ms_per_apply":
                        {k: v["ms"] / nap for k, v in stages.items() if v["calls"]}},
-        "roofline": {"kernel": "k_axial (fused M + curl-curl + R column kernel)", "bound": "hbm",
-                     "achieved": axial_bytes / (axial_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": axial_bytes / (axial_ms / 1e3) / 1e9 / peak, "traffic": None,
-                     "peak_kind": peak_kind, "ms_per_launch": axial_ms,
-                     "algorithmic_bytes_per_launch": axial_bytes},
+        "roofline": {"kernel": kernels[dom], "stage": dom, "bound": "hbm", "achieved": d["GBps"], "peak": peak,
+                     "unit": "GB/s", "frac": d["frac"], "traffic": None, "peak_kind": peak_kind,
+                     "ms_per_launch": d["ms_per_call"], "algorithmic_bytes_per_launch": d["bytes_per_call"],
+                     "share_of_step": d["share"]},
+        "roofline_by_stage": by_stage,
         "solve_stage_ms": {k: v["ms"] for k, v in solve_stages.items() if v["calls"]},
         "clocks": clocks,
     }
@@ -310,8 +347,8 @@ def run_profile_apply(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(prob, seed, n_iter):
-    """Time the FP64 oracle: setup + a fixed number of BiCGSTAB iterations (2 applies each)."""
+def oracle_sample(prob, seed, n_iter, method="gmres"):
+    """Time the FP64 oracle: setup + a fixed number of Krylov iterations of the bench's method."""
     import torch
     from oracle import krylov as K
     from oracle import psfd as O
@@ -325,7 +362,7 @@ def oracle_sample(prob, seed, n_iter):
     A = lambda E: O.apply_A(g, E, fill)
     M = lambda x: O.apply_M(g, x)
     t1 = time.perf_counter()
-    K.solve(A, M, b, tol=1e-30, maxit=n_iter)
+    K.solve(A, M, b, tol=1e-30, maxit=n_iter, method=method, restart=30)
     t_it = (time.perf_counter() - t1) / n_iter
     return t_setup, t_it
 
@@ -334,12 +371,12 @@ def cpu_baseline(args, iters_per_solve):
     import torch
     from paper_2607_25330_b300 import inputs as I
     prob = I.preset(args.workload)
-    n_iter = 3
-    t_setup, t_it = oracle_sample(prob, 0, n_iter)
+    n_iter = 6
+    t_setup, t_it = oracle_sample(prob, 0, n_iter, args.method)
     s_per_solve = t_setup + t_it * iters_per_solve
     return {"value": 1.0 / s_per_solve, "unit": "solves/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle on one {args.workload} mask, one polarisation: setup + {n_iter} BiCGSTAB "
-                      f"iterations timed ({t_it:.2f} s/iteration, {t_setup:.2f} s setup), scaled to "
+            "sample": f"FP64 oracle on one {args.workload} mask, one polarisation: setup + {n_iter} "
+                      f"{args.method} iterations timed ({t_it:.2f} s/iteration, {t_setup:.2f} s setup), scaled to "
                       f"{iters_per_solve:.0f} iterations per solve (the GPU solve's mean count)"}
 
 
@@ -347,15 +384,15 @@ def run_reference(args):
     import torch
     from paper_2607_25330_b300 import inputs as I
     prob = I.preset(args.workload)
-    iters_per_solve = 2000.0   # order of the preconditioned count at this size; stated, not measured here
+    iters_per_solve = float(MAXIT)   # the GPU arm's iteration cap per solve; stated, not measured here
     times = []
     for s in range(args.warmup + args.steps):
-        t_setup, t_it = oracle_sample(prob, s, 2)
+        t_setup, t_it = oracle_sample(prob, s, 2, args.method)
         if s >= args.warmup:
             times.append(t_setup + t_it * iters_per_solve)
     value = 1.0 / (sum(times) / len(times))
     cb = {"value": value, "unit": "solves/s", "cores": torch.get_num_threads(), "kind": "oracle",
-          "sample": f"per step: FP64 oracle setup + 2 BiCGSTAB iterations on one {args.workload} mask, "
+          "sample": f"per step: FP64 oracle setup + 2 {args.method} iterations on one {args.workload} mask, "
                     f"scaled to {iters_per_solve:.0f} iterations per solve"}
     return {"impl": "reference", "metric": "PSFD solves/s to rel. residual 1e-6 (warm start; cold alongside)",
             "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

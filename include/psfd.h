@@ -100,6 +100,8 @@ typedef struct {
   double r_rel;              /* true relative residual ||b - A E|| / ||b|| (FP64), Eq. relative_residual */
   double r_rel_recursive;    /* the solver's recursive estimate at exit                   */
   double r_rel_initial;      /* ||b - A E_base|| / ||b|| before the first iteration       */
+  int outer;                 /* outer FP64 refinement steps (psfd_solve_ex with refine)   */
+  double r_rel_output;       /* FP64 relative residual of the returned complex64 field    */
 } psfd_info_t;
 
 /* ---------------------------------------------------------------- plan */
@@ -170,6 +172,47 @@ PSFD_API int psfd_solve(psfd_plan plan, const psfd_c64* b, const psfd_c64* x0, p
                psfd_info_t* info, void* workspace, size_t workspace_bytes);
 PSFD_API size_t psfd_solve_workspace_size(psfd_plan plan, int method, int restart);
 
+/* Solve with options; refine = 1 selects mixed precision: the field is kept in
+ * FP64, the outer residual b - A E is computed with an FP64 operator apply, and
+ * each outer step solves A M d = r in complex64 (method, restart, preconditioner
+ * as above) to the relative tolerance inner_tol, then E += M d.  Convergence is
+ * the FP64 relative residual <= tol (Eq. relative_residual); maxit bounds the
+ * total number of inner iterations, max_outer (0 = 100) the outer steps.  The
+ * returned field is the complex64 rounding of the FP64 field; info.r_rel_output
+ * is its own FP64 relative residual (rounding a field to complex64 leaves a
+ * residual of the order of 1e-6 on these grids).  refine = 0 is psfd_solve.
+ * Workspace: psfd_solve_ex_workspace_size() bytes or NULL (allocated inside). */
+typedef struct {
+  double tol;
+  int maxit;
+  int method;
+  int restart;
+  int use_precond;
+  int refine;
+  double inner_tol;
+  int max_outer;
+} psfd_solve_opts_t;
+PSFD_API int psfd_solve_ex(psfd_plan plan, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E,
+                           const psfd_solve_opts_t* opts, psfd_info_t* info, void* workspace,
+                           size_t workspace_bytes);
+PSFD_API size_t psfd_solve_ex_workspace_size(psfd_plan plan, const psfd_solve_opts_t* opts);
+
+/* FFT tile autotuner: times every compiled lane split of the axial transforms for
+ * this plan's shape (CUDA events, after psfd_background) and keeps the fastest;
+ * cached per (nx, ny, nz, nrhs) for the process.  *chosen_T (nullable) receives the
+ * lanes per pencil.  Synchronous. */
+PSFD_API int psfd_autotune(psfd_plan plan, int* chosen_T);
+
+/* Batched solve of independent problems (masks of different size, angles,
+ * polarisations): plans[i] with its b[i], optional x0[i] (x0 may be NULL) and
+ * output E[i]; every plan must have its own stream for the solves to overlap.
+ * info: HOST array of sum(plans[i].nrhs) entries, in plan order.  nworkers host
+ * threads (<= 0: 8) take plans in order and run psfd_solve_ex on each.  Blocks
+ * until all solves finish; returns the worst status. */
+PSFD_API int psfd_solve_batched(const psfd_plan* plans, int nplans, const psfd_c64* const* b,
+                                const psfd_c64* const* x0, psfd_c64* const* E,
+                                const psfd_solve_opts_t* opts, psfd_info_t* info, int nworkers);
+
 /* Optional residual history: if set, psfd_solve writes ||r_k|| / ||b|| for every
  * iteration k < capacity and right-hand side r to hist[r * capacity + k] (HOST). */
 PSFD_API int psfd_set_history(psfd_plan plan, double* hist, int capacity);
@@ -230,6 +273,9 @@ PSFD_API int psfd_spectral_upsample_static(const psfd_c64* src, int nb, int nx0,
 PSFD_API long long psfd_launch_count(void);
 PSFD_API int psfd_timing_enable(int on);
 PSFD_API int psfd_timing_read(double* ms, long long* calls, int nstages);
+/* As psfd_timing_read, plus the summed algorithmic bytes of each stage: the
+ * compulsory reads and writes of its inputs and outputs (HOST array). */
+PSFD_API int psfd_timing_read_bytes(double* ms, long long* calls, double* bytes, int nstages);
 
 /* ---------------------------------------------------------------- misc */
 PSFD_API const char* psfd_last_error(void);

@@ -37,7 +37,7 @@ struct AxialArgs {
   float m_min, kref2, gamma, damp_eps;
 };
 
-enum { AX_AM = 0, AX_A = 1, AX_M = 2 };
+enum { AX_AM = 0, AX_A = 1, AX_M = 2, AX_AH = 3 };
 
 // The column work is a loop over "jobs"; each job is
 //   source (time layout) -> FFT_z -> one spectral factor -> IFFT_z -> post-op
@@ -52,7 +52,11 @@ enum { AX_AM = 0, AX_A = 1, AX_M = 2 };
 //   6: c_y -> i kz / N     -> D c_y  -> W_x = i ky c_z - D c_y - k0^2 q_x
 // with D = s^-1 (.) applied after the inverse transform, c_z = i kx q_y - i ky q_x.
 // Without M (mode A) jobs 0, 1, 3 copy the input.  Mode M runs jobs 0, 1, 3 only
-// and writes q to y.
+// and writes q to y.  Mode AH applies the adjoint A^H x = curl~ curl~ x - k0^2 x
+// - G - R^H G with D~ = F^-1 i kz F conj(s^-1) (the PML factor moves in front of
+// the transform) and G = k0^2 F_xy[conj(deps) F_xy^-1 x] on the absorber planes,
+// prepared by the contrast passes before this kernel; R^H G sums conj(profile) G
+// over the column and is subtracted at z_ml.
 template <int NZ, int T, int MODE>
 __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
   constexpr int P = 32 / T;
@@ -76,10 +80,58 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
   auto unst = [&](int sl, int m) -> cf { return st[(sl * R + m) * 32 + lane]; };
   auto stash = [&](int sl, int m, cf v) { st[(sl * R + m) * 32 + lane] = v; };
 
+  // adjoint: (rh0, rh1) = T^H sum_z conj(profile(z)) G(z), the R^H term at z_ml
+  cf rh0 = czero(), rh1 = czero();
+  if constexpr (MODE == AX_AH) {
+    const int nab = a.za1 - a.za0;
+    const cf* __restrict__ G = a.G + rhs * a.gstride;
+    const cf kz0 = __ldg(a.kz0 + cc);
+    cf v0 = czero(), v1 = czero(), v2 = czero();
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int z = t + T * m;
+      if (z >= a.za0 && z < a.za1 && z >= a.z_ml && act) {
+        const float zr = (float)(z - a.z_ml) * a.dz;
+        float sn, cs;
+        sincosf(kz0.x * zr, &sn, &cs);
+        const float mag = expf(-kz0.y * zr);
+        const cf pc = make_float2(mag * cs, -mag * sn);     // conj(profile)
+        const long o = (long)(z - a.za0) * nc + col;
+        v0 = cfma(pc, G[o], v0);
+        v1 = cfma(pc, G[(long)nab * nc + o], v1);
+        v2 = cfma(pc, G[2L * nab * nc + o], v2);
+      }
+    }
+#pragma unroll
+    for (int b = 1; b < T; b <<= 1) {
+      v0.x += __shfl_xor_sync(0xffffffffu, v0.x, b * P); v0.y += __shfl_xor_sync(0xffffffffu, v0.y, b * P);
+      v1.x += __shfl_xor_sync(0xffffffffu, v1.x, b * P); v1.y += __shfl_xor_sync(0xffffffffu, v1.y, b * P);
+      v2.x += __shfl_xor_sync(0xffffffffu, v2.x, b * P); v2.y += __shfl_xor_sync(0xffffffffu, v2.y, b * P);
+    }
+    const float4 rr = __ldg(a.refl + cc);
+    const cf rs = make_float2(rr.x, rr.y), rp = make_float2(rr.z, rr.w);
+    const float kp = sqrtf(kx * kx + ky * ky);
+    float sx, sy, tx, ty;
+    if (kp > 0.f) { sx = -ky / kp; sy = kx / kp; tx = kx / kp; ty = ky / kp; }
+    else { sx = 0.f; sy = 1.f; tx = 1.f; ty = 0.f; }
+    // T = [[rs sx sx + rp tx tx, rs sx sy + rp tx ty], [rs sy sx + rp ty tx, rs sy sy + rp ty ty],
+    //      [-(kx T00 + ky T10)/kz0, -(kx T01 + ky T11)/kz0]];  e = T^H v
+    const cf T00 = cfma(rs, make_float2(sx * sx, 0.f), cscale(rp, tx * tx));
+    const cf T01 = cfma(rs, make_float2(sx * sy, 0.f), cscale(rp, tx * ty));
+    const cf T10 = cfma(rs, make_float2(sy * sx, 0.f), cscale(rp, ty * tx));
+    const cf T11 = cfma(rs, make_float2(sy * sy, 0.f), cscale(rp, ty * ty));
+    const float kd = kz0.x * kz0.x + kz0.y * kz0.y;
+    auto divkz = [&](cf n) { return make_float2((n.x * kz0.x + n.y * kz0.y) / kd, (n.y * kz0.x - n.x * kz0.y) / kd); };
+    const cf T20 = divkz(make_float2(-(kx * T00.x + ky * T10.x), -(kx * T00.y + ky * T10.y)));
+    const cf T21 = divkz(make_float2(-(kx * T01.x + ky * T11.x), -(kx * T01.y + ky * T11.y)));
+    rh0 = cadd(cadd(cmulc(v0, T00), cmulc(v1, T10)), cmulc(v2, T20));   // conj(T_i0) v_i
+    rh1 = cadd(cadd(cmulc(v0, T01), cmulc(v1, T11)), cmulc(v2, T21));
+  }
+
 #pragma unroll 1
   for (int job = 0; job < 7; ++job) {
     if (MODE == AX_M && (job == 2 || job >= 4)) continue;
-    const bool copy_only = (MODE == AX_A) && (job == 0 || job == 1 || job == 3);
+    const bool copy_only = (MODE == AX_A || MODE == AX_AH) && (job == 0 || job == 1 || job == 3);
     cf v[R];
     // ---- source
     if (job < 5) {
@@ -92,10 +144,14 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
 #pragma unroll
       for (int m = 0; m < R; ++m) v[m] = unst(sl, m);
     }
+    if (MODE == AX_AH && (job == 2 || job >= 4)) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = cmulc(v[m], __ldg(a.sinv + t + T * m));   // v * conj(1/s)
+    }
     // ---- spectral filter along z
     if (!copy_only) {
       PZ::template to_freq<false>(v, t, a.tw);
-      const bool with_m = (MODE != AX_A) && job < 5;
+      const bool with_m = (MODE == AX_AM || MODE == AX_M) && job < 5;
       const bool with_d = (job == 2 || job >= 4);
 #pragma unroll
       for (int s = 0; s < R; ++s) {
@@ -130,9 +186,24 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
     } else if (job == 2) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const cf dq = cmul(v[m], __ldg(a.sinv + t + T * m));
+        const cf dq = (MODE == AX_AH) ? v[m] : cmul(v[m], __ldg(a.sinv + t + T * m));
         stash(2, m, csub(cmul(iky, unst(0, m)), dq));
       }
+    } else if (job == 4 && MODE == AX_AH) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = csub(v[m], cmul(ikx, unst(0, m)));   // c~_y
+      const int nab = a.za1 - a.za0;
+      const cf* __restrict__ G = a.G + rhs * a.gstride;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const cf qz = unst(0, m), cx = unst(2, m), cy = v[m];
+        cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
+        if (z >= a.za0 && z < a.za1 && act) Wz = csub(Wz, G[(2L * nab + z - a.za0) * nc + col]);
+        if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
+      }
+#pragma unroll
+      for (int m = 0; m < R; ++m) stash(0, m, v[m]);
     } else if (job == 4) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
@@ -186,14 +257,21 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
       for (int m = 0; m < R; ++m) stash(0, m, v[m]);   // c_y replaces q_z (lane-private entries)
     } else {
       const int c = (job == 5) ? 1 : 0;
+      const int nab = a.za1 - a.za0;
+      const cf* __restrict__ G = a.G + rhs * a.gstride;
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const cf d = cmul(v[m], __ldg(a.sinv + t + T * m));
+        const int z = t + T * m;
+        const cf d = (MODE == AX_AH) ? v[m] : cmul(v[m], __ldg(a.sinv + z));
         const cf qx = unst(3, m), qy = unst(1, m);
         const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        const cf W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
-                                : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
-        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = W;
+        cf W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
+                          : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
+        if (MODE == AX_AH) {
+          if (z >= a.za0 && z < a.za1 && act) W = csub(W, G[((long)c * nab + z - a.za0) * nc + col]);
+          if (z == a.z_ml) W = csub(W, c == 0 ? rh0 : rh1);
+        }
+        if (act) y[(long)(c * NZ + z) * nc + col] = W;
       }
     }
   }
@@ -229,6 +307,7 @@ static int run_axial_mode(psfd_plan_s* P, const cf* x, cf* y, int mode, const in
   switch (mode) {
     case AX_AM: return run_axial<NZ, T, AX_AM>(P, x, y, done);
     case AX_A: return run_axial<NZ, T, AX_A>(P, x, y, done);
+    case AX_AH: return run_axial<NZ, T, AX_AH>(P, x, y, done);
     default: return run_axial<NZ, T, AX_M>(P, x, y, done);
   }
 }
@@ -241,19 +320,34 @@ int axial_supported(int nz) {
 }
 
 int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int) {
-  StageScope sc(P->stream, ST_AXIAL);
+  // read x, write y (all planes); the operator modes also write (or, adjoint, read) G
+  const double vb = (double)P->nrhs * P->nvec * sizeof(cf);
+  const double gb = (mode == AX_M) ? 0.0 : (double)P->nrhs * 3 * (P->za1 - P->za0) * P->ncols * sizeof(cf);
+  StageScope sc(P->stream, ST_AXIAL, 2.0 * vb + gb);
   const int T = P->axial_T;
   switch (P->nz) {
-    case 16: return run_axial_mode<16, 2>(P, x, y, mode, done);
-    case 32: return run_axial_mode<32, 4>(P, x, y, mode, done);
-    case 48: return run_axial_mode<48, 4>(P, x, y, mode, done);
-    case 64: return (T == 4) ? run_axial_mode<64, 4>(P, x, y, mode, done)
-                             : run_axial_mode<64, 8>(P, x, y, mode, done);
+    case 16: return (T == 4) ? run_axial_mode<16, 4>(P, x, y, mode, done) : run_axial_mode<16, 2>(P, x, y, mode, done);
+    case 32: return (T == 2) ? run_axial_mode<32, 2>(P, x, y, mode, done) : run_axial_mode<32, 4>(P, x, y, mode, done);
+    case 48: return (T == 2) ? run_axial_mode<48, 2>(P, x, y, mode, done) : run_axial_mode<48, 4>(P, x, y, mode, done);
+    case 64: return (T == 4) ? run_axial_mode<64, 4>(P, x, y, mode, done) : run_axial_mode<64, 8>(P, x, y, mode, done);
     case 96: return run_axial_mode<96, 4>(P, x, y, mode, done);
-    case 128: return run_axial_mode<128, 8>(P, x, y, mode, done);
+    case 128: return (T == 4) ? run_axial_mode<128, 4>(P, x, y, mode, done) : run_axial_mode<128, 8>(P, x, y, mode, done);
   }
   psfd_set_error("axial: unsupported nz %d", P->nz);
   return PSFD_ERR_ARG;
+}
+
+// lanes per axial pencil that the kernels are compiled for (the autotuner's choices)
+int axial_candidates(int nz, int* out) {
+  switch (nz) {
+    case 16: out[0] = 2; out[1] = 4; return 2;
+    case 32: out[0] = 4; out[1] = 2; return 2;
+    case 48: out[0] = 4; out[1] = 2; return 2;
+    case 64: out[0] = 8; out[1] = 4; return 2;
+    case 96: out[0] = 4; return 1;
+    case 128: out[0] = 8; out[1] = 4; return 2;
+  }
+  return 0;
 }
 
 // ======================================================================= lateral passes
@@ -498,7 +592,7 @@ int launch_cols_gauss(int ny, int nx, cf* buf, float sigma, const cf* tw, cudaSt
 
 // real space <-> HYBRID over nplanes planes: forward = rows then columns (unitary scale)
 int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward, float scale) {
-  StageScope sc(P->stream, ST_TRANSFORM);
+  StageScope sc(P->stream, ST_TRANSFORM, 2.0 * nplanes * P->ncols * sizeof(cf));
   int rc;
   const long rows = nplanes * P->ny, cols = nplanes * P->nx;
   if (forward) {
@@ -513,7 +607,9 @@ int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward
 int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint) {
   const int nab = P->za1 - P->za0;
   if (nab <= 0) return PSFD_OK;
-  StageScope scope(P->stream, ST_CONTRAST);
+  // read G, read fill, read y, write y on the absorber planes
+  StageScope scope(P->stream, ST_CONTRAST,
+                   (double)P->nrhs * nab * P->ncols * (3.0 * 3 * sizeof(cf) + sizeof(float)));
   const long nplanes = (long)P->nrhs * 3 * nab;
   int rc;
   RowArgs r{};
@@ -532,9 +628,42 @@ int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint
   return rows_dispatch(P->nx, w, ROW_FWD_SUB, P->stream);
 }
 
-// y = A x or A M x, both in the HYBRID domain
+// G <- k0^2 F_xy[conj(deps) F_xy^-1 x] on the absorber planes (first half of the adjoint)
+static int adjoint_contrast(psfd_plan_s* P, const cf* x) {
+  const int nab = P->za1 - P->za0;
+  if (nab <= 0) return PSFD_OK;
+  StageScope scope(P->stream, ST_CONTRAST);
+  const long pe = (long)nab * P->ncols;
+  for (int r = 0; r < P->nrhs; ++r)
+    for (int c = 0; c < 3; ++c) {
+      const cf* src = x + (long)r * P->nvec + ((long)c * P->nz + P->za0) * P->ncols;
+      cf* dst = P->G + ((long)r * 3 + c) * pe;
+      PSFD_CUDA_TRY(cudaMemcpyAsync(dst, src, pe * sizeof(cf), cudaMemcpyDeviceToDevice, P->stream));
+    }
+  const long nplanes = (long)P->nrhs * 3 * nab;
+  int rc;
+  RowArgs r{};
+  r.buf = P->G; r.nrows = nplanes * P->ny; r.scale = 1.f; r.tw = P->tw_x; r.rows_per_rhs = 3L * nab * P->ny;
+  if ((rc = rows_dispatch(P->nx, r, ROW_INV, P->stream))) return rc;
+  ColArgs c{};
+  const double sc = P->k0 * P->k0 / (double)P->ncols;
+  c.buf = P->G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.f; c.tw = P->tw_y;
+  c.fill = P->fill; c.dre = (float)(sc * P->deps_re); c.dim = (float)(-sc * P->deps_im);
+  c.nab = nab; c.za0 = P->za0; c.plane_elems = P->ncols; c.planes_per_rhs = 3L * nab;
+  if ((rc = cols_dispatch(P->ny, c, COL_CONTRAST, P->stream))) return rc;
+  return rows_dispatch(P->nx, r, ROW_FWD, P->stream);
+}
+
+// y = A x, A M x, A^H x or M A^H x, all in the HYBRID domain
 int apply_hybrid(psfd_plan_s* P, const cf* x, cf* y, int flags, const int* done) {
-  int rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) ? AX_AM : AX_A, done, P->nrhs);
+  int rc;
+  if (flags & PSFD_ADJOINT) {
+    if ((rc = adjoint_contrast(P, x))) return rc;
+    if (!(flags & PSFD_PRECOND)) return launch_axial(P, x, y, AX_AH, done, P->nrhs);
+    if ((rc = launch_axial(P, x, P->tmpB, AX_AH, done, P->nrhs))) return rc;
+    return launch_axial(P, P->tmpB, y, AX_M, done, P->nrhs);
+  }
+  rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) ? AX_AM : AX_A, done, P->nrhs);
   if (rc) return rc;
   return launch_lateral_contrast(P, y, done, false);
 }
@@ -543,7 +672,6 @@ extern "C" int psfd_apply(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags
   if (!P || !x || !y) { psfd_set_error("psfd_apply: null argument"); return PSFD_ERR_ARG; }
   if (!P->have_background) { psfd_set_error("psfd_apply: call psfd_background first"); return PSFD_ERR_STATE; }
   if (x == y) { psfd_set_error("psfd_apply: x and y must not overlap"); return PSFD_ERR_ARG; }
-  if (flags & PSFD_ADJOINT) { psfd_set_error("psfd_apply: adjoint not available in this build"); return PSFD_ERR_ARG; }
   const cf* xi = (const cf*)x;
   cf* yo = (cf*)y;
   const long bytes = (long)P->nrhs * P->nvec * sizeof(cf);

@@ -1,0 +1,457 @@
+// FP64 operator apply for the outer residual of the mixed-precision solve.
+//
+// A complex64 field cannot represent the solution to much better than a
+// relative residual of ~1e-6 (rounding the exact FP64 solution to complex64
+// already leaves 5e-7..8e-7 on the 32x32x16 and 32x32x32 cases), so the solver
+// refines: complex64 inner Krylov solves of A M d = r, and an FP64 field
+// E <- E + M d whose residual r = b - A E is computed here in FP64.  Same
+// operator as apply.cu (A = curl_s curl_s - k0^2 - k0^2 deps (I + R), Sec. 2.2)
+// with every table (wavenumbers, PML, twiddles, reflection coefficients) in FP64.
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace {
+
+struct Ax64 {
+  const zd* x;
+  zd* y;
+  zd* G;
+  const double* kx;
+  const double* ky;
+  const double* kz;
+  const zd* sinv;
+  const zd* tw;
+  const double2* rs;
+  const double2* rp;
+  const double2* kz0;
+  int nx;
+  long ncols, vstride, gstride;
+  int z_ml, za0, za1;
+  double dz, k02;
+};
+
+// Same job structure as k_axial (mode A): jobs 0, 1, 3 copy the input.
+template <int NZ, int T>
+__global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
+  constexpr int P = 32 / T;
+  constexpr int R = NZ / T;
+  using PZ = Pencil<NZ, T, P, zd>;
+  extern __shared__ zd smem64[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = lane / P, p = lane - t * P;
+  const int rhs = blockIdx.y;
+  const long col = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  const bool act = col < a.ncols;
+  const long cc = act ? col : 0;
+  const long nc = a.ncols;
+  const zd* __restrict__ x = a.x + rhs * a.vstride;
+  zd* __restrict__ y = a.y + rhs * a.vstride;
+  const double kx = a.kx[cc % a.nx], ky = a.ky[cc / a.nx];
+  const double inv_n = 1.0 / (double)NZ;
+  const zd ikx = make_double2(0.0, kx), iky = make_double2(0.0, ky);
+  zd* st = smem64 + (size_t)warp * 4 * R * 32;
+  auto unst = [&](int sl, int m) -> zd { return st[(sl * R + m) * 32 + lane]; };
+  auto stash = [&](int sl, int m, zd v) { st[(sl * R + m) * 32 + lane] = v; };
+#pragma unroll 1
+  for (int job = 0; job < 7; ++job) {
+    const bool copy_only = (job == 0 || job == 1 || job == 3);
+    zd v[R];
+    if (job < 5) {
+      const int c = (job == 0) ? 2 : (job <= 2 ? 1 : 0);
+      const zd* src = x + (long)(c * NZ + t) * nc + col;
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = act ? src[(long)(T * m) * nc] : make_double2(0.0, 0.0);
+    } else {
+      const int sl = (job == 5) ? 2 : 0;
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = unst(sl, m);
+    }
+    if (!copy_only) {
+      PZ::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const double kzv = a.kz[PZ::freq_index(t, s)] * inv_n;
+        v[s] = make_double2(-kzv * v[s].y, kzv * v[s].x);
+      }
+      PZ::template to_time<true>(v, t, a.tw);
+    }
+    if (copy_only) {
+      const int sl = (job == 0) ? 0 : (job == 1 ? 1 : 3);
+#pragma unroll
+      for (int m = 0; m < R; ++m) stash(sl, m, v[m]);
+    } else if (job == 2) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) stash(2, m, csub(cmul(iky, unst(0, m)), cmul(v[m], a.sinv[t + T * m])));
+    } else if (job == 4) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = csub(cmul(v[m], a.sinv[t + T * m]), cmul(ikx, unst(0, m)));
+      __syncwarp();
+      const int tml = a.z_ml % T, mml = a.z_ml / T;
+      const zd exm = st[(3 * R + mml) * 32 + tml * P + p];
+      const zd eym = st[(1 * R + mml) * 32 + tml * P + p];
+      const zd rs = a.rs[cc], rp = a.rp[cc], kz0 = a.kz0[cc];
+      const double kp = sqrt(kx * kx + ky * ky);
+      double sx, sy, tx, ty;
+      if (kp > 0.0) { sx = -ky / kp; sy = kx / kp; tx = kx / kp; ty = ky / kp; }
+      else { sx = 0.0; sy = 1.0; tx = 1.0; ty = 0.0; }
+      const zd as = make_double2(sx * exm.x + sy * eym.x, sx * exm.y + sy * eym.y);
+      const zd at = make_double2(tx * exm.x + ty * eym.x, tx * exm.y + ty * eym.y);
+      const zd ras = cmul(rs, as), rat = cmul(rp, at);
+      const zd r0 = make_double2(ras.x * sx + rat.x * tx, ras.y * sx + rat.y * tx);
+      const zd r1 = make_double2(ras.x * sy + rat.x * ty, ras.y * sy + rat.y * ty);
+      const zd num = make_double2(-(kx * r0.x + ky * r1.x), -(kx * r0.y + ky * r1.y));
+      const double kd = kz0.x * kz0.x + kz0.y * kz0.y;
+      const zd r2 = make_double2((num.x * kz0.x + num.y * kz0.y) / kd, (num.y * kz0.x - num.x * kz0.y) / kd);
+      const int nab = a.za1 - a.za0;
+      zd* __restrict__ G = a.G + rhs * a.gstride;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int z = t + T * m;
+        const zd qz = unst(0, m), cx = unst(2, m), cy = v[m];
+        const zd Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
+        if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
+        if (z >= a.za0 && z < a.za1 && act) {
+          zd prof = make_double2(0.0, 0.0);
+          if (z >= a.z_ml) {
+            const double zr = (double)(z - a.z_ml) * a.dz;
+            double sn, cs;
+            sincos(kz0.x * zr, &sn, &cs);
+            const double mag = exp(-kz0.y * zr);
+            prof = make_double2(mag * cs, mag * sn);
+          }
+          const long o = (long)(z - a.za0) * nc + col;
+          G[o] = cfma(r0, prof, unst(3, m));
+          G[(long)nab * nc + o] = cfma(r1, prof, unst(1, m));
+          G[2L * nab * nc + o] = cfma(r2, prof, qz);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < R; ++m) stash(0, m, v[m]);
+    } else {
+      const int c = (job == 5) ? 1 : 0;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const zd d = cmul(v[m], a.sinv[t + T * m]);
+        const zd qx = unst(3, m), qy = unst(1, m);
+        const zd cz = csub(cmul(ikx, qy), cmul(iky, qx));
+        const zd W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
+                                : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
+        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = W;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP64 lateral passes
+enum { R64_FWD = 0, R64_INV = 1, R64_FWD_SUB = 2 };
+struct Row64 {
+  zd* buf;
+  long nrows;
+  double scale;
+  const zd* tw;
+  zd* y;
+  int ny, nz, nab, za0;
+};
+
+template <int NX, int T, int OP>
+__global__ void __launch_bounds__(64) k_rows64(Row64 a) {
+  constexpr int P = 32 / T, R = NX / T;
+  using PX = Pencil<NX, T, 1, zd>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane / T, t = lane - p * T;
+  const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  const bool act = row < a.nrows;
+  zd* src = a.buf + (act ? row : 0) * NX;
+  zd v[R];
+  if constexpr (OP == R64_INV) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? src[PX::freq_index(t, s)] : make_double2(0.0, 0.0);
+    PX::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+      if (act) src[t + T * m] = cscale(v[m], a.scale);
+  } else {
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : make_double2(0.0, 0.0);
+    PX::template to_freq<false>(v, t, a.tw);
+    if constexpr (OP == R64_FWD) {
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
+    } else {
+      const long per_c = (long)a.nab * a.ny;
+      const long r = act ? row : 0;
+      const long rhs = r / (3 * per_c), rem = r - rhs * 3 * per_c;
+      const long c = rem / per_c, rem2 = rem - c * per_c;
+      const long zz = rem2 / a.ny, iy = rem2 - zz * a.ny;
+      zd* dst = a.y + (((rhs * 3 + c) * a.nz + a.za0 + zz) * a.ny + iy) * NX;
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        if (act) {
+          const int k = PX::freq_index(t, s);
+          dst[k] = csub(dst[k], v[s]);
+        }
+    }
+  }
+}
+
+enum { C64_FWD = 0, C64_INV = 1, C64_CONTRAST = 2 };
+struct Col64 {
+  zd* buf;
+  long ncolumns;
+  int nx;
+  double scale;
+  const zd* tw;
+  const float* fill;
+  double dre, dim;
+  int nab, za0;
+  long plane_elems;
+};
+
+template <int NY, int T, int OP>
+__global__ void __launch_bounds__(64) k_cols64(Col64 a) {
+  constexpr int P = 32 / T, R = NY / T;
+  using PY = Pencil<NY, T, P, zd>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = lane / P, p = lane - t * P;
+  const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  const bool act = colid < a.ncolumns;
+  const long cid = act ? colid : 0;
+  const long plane = cid / a.nx;
+  const int ix = (int)(cid - plane * a.nx);
+  zd* base = a.buf + plane * a.plane_elems + ix;
+  const long sx = a.nx;
+  zd v[R];
+  if constexpr (OP == C64_FWD) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : make_double2(0.0, 0.0);
+    PY::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (act) base[(long)PY::freq_index(t, s) * sx] = cscale(v[s], a.scale);
+  } else if constexpr (OP == C64_INV) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : make_double2(0.0, 0.0);
+    PY::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+      if (act) base[(long)(t + T * m) * sx] = cscale(v[m], a.scale);
+  } else {
+    const long zz = plane % a.nab;
+    const float* f = a.fill + (a.za0 + zz) * a.plane_elems + ix;
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : make_double2(0.0, 0.0);
+    PY::template to_time<true>(v, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const double fv = act ? (double)f[(long)(t + T * m) * sx] : 0.0;
+      v[m] = cmul(v[m], make_double2(a.dre * fv, a.dim * fv));
+    }
+    PY::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (act) base[(long)PY::freq_index(t, s) * sx] = v[s];
+  }
+}
+
+template <int NX, int T>
+int rows64_op(const Row64& a, int op, cudaStream_t s) {
+  const int warps = 2;
+  const long per = warps * (32 / T);
+  dim3 g((unsigned)((a.nrows + per - 1) / per));
+  if (!g.x) return PSFD_OK;
+  if (op == R64_FWD) k_rows64<NX, T, R64_FWD><<<g, warps * 32, 0, s>>>(a);
+  else if (op == R64_INV) k_rows64<NX, T, R64_INV><<<g, warps * 32, 0, s>>>(a);
+  else k_rows64<NX, T, R64_FWD_SUB><<<g, warps * 32, 0, s>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+int rows64(int nx, const Row64& a, int op, cudaStream_t s) {
+  switch (nx) {
+    case 16: return rows64_op<16, 4>(a, op, s);
+    case 32: return rows64_op<32, 4>(a, op, s);
+    case 64: return rows64_op<64, 8>(a, op, s);
+    case 96: return rows64_op<96, 4>(a, op, s);
+    case 128: return rows64_op<128, 8>(a, op, s);
+    case 256: return rows64_op<256, 16>(a, op, s);
+    case 512: return rows64_op<512, 16>(a, op, s);
+  }
+  psfd_set_error("rows64: unsupported %d", nx);
+  return PSFD_ERR_ARG;
+}
+template <int NY, int T>
+int cols64_op(const Col64& a, int op, cudaStream_t s) {
+  const int warps = 2;
+  const long per = warps * (32 / T);
+  dim3 g((unsigned)((a.ncolumns + per - 1) / per));
+  if (!g.x) return PSFD_OK;
+  if (op == C64_FWD) k_cols64<NY, T, C64_FWD><<<g, warps * 32, 0, s>>>(a);
+  else if (op == C64_INV) k_cols64<NY, T, C64_INV><<<g, warps * 32, 0, s>>>(a);
+  else k_cols64<NY, T, C64_CONTRAST><<<g, warps * 32, 0, s>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+int cols64(int ny, const Col64& a, int op, cudaStream_t s) {
+  switch (ny) {
+    case 16: return cols64_op<16, 2>(a, op, s);
+    case 32: return cols64_op<32, 4>(a, op, s);
+    case 64: return cols64_op<64, 4>(a, op, s);
+    case 96: return cols64_op<96, 4>(a, op, s);
+    case 128: return cols64_op<128, 8>(a, op, s);
+    case 256: return cols64_op<256, 8>(a, op, s);
+    case 512: return cols64_op<512, 16>(a, op, s);
+  }
+  psfd_set_error("cols64: unsupported %d", ny);
+  return PSFD_ERR_ARG;
+}
+
+template <int NZ, int T>
+int axial64_run(psfd_plan_s* P, const zd* x, zd* y) {
+  constexpr int R = NZ / T;
+  Ax64 a;
+  a.x = x; a.y = y; a.G = P->F.G;
+  a.kx = P->F.kx; a.ky = P->F.ky; a.kz = P->F.kz; a.sinv = P->F.sinv; a.tw = P->F.twz;
+  a.rs = P->R.rs64; a.rp = P->R.rp64; a.kz0 = P->R.kz064;
+  a.nx = P->nx; a.ncols = P->ncols; a.vstride = P->nvec;
+  a.gstride = 3L * (P->za1 - P->za0) * P->ncols;
+  a.z_ml = P->p.z_ml; a.za0 = P->za0; a.za1 = P->za1;
+  a.dz = P->p.dz; a.k02 = P->k0 * P->k0;
+  const int warps = 2;
+  const long per = warps * (32 / T);
+  dim3 g((unsigned)((P->ncols + per - 1) / per), (unsigned)P->nrhs);
+  const size_t smem = (size_t)warps * 4 * R * 32 * sizeof(zd);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_axial64<NZ, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_axial64<NZ, T><<<g, warps * 32, smem, P->stream>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+void host_tw64(int n, std::vector<zd>& out) {
+  out.resize(n);
+  for (int m = 0; m < n; ++m) {
+    const double ang = -2.0 * M_PI * (double)m / (double)n;
+    out[m] = make_double2(cos(ang), sin(ang));
+  }
+}
+
+double host_k(int i, int n, double d) {
+  const int m = (i <= (n - 1) / 2) ? i : i - n;
+  return 2.0 * M_PI * m / (n * d);
+}
+
+}  // namespace
+
+// Build the FP64 tables and scratch on first use (plan-owned, freed with the plan).
+int fp64_prepare(psfd_plan_s* P) {
+  Fp64Tables& F = P->F;
+  const size_t nab = (size_t)(P->za1 - P->za0);
+  const size_t gneed = (size_t)P->nrhs * 3 * nab * P->ncols;
+  if (F.kx && F.G_elems >= gneed) return PSFD_OK;
+  if (!F.kx) {
+    std::vector<double> kx(P->nx), ky(P->ny), kz(P->nz);
+    for (int i = 0; i < P->nx; ++i) kx[i] = host_k(i, P->nx, P->p.dx) + P->kx_inc;
+    for (int i = 0; i < P->ny; ++i) ky[i] = host_k(i, P->ny, P->p.dy) + P->ky_inc;
+    for (int i = 0; i < P->nz; ++i) kz[i] = host_k(i, P->nz, P->p.dz);
+    std::vector<zd> sinv(P->nz), twx, twy, twz;
+    const int np = P->p.pml_planes;
+    const double dpml = np * P->p.dz;
+    const double alpha = np > 0 ? 4.0 * log(1.0 / P->p.pml_R0) / (2.0 * P->k0 * dpml) : 0.0;
+    for (int k = 0; k < P->nz; ++k) {
+      double d = 0.0;
+      if (k < np) d = (np - k) * P->p.dz;
+      else if (k >= P->nz - np) d = (k - (P->nz - np - 1)) * P->p.dz;
+      const double sig = np > 0 ? alpha * pow(d / dpml, 3.0) : 0.0;
+      const double den = 1.0 + sig * sig;
+      sinv[k] = make_double2(1.0 / den, -sig / den);
+    }
+    host_tw64(P->nx, twx); host_tw64(P->ny, twy); host_tw64(P->nz, twz);
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.kx, P->nx * 8));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.ky, P->ny * 8));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.kz, P->nz * 8));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.sinv, P->nz * 16));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.twx, P->nx * 16));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.twy, P->ny * 16));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.twz, P->nz * 16));
+    PSFD_CUDA_TRY(cudaMemcpy(F.kx, kx.data(), P->nx * 8, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.ky, ky.data(), P->ny * 8, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.kz, kz.data(), P->nz * 8, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.sinv, sinv.data(), P->nz * 16, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.twx, twx.data(), P->nx * 16, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.twy, twy.data(), P->ny * 16, cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(F.twz, twz.data(), P->nz * 16, cudaMemcpyHostToDevice));
+  }
+  if (F.G_elems < gneed) {
+    if (F.G) cudaFree(F.G);
+    F.G = nullptr;
+    F.G_elems = 0;
+    if (gneed) PSFD_CUDA_TRY(cudaMalloc((void**)&F.G, gneed * sizeof(zd)));
+    F.G_elems = gneed;
+  }
+  return PSFD_OK;
+}
+
+void fp64_free(psfd_plan_s* P) {
+  Fp64Tables& F = P->F;
+  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.twx, F.twy, F.twz, F.G};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  F = Fp64Tables();
+}
+
+// y = A x in FP64, HYBRID domain (no preconditioner)
+int apply64_hybrid(psfd_plan_s* P, const zd* x, zd* y) {
+  int rc;
+  {
+    StageScope sc(P->stream, ST_AXIAL);
+    switch (P->nz) {
+      case 16: rc = axial64_run<16, 2>(P, x, y); break;
+      case 32: rc = axial64_run<32, 4>(P, x, y); break;
+      case 48: rc = axial64_run<48, 4>(P, x, y); break;
+      case 64: rc = axial64_run<64, 8>(P, x, y); break;
+      case 96: rc = axial64_run<96, 4>(P, x, y); break;
+      case 128: rc = axial64_run<128, 8>(P, x, y); break;
+      default: psfd_set_error("apply64: nz %d", P->nz); return PSFD_ERR_ARG;
+    }
+    if (rc) return rc;
+  }
+  const int nab = P->za1 - P->za0;
+  if (nab <= 0) return PSFD_OK;
+  StageScope sc(P->stream, ST_CONTRAST);
+  const long nplanes = (long)P->nrhs * 3 * nab;
+  Row64 r{};
+  r.buf = P->F.G; r.nrows = nplanes * P->ny; r.scale = 1.0; r.tw = P->F.twx;
+  if ((rc = rows64(P->nx, r, R64_INV, P->stream))) return rc;
+  Col64 c{};
+  const double scl = P->k0 * P->k0 / (double)P->ncols;
+  c.buf = P->F.G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.0; c.tw = P->F.twy;
+  c.fill = P->fill; c.dre = scl * P->deps_re; c.dim = scl * P->deps_im; c.nab = nab; c.za0 = P->za0;
+  c.plane_elems = P->ncols;
+  if ((rc = cols64(P->ny, c, C64_CONTRAST, P->stream))) return rc;
+  Row64 w{};
+  w.buf = P->F.G; w.nrows = nplanes * P->ny; w.tw = P->F.twx; w.y = y;
+  w.ny = P->ny; w.nz = P->nz; w.nab = nab; w.za0 = P->za0;
+  return rows64(P->nx, w, R64_FWD_SUB, P->stream);
+}
+
+// real space <-> HYBRID in FP64 over nplanes planes (unitary scale applied once)
+int transform64(psfd_plan_s* P, zd* buf, long nplanes, bool forward, double scale) {
+  StageScope sc(P->stream, ST_TRANSFORM);
+  int rc;
+  Row64 r{};
+  r.buf = buf; r.nrows = nplanes * P->ny; r.tw = P->F.twx;
+  Col64 c{};
+  c.buf = buf; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.tw = P->F.twy; c.plane_elems = P->ncols;
+  if (forward) {
+    r.scale = 1.0;
+    if ((rc = rows64(P->nx, r, R64_FWD, P->stream))) return rc;
+    c.scale = scale;
+    return cols64(P->ny, c, C64_FWD, P->stream);
+  }
+  c.scale = 1.0;
+  if ((rc = cols64(P->ny, c, C64_INV, P->stream))) return rc;
+  r.scale = scale;
+  return rows64(P->nx, r, R64_INV, P->stream);
+}

@@ -25,6 +25,32 @@ __device__ __forceinline__ cf cfma(cf a, cf b, cf c) {                          
 }
 __device__ __forceinline__ cf czero() { return make_float2(0.f, 0.f); }
 
+// complex128 overloads (same names) for the FP64 residual path
+typedef double2 zd;
+__device__ __forceinline__ zd cadd(zd a, zd b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ zd csub(zd a, zd b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ zd cmul(zd a, zd b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ zd cscale(zd a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ zd ctimesi(zd a) { return make_double2(-a.y, a.x); }
+__device__ __forceinline__ zd ctimesmi(zd a) { return make_double2(a.y, -a.x); }
+__device__ __forceinline__ zd cfma(zd a, zd b, zd c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+template <class C> struct CTraits;
+template <> struct CTraits<cf> {
+  using R = float;
+  static __device__ __forceinline__ cf zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ cf make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct CTraits<zd> {
+  using R = double;
+  static __device__ __forceinline__ zd zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ zd make(double a, double b) { return make_double2(a, b); }
+};
+
 // ------------------------------------------------------------ compile-time loops
 template <int B, int E, class F>
 __device__ __forceinline__ void static_for(F&& f) {
@@ -73,22 +99,23 @@ constexpr SinCos sincos2pi(long J, long N) {
 
 // a * exp(sign * 2 pi i J / N) with sign = -1 (forward) or +1 (INV); the
 // special angles become sign flips and swaps.
-template <int N, int J, bool INV>
-__device__ __forceinline__ cf twmul(cf a) {
+template <int N, int J, bool INV, class C>
+__device__ __forceinline__ C twmul(C a) {
+  using R = typename CTraits<C>::R;
   constexpr int j = ((J % N) + N) % N;
   if constexpr (j == 0) {
     return a;
   } else if constexpr (2 * j == N) {
-    return make_float2(-a.x, -a.y);
+    return CTraits<C>::make(-a.x, -a.y);
   } else if constexpr (4 * j == N) {
     return INV ? ctimesi(a) : ctimesmi(a);
   } else if constexpr (4 * j == 3 * N) {
     return INV ? ctimesmi(a) : ctimesi(a);
   } else {
     constexpr ct::SinCos sc = ct::sincos2pi(j, N);
-    constexpr float c = (float)sc.c;
-    constexpr float s = INV ? (float)sc.s : (float)(-sc.s);
-    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+    constexpr R c = (R)sc.c;
+    constexpr R s = INV ? (R)sc.s : (R)(-sc.s);
+    return CTraits<C>::make(a.x * c - a.y * s, a.x * s + a.y * c);
   }
 }
 
@@ -119,10 +146,15 @@ void psfd_count_launch();
 
 // Optional per-stage timing with CUDA events on the launching stream.
 enum { ST_AXIAL = 0, ST_CONTRAST = 1, ST_KRYLOV = 2, ST_TRANSFORM = 3, ST_FNO = 4, ST_N = 5 };
-void stage_mark(cudaStream_t s, int stage, bool begin);
+// `bytes` is the stage's algorithmic traffic: the compulsory reads and writes of its
+// inputs and outputs (intermediate passes of a multi-kernel stage are not counted).
+void stage_mark(cudaStream_t s, int stage, bool begin, double bytes = 0.0);
 struct StageScope {
   cudaStream_t s;
   int st;
-  StageScope(cudaStream_t s_, int st_) : s(s_), st(st_) { stage_mark(s, st, true); }
-  ~StageScope() { stage_mark(s, st, false); }
+  double bytes;
+  StageScope(cudaStream_t s_, int st_, double bytes_ = 0.0) : s(s_), st(st_), bytes(bytes_) {
+    stage_mark(s, st, true);
+  }
+  ~StageScope() { stage_mark(s, st, false, bytes); }
 };

@@ -12,45 +12,46 @@
 #include "common.cuh"
 
 // ------------------------------------------------------------ register DFTs
-template <int N, bool INV>
+template <int N, bool INV, class C = cf>
 struct DFT;
 
-template <bool INV>
-struct DFT<1, INV> {
-  static __device__ __forceinline__ void run(cf*) {}
+template <bool INV, class C>
+struct DFT<1, INV, C> {
+  static __device__ __forceinline__ void run(C*) {}
 };
 
-template <bool INV>
-struct DFT<2, INV> {
-  static __device__ __forceinline__ void run(cf* x) {
-    cf a = x[0], b = x[1];
+template <bool INV, class C>
+struct DFT<2, INV, C> {
+  static __device__ __forceinline__ void run(C* x) {
+    C a = x[0], b = x[1];
     x[0] = cadd(a, b);
     x[1] = csub(a, b);
   }
 };
 
-template <bool INV>
-struct DFT<3, INV> {
-  static __device__ __forceinline__ void run(cf* x) {
-    constexpr float h = 0.86602540378443864676f;  // sqrt(3)/2
-    cf a = x[0], b = x[1], c = x[2];
-    cf s = cadd(b, c);
-    cf d = csub(b, c);
-    cf m = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
-    cf r = INV ? make_float2(-h * d.y, h * d.x) : make_float2(h * d.y, -h * d.x);  // +-i h d
+template <bool INV, class C>
+struct DFT<3, INV, C> {
+  static __device__ __forceinline__ void run(C* x) {
+    using R = typename CTraits<C>::R;
+    constexpr R h = (R)0.86602540378443864676;  // sqrt(3)/2
+    C a = x[0], b = x[1], c = x[2];
+    C s = cadd(b, c);
+    C d = csub(b, c);
+    C m = CTraits<C>::make(a.x - (R)0.5 * s.x, a.y - (R)0.5 * s.y);
+    C r = INV ? CTraits<C>::make(-h * d.y, h * d.x) : CTraits<C>::make(h * d.y, -h * d.x);  // +-i h d
     x[0] = cadd(a, s);
     x[1] = cadd(m, r);
     x[2] = csub(m, r);
   }
 };
 
-template <bool INV>
-struct DFT<4, INV> {
-  static __device__ __forceinline__ void run(cf* x) {
-    cf a = x[0], b = x[1], c = x[2], d = x[3];
-    cf s0 = cadd(a, c), d0 = csub(a, c);
-    cf s1 = cadd(b, d), d1 = csub(b, d);
-    cf r = INV ? ctimesi(d1) : ctimesmi(d1);
+template <bool INV, class C>
+struct DFT<4, INV, C> {
+  static __device__ __forceinline__ void run(C* x) {
+    C a = x[0], b = x[1], c = x[2], d = x[3];
+    C s0 = cadd(a, c), d0 = csub(a, c);
+    C s1 = cadd(b, d), d1 = csub(b, d);
+    C r = INV ? ctimesi(d1) : ctimesmi(d1);
     x[0] = cadd(s0, s1);
     x[2] = csub(s0, s1);
     x[1] = cadd(d0, r);
@@ -59,30 +60,30 @@ struct DFT<4, INV> {
 };
 
 // Mixed-radix decimation in time: N = P * Q, P in {4, 2, 3}.
-template <int N, bool INV>
+template <int N, bool INV, class C>
 struct DFT {
   static constexpr int P = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 3);
   static constexpr int Q = N / P;
   static_assert(P * Q == N, "DFT size must be 2^a 3^b");
-  static __device__ __forceinline__ void run(cf* x) {
-    cf t[N];
+  static __device__ __forceinline__ void run(C* x) {
+    C t[N];
     static_for<0, P>([&](auto pp) {
       constexpr int p = decltype(pp)::value;
-      cf s[Q];
+      C s[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) s[q] = x[q * P + p];
-      DFT<Q, INV>::run(s);
+      DFT<Q, INV, C>::run(s);
 #pragma unroll
       for (int q = 0; q < Q; ++q) t[p * Q + q] = s[q];
     });
     static_for<0, Q>([&](auto kk) {
       constexpr int k = decltype(kk)::value;
-      cf u[P];
+      C u[P];
       static_for<0, P>([&](auto pp) {
         constexpr int p = decltype(pp)::value;
         u[p] = twmul<N, p * k, INV>(t[p * Q + k]);
       });
-      DFT<P, INV>::run(u);
+      DFT<P, INV, C>::run(u);
 #pragma unroll
       for (int m = 0; m < P; ++m) x[k + Q * m] = u[m];
     });
@@ -92,14 +93,14 @@ struct DFT {
 // ------------------------------------------------------------ warp pencils
 // LS: lane stride between the T lanes of one pencil (partner of lane bit b is
 // lane ^ (b * LS)).  tw: device table exp(-2 pi i m / N), m < N.
-template <int N, int T, int LS>
+template <int N, int T, int LS, class C = cf>
 struct Pencil {
   static constexpr int R = N / T;
   static constexpr int B = R / T;
   static_assert(T * R == N && (T == 1 || B * T == R), "pencil needs N = T*R with T | R");
 
   // all-to-all among the T lanes: slot (x, i) of lane t ends holding slot (t, i) of lane x
-  static __device__ __forceinline__ void all2all(cf* v, int t) {
+  static __device__ __forceinline__ void all2all(C* v, int t) {
     static_for<0, 5>([&](auto bb) {
       constexpr int b = 1 << decltype(bb)::value;
       if constexpr (b < T) {
@@ -110,8 +111,8 @@ struct Pencil {
 #pragma unroll
             for (int i = 0; i < B; ++i) {
               const int s0 = x0 * B + i, s1 = (x0 | b) * B + i;
-              cf send = tb ? v[s0] : v[s1];
-              cf got;
+              C send = tb ? v[s0] : v[s1];
+              C got;
               got.x = __shfl_xor_sync(0xffffffffu, send.x, b * LS);
               got.y = __shfl_xor_sync(0xffffffffu, send.y, b * LS);
               if (tb) v[s0] = got; else v[s1] = got;
@@ -123,11 +124,11 @@ struct Pencil {
   }
 
   template <bool INV>
-  static __device__ __forceinline__ void twiddle(cf* v, int t, const cf* __restrict__ tw) {
+  static __device__ __forceinline__ void twiddle(C* v, int t, const C* __restrict__ tw) {
     if constexpr (T > 1) {
 #pragma unroll
       for (int k = 1; k < R; ++k) {
-        cf w = __ldg(tw + t * k);   // t*k < T*R = N
+        C w = __ldg(tw + t * k);   // t*k < T*R = N
         if (INV) w.y = -w.y;
         v[k] = cmul(v[k], w);
       }
@@ -136,17 +137,17 @@ struct Pencil {
 
   // time layout -> freq layout
   template <bool INV>
-  static __device__ __forceinline__ void to_freq(cf* v, int t, const cf* __restrict__ tw) {
-    DFT<R, INV>::run(v);
+  static __device__ __forceinline__ void to_freq(C* v, int t, const C* __restrict__ tw) {
+    DFT<R, INV, C>::run(v);
     if constexpr (T > 1) {
       twiddle<INV>(v, t, tw);
       all2all(v, t);
 #pragma unroll
       for (int i = 0; i < B; ++i) {
-        cf u[T];
+        C u[T];
 #pragma unroll
         for (int x = 0; x < T; ++x) u[x] = v[x * B + i];
-        DFT<T, INV>::run(u);
+        DFT<T, INV, C>::run(u);
 #pragma unroll
         for (int x = 0; x < T; ++x) v[x * B + i] = u[x];
       }
@@ -155,21 +156,21 @@ struct Pencil {
 
   // freq layout -> time layout
   template <bool INV>
-  static __device__ __forceinline__ void to_time(cf* v, int t, const cf* __restrict__ tw) {
+  static __device__ __forceinline__ void to_time(C* v, int t, const C* __restrict__ tw) {
     if constexpr (T > 1) {
 #pragma unroll
       for (int i = 0; i < B; ++i) {
-        cf u[T];
+        C u[T];
 #pragma unroll
         for (int x = 0; x < T; ++x) u[x] = v[x * B + i];
-        DFT<T, INV>::run(u);
+        DFT<T, INV, C>::run(u);
 #pragma unroll
         for (int x = 0; x < T; ++x) v[x * B + i] = u[x];
       }
       all2all(v, t);
       twiddle<INV>(v, t, tw);
     }
-    DFT<R, INV>::run(v);
+    DFT<R, INV, C>::run(v);
   }
 
   // index helpers

@@ -14,6 +14,18 @@ struct ReflTables {
   cf* kz0 = nullptr;         // kz0 per mode (float)
 };
 
+struct Fp64Tables {
+  double* kx = nullptr;
+  double* ky = nullptr;
+  double* kz = nullptr;
+  double2* sinv = nullptr;
+  double2* twx = nullptr;
+  double2* twy = nullptr;
+  double2* twz = nullptr;
+  double2* G = nullptr;
+  size_t G_elems = 0;
+};
+
 struct psfd_plan_s {
   psfd_params_t p{};
   cudaStream_t stream = nullptr;
@@ -47,7 +59,15 @@ struct psfd_plan_s {
   int hist_cap = 0;
   // launch choices (set by the tuner)
   int axial_T = 0;
+  // FP64 residual path (built on first refined solve)
+  Fp64Tables F;
 };
+
+// apply64.cu
+int fp64_prepare(psfd_plan_s* P);
+void fp64_free(psfd_plan_s* P);
+int apply64_hybrid(psfd_plan_s* P, const double2* x, double2* y);
+int transform64(psfd_plan_s* P, double2* buf, long nplanes, bool forward, double scale);
 
 // apply.cu
 int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int nrhs_active);
@@ -59,6 +79,7 @@ int launch_cols(int n, int nx, cf* buf, long ncols_total, bool forward, float sc
                 cudaStream_t s);
 int launch_cols_gauss(int ny, int nx, cf* buf, float sigma, const cf* tw, cudaStream_t s);
 int axial_supported(int nz);
+int axial_candidates(int nz, int* out);
 int lateral_supported(int n);
 
 // plan.cu

@@ -9,6 +9,7 @@
 // which gives twice-float accuracy per thread; the per-thread results are then
 // summed in FP64 in a fixed order (warp tree, block tree, blocks in index
 // order by the last block to finish), so results are reproducible run to run.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -28,21 +29,25 @@ struct KScal {
   double tol2;
 };
 
+// Per-thread compensated accumulator: Kahan summation of the rounded products
+// p = fl(a b) plus a separate sum of their exact rounding errors fma(a, b, -p).
+// Error of a partial: about 2u * sum|p| (u = 2^-24), far below float rounding of
+// a plain sum; partials are then summed in FP64.
 struct Acc2 {
-  float s, c;
+  float s, c, e;
 };
 
-__device__ __forceinline__ void acc_add(Acc2& A, float p, float ep) {
-  const float s = __fadd_rn(A.s, p);
-  const float bb = __fsub_rn(s, A.s);
-  const float e = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  A.s = s;
-  A.c = __fadd_rn(A.c, __fadd_rn(e, ep));
-}
 __device__ __forceinline__ void acc_prod(Acc2& A, float a, float b) {
   const float p = __fmul_rn(a, b);
   const float ep = fmaf(a, b, -p);
-  acc_add(A, p, ep);
+  const float y = __fsub_rn(p, A.c);
+  const float t = __fadd_rn(A.s, y);
+  A.c = __fsub_rn(__fsub_rn(t, A.s), y);
+  A.s = t;
+  A.e = __fadd_rn(A.e, ep);
+}
+__device__ __forceinline__ double acc_value(const Acc2& A) {
+  return (double)A.s - (double)A.c + (double)A.e;
 }
 // re/im of conj(a) * b
 __device__ __forceinline__ void acc_cdot(Acc2& re, Acc2& im, cf a, cf b) {
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   const long stride = (long)gridDim.x * blockDim.x;
   Acc2 acc[kMaxQ];
 #pragma unroll
-  for (int q = 0; q < kMaxQ; ++q) acc[q] = {0.f, 0.f};
+  for (int q = 0; q < kMaxQ; ++q) acc[q] = {0.f, 0.f, 0.f};
 
   cf beta = czero(), omg = czero(), alp = czero();
   if constexpr (OP == OK_P) {
@@ -178,7 +183,11 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   if constexpr (OP == OK_S || OP == OK_XR) alp = zf(S->alpha);
   if constexpr (OP == OK_XR) omg = zf(S->omega);
 
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+  // two independent elements per iteration (separate accumulators) for memory-level parallelism
+  Acc2 accB[kMaxQ];
+#pragma unroll
+  for (int q = 0; q < kMaxQ; ++q) accB[q] = {0.f, 0.f, 0.f};
+  auto body = [&](long i, Acc2* A) {
     const long e = off / 2 + i;
     if constexpr (OP == OK_INIT) {
       // v0 = r, v1 = rhat, v2 = p, v3 = v, v4 = y
@@ -188,8 +197,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       reinterpret_cast<float4*>(a.v2)[e] = z;
       reinterpret_cast<float4*>(a.v3)[e] = z;
       reinterpret_cast<float4*>(a.v4)[e] = z;
-      acc_cdot(acc[0], acc[1], make_float2(r.x, r.y), make_float2(r.x, r.y));
-      acc_cdot(acc[0], acc[1], make_float2(r.z, r.w), make_float2(r.z, r.w));
+      acc_cdot(A[0], A[1], make_float2(r.x, r.y), make_float2(r.x, r.y));
+      acc_cdot(A[0], A[1], make_float2(r.z, r.w), make_float2(r.z, r.w));
     } else if constexpr (OP == OK_P) {
       // v0 = p (in/out), v1 = r, v2 = v
       const float4 pp = reinterpret_cast<const float4*>(a.v0)[e];
@@ -205,8 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       // v0 = rhat, v1 = v
       const float4 h = reinterpret_cast<const float4*>(a.v0)[e];
       const float4 v = reinterpret_cast<const float4*>(a.v1)[e];
-      acc_cdot(acc[0], acc[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
-      acc_cdot(acc[0], acc[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
+      acc_cdot(A[0], A[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
+      acc_cdot(A[0], A[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
     } else if constexpr (OP == OK_S) {
       // v0 = s (out), v1 = r, v2 = v
       const float4 rr = reinterpret_cast<const float4*>(a.v1)[e];
@@ -219,10 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       const float4 tt = reinterpret_cast<const float4*>(a.v0)[e];
       const float4 ss = reinterpret_cast<const float4*>(a.v1)[e];
       cf t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
-      acc_cdot(acc[0], acc[1], t0, make_float2(ss.x, ss.y));
-      acc_cdot(acc[0], acc[1], t1, make_float2(ss.z, ss.w));
-      acc_cdot(acc[2], acc[3], t0, t0);
-      acc_cdot(acc[2], acc[3], t1, t1);
+      acc_cdot(A[0], A[1], t0, make_float2(ss.x, ss.y));
+      acc_cdot(A[0], A[1], t1, make_float2(ss.z, ss.w));
+      acc_cdot(A[2], A[3], t0, t0);
+      acc_cdot(A[2], A[3], t1, t1);
     } else if constexpr (OP == OK_XR) {
       // v0 = y, v1 = r (out), v2 = p, v3 = s, v4 = t, v5 = rhat
       const float4 yy = reinterpret_cast<const float4*>(a.v0)[e];
@@ -239,34 +248,38 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       cf r1 = csub(s1, cmul(omg, make_float2(tt.z, tt.w)));
       reinterpret_cast<float4*>(a.v0)[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
       reinterpret_cast<float4*>(a.v1)[e] = make_float4(r0.x, r0.y, r1.x, r1.y);
-      acc_cdot(acc[0], acc[1], make_float2(hh.x, hh.y), r0);
-      acc_cdot(acc[0], acc[1], make_float2(hh.z, hh.w), r1);
-      acc_cdot(acc[2], acc[3], r0, r0);
-      acc_cdot(acc[2], acc[3], r1, r1);
+      acc_cdot(A[0], A[1], make_float2(hh.x, hh.y), r0);
+      acc_cdot(A[0], A[1], make_float2(hh.z, hh.w), r1);
+      acc_cdot(A[2], A[3], r0, r0);
+      acc_cdot(A[2], A[3], r1, r1);
     } else if constexpr (OP == OK_NORM) {
       const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
-      acc_cdot(acc[0], acc[1], make_float2(x.x, x.y), make_float2(x.x, x.y));
-      acc_cdot(acc[0], acc[1], make_float2(x.z, x.w), make_float2(x.z, x.w));
+      acc_cdot(A[0], A[1], make_float2(x.x, x.y), make_float2(x.x, x.y));
+      acc_cdot(A[0], A[1], make_float2(x.z, x.w), make_float2(x.z, x.w));
     } else if constexpr (OP == OK_SUB) {
       // v2 = v0 - v1
       const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
       const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
       const float4 c = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
       reinterpret_cast<float4*>(a.v2)[e] = c;
-      acc_cdot(acc[0], acc[1], make_float2(c.x, c.y), make_float2(c.x, c.y));
-      acc_cdot(acc[0], acc[1], make_float2(c.z, c.w), make_float2(c.z, c.w));
+      acc_cdot(A[0], A[1], make_float2(c.x, c.y), make_float2(c.x, c.y));
+      acc_cdot(A[0], A[1], make_float2(c.z, c.w), make_float2(c.z, c.w));
     } else if constexpr (OP == OK_AXPY) {
       const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
       const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
       reinterpret_cast<float4*>(a.v2)[e] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
     }
+    };
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    body(i, acc);
+    if (i + stride < n2) body(i + stride, accB);
   }
 
   constexpr int NQ = (OP == OK_TS || OP == OK_XR) ? 4 : ((OP == OK_INIT || OP == OK_RV || OP == OK_NORM || OP == OK_SUB) ? 2 : 0);
   if constexpr (NQ > 0) {
     double val[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) val[q] = (double)acc[q].s + (double)acc[q].c;
+    for (int q = 0; q < NQ; ++q) val[q] = acc_value(acc[q]) + acc_value(accB[q]);
     double tot[NQ];
     if (!reduce_finish<NQ>(val, a.partials, a.counters, tot)) return;
     if (threadIdx.x != 0) return;
@@ -319,9 +332,15 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   }
 }
 
+// compulsory complex64 vector passes (reads + writes) of each vector kernel
+constexpr int vec_passes(int op) {
+  return op == OK_INIT ? 5 : op == OK_P ? 4 : op == OK_RV ? 2 : op == OK_S ? 3 : op == OK_TS ? 2
+       : op == OK_XR ? 7 : op == OK_NORM ? 1 : op == OK_SUB ? 3 : 3;
+}
+
 template <int OP>
 int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
-  StageScope sc(s, ST_KRYLOV);
+  StageScope sc(s, ST_KRYLOV, (double)vec_passes(OP) * nrhs * a.n * sizeof(cf));
   dim3 grid((unsigned)nblocks, (unsigned)nrhs);
   k_vec<OP><<<grid, kThreads, 0, s>>>(a);
   PSFD_CHECK_LAUNCH();
@@ -380,38 +399,56 @@ struct GArgs {
 // mask: nonzero = skip this right-hand side (same convention as the operator kernels)
 __device__ __forceinline__ bool skip_rhs(const GArgs& a, int rhs) { return a.mask && a.mask[rhs]; }
 
-// h[i] = <V_i, w>, i in [chunk*GCH, min(nv, chunk*GCH+GCH))
+// h[i] = <V_i, w>, i in [chunk*GCH, min(nv, chunk*GCH+GCH)).  Per-thread partial sums are
+// plain float over ~20 elements (two interleaved accumulators), summed in FP64 across
+// threads and blocks; a second Gram-Schmidt pass is taken whenever the first one
+// cancels more than half of ||w||^2, which also absorbs the rounding of these partials.
 __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
   const int rhs = blockIdx.y, chunk = blockIdx.z;
   if (skip_rhs(a, rhs)) return;
   const int i0 = chunk * GCH;
   const int nq = min(GCH, a.nv - i0);
   if (nq <= 0) return;
-  Acc2 acc[2 * GCH];
+  float sr[GCH], si[GCH];
 #pragma unroll
-  for (int q = 0; q < 2 * GCH; ++q) acc[q] = {0.f, 0.f};
+  for (int q = 0; q < GCH; ++q) { sr[q] = 0.f; si[q] = 0.f; }
   const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
   const float4* w4 = reinterpret_cast<const float4*>(a.w);
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
     const float4 wv = w4[off2 + i];
-    const cf w0 = make_float2(wv.x, wv.y), w1 = make_float2(wv.z, wv.w);
 #pragma unroll
     for (int q = 0; q < GCH; ++q) {
       if (q < nq) {
         const float4 vv = reinterpret_cast<const float4*>(a.V + (i0 + q) * a.vs)[off2 + i];
-        acc_cdot(acc[2 * q], acc[2 * q + 1], make_float2(vv.x, vv.y), w0);
-        acc_cdot(acc[2 * q], acc[2 * q + 1], make_float2(vv.z, vv.w), w1);
+        // conj(v) * w for the two complex entries
+        sr[q] = fmaf(vv.x, wv.x, fmaf(vv.y, wv.y, fmaf(vv.z, wv.z, fmaf(vv.w, wv.w, sr[q]))));
+        si[q] = fmaf(vv.x, wv.y, fmaf(-vv.y, wv.x, fmaf(vv.z, wv.w, fmaf(-vv.w, wv.z, si[q]))));
       }
     }
   }
   double val[2 * GCH];
 #pragma unroll
-  for (int q = 0; q < 2 * GCH; ++q) val[q] = (double)acc[q].s + (double)acc[q].c;
+  for (int q = 0; q < GCH; ++q) { val[2 * q] = (double)sr[q]; val[2 * q + 1] = (double)si[q]; }
   double tot[2 * GCH];
   double* pbase = a.partials + ((long)rhs * gridDim.z + chunk) * gridDim.x * (2 * GCH);
   if (!reduce_group<2 * GCH, 2 * GCH>(val, pbase, a.counters + rhs * gridDim.z + chunk, tot)) return;
   if (threadIdx.x == 0)
     for (int q = 0; q < nq; ++q) a.hout[rhs * GMAX + i0 + q] = make_double2(tot[2 * q], tot[2 * q + 1]);
+}
+
+// per rhs: keep the norm of w before orthogonalisation (res0 -> tt), zero the second-pass
+// coefficients, and after the first pass decide whether a second one is needed
+__global__ void k_gsave(KScal* sc, double2* h2, int nrhs, int nv) {
+  const int r = blockIdx.x;
+  if (r >= nrhs) return;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) h2[r * GMAX + i] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) sc[r].tt = sc[r].res0;
+}
+__global__ void k_greorth(const KScal* sc, const int* skip, int* skip2, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  // second pass when ||w_after||^2 < ||w_before||^2 / 2 (Daniel-Gragg-Kaufman-Stewart, eta = 1/sqrt(2))
+  skip2[r] = (skip && skip[r]) || !(sc[r].res0 < 0.5 * sc[r].tt);
 }
 
 // w -= sum_i h[i] V_i  (h from hout)   or   y += sum_i z[i] V_i (ADD, count jd per rhs)
@@ -562,6 +599,7 @@ struct SolveWs {
   KScal* sc;
   int* done;
   int* active;
+  int* skip2;
   double* partials;
   unsigned* counters;
   GState* gs;
@@ -598,6 +636,7 @@ static size_t ws_layout(psfd_plan_s* P, int method, int restart, SolveWs* w, cha
   w->sc = (KScal*)take(sizeof(KScal) * nr);
   w->done = (int*)take(sizeof(int) * nr);
   w->active = (int*)take(sizeof(int) * nr);
+  w->skip2 = (int*)take(sizeof(int) * nr);
   w->partials = (double*)take(sizeof(double) * (size_t)nr * nb * (gm ? nch * 2 * GCH : kMaxQ));
   w->counters = (unsigned*)take(sizeof(unsigned) * nr * (gm ? nch : 1));
   w->gs = gm ? (GState*)take(sizeof(GState) * nr) : nullptr;
@@ -693,18 +732,37 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
       if ((rc = apply_hybrid(P, Vj, Wn, aflags, w.active))) return rc;
       g.w = Wn; g.nv = j + 1; g.j = j;
       const int nch = (j + 1 + GCH - 1) / GCH;
-      for (int pass = 0; pass < 2; ++pass) {
-        g.hout = pass == 0 ? w.h1 : w.h2;
-        StageScope sc(st, ST_KRYLOV);
+      va.v0 = Wn;
+      va.done = w.active;  // w.active holds the skip flags here
+      va.use_done = true;
+      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 before
+      k_gsave<<<nr, 64, 0, st>>>(w.sc, w.h2, nr, j + 1);
+      PSFD_CHECK_LAUNCH();
+      {
+        // dot: read w + (j+1) basis vectors; update: read (j+1) + read/write w
+        StageScope sc(st, ST_KRYLOV, (2.0 * (j + 1) + 3.0) * nr * n * sizeof(cf));
+        g.hout = w.h1;
         k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
         k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
       }
-      va.v0 = Wn;
-      va.done = w.active;  // w.active holds the skip flags here
-      va.use_done = true;
-      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;
+      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 after pass 1
+      k_greorth<<<1, tpb, 0, st>>>(w.sc, w.active, w.skip2, nr);
+      PSFD_CHECK_LAUNCH();
+      {
+        StageScope sc(st, ST_KRYLOV, 0.0);   // second pass: data-dependent, not counted as algorithmic
+        const int* keep = g.mask;
+        g.mask = w.skip2;
+        g.hout = w.h2;
+        k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
+        PSFD_CHECK_LAUNCH();
+        k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+        PSFD_CHECK_LAUNCH();
+        g.mask = keep;
+      }
+      va.done = w.skip2;
+      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 after pass 2 (if taken)
       va.done = w.done;
       va.use_done = false;
       k_givens<<<1, tpb, 0, st>>>(w.gs, w.h1, w.h2, w.sc, w.active, va.hist, va.hist_cap, nr, j);
@@ -837,7 +895,250 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
     info[r].r_rel = bn > 0 ? sqrt(hs[r].res1 / bn) : 0.0;
     info[r].r_rel_recursive = bn > 0 ? sqrt(hs[r].rr / bn) : 0.0;
     info[r].r_rel_initial = bn > 0 ? sqrt(hs[r].rr0 / bn) : 0.0;
+    info[r].outer = 0;
+    info[r].r_rel_output = info[r].r_rel;
     if (info[r].status != PSFD_OK && worst == PSFD_OK) worst = info[r].status;
+  }
+  if (own) PSFD_CUDA_TRY(cudaFreeAsync(base, st));
+  return worst;
+}
+
+// ======================================================================= mixed-precision refinement
+// Outer loop in FP64:  r = b - A E (FP64 operator apply, FP64 field E),
+// inner complex64 Krylov solve of A M d = r to a relative tolerance, E += M d.
+namespace {
+
+enum { V64_PROMOTE = 0, V64_RES = 1, V64_CAST = 2, V64_ADD = 3, V64_NORM = 4 };
+
+struct V64Args {
+  const zd* a64;
+  zd* o64;
+  const cf* a32;
+  cf* o32;
+  const zd* b64;
+  long n;
+  KScal* sc;
+  const int* skip;   // V64_CAST: write zero for rhs with skip != 0
+  double* partials;
+  unsigned* counters;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) k_v64(V64Args a) {
+  const int rhs = blockIdx.y;
+  const long off = (long)rhs * a.n;
+  const long stride = (long)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  const bool zero = (OP == V64_CAST) && a.skip && a.skip[rhs];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const long e = off + i;
+    if constexpr (OP == V64_PROMOTE) {
+      const cf x = a.a32[e];
+      a.o64[e] = make_double2((double)x.x, (double)x.y);
+    } else if constexpr (OP == V64_RES) {
+      const zd b = a.b64[e], v = a.a64[e];
+      const zd r = make_double2(b.x - v.x, b.y - v.y);
+      a.o64[e] = r;
+      acc = fma(r.x, r.x, fma(r.y, r.y, acc));
+    } else if constexpr (OP == V64_CAST) {
+      const zd x = a.a64[e];
+      a.o32[e] = zero ? czero() : make_float2((float)x.x, (float)x.y);
+    } else if constexpr (OP == V64_ADD) {
+      const cf d = a.a32[e];
+      zd x = a.o64[e];
+      x.x += (double)d.x;
+      x.y += (double)d.y;
+      a.o64[e] = x;
+    } else {
+      const zd x = a.a64[e];
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+  }
+  if constexpr (OP == V64_RES || OP == V64_NORM) {
+    double val[2] = {acc, 0.0};
+    double tot[2];
+    if (!reduce_finish<2>(val, a.partials, a.counters, tot)) return;
+    if (threadIdx.x == 0) {
+      if (OP == V64_RES) a.sc[rhs].res1 = tot[0];
+      else a.sc[rhs].res0 = tot[0];
+    }
+  }
+}
+
+template <int OP>
+int launch_v64(const V64Args& a, int nrhs, cudaStream_t s, int nb) {
+  StageScope sc(s, ST_KRYLOV);
+  k_v64<OP><<<dim3(nb, nrhs), kThreads, 0, s>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+}  // namespace
+
+static size_t refine_extra_bytes(psfd_plan_s* P) {
+  return 3 * align256((size_t)P->nrhs * P->nvec * sizeof(zd));
+}
+
+extern "C" size_t psfd_solve_ex_workspace_size(psfd_plan P, const psfd_solve_opts_t* o) {
+  if (!P || !o) return 0;
+  SolveWs w;
+  size_t base = ws_layout(P, o->method, o->restart, &w, nullptr);
+  return base + (o->refine ? refine_extra_bytes(P) : 0);
+}
+
+extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E,
+                             const psfd_solve_opts_t* o, psfd_info_t* info, void* workspace,
+                             size_t workspace_bytes) {
+  if (!P || !b || !E || !info || !o) { psfd_set_error("psfd_solve_ex: null argument"); return PSFD_ERR_ARG; }
+  if (!o->refine) {
+    int rc = psfd_solve(P, b, x0, E, o->tol, o->maxit, o->method, o->restart, o->use_precond, info, workspace,
+                        workspace_bytes);
+    for (int r = 0; r < P->nrhs; ++r) { info[r].outer = 0; info[r].r_rel_output = info[r].r_rel; }
+    return rc;
+  }
+  if (!P->have_background) { psfd_set_error("psfd_solve_ex: call psfd_background first"); return PSFD_ERR_STATE; }
+  if (!(o->tol > 0) || o->maxit < 0 || !(o->inner_tol > 0 && o->inner_tol < 1)) {
+    psfd_set_error("psfd_solve_ex: bad tol / inner_tol / maxit");
+    return PSFD_ERR_ARG;
+  }
+  if (o->method != PSFD_BICGSTAB && o->method != PSFD_GMRES) { psfd_set_error("psfd_solve_ex: unknown method"); return PSFD_ERR_ARG; }
+  if (o->method == PSFD_GMRES && (o->restart < 1 || o->restart > GMAX)) {
+    psfd_set_error("psfd_solve_ex: GMRES restart must be in [1, %d]", GMAX);
+    return PSFD_ERR_ARG;
+  }
+  int rc = fp64_prepare(P);
+  if (rc) return rc;
+  cudaStream_t st = P->stream;
+  SolveWs w;
+  const size_t base_need = ws_layout(P, o->method, o->restart, &w, nullptr);
+  const size_t need = base_need + refine_extra_bytes(P);
+  char* base = (char*)workspace;
+  bool own = false;
+  if (!base) {
+    PSFD_CUDA_TRY(cudaMallocAsync((void**)&base, need, st));
+    own = true;
+  } else if (workspace_bytes < need) {
+    psfd_set_error("psfd_solve_ex: workspace too small (%zu < %zu)", workspace_bytes, need);
+    return PSFD_ERR_ARG;
+  }
+  ws_layout(P, o->method, o->restart, &w, base);
+  const size_t v64b = align256((size_t)P->nrhs * P->nvec * sizeof(zd));
+  zd* b64 = (zd*)(base + base_need);
+  zd* E64 = (zd*)(base + base_need + v64b);
+  zd* r64 = (zd*)(base + base_need + 2 * v64b);
+  const int nr = P->nrhs;
+  const long n = P->nvec;
+  const size_t vbytes = (size_t)nr * n * sizeof(cf);
+  const int nb = nblocks_for(n);
+  const long nplanes = (long)nr * 3 * P->nz;
+  const double us = 1.0 / sqrt((double)P->ncols);
+  const unsigned tpb = 32 * ((nr + 31) / 32);
+  auto fail = [&](int code) { if (own) cudaFreeAsync(base, st); return code; };
+
+  const int nch_max = (GMAX + GCH - 1) / GCH;
+  PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr * (o->method == PSFD_GMRES ? nch_max : 1), st));
+  k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, 0.0, 0);
+  PSFD_CHECK_LAUNCH();
+  V64Args a64{};
+  a64.n = n; a64.sc = w.sc; a64.partials = w.partials; a64.counters = w.counters;
+  // b (complex64, real space) -> FP64 HYBRID
+  a64.a32 = (const cf*)b; a64.o64 = b64;
+  if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
+  if ((rc = transform64(P, b64, nplanes, true, us))) return fail(rc);
+  a64.a64 = b64;
+  if ((rc = launch_v64<V64_NORM>(a64, nr, st, nb))) return fail(rc);
+  std::vector<KScal> hs(nr);
+  PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> bnorm2(nr), rr(nr, 0.0), rr0(nr, 0.0);
+  for (int r = 0; r < nr; ++r) bnorm2[r] = hs[r].res0;
+  // E64 = x0 (HYBRID, FP64) or 0
+  if (x0) {
+    a64.a32 = (const cf*)x0; a64.o64 = E64;
+    if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
+    if ((rc = transform64(P, E64, nplanes, true, us))) return fail(rc);
+  } else {
+    PSFD_CUDA_TRY(cudaMemsetAsync(E64, 0, (size_t)nr * n * sizeof(zd), st));
+  }
+  std::vector<int> conv(nr, 0), status(nr, PSFD_NOT_CONVERGED), inner_its(nr, 0);
+  int* dskip = w.active;  // reused as the per-rhs "outer converged" flag
+  int outer = 0;
+  const int max_outer = o->max_outer > 0 ? o->max_outer : 100;
+  const int aflags = o->use_precond ? PSFD_PRECOND : 0;
+  VArgs va{};
+  va.n = n; va.sc = w.sc; va.done = w.done; va.partials = w.partials; va.counters = w.counters;
+  for (;; ++outer) {
+    // r = b - A E in FP64
+    if ((rc = apply64_hybrid(P, E64, r64))) return fail(rc);
+    a64.b64 = b64; a64.a64 = r64; a64.o64 = r64;
+    if ((rc = launch_v64<V64_RES>(a64, nr, st, nb))) return fail(rc);
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    int total_max = 0;
+    for (int r = 0; r < nr; ++r) {
+      rr[r] = hs[r].res1;
+      if (outer == 0) rr0[r] = rr[r];
+      if (bnorm2[r] == 0.0 || rr[r] <= o->tol * o->tol * bnorm2[r]) { conv[r] = 1; status[r] = PSFD_OK; }
+      else if (!std::isfinite(rr[r])) { conv[r] = 1; status[r] = PSFD_ERR_BREAKDOWN; }
+      else if (inner_its[r] >= o->maxit || outer >= max_outer) { conv[r] = 1; status[r] = PSFD_NOT_CONVERGED; }
+      all = all && conv[r];
+      total_max = std::max(total_max, inner_its[r]);
+    }
+    if (all) break;
+    PSFD_CUDA_TRY(cudaMemcpyAsync(dskip, conv.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    a64.a64 = r64; a64.o32 = w.r; a64.skip = dskip;
+    if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
+    // inner complex64 solve of A M y = r to inner_tol (relative to ||r||)
+    const int inner_max = std::max(1, o->maxit - total_max);
+    k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, o->inner_tol * o->inner_tol, inner_max);
+    PSFD_CHECK_LAUNCH();
+    va.use_done = false;
+    va.v0 = w.r;
+    if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return fail(rc);
+    k_copy_bnorm<<<1, tpb, 0, st>>>(w.sc, nr);
+    PSFD_CHECK_LAUNCH();
+    if (o->method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, inner_max, aflags, nb);
+    else rc = gmres_loop(P, w, va, o->inner_tol, inner_max, o->restart, aflags, nb);
+    if (rc) return fail(rc);
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int r = 0; r < nr; ++r)
+      if (!conv[r]) inner_its[r] += hs[r].iters;
+    // E += M y
+    cf* My = w.t;
+    if (o->use_precond) {
+      if ((rc = launch_axial(P, w.y, My, 2, nullptr, nr))) return fail(rc);
+    } else {
+      PSFD_CUDA_TRY(cudaMemcpyAsync(My, w.y, vbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    a64.a32 = My; a64.o64 = E64;
+    if ((rc = launch_v64<V64_ADD>(a64, nr, st, nb))) return fail(rc);
+  }
+  // output: E = complex64(F^-1 E64), transformed in FP64
+  PSFD_CUDA_TRY(cudaMemcpyAsync(r64, E64, (size_t)nr * n * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+  if ((rc = transform64(P, r64, nplanes, false, us))) return fail(rc);
+  a64.a64 = r64; a64.o32 = (cf*)E; a64.skip = nullptr;
+  if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
+  // FP64 residual of the returned complex64 field
+  a64.a32 = (const cf*)E; a64.o64 = r64;
+  if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
+  if ((rc = transform64(P, r64, nplanes, true, us))) return fail(rc);
+  if ((rc = apply64_hybrid(P, r64, E64))) return fail(rc);
+  a64.b64 = b64; a64.a64 = E64; a64.o64 = E64;
+  if ((rc = launch_v64<V64_RES>(a64, nr, st, nb))) return fail(rc);
+  PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+  int worst = PSFD_OK;
+  for (int r = 0; r < nr; ++r) {
+    info[r].iters = inner_its[r];
+    info[r].status = status[r];
+    info[r].outer = outer;
+    info[r].r_rel = bnorm2[r] > 0 ? sqrt(rr[r] / bnorm2[r]) : 0.0;
+    info[r].r_rel_recursive = info[r].r_rel;
+    info[r].r_rel_initial = bnorm2[r] > 0 ? sqrt(rr0[r] / bnorm2[r]) : 0.0;
+    info[r].r_rel_output = bnorm2[r] > 0 ? sqrt(hs[r].res1 / bnorm2[r]) : 0.0;
+    if (status[r] != PSFD_OK && worst == PSFD_OK) worst = status[r];
   }
   if (own) PSFD_CUDA_TRY(cudaFreeAsync(base, st));
   return worst;

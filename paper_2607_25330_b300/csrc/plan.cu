@@ -22,6 +22,7 @@ namespace {
 struct StageRec {
   int stage;
   cudaEvent_t a, b;
+  double bytes;
 };
 std::mutex g_tmu;
 bool g_timing = false;
@@ -29,6 +30,7 @@ std::vector<StageRec> g_open[ST_N];   // begun, not yet ended (stack per stage)
 std::vector<StageRec> g_done;
 std::vector<cudaEvent_t> g_pool;
 double g_ms[ST_N];
+double g_bytes[ST_N];
 long long g_calls[ST_N];
 
 cudaEvent_t ev_get() {
@@ -45,6 +47,7 @@ void harvest(bool wait) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, r.a, r.b);
       g_ms[r.stage] += ms;
+      g_bytes[r.stage] += r.bytes;
       g_calls[r.stage] += 1;
       g_pool.push_back(r.a);
       g_pool.push_back(r.b);
@@ -56,17 +59,18 @@ void harvest(bool wait) {
 }
 }  // namespace
 
-void stage_mark(cudaStream_t s, int stage, bool begin) {
+void stage_mark(cudaStream_t s, int stage, bool begin, double bytes) {
   if (!g_timing) return;
   std::lock_guard<std::mutex> lk(g_tmu);
   if (begin) {
-    StageRec r{stage, ev_get(), nullptr};
+    StageRec r{stage, ev_get(), nullptr, 0.0};
     cudaEventRecord(r.a, s);
     g_open[stage].push_back(r);
   } else if (!g_open[stage].empty()) {
     StageRec r = g_open[stage].back();
     g_open[stage].pop_back();
     r.b = ev_get();
+    r.bytes = bytes;
     cudaEventRecord(r.b, s);
     g_done.push_back(r);
     if (g_done.size() > 4096) harvest(true);
@@ -76,17 +80,22 @@ void stage_mark(cudaStream_t s, int stage, bool begin) {
 extern "C" int psfd_timing_enable(int on) {
   std::lock_guard<std::mutex> lk(g_tmu);
   harvest(true);
-  for (int i = 0; i < ST_N; ++i) { g_ms[i] = 0; g_calls[i] = 0; g_open[i].clear(); }
+  for (int i = 0; i < ST_N; ++i) { g_ms[i] = 0; g_bytes[i] = 0; g_calls[i] = 0; g_open[i].clear(); }
   g_timing = on != 0;
   return PSFD_OK;
 }
 
 extern "C" int psfd_timing_read(double* ms, long long* calls, int nstages) {
+  return psfd_timing_read_bytes(ms, calls, nullptr, nstages);
+}
+
+extern "C" int psfd_timing_read_bytes(double* ms, long long* calls, double* bytes, int nstages) {
   std::lock_guard<std::mutex> lk(g_tmu);
   harvest(true);
   for (int i = 0; i < nstages && i < ST_N; ++i) {
     if (ms) ms[i] = g_ms[i];
     if (calls) calls[i] = g_calls[i];
+    if (bytes) bytes[i] = g_bytes[i];
   }
   return PSFD_OK;
 }
@@ -221,44 +230,48 @@ struct SourceArgs {
   int pol;
 };
 
+// grid: (ceil(ncols / blockDim), nz); the z-only factors are computed once per block
 __global__ void k_source(SourceArgs a) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long n = a.ncols * a.nz;
-  if (i >= n) return;
-  int z = (int)(i / a.ncols);
-  double f = a.fill[i];
-  double k02 = a.k0 * a.k0;
-  cd de = {f * a.deps_re * k02, f * a.deps_im * k02};
-  // polarisation vector and wave vector of the incident wave
-  double st = sin(a.theta), ctt = cos(a.theta), sp = sin(a.phi), cp = cos(a.phi);
-  double e[3];
-  if (a.pol == 0) { e[0] = -sp; e[1] = cp; e[2] = 0.0; }
-  else { e[0] = ctt * cp; e[1] = ctt * sp; e[2] = st; }
-  double kx = a.k0 * st * cp, ky = a.k0 * st * sp;
-  double kpar = sqrt(kx * kx + ky * ky);
-  double sx, sy, tx, ty;
-  if (kpar < 1e-12 * a.k0) { sx = 0; sy = 1; tx = 1; ty = 0; }
-  else { sx = -ky / kpar; sy = kx / kpar; tx = kx / kpar; ty = ky / kpar; }
-  cd rs = {a.rs64[0].x, a.rs64[0].y}, rp = {a.rp64[0].x, a.rp64[0].y};
-  cd kz0 = {a.kz064[0].x, a.kz064[0].y};
-  double as = sx * e[0] + sy * e[1], at = tx * e[0] + ty * e[1];
-  cd r0 = as * sx * rs + at * tx * rp;
-  cd r1 = as * sy * rs + at * ty * rp;
-  cd r2 = cdiv(cd_(-1, 0) * (kx * r0 + ky * r1), kz0);
-  double zr = (z - a.z_ml) * a.dz;
-  double kzi = a.k0 * ctt;
-  cd einc = {cos(kzi * zr), -sin(kzi * zr)};
-  cd prof = {0, 0};
-  if (zr >= 0) {
-    double mag = exp(-kz0.im * zr);
-    prof = {mag * cos(kz0.re * zr), mag * sin(kz0.re * zr)};
+  __shared__ double f_tot[6];   // (re, im) of E_inc + R E_inc for the three components at this z
+  const int z = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double st = sin(a.theta), ctt = cos(a.theta), sp = sin(a.phi), cp = cos(a.phi);
+    double e[3];
+    if (a.pol == 0) { e[0] = -sp; e[1] = cp; e[2] = 0.0; }
+    else { e[0] = ctt * cp; e[1] = ctt * sp; e[2] = st; }
+    double kx = a.k0 * st * cp, ky = a.k0 * st * sp;
+    double kpar = sqrt(kx * kx + ky * ky);
+    double sx, sy, tx, ty;
+    if (kpar < 1e-12 * a.k0) { sx = 0; sy = 1; tx = 1; ty = 0; }
+    else { sx = -ky / kpar; sy = kx / kpar; tx = kx / kpar; ty = ky / kpar; }
+    cd rs = {a.rs64[0].x, a.rs64[0].y}, rp = {a.rp64[0].x, a.rp64[0].y};
+    cd kz0 = {a.kz064[0].x, a.kz064[0].y};
+    double as = sx * e[0] + sy * e[1], at = tx * e[0] + ty * e[1];
+    cd r0 = as * sx * rs + at * tx * rp;
+    cd r1 = as * sy * rs + at * ty * rp;
+    cd r2 = cdiv(cd_(-1, 0) * (kx * r0 + ky * r1), kz0);
+    double zr = (z - a.z_ml) * a.dz;
+    double kzi = a.k0 * ctt;
+    cd einc = {cos(kzi * zr), -sin(kzi * zr)};
+    cd prof = {0, 0};
+    if (zr >= 0) {
+      double mag = exp(-kz0.im * zr);
+      prof = {mag * cos(kz0.re * zr), mag * sin(kz0.re * zr)};
+    }
+    cd tot[3] = {e[0] * einc + r0 * prof, e[1] * einc + r1 * prof, e[2] * einc + r2 * prof};
+    for (int c = 0; c < 3; ++c) { f_tot[2 * c] = tot[c].re; f_tot[2 * c + 1] = tot[c].im; }
   }
-  cd tot[3] = {e[0] * einc + r0 * prof, e[1] * einc + r1 * prof, e[2] * einc + r2 * prof};
-  long plane = a.ncols * a.nz;
-  long xy = i % a.ncols;
+  __syncthreads();
+  const long xy = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (xy >= a.ncols) return;
+  const long i = (long)z * a.ncols + xy;
+  const double f = a.fill[i];
+  const double k02 = a.k0 * a.k0;
+  const cd de = {f * a.deps_re * k02, f * a.deps_im * k02};
+  const long plane = a.ncols * a.nz;
   for (int c = 0; c < 3; ++c) {
-    cd v = de * tot[c];
-    a.b[c * plane + (long)z * a.ncols + xy] = make_float2((float)v.re, (float)v.im);
+    const cd v = de * cd_(f_tot[2 * c], f_tot[2 * c + 1]);
+    a.b[c * plane + i] = make_float2((float)v.re, (float)v.im);
   }
 }
 
@@ -308,6 +321,7 @@ static int upload(void** dst, const void* src, size_t bytes) {
 }
 
 static void plan_free(psfd_plan_s* P) {
+  fp64_free(P);
   void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
                   P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB};
   for (void* q : ptrs)
@@ -506,8 +520,8 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
     a.deps_re = P->deps_re; a.deps_im = P->deps_im;
     a.rs64 = P->R.rs64; a.rp64 = P->R.rp64; a.kz064 = P->R.kz064;
     a.pol = pol[r];
-    long n = nm * P->nz;
-    k_source<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    dim3 grid((unsigned)((nm + 255) / 256), (unsigned)P->nz);
+    k_source<<<grid, 256, 0, s>>>(a);
     PSFD_CHECK_LAUNCH();
   }
   P->have_background = true;

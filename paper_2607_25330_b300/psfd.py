@@ -46,7 +46,13 @@ class Stack(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("r_rel", C.c_double),
-                ("r_rel_recursive", C.c_double), ("r_rel_initial", C.c_double)]
+                ("r_rel_recursive", C.c_double), ("r_rel_initial", C.c_double),
+                ("outer", C.c_int), ("r_rel_output", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("method", C.c_int), ("restart", C.c_int),
+                ("use_precond", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int)]
 
 
 class FnoWeights(C.Structure):
@@ -80,6 +86,11 @@ def lib() -> C.CDLL:
         "psfd_solve": (i, [vp, vp, vp, vp, d, i, i, i, i, C.POINTER(Info), vp, sz]),
         "psfd_solve_workspace_size": (sz, [vp, i, i]),
         "psfd_set_history": (i, [vp, C.POINTER(C.c_double), i]),
+        "psfd_solve_ex": (i, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(Info), vp, sz]),
+        "psfd_solve_ex_workspace_size": (sz, [vp, C.POINTER(SolveOpts)]),
+        "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
+        "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
+                                   C.POINTER(Info), i]),
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
         "fno_forward": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, vp]),
         "psfd_spectral_upsample": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
@@ -87,6 +98,7 @@ def lib() -> C.CDLL:
         "psfd_launch_count": (C.c_longlong, []),
         "psfd_timing_enable": (i, [i]),
         "psfd_timing_read": (i, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]),
+        "psfd_timing_read_bytes": (i, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double), i]),
         "psfd_last_error": (C.c_char_p, []),
         "psfd_version": (C.c_char_p, []),
     }
@@ -102,8 +114,9 @@ def declared_symbols() -> List[str]:
     """Names of the functions the binding expects the library to export."""
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
-            "psfd_set_history", "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
-            "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_last_error", "psfd_version"]
+            "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
+            "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
+            "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
 
 
 def _check(code: int, what: str, allow=()):
@@ -207,6 +220,30 @@ class Plan:
         _check(lib().psfd_precond(self.h, _ptr(x), _ptr(y), flags), "psfd_precond")
         return y
 
+    def solve_ex(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-6, maxit: int = 20000,
+                 method: int = PSFD_GMRES, restart: int = 30, precond: bool = True, refine: bool = True,
+                 inner_tol: float = 1e-2, max_outer: int = 0, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None):
+        """Mixed-precision solve (FP64 outer residual and field, complex64 inner Krylov)."""
+        E = self.empty() if out is None else out
+        info = (Info * self.nrhs)()
+        o = SolveOpts(tol, maxit, method, restart, 1 if precond else 0, 1 if refine else 0, inner_tol, max_outer)
+        ws, wsb = None, 0
+        if workspace is not None:
+            ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
+        code = lib().psfd_solve_ex(self.h, _ptr(b), _ptr(x0), _ptr(E), C.byref(o), info, ws, wsb)
+        _check(code, "psfd_solve_ex", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
+        return {"E": E, "info": [info_dict(i) for i in info], "code": code}
+
+    def autotune(self) -> int:
+        T = C.c_int(0)
+        _check(lib().psfd_autotune(self.h, C.byref(T)), "psfd_autotune")
+        return T.value
+
+    def workspace_size_ex(self, method: int = PSFD_GMRES, restart: int = 30, refine: bool = True) -> int:
+        o = SolveOpts(1e-6, 1, method, restart, 1, 1 if refine else 0, 1e-2, 0)
+        return int(lib().psfd_solve_ex_workspace_size(self.h, C.byref(o)))
+
     def workspace_size(self, method: int = PSFD_BICGSTAB, restart: int = 30) -> int:
         return int(lib().psfd_solve_workspace_size(self.h, method, restart))
 
@@ -229,12 +266,16 @@ class Plan:
         if history > 0:
             lib().psfd_set_history(self.h, None, 0)
         _check(code, "psfd_solve", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
-        res = [{"iters": i.iters, "status": i.status, "r_rel": i.r_rel, "r_rel_recursive": i.r_rel_recursive,
-                "r_rel_initial": i.r_rel_initial} for i in info]
+        res = [info_dict(i) for i in info]
         out_d = {"E": E, "info": res, "code": code}
         if hist is not None:
             out_d["history"] = hist.reshape(self.nrhs, history)
         return out_d
+
+
+def info_dict(i: Info) -> Dict:
+    return {"iters": i.iters, "status": i.status, "r_rel": i.r_rel, "r_rel_recursive": i.r_rel_recursive,
+            "r_rel_initial": i.r_rel_initial, "outer": i.outer, "r_rel_output": i.r_rel_output}
 
 
 def fno_struct(w: Dict[str, torch.Tensor], shape) -> FnoWeights:
@@ -281,6 +322,28 @@ def spectral_upsample_static(src: torch.Tensor, nz: int, ny: int, nx: int,
     return dst
 
 
+def solve_batched(plans: Sequence["Plan"], bs: Sequence[torch.Tensor], x0s=None, tol: float = 1e-6,
+                  maxit: int = 20000, method: int = PSFD_GMRES, restart: int = 30, precond: bool = True,
+                  refine: bool = False, inner_tol: float = 1e-2, nworkers: int = 8):
+    """Solve independent problems concurrently (one stream per plan); returns (fields, infos)."""
+    n = len(plans)
+    Es = [p.empty() for p in plans]
+    arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() if t is not None else None for t in ts])
+    total = sum(p.nrhs for p in plans)
+    info = (Info * total)()
+    o = SolveOpts(tol, maxit, method, restart, 1 if precond else 0, 1 if refine else 0, inner_tol, 0)
+    for t in list(bs) + ([t for t in x0s if t is not None] if x0s else []):
+        _ptr(t)
+    code = lib().psfd_solve_batched((C.c_void_p * n)(*[p.h for p in plans]), n, arr(bs),
+                                    arr(x0s) if x0s is not None else None, arr(Es), C.byref(o), info, nworkers)
+    _check(code, "psfd_solve_batched", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
+    infos, k = [], 0
+    for p in plans:
+        infos.append([info_dict(info[k + r]) for r in range(p.nrhs)])
+        k += p.nrhs
+    return Es, infos
+
+
 STAGES = ("axial", "contrast", "krylov", "transform", "fno")
 
 
@@ -293,7 +356,9 @@ def timing_enable(on: bool = True):
 
 
 def timing_read() -> Dict[str, Dict[str, float]]:
+    """Per stage: summed ms, number of timed launch groups, summed algorithmic bytes."""
     ms = (C.c_double * len(STAGES))()
     calls = (C.c_longlong * len(STAGES))()
-    lib().psfd_timing_read(ms, calls, len(STAGES))
-    return {s: {"ms": ms[i], "calls": int(calls[i])} for i, s in enumerate(STAGES)}
+    nbytes = (C.c_double * len(STAGES))()
+    lib().psfd_timing_read_bytes(ms, calls, nbytes, len(STAGES))
+    return {s: {"ms": ms[i], "calls": int(calls[i]), "bytes": nbytes[i]} for i, s in enumerate(STAGES)}

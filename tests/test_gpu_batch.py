@@ -1,0 +1,60 @@
+"""Batched multi-mask solve (masks of uneven lateral size and depth, several angles and both
+polarisations) and the FFT tile autotuner."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import psfd as O
+from paper_2607_25330_b300 import inputs as I
+from tests.helpers import oracle_setup, problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def make(nx, nz, theta, seed):
+    from paper_2607_25330_b300 import psfd
+    prob = problem(nx, nx, nz, theta=theta, pols=[0, 1])
+    a = I.mask_for(prob, seed)
+    plan = psfd.Plan(prob, stream=torch.cuda.Stream())
+    with torch.cuda.stream(plan.stream):
+        fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+        b = plan.background(prob.stack(), fill, prob.pols)
+    plan.stream.synchronize()
+    return prob, a, plan, fill, b
+
+
+def test_batched_solve_equals_individual_solves():
+    from paper_2607_25330_b300 import psfd
+    specs = [(32, 32, 4.0, 1), (64, 48, 6.0, 2), (96, 32, 8.0, 3), (64, 64, 4.0, 4), (32, 48, 8.0, 5), (128, 32, 6.0, 6)]
+    items = [make(*s) for s in specs]
+    plans = [it[2] for it in items]
+    bs = [it[4] for it in items]
+    Es, infos = psfd.solve_batched(plans, bs, tol=1e-3, maxit=3000, method=psfd.PSFD_GMRES, restart=30)
+    torch.cuda.synchronize()
+    for (prob, a, plan, fill, b), E, inf in zip(items, Es, infos):
+        for r in range(2):
+            assert inf[r]["status"] == 0 and inf[r]["r_rel"] <= 1.05e-3, inf[r]
+        solo = plan.solve(b, tol=1e-3, maxit=3000, method=psfd.PSFD_GMRES, restart=30)
+        torch.cuda.synchronize()
+        assert rel_l2(E.cpu(), solo["E"].cpu()) < 1e-6
+    # one member against the FP64 oracle: its true residual is the solver's
+    prob, a, plan, fill, b = items[1]
+    g, fill_o = oracle_setup(prob, a)
+    for r, pol in enumerate(prob.pols):
+        bo = O.source_b(g, fill_o, pol)
+        assert O.rel_residual(g, Es[1][r].cpu().to(torch.complex128), fill_o, bo) < 1.1e-3
+
+
+@pytest.mark.parametrize("nz", [16, 32, 48, 64, 128])
+def test_every_tuned_tile_gives_the_same_operator(nz):
+    from paper_2607_25330_b300 import psfd
+    prob = problem(32, 32, nz, theta=6.0, pols=[0])
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(I.mask_for(prob, 1)), prob.zprofile())
+    plan.background(prob.stack(), fill, prob.pols)
+    x = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64).cuda()
+    T = plan.autotune()
+    assert T in (2, 4, 8)
+    ref = plan.apply(x, flags=psfd.PSFD_PRECOND).cpu()
+    g, fill_o = oracle_setup(prob, I.mask_for(prob, 1))
+    assert rel_l2(ref[0], O.apply_A(g, O.apply_M(g, x[0].cpu().to(torch.complex128)), fill_o)) < 1e-4

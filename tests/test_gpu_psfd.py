@@ -198,3 +198,66 @@ def test_solver_history_and_initial_residual():
     h = res["history"][0]
     assert abs(res["info"][0]["r_rel_initial"] - 1.0) < 1e-6      # null initialisation: r0 = b
     assert h[it - 1] <= 1e-6 and np.all(h[:it] > 0)
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "gmres"])
+def test_refined_solve_reaches_fp64_residual(method):
+    """Mixed precision (FP64 outer residual and field, complex64 inner Krylov): the FP64
+    residual of the internal field meets 1e-8, far below the complex64 floor, and the
+    returned complex64 field sits at that floor."""
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    g, fill_o = oracle_setup(prob, a)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    m = psfd.PSFD_GMRES if method == "gmres" else psfd.PSFD_BICGSTAB
+    res = plan.solve_ex(b, tol=1e-8, maxit=4000, method=m, restart=30, inner_tol=1e-2)
+    info = res["info"][0]
+    assert info["status"] == 0, info
+    assert info["r_rel"] <= 1e-8 and info["outer"] >= 2
+    bo = b[0].cpu().to(torch.complex128)          # the problem solved is A E = b (complex64 b)
+    r_out = O.rel_residual(g, res["E"][0].cpu().to(torch.complex128), fill_o, bo)
+    assert abs(r_out - info["r_rel_output"]) < 0.05 * r_out + 1e-9
+    assert r_out < 2e-6
+    ref = K.solve(lambda E: O.apply_A(g, E, fill_o), lambda x: O.apply_M(g, x), bo, tol=1e-12, maxit=6000)
+    assert rel_l2(res["E"][0].cpu(), ref["E"]) < 2e-6
+
+
+@pytest.mark.parametrize("grid", GRIDS[:4])
+@pytest.mark.parametrize("flags", [4, 5])
+def test_adjoint_matches_oracle(grid, flags):
+    """A^H (flags 4) and (A M)^H = M A^H (flags 5) against the oracle's adjoint, and the
+    adjoint identity <A x, y> = <x, A^H y> on the GPU."""
+    from paper_2607_25330_b300 import psfd
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
+    y = torch.from_numpy(I.random_field(plan.shape, 11)).to(torch.complex64)
+    out = plan.apply(y.cuda(), flags=flags).cpu()
+    for r in range(plan.nrhs):
+        ref = O.apply_AH(g, y[r].to(torch.complex128), fill_o)
+        if flags & psfd.PSFD_PRECOND:
+            ref = O.apply_M(g, ref)
+        assert rel_l2(out[r], ref) < TOL_C64, (grid, flags, r)
+    x = torch.from_numpy(I.random_field(plan.shape, 12)).to(torch.complex64).cuda()
+    Ax = plan.apply(x, flags=flags & psfd.PSFD_PRECOND)
+    lhs = torch.vdot(Ax.flatten().to(torch.complex128), y.cuda().flatten().to(torch.complex128))
+    rhs = torch.vdot(x.flatten().to(torch.complex128), out.cuda().flatten().to(torch.complex128))
+    assert abs(complex(lhs - rhs)) < 1e-5 * abs(complex(lhs))
+
+
+def test_physics_loss_gradient_matches_oracle():
+    """Eq. loss and its gradient w.r.t. the field through the hand-written adjoint (autograd.Function)."""
+    from oracle import fno as OF
+    from paper_2607_25330_b300 import autograd as AG
+    prob, a, g, fill_o, plan, fill, b = setup(32, 32, 16, 6.0, 0.0, 1)
+    E0 = torch.from_numpy(I.random_field(plan.shape, 13) * 0.2).to(torch.complex64)
+    E = E0.cuda().requires_grad_(True)
+    J = AG.physics_loss(plan, E, b)
+    J.backward()
+    Eo = E0[0].to(torch.complex128).requires_grad_(True)
+    bo = b[0].cpu().to(torch.complex128)
+    Jo = OF.loss(lambda X: O.apply_A(g, X, fill_o), Eo, bo)
+    Jo.backward()
+    assert abs(float(J) - float(Jo)) < 1e-4 * abs(float(Jo))
+    assert rel_l2(E.grad[0].cpu(), Eo.grad) < 1e-4
