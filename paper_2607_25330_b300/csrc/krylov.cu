@@ -394,6 +394,8 @@ struct GArgs {
   double2* hout;   // [nrhs][GMAX] results of the multi-dot
   cf* w;           // target vector (V_{j+1})
   cf* y;           // solution accumulator
+  KScal* sc;       // per-rhs scalars: res0 <- ||w||^2 after an update, tt <- ||w||^2 before
+  bool save_norm;  // k_gdot: also reduce ||w||^2 (chunk 0) into sc.tt
 };
 
 // mask: nonzero = skip this right-hand side (same convention as the operator kernels)
@@ -412,10 +414,13 @@ __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
   float sr[GCH], si[GCH];
 #pragma unroll
   for (int q = 0; q < GCH; ++q) { sr[q] = 0.f; si[q] = 0.f; }
+  float ww = 0.f;
+  const bool want_ww = a.save_norm && chunk == 0;
   const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
   const float4* w4 = reinterpret_cast<const float4*>(a.w);
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
     const float4 wv = w4[off2 + i];
+    if (want_ww) ww = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, fmaf(wv.z, wv.z, fmaf(wv.w, wv.w, ww))));
 #pragma unroll
     for (int q = 0; q < GCH; ++q) {
       if (q < nq) {
@@ -426,23 +431,26 @@ __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
       }
     }
   }
-  double val[2 * GCH];
+  constexpr int NQ = 2 * GCH + 1;
+  double val[NQ];
 #pragma unroll
   for (int q = 0; q < GCH; ++q) { val[2 * q] = (double)sr[q]; val[2 * q + 1] = (double)si[q]; }
-  double tot[2 * GCH];
-  double* pbase = a.partials + ((long)rhs * gridDim.z + chunk) * gridDim.x * (2 * GCH);
-  if (!reduce_group<2 * GCH, 2 * GCH>(val, pbase, a.counters + rhs * gridDim.z + chunk, tot)) return;
-  if (threadIdx.x == 0)
+  val[2 * GCH] = (double)ww;
+  double tot[NQ];
+  double* pbase = a.partials + ((long)rhs * gridDim.z + chunk) * gridDim.x * (NQ + 1);
+  if (!reduce_group<NQ, NQ + 1>(val, pbase, a.counters + rhs * gridDim.z + chunk, tot)) return;
+  if (threadIdx.x == 0) {
     for (int q = 0; q < nq; ++q) a.hout[rhs * GMAX + i0 + q] = make_double2(tot[2 * q], tot[2 * q + 1]);
+    if (want_ww) a.sc[rhs].tt = tot[2 * GCH];
+  }
 }
 
 // per rhs: keep the norm of w before orthogonalisation (res0 -> tt), zero the second-pass
 // coefficients, and after the first pass decide whether a second one is needed
-__global__ void k_gsave(KScal* sc, double2* h2, int nrhs, int nv) {
+__global__ void k_gsave(double2* h2, int nrhs, int nv) {
   const int r = blockIdx.x;
   if (r >= nrhs) return;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) h2[r * GMAX + i] = make_double2(0.0, 0.0);
-  if (threadIdx.x == 0) sc[r].tt = sc[r].res0;
 }
 __global__ void k_greorth(const KScal* sc, const int* skip, int* skip2, int nrhs) {
   const int r = threadIdx.x;
@@ -466,6 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
   __syncthreads();
   const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
   float4* t4 = reinterpret_cast<float4*>(ADD ? a.y : a.w);
+  float ww = 0.f;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
     float4 acc = t4[off2 + i];
     cf a0 = make_float2(acc.x, acc.y), a1 = make_float2(acc.z, acc.w);
@@ -475,6 +484,14 @@ __global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
       a1 = cfma(coef[q], make_float2(vv.z, vv.w), a1);
     }
     t4[off2 + i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+    if (!ADD) ww = fmaf(a0.x, a0.x, fmaf(a0.y, a0.y, fmaf(a1.x, a1.x, fmaf(a1.y, a1.y, ww))));
+  }
+  if constexpr (!ADD) {
+    // ||w||^2 after the update (per-thread float partials, FP64 across threads)
+    double val[2] = {(double)ww, 0.0};
+    double tot[2];
+    if (!reduce_group<2, kMaxQ>(val, a.partials + (long)rhs * gridDim.x * kMaxQ, a.counters + rhs, tot)) return;
+    if (threadIdx.x == 0) a.sc[rhs].res0 = tot[0];
   }
 }
 
@@ -637,7 +654,7 @@ static size_t ws_layout(psfd_plan_s* P, int method, int restart, SolveWs* w, cha
   w->done = (int*)take(sizeof(int) * nr);
   w->active = (int*)take(sizeof(int) * nr);
   w->skip2 = (int*)take(sizeof(int) * nr);
-  w->partials = (double*)take(sizeof(double) * (size_t)nr * nb * (gm ? nch * 2 * GCH : kMaxQ));
+  w->partials = (double*)take(sizeof(double) * (size_t)nr * nb * (gm ? nch * (2 * GCH + 2) : kMaxQ));
   w->counters = (unsigned*)take(sizeof(unsigned) * nr * (gm ? nch : 1));
   w->gs = gm ? (GState*)take(sizeof(GState) * nr) : nullptr;
   w->h1 = gm ? (double2*)take(sizeof(double2) * nr * GMAX) : nullptr;
@@ -700,6 +717,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
   PSFD_CHECK_LAUNCH();
   GArgs g{};
   g.V = w.V; g.vs = vs; g.n = n; g.gs = w.gs; g.partials = w.partials; g.counters = w.counters; g.y = w.y;
+  g.sc = w.sc; g.save_norm = false;
   std::vector<int> hv(nr);
   bool first = true;
   for (int cycle = 0;; ++cycle) {
@@ -732,22 +750,20 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
       if ((rc = apply_hybrid(P, Vj, Wn, aflags, w.active))) return rc;
       g.w = Wn; g.nv = j + 1; g.j = j;
       const int nch = (j + 1 + GCH - 1) / GCH;
-      va.v0 = Wn;
-      va.done = w.active;  // w.active holds the skip flags here
-      va.use_done = true;
-      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 before
-      k_gsave<<<nr, 64, 0, st>>>(w.sc, w.h2, nr, j + 1);
+      k_gsave<<<nr, 64, 0, st>>>(w.h2, nr, j + 1);
       PSFD_CHECK_LAUNCH();
       {
-        // dot: read w + (j+1) basis vectors; update: read (j+1) + read/write w
+        // dot (+ ||w||^2 before): read w + (j+1) basis vectors; update (+ ||w||^2 after):
+        // read (j+1) + read/write w
         StageScope sc(st, ST_KRYLOV, (2.0 * (j + 1) + 3.0) * nr * n * sizeof(cf));
         g.hout = w.h1;
+        g.save_norm = true;
         k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
+        g.save_norm = false;
         k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
       }
-      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 after pass 1
       k_greorth<<<1, tpb, 0, st>>>(w.sc, w.active, w.skip2, nr);
       PSFD_CHECK_LAUNCH();
       {
@@ -761,10 +777,6 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         PSFD_CHECK_LAUNCH();
         g.mask = keep;
       }
-      va.done = w.skip2;
-      if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return rc;       // ||w||^2 after pass 2 (if taken)
-      va.done = w.done;
-      va.use_done = false;
       k_givens<<<1, tpb, 0, st>>>(w.gs, w.h1, w.h2, w.sc, w.active, va.hist, va.hist_cap, nr, j);
       PSFD_CHECK_LAUNCH();
       k_gscale<<<dim3(nb, nr), kThreads, 0, st>>>(g, false);
