@@ -603,6 +603,182 @@ int launch_lateral_transform(psfd_plan_s* P, cf* buf, long nplanes, bool forward
   return launch_rows(P->nx, buf, rows, false, scale, P->tw_x, P->stream);
 }
 
+// ======================================================================= single-pass plane kernel
+// One CTA per (rhs, component, absorber plane) of a square N x N grid (N <= 128):
+// the G plane and the fill plane are brought into shared memory with bulk async
+// copies (cp.async.bulk, completion on an mbarrier, bounded wait), then
+//   row IFFT_x -> column IFFT_y * k0^2 deps fill / N^2 * FFT_y -> row FFT_x,
+// and the result is subtracted from y (forward operator) or written back to G
+// (adjoint preparation).  The plane crosses HBM once instead of three times.
+// Rows of the staged plane are padded by 4 complex entries so that the column
+// pass (T rows x P consecutive columns per warp access) is free of bank conflicts.
+constexpr int kPlaneThreads = 512;
+constexpr int kRowPad = 4;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+struct PlaneArgs {
+  cf* G;
+  cf* y;
+  const float* fill;
+  const cf* twx;
+  const cf* twy;
+  const int* done;
+  int* err;
+  int nz, nab, za0;
+  float dre, dim;
+  bool to_y;   // true: y -= result (forward); false: G <- result (adjoint preparation)
+};
+
+template <int N, int TR, int TC>
+__global__ void __launch_bounds__(kPlaneThreads) k_plane(PlaneArgs a) {
+  constexpr int RS = N + kRowPad;
+  constexpr int PR = 32 / TR, RR = N / TR;   // rows: lane = p*TR + t
+  constexpr int PC = 32 / TC, RC = N / TC;   // columns: lane = t*PC + p
+  using PX = Pencil<N, TR, 1>;
+  using PY = Pencil<N, TC, PC>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cf* S = reinterpret_cast<cf*>(smem_raw);                             // N x RS complex
+  float* F = reinterpret_cast<float*>(smem_raw + sizeof(cf) * N * RS);  // N x N fill
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(cf) * N * RS + sizeof(float) * N * N);
+  const long plane = blockIdx.x;
+  const long per_rhs = 3L * a.nab;
+  const long rhs = plane / per_rhs;
+  if (a.done && a.done[rhs]) return;
+  const int c = (int)((plane / a.nab) % 3);
+  const int zz = (int)(plane % a.nab);
+  cf* Gp = a.G + plane * (long)N * N;
+  const float* Fp = a.fill + (long)(a.za0 + zz) * N * N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = kPlaneThreads / 32;
+
+  // ---- stage G (row by row, padded) and the fill plane with bulk async copies
+  const unsigned mb = smem_u32(bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned tx = (unsigned)(sizeof(cf) * N * N + sizeof(float) * N * N);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(tx) : "memory");
+    for (int r = 0; r < N; ++r) {
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   :: "r"(smem_u32(S + r * RS)), "l"(Gp + (long)r * N), "r"((unsigned)(sizeof(cf) * N)), "r"(mb)
+                   : "memory");
+    }
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(F)), "l"(Fp), "r"((unsigned)(sizeof(float) * N * N)), "r"(mb) : "memory");
+  }
+  // bounded wait on phase 0 of the barrier
+  {
+    unsigned ok = 0;
+    for (long it = 0; it < (1L << 26) && !ok; ++it) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(ok) : "r"(mb) : "memory");
+    }
+    // leave together: a thread that gave up makes the whole block return
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(a.err, 1);
+      return;
+    }
+  }
+
+  // ---- row IFFT_x (kx -> x)
+  for (int r0 = warp * PR; r0 < N; r0 += nwarps * PR) {
+    const int p = lane / TR, t = lane - p * TR;
+    const int row = r0 + p;
+    cf v[RR];
+#pragma unroll
+    for (int s = 0; s < RR; ++s) v[s] = S[row * RS + PX::freq_index(t, s)];
+    PX::template to_time<true>(v, t, a.twx);
+#pragma unroll
+    for (int m = 0; m < RR; ++m) S[row * RS + t + TR * m] = v[m];
+  }
+  __syncthreads();
+  // ---- columns: IFFT_y (ky -> y), * k0^2 deps fill / N^2, FFT_y
+  for (int c0 = warp * PC; c0 < N; c0 += nwarps * PC) {
+    const int t = lane / PC, p = lane - t * PC;
+    const int col = c0 + p;
+    cf v[RC];
+#pragma unroll
+    for (int s = 0; s < RC; ++s) v[s] = S[PY::freq_index(t, s) * RS + col];
+    PY::template to_time<true>(v, t, a.twy);
+#pragma unroll
+    for (int m = 0; m < RC; ++m) {
+      const float fv = F[(t + TC * m) * N + col];
+      v[m] = cmul(v[m], make_float2(a.dre * fv, a.dim * fv));
+    }
+    PY::template to_freq<false>(v, t, a.twy);
+#pragma unroll
+    for (int s = 0; s < RC; ++s) S[PY::freq_index(t, s) * RS + col] = v[s];
+  }
+  __syncthreads();
+  // ---- row FFT_x (x -> kx) and combine
+  cf* yp = a.to_y ? a.y + (((rhs * 3 + c) * a.nz + a.za0 + zz) * (long)N) * N : Gp;
+  for (int r0 = warp * PR; r0 < N; r0 += nwarps * PR) {
+    const int p = lane / TR, t = lane - p * TR;
+    const int row = r0 + p;
+    cf v[RR];
+#pragma unroll
+    for (int m = 0; m < RR; ++m) v[m] = S[row * RS + t + TR * m];
+    PX::template to_freq<false>(v, t, a.twx);
+#pragma unroll
+    for (int s = 0; s < RR; ++s) {
+      const long o = (long)row * N + PX::freq_index(t, s);
+      if (a.to_y) {
+        const cf old = yp[o];
+        yp[o] = csub(old, v[s]);
+      } else {
+        yp[o] = v[s];
+      }
+    }
+  }
+}
+
+template <int N, int TR, int TC>
+static int run_plane(psfd_plan_s* P, const PlaneArgs& a, long nplanes) {
+  const size_t smem = sizeof(cf) * N * (N + kRowPad) + sizeof(float) * N * N + 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_plane<N, TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_plane<N, TR, TC><<<(unsigned)nplanes, kPlaneThreads, smem, P->stream>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+// 1 if the single-pass plane kernel handles this grid, and launches it
+static int plane_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint, bool to_y, bool* handled) {
+  *handled = false;
+  if (P->nx != P->ny || P->nx > 128 || P->plane_off) return PSFD_OK;
+  if (!P->err) PSFD_CUDA_TRY(cudaMalloc((void**)&P->err, sizeof(int)));
+  const int nab = P->za1 - P->za0;
+  PlaneArgs a;
+  a.G = P->G; a.y = y; a.fill = P->fill; a.twx = P->tw_x; a.twy = P->tw_y; a.done = done; a.err = P->err;
+  a.nz = P->nz; a.nab = nab; a.za0 = P->za0;
+  const double sc = P->k0 * P->k0 / (double)P->ncols;
+  a.dre = (float)(sc * P->deps_re);
+  a.dim = (float)(sc * (adjoint ? -P->deps_im : P->deps_im));
+  a.to_y = to_y;
+  const long nplanes = (long)P->nrhs * 3 * nab;
+  int rc = PSFD_OK;
+  switch (P->nx) {
+    case 16: rc = run_plane<16, 4, 2>(P, a, nplanes); break;
+    case 32: rc = run_plane<32, 4, 4>(P, a, nplanes); break;
+    case 64: rc = run_plane<64, 8, 4>(P, a, nplanes); break;
+    case 96: rc = run_plane<96, 4, 4>(P, a, nplanes); break;
+    case 128: rc = run_plane<128, 8, 8>(P, a, nplanes); break;
+    default: return PSFD_OK;
+  }
+  if (rc) return rc;
+  *handled = true;
+  return PSFD_OK;
+}
+
 // y (absorber planes) -= k0^2 F_xy[deps F_xy^-1 G] / (nx ny): G is consumed.
 int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint) {
   const int nab = P->za1 - P->za0;
@@ -612,6 +788,9 @@ int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint
                    (double)P->nrhs * nab * P->ncols * (3.0 * 3 * sizeof(cf) + sizeof(float)));
   const long nplanes = (long)P->nrhs * 3 * nab;
   int rc;
+  bool handled = false;
+  if ((rc = plane_contrast(P, y, done, adjoint, true, &handled))) return rc;
+  if (handled) return PSFD_OK;
   RowArgs r{};
   r.buf = P->G; r.nrows = nplanes * P->ny; r.scale = 1.f; r.tw = P->tw_x; r.done = done;
   r.rows_per_rhs = 3L * nab * P->ny;
@@ -642,6 +821,9 @@ static int adjoint_contrast(psfd_plan_s* P, const cf* x) {
     }
   const long nplanes = (long)P->nrhs * 3 * nab;
   int rc;
+  bool handled = false;
+  if ((rc = plane_contrast(P, nullptr, nullptr, true, false, &handled))) return rc;
+  if (handled) return PSFD_OK;
   RowArgs r{};
   r.buf = P->G; r.nrows = nplanes * P->ny; r.scale = 1.f; r.tw = P->tw_x; r.rows_per_rhs = 3L * nab * P->ny;
   if ((rc = rows_dispatch(P->nx, r, ROW_INV, P->stream))) return rc;

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -323,7 +324,7 @@ static int upload(void** dst, const void* src, size_t bytes) {
 static void plan_free(psfd_plan_s* P) {
   fp64_free(P);
   void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
-                  P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB};
+                  P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -423,6 +424,10 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
     delete P;
     return PSFD_ERR_CUDA;
   }
+  // PSFD_PLANE_OFF=1 selects the three-pass lateral contrast even where the single-pass
+  // plane kernel applies (used to cross-check the two paths)
+  const char* po = getenv("PSFD_PLANE_OFF");
+  P->plane_off = po && po[0] == '1';
   *out = P;
   return PSFD_OK;
 }
