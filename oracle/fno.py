@@ -15,7 +15,8 @@ erf form.  The retained-mode tables hold k = -m/2 .. m/2-1 in that (centred) ord
 
 ``mix_bf16=True`` rounds both operands of the per-mode channel mixing to
 bfloat16 (round to nearest even) before the float64 accumulation: the
-arithmetic the workload prescribes for the mixing, done exactly.
+arithmetic the workload prescribes for the mixing, done exactly.  Gradients
+(torch autograd through this file) pass the rounding straight through.
 
 Loss, Eq. loss:
   J = (1/N) sum_a ||r_a||^2 + (lambda_hf/N) sum_a || w(nu) F3[r_a] ||^2,
@@ -27,7 +28,8 @@ Parity pins (tests/test_oracle_fno.py): a layer whose kernels are the
 identity on the retained modes equals an explicit low-pass projection written
 with a DFT matrix; zero spectral and MLP weights leave the lifted field
 unchanged; GELU against math.erf; loss gradients against central finite
-differences.
+differences; parameter gradients of the network (float64 mixing) against
+central finite differences.
 """
 from __future__ import annotations
 
@@ -57,10 +59,21 @@ def table_rows(n: int, m: int) -> torch.Tensor:
     return torch.arange(-(mm // 2), mm - mm // 2) + m // 2
 
 
-def _bf16(x: torch.Tensor) -> torch.Tensor:
-    if x.is_complex():
-        return torch.complex(x.real.to(torch.bfloat16).to(F64), x.imag.to(torch.bfloat16).to(F64))
+def _round_bf16(x: torch.Tensor) -> torch.Tensor:
     return x.to(torch.bfloat16).to(F64)
+
+
+def _bf16(x: torch.Tensor) -> torch.Tensor:
+    """Round to bfloat16 (nearest even); under autograd the rounding is passed straight through.
+
+    x + (round(x) - x) equals round(x) exactly in float64 (the difference is exact),
+    and the detached difference makes the derivative the identity, so that
+    gradients of the mixing are dK = dU conj(bf16(V)) and dV = bf16(K)^H dU.
+    """
+    if x.is_complex():
+        re, im = x.real, x.imag
+        return torch.complex(re + (_round_bf16(re) - re).detach(), im + (_round_bf16(im) - im).detach())
+    return x + (_round_bf16(x) - x).detach()
 
 
 def _t(w, dtype=F64):

@@ -129,3 +129,56 @@ def test_loss_gradient_matches_central_differences():
     hf = torch.fft.ifftn(w2 * torch.fft.fftn(r, dim=(-3, -2, -1), norm="ortho"), dim=(-3, -2, -1), norm="ortho")
     adj = 2.0 / N * (O.apply_AH(g, r, fill) + 0.1 * O.apply_AH(g, hf, fill))
     assert float((adj - grad).abs().max()) < 1e-12 * float(grad.abs().max())
+
+
+def _tiny_net(seed=31):
+    S = I.FNOShape(dv=4, dh=6, layers=2, mx=4, my=4, mz=2, dq=5)
+    w = I.fno_weights(S, seed, spectral_scale=8.0)
+    return S, {k: torch.from_numpy(np.asarray(v)).to(torch.complex128 if np.iscomplexobj(v) else F64)
+               for k, v in w.items()}
+
+
+def test_network_parameter_gradients_match_central_differences():
+    """Autograd through the float64 network (Eqs. 1-5) against central differences of J = Re<c, E>."""
+    S, w = _tiny_net()
+    a = torch.from_numpy(np.random.default_rng(8).random((1, 4, 8, 6)))
+    c = torch.from_numpy(np.random.default_rng(9).standard_normal((1, 3, 4, 8, 6))
+                         + 1j * np.random.default_rng(10).standard_normal((1, 3, 4, 8, 6)))
+    J = lambda ww: float((c.conj() * F.forward(ww, a, mix_bf16=False)).real.sum())
+    params = {k: v.clone().requires_grad_(True) for k, v in w.items()}
+    (c.conj() * F.forward(params, a, mix_bf16=False)).real.sum().backward()
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    for name in ("lift_w", "lift_b", "kxy", "kz", "w1", "b2", "q1", "qb2"):
+        g = params[name].grad
+        for _ in range(2):
+            idx = tuple(int(rng.integers(0, s)) for s in w[name].shape)
+            for unit in ((1.0, 1j) if w[name].is_complex() else (1.0,)):
+                wp = {k: v.clone() for k, v in w.items()}
+                wm = {k: v.clone() for k, v in w.items()}
+                wp[name][idx] += h * unit
+                wm[name][idx] -= h * unit
+                fd = (J(wp) - J(wm)) / (2 * h)
+                # torch's gradient of a complex parameter is dJ/dRe + i dJ/dIm
+                lin = float(g[idx].real) if unit == 1.0 else float(g[idx].imag)
+                assert abs(fd - lin) < 1e-6 * max(1.0, abs(lin)), (name, idx, unit, fd, lin)
+
+
+def test_bf16_mixing_gradient_is_straight_through():
+    """With mix_bf16 the forward uses rounded operands; the gradient is the float64 chain rule
+    evaluated at the rounded operands (dK = dU conj(bf16 V), dV = bf16(K)^H dU)."""
+    rng = np.random.default_rng(12)
+    K = torch.from_numpy(rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))).requires_grad_(True)
+    V = torch.from_numpy(rng.standard_normal((3, 5)) + 1j * rng.standard_normal((3, 5))).requires_grad_(True)
+    dU = torch.from_numpy(rng.standard_normal((3, 5)) + 1j * rng.standard_normal((3, 5)))
+    U = F._bf16(K) @ F._bf16(V)
+    # forward: exactly the product of the rounded operands
+    Kr = torch.complex(K.real.detach().to(torch.bfloat16).to(F64), K.imag.detach().to(torch.bfloat16).to(F64))
+    Vr = torch.complex(V.real.detach().to(torch.bfloat16).to(F64), V.imag.detach().to(torch.bfloat16).to(F64))
+    assert torch.equal(U.detach(), Kr @ Vr)
+    (dU.conj() * U).real.sum().backward()
+    # the same products with the rounded values as plain float64 leaves
+    Kl, Vl = Kr.clone().requires_grad_(True), Vr.clone().requires_grad_(True)
+    (dU.conj() * (Kl @ Vl)).real.sum().backward()
+    assert torch.allclose(K.grad, Kl.grad, rtol=0, atol=1e-14)
+    assert torch.allclose(V.grad, Vl.grad, rtol=0, atol=1e-14)
