@@ -240,6 +240,40 @@ PSFD_API size_t fno_workspace_size(const fno_weights_t* w, int B, int nx, int ny
 PSFD_API int fno_forward(const fno_weights_t* w, const float* a, int B, int nx, int ny, int nz,
                 psfd_c64* E_out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- FNO training (physics-informed, Sec. 2.2)
+ * Gradient buffers of the same shapes as fno_weights_t (device, float32 /
+ * complex64).  fno_backward ADDS to them, so zero them before a step.  For a
+ * complex kernel entry K the gradient is dJ/dRe K + i dJ/dIm K (the convention
+ * of torch's complex autograd).  The bfloat16 rounding of the mixing operands is
+ * passed straight through: dK = dU conj(bf16(V)), dV = bf16(K)^H dU. */
+typedef struct {
+  float* lift_w; float* lift_b;
+  psfd_c64* kxy; psfd_c64* kz;
+  float* w1; float* b1; float* w2; float* b2;
+  float* q1; float* qb1; float* q2; float* qb2;
+} fno_grads_t;
+
+/* Workspace of a training pass.  checkpoint = 0 (stored): the forward keeps,
+ * per layer, the branch outputs u_xy, u_z and the retained spectra V, W
+ * (Eqs. 2-3) for the backward.  checkpoint != 0 (activation checkpointing): it
+ * keeps only each layer's input v_l, and the backward recomputes that layer's
+ * branches first (one more forward pass of the spectral branches, about a
+ * third of the memory at dv = 32).  Both give the same gradients. */
+PSFD_API size_t fno_train_workspace_size(const fno_weights_t* w, int B, int nx, int ny, int nz, int checkpoint);
+/* Same result as fno_forward; keeps what fno_backward needs in the workspace
+ * (fno_train_workspace_size bytes for the same checkpoint flag). */
+PSFD_API int fno_forward_train(const fno_weights_t* w, const float* a, int B, int nx, int ny, int nz,
+                               psfd_c64* E_out, void* workspace, size_t workspace_bytes, int checkpoint,
+                               void* stream);
+/* Reverse pass of the fno_forward_train that last used `workspace` (same w, a,
+ * sizes and checkpoint flag; w unchanged since): dE device [B][3][nz][ny][nx]
+ * complex64 = dJ/dRe E + i dJ/dIm E; the gradients of every parameter are
+ * added into g.  Errors: PSFD_ERR_ARG for null pointers, unsupported sizes or a
+ * small workspace. */
+PSFD_API int fno_backward(const fno_weights_t* w, const fno_grads_t* g, const float* a, int B, int nx, int ny,
+                          int nz, const psfd_c64* dE, void* workspace, size_t workspace_bytes, int checkpoint,
+                          void* stream);
+
 /* Zero-pad the 3-D spectrum of src [nb][nz0][ny0][nx0] to dst [nb][nz][ny][nx]
  * (spectral interpolation of a coarse prediction, amplitude preserving). */
 PSFD_API int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,

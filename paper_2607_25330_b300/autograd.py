@@ -7,6 +7,10 @@ physics-informed loss of Eq. loss,
 can be differentiated with respect to a predicted field E without precomputed
 solutions.  Both directions run in the library's kernels; torch only holds the
 tensors (the loss reductions and F3 of the penalty term are torch GPU ops).
+
+FNOApply wraps the factorised FNO (Sec. 2.1) with its hand-written reverse pass
+(fno_forward_train / fno_backward), so that J can be minimised over the network
+parameters (Sec. 2.2).
 """
 from __future__ import annotations
 
@@ -25,6 +29,29 @@ class PSFDApply(torch.autograd.Function):
     def backward(ctx, g: torch.Tensor):
         # torch's complex convention: for a linear map y = A E the input gradient is A^H g
         return ctx.plan.apply(g.contiguous(), flags=psfd.PSFD_ADJOINT), None
+
+
+class FNOApply(torch.autograd.Function):
+    """E = G_theta(a); params in psfd.FNO_PARAM_NAMES order (CUDA tensors, kernels complex64)."""
+
+    @staticmethod
+    def forward(ctx, a: torch.Tensor, trainer: "psfd.FnoTrainer", *params):
+        a = a.contiguous()
+        ctx.trainer, ctx.a = trainer, a
+        ctx.shapes = [(p.shape, p.dtype) for p in params]
+        return trainer.forward(a)
+
+    @staticmethod
+    def backward(ctx, gE: torch.Tensor):
+        grads = {n: torch.zeros(s, dtype=dt, device=gE.device)
+                 for n, (s, dt) in zip(psfd.FNO_PARAM_NAMES, ctx.shapes)}
+        ctx.trainer.backward(ctx.a, gE.to(torch.complex64), grads)
+        return (None, None) + tuple(grads[n] for n in psfd.FNO_PARAM_NAMES)
+
+
+def fno_apply(trainer: "psfd.FnoTrainer", params, a: torch.Tensor) -> torch.Tensor:
+    """Differentiable E = G_theta(a); params: dict of CUDA tensors whose pointers the trainer's struct holds."""
+    return FNOApply.apply(a, trainer, *[params[n] for n in psfd.FNO_PARAM_NAMES])
 
 
 def frequency_weight(nz: int, ny: int, nx: int, w0: float = 1.0, eta_hf: float = 1.0, device="cuda"):

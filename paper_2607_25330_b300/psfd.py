@@ -62,6 +62,13 @@ class FnoWeights(C.Structure):
                                           "q1", "qb1", "q2", "qb2")]
 
 
+class FnoGrads(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("lift_w", "lift_b", "kxy", "kz", "w1", "b1", "w2", "b2",
+                                          "q1", "qb1", "q2", "qb2")]
+
+
+FNO_PARAM_NAMES = ("lift_w", "lift_b", "kxy", "kz", "w1", "b1", "w2", "b2", "q1", "qb1", "q2", "qb2")
+
 _lib = None
 
 
@@ -93,6 +100,9 @@ def lib() -> C.CDLL:
                                    C.POINTER(Info), i]),
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
         "fno_forward": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, vp]),
+        "fno_train_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i, i]),
+        "fno_forward_train": (i, [C.POINTER(FnoWeights), vp, i, i, i, i, vp, vp, sz, i, vp]),
+        "fno_backward": (i, [C.POINTER(FnoWeights), C.POINTER(FnoGrads), vp, i, i, i, i, vp, vp, sz, i, vp]),
         "psfd_spectral_upsample": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
         "psfd_spectral_upsample_static": (i, [vp, i, i, i, i, vp, i, i, i, vp]),
         "psfd_launch_count": (C.c_longlong, []),
@@ -115,7 +125,8 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
-            "fno_workspace_size", "fno_forward", "psfd_spectral_upsample",
+            "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
+            "psfd_spectral_upsample",
             "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
 
 
@@ -280,9 +291,8 @@ def info_dict(i: Info) -> Dict:
 
 def fno_struct(w: Dict[str, torch.Tensor], shape) -> FnoWeights:
     """Device weights (dict of CUDA tensors, complex kernels as complex64) -> fno_weights_t."""
-    names = ("lift_w", "lift_b", "kxy", "kz", "w1", "b1", "w2", "b2", "q1", "qb1", "q2", "qb2")
     s = FnoWeights(shape.dv, shape.dh, shape.layers, shape.mx, shape.my, shape.mz, shape.dq,
-                   *[_ptr(w[n]) for n in names])
+                   *[_ptr(w[n]) for n in FNO_PARAM_NAMES])
     s._keep = w
     return s
 
@@ -297,6 +307,36 @@ def fno_forward(wt: FnoWeights, a: torch.Tensor, out: Optional[torch.Tensor] = N
     _check(L.fno_forward(C.byref(wt), _ptr(a.contiguous()), B, nx, ny, nz, _ptr(E), _ptr(ws), n,
                          _stream_handle(stream)), "fno_forward")
     return E
+
+
+class FnoTrainer:
+    """Owns the workspace of a training pass (fno_forward_train / fno_backward) for one (B, grid).
+
+    checkpoint=True keeps only the layer inputs and recomputes the spectral branches in the backward.
+    """
+
+    def __init__(self, wt: FnoWeights, B: int, nz: int, ny: int, nx: int, checkpoint: bool = False):
+        self.wt, self.B, self.shape, self.ckpt = wt, B, (nz, ny, nx), int(bool(checkpoint))
+        self.n = int(lib().fno_train_workspace_size(C.byref(wt), B, nx, ny, nz, self.ckpt))
+        self.ws = torch.empty(max(self.n, 1), dtype=torch.uint8, device="cuda")
+
+    def forward(self, a: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        nz, ny, nx = self.shape
+        assert a.shape == (self.B, nz, ny, nx) and a.dtype == torch.float32 and a.is_contiguous()
+        E = torch.empty((self.B, 3, nz, ny, nx), dtype=torch.complex64, device="cuda")
+        _check(lib().fno_forward_train(C.byref(self.wt), _ptr(a), self.B, nx, ny, nz, _ptr(E), _ptr(self.ws),
+                                       self.n, self.ckpt, _stream_handle(stream)), "fno_forward_train")
+        return E
+
+    def backward(self, a: torch.Tensor, dE: torch.Tensor, grads: Dict[str, torch.Tensor],
+                 stream: Optional[torch.cuda.Stream] = None) -> None:
+        """Add the parameter gradients of the last forward, given dE = dJ/dRe E + i dJ/dIm E, into grads."""
+        nz, ny, nx = self.shape
+        dE = dE.contiguous()
+        assert dE.dtype == torch.complex64 and dE.shape == (self.B, 3, nz, ny, nx)
+        g = FnoGrads(*[_ptr(grads[n]) for n in FNO_PARAM_NAMES])
+        _check(lib().fno_backward(C.byref(self.wt), C.byref(g), _ptr(a), self.B, nx, ny, nz, _ptr(dE),
+                                  _ptr(self.ws), self.n, self.ckpt, _stream_handle(stream)), "fno_backward")
 
 
 def spectral_upsample(src: torch.Tensor, nz: int, ny: int, nx: int,
