@@ -754,7 +754,7 @@ static int run_plane(psfd_plan_s* P, const PlaneArgs& a, long nplanes) {
 // 1 if the single-pass plane kernel handles this grid, and launches it
 static int plane_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint, bool to_y, bool* handled) {
   *handled = false;
-  if (P->nx != P->ny || P->nx > 128 || P->plane_off) return PSFD_OK;
+  if (P->nx != P->ny || P->nx > 128 || !P->use_plane) return PSFD_OK;
   if (!P->err) PSFD_CUDA_TRY(cudaMalloc((void**)&P->err, sizeof(int)));
   const int nab = P->za1 - P->za0;
   PlaneArgs a;

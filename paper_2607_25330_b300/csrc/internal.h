@@ -61,9 +61,9 @@ struct psfd_plan_s {
   int axial_T = 0;
   // FP64 residual path (built on first refined solve)
   Fp64Tables F;
-  // single-pass plane kernel: error word of its bounded waits; plane_off forces the 3-pass path
+  // single-pass plane kernel: error word of its bounded waits; use_plane enables the kernel
   int* err = nullptr;
-  bool plane_off = false;
+  bool use_plane = false;
 };
 
 // apply64.cu

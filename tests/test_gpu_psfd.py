@@ -271,8 +271,8 @@ def test_single_pass_plane_kernel_equals_three_pass_contrast(n, monkeypatch):
     prob = problem(n, n, 32, theta=6.0, pols=[0, 1])
     a = I.mask_for(prob, 2)
     plans = []
-    for off in ("0", "1"):
-        monkeypatch.setenv("PSFD_PLANE_OFF", off)
+    for on in ("1", "0"):
+        monkeypatch.setenv("PSFD_PLANE", on)
         p = psfd.Plan(prob)
         fill = p.mask_fill(torch.from_numpy(a), prob.zprofile())
         p.background(prob.stack(), fill, prob.pols)
