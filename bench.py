@@ -4,11 +4,14 @@ One step = the whole hot path for one synthetic mask of the 128x128x64 workload
 (2 nm pixels, random Manhattan layout of 4-24 rectangles, absorber n = 0.94+0.04i
 with capping layer, TE + TM at 6 deg = 2 right-hand sides sharing one operator):
   mask -> smoothed fill (psfd_mask_fill) -> FP64 multilayer reflection and source
-  b (psfd_background) -> factorised-FNO warm start for each polarisation
-  (fno_forward, seed-initialised weights) -> spectral-damping right-preconditioned
-  BiCGSTAB to ||b - A E|| / ||b|| <= 1e-6 (psfd_solve with x0) -> true residual.
+  b (psfd_background) -> layered-background preconditioner blocks (psfd_layered_build)
+  -> factorised-FNO warm start for each polarisation (fno_forward, seed-initialised
+  weights) -> right-preconditioned GMRES(30) inside FP64 iterative refinement to
+  ||b - A E|| / ||b|| <= 1e-6 (psfd_solve_ex with x0) -> FP64 true residual.
 `value` counts solved right-hand sides per second over the timed steps.  The same
-step without the warm start (null initialisation) is reported as `cold`.
+step without the warm start (null initialisation) is reported as `cold`; the
+paper's own configurations (spectral damping M warm and cold, and no
+preconditioner) run on the same masks under `paper_configurations`.
 
   python bench.py --gpus N --steps K --warmup W [--impl reference]
 
@@ -36,7 +39,7 @@ if ROOT not in sys.path:
 WORKLOAD = "manhattan_128x128x64"
 TOL = 1e-6
 PRACTICAL_TOL = 5e-2      # the paper's practical criterion (Sec. 3, Fig. 5a discussion)
-MAXIT = 4000
+MAXIT = 600
 BYTES_PER_POINT = 52.0   # algorithmic bytes of one A M apply per grid point and rhs
 
 
@@ -55,6 +58,11 @@ def parse():
     ap.add_argument("--profile-apply", type=int, default=0,
                     help="run N HYBRID A M applies on one mask and exit (small ncu captures)")
     ap.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
+    ap.add_argument("--precond", default="layered", choices=["layered", "damping"],
+                    help="headline preconditioner: layered-background P (default) or the paper's damping M")
+    ap.add_argument("--maxit-paper", type=int, default=2000,
+                    help="iteration cap of the paper-configuration arms at 1e-6 and of the null arm")
+    ap.add_argument("--skip-paper-arms", action="store_true")
     return ap.parse_args()
 
 
@@ -111,6 +119,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp32_peak_tflops():
+    """FP32 FMA peak of a B300 from its unit counts: 148 SMs x 128 lanes x 2 flop x 2.032 GHz."""
+    return 148 * 128 * 2 * 2.032e9 / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -147,8 +160,8 @@ def run_ours(args, rank, world):
     stack = prob.stack()
     zprof = prob.zprofile()
     method = psfd.PSFD_GMRES if args.method == "gmres" else psfd.PSFD_BICGSTAB
+    pc_main = psfd.PC_LAYERED if args.precond == "layered" else psfd.PC_DAMPING
     nsteps = args.warmup + args.steps
-    tol_run = TOL
     # one seeded mask per step (rank-dependent seeds: independent problems per GPU)
     masks_host = [I.mask_for(prob, 1000 * rank + s) for s in range(nsteps)]
     masks = [torch.from_numpy(m).cuda() for m in masks_host]
@@ -166,23 +179,25 @@ def run_ours(args, rank, world):
     E_host = torch.empty(plan.shape, dtype=torch.complex64).pin_memory()
     stream = torch.cuda.current_stream()
 
-    def step(i, warm=True, mask=None):
+    def step(i, warm=True, mask=None, pc=pc_main, tol=TOL, maxit=args.maxit):
+        """The whole hot path for mask i: fill, background, preconditioner set-up, warm start, solve."""
         fill = plan.mask_fill(masks[i] if mask is None else mask, zprof)
         b = plan.background(stack, fill, prob.pols)
+        if pc == psfd.PC_LAYERED:
+            plan.layered_build()
         if warm:
             a = fill.unsqueeze(0).contiguous()
             for r, m in enumerate(models):
                 psfd.fno_forward(m, a, out=x0[r:r + 1])
-        res = plan.solve_ex(b, x0=x0 if warm else None, tol=tol_run, maxit=args.maxit, method=method,
-                            restart=args.restart, refine=True, inner_tol=1e-2, out=E, workspace=ws)
-        return res
+        return plan.solve_ex(b, x0=x0 if warm else None, tol=tol, maxit=maxit, method=method,
+                             restart=args.restart, precond=pc, refine=True, inner_tol=1e-2, out=E, workspace=ws)
 
     # warm-up (also exercises every kernel once)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
 
-    def timed(warm):
+    def timed(**kw):
         infos = []
         if world > 1:
             torch.distributed.barrier()
@@ -191,27 +206,35 @@ def run_ours(args, rank, world):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(args.warmup, nsteps):
-            infos.append(step(i, warm)["info"])
+            infos.append(step(i, **kw)["info"])
         e1.record(stream)
         torch.cuda.synchronize()
-        launches = psfd.launch_count() - l0
-        ms = e0.elapsed_time(e1)
-        return ms, infos, launches
+        return e0.elapsed_time(e1), infos, psfd.launch_count() - l0
+
+    def converged(infos):
+        return sum(1 for inf in infos for r in inf if r["status"] == 0)
+
+    # only right-hand sides that reached the tolerance count as solves; units summed over the
+    # replicas, time = the slowest replica's timed region
+    def rate(infos, ms):
+        units, ms_max = job_throughput(converged(infos), ms, world)
+        return units / (ms_max / 1e3), ms_max
+
+    def arm(t):
+        ms, infos, _ = t
+        v, msm = rate(infos, ms)
+        return {"value": v, "ms_per_step": msm / args.steps, "converged": f"{converged(infos)} of "
+                f"{sum(len(x) for x in infos)}", "iters": [r["iters"] for inf in infos for r in inf],
+                "r_rel_fp64": [r["r_rel"] for inf in infos for r in inf]}
 
     clk = ClockSampler(dev)
     clk.start()
-    ms_warm, info_warm, launches = timed(True)
+    ms_warm, info_warm, launches = timed(warm=True)
     clocks = clk.stop()
-    ms_cold, info_cold, _ = timed(False)
-    # the same steps to the paper's practical criterion r_rel <= 5e-2
-    tol_run = PRACTICAL_TOL
-    ms_pw, info_pw, _ = timed(True)
-    ms_pc, info_pc, _ = timed(False)
-    tol_run = TOL
+    ms_cold, info_cold, _ = timed(warm=False)
 
     # end to end through the public API: host mask in, host field out, copies inside the region
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     info_e2e = []
@@ -225,71 +248,91 @@ def run_ours(args, rank, world):
     h2d = pinned[0].numel() * pinned[0].element_size()
     d2h = E_host.numel() * E_host.element_size()
 
-    # dominant operation: the A M matvec in the HYBRID domain, timed live with events
-    x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")
-    y = torch.empty_like(x)
-    flags = psfd.PSFD_PRECOND | psfd.PSFD_HYBRID
-    fill = plan.mask_fill(masks[0], zprof)
-    plan.background(stack, fill, prob.pols)
-    for _ in range(5):
-        plan.apply(x, flags=flags, out=y)
-    psfd.timing_enable(True)
-    nap = 30
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ea.record(stream)
-    for _ in range(nap):
-        plan.apply(x, flags=flags, out=y)
-    eb.record(stream)
-    torch.cuda.synchronize()
-    stages = psfd.timing_read()
-    psfd.timing_enable(False)
-    ms_apply = ea.elapsed_time(eb) / nap
-    # per-stage shares inside a warm solve step
+    # the paper's configurations on the same masks: spectral damping M (warm, cold) and the null
+    # configuration (no preconditioner, cold), at 1e-6 and at the practical 5e-2
+    paper = {}
+    if not args.skip_paper_arms:
+        pd = psfd.PC_DAMPING
+        paper["damping_warm_1e-6"] = arm(timed(warm=True, pc=pd, maxit=args.maxit_paper))
+        paper["damping_cold_1e-6"] = arm(timed(warm=False, pc=pd, maxit=args.maxit_paper))
+        paper["damping_warm_5e-2"] = arm(timed(warm=True, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
+        paper["damping_cold_5e-2"] = arm(timed(warm=False, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
+        paper["null_cold_5e-2"] = arm(timed(warm=False, pc=psfd.PC_NONE, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
+        for k in paper:
+            paper[k]["maxit"] = args.maxit_paper
+        paper["note"] = ("the paper's spectral damping M and null configuration on the same masks and solver; "
+                         "only right-hand sides that reached the tolerance within maxit count")
+
+    # per-stage CUDA-event timing inside one headline step (stage byte counts are algorithmic)
     psfd.timing_enable(True)
     step(args.warmup, True)
     torch.cuda.synchronize()
     solve_stages = psfd.timing_read()
     psfd.timing_enable(False)
 
+    # dominant operations timed live: the A P matvec pieces in the HYBRID domain
+    x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    nap = 20
+    psfd.timing_enable(True)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(nap):
+        plan.apply(x, flags=psfd.PSFD_HYBRID | (psfd.PSFD_LAYERED if pc_main == psfd.PC_LAYERED else psfd.PSFD_PRECOND),
+                   out=y)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    mv_stages = psfd.timing_read()
+    psfd.timing_enable(False)
+    ms_apply = ea.elapsed_time(eb) / nap
+
     npts = prob.nx * prob.ny * prob.nz * nrhs
     peak, peak_kind = measured_peaks()
-    apply_bytes = npts * BYTES_PER_POINT
-    # roofline of each stage inside the solve step: algorithmic bytes / CUDA-event time
-    kernels = {"axial": "k_axial (fused M + stretched curl-curl + R column kernel)",
+    fp32_peak = fp32_peak_tflops()
+    # Gauss-Jordan inversion of the TE (nz) and TM (2 nz) blocks of every lateral column:
+    # N^3 complex multiply-adds (8 real flops each) per N x N block
+    lay_flops = prob.nx * prob.ny * 8.0 * (prob.nz ** 3 + (2 * prob.nz) ** 3)
+    kernels = {"axial": "k_axial (fused curl-curl + R column kernel)",
                "contrast": "k_rows/k_cols contrast passes (absorber planes)",
                "krylov": "Krylov vector kernels (k_vec, k_gdot, k_gupd, k_v64)",
-               "transform": "lateral real<->HYBRID transforms (k_rows/k_cols)"}
+               "transform": "lateral real<->HYBRID transforms (k_rows/k_cols)",
+               "precond": "k_lay_apply (per-column TE/TM inverse blocks x vector)",
+               "lay_build": "k_lay_inv (per-column TE/TM assembly + Gauss-Jordan inversion, FP32)",
+               "fno": "FNO forward kernels"}
     by_stage = {}
-    for k, v in solve_stages.items():
-        if v["calls"] and v["bytes"] > 0 and k in kernels:
-            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
-            by_stage[k] = {"ms": v["ms"], "share": None, "GBps": gbs, "frac": gbs / peak,
-                           "bytes_per_call": v["bytes"] / v["calls"], "ms_per_call": v["ms"] / v["calls"]}
     tot_ms = sum(v["ms"] for v in solve_stages.values() if v["calls"])
-    for k in by_stage:
-        by_stage[k]["share"] = by_stage[k]["ms"] / tot_ms
+    for k, v in solve_stages.items():
+        if not v["calls"] or k not in kernels:
+            continue
+        e = {"ms": v["ms"], "share": v["ms"] / tot_ms, "calls": v["calls"], "ms_per_call": v["ms"] / v["calls"]}
+        if k == "lay_build":
+            tf = lay_flops / (v["ms"] / v["calls"] / 1e3) / 1e12
+            e.update({"bound": "alu", "TFLOPs_fp32": tf, "frac": tf / fp32_peak,
+                      "flops_per_call": lay_flops})
+        elif v["bytes"] > 0:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            e.update({"bound": "hbm", "GBps": gbs, "frac": gbs / peak, "bytes_per_call": v["bytes"] / v["calls"]})
+        by_stage[k] = e
     dom = max(by_stage, key=lambda k: by_stage[k]["ms"])
     d = by_stage[dom]
+    if d.get("bound") == "alu":
+        roof = {"kernel": kernels[dom], "stage": dom, "bound": "alu", "achieved": d["TFLOPs_fp32"],
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": d["frac"], "traffic": None,
+                "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                "ms_per_launch": d["ms_per_call"], "algorithmic_flops_per_launch": lay_flops,
+                "share_of_step": d["share"]}
+    else:
+        roof = {"kernel": kernels[dom], "stage": dom, "bound": "hbm", "achieved": d["GBps"], "peak": peak,
+                "unit": "GB/s", "frac": d["frac"], "traffic": None, "peak_kind": peak_kind,
+                "ms_per_launch": d["ms_per_call"], "algorithmic_bytes_per_launch": d["bytes_per_call"],
+                "share_of_step": d["share"]}
     K = args.steps
-
-    def converged(infos):
-        return sum(1 for inf in infos for r in inf if r["status"] == 0)
-
-    # only right-hand sides that reached the tolerance count as solves; units summed over the
-    # replicas, time = the slowest replica's timed region
-    def rate(infos, ms):
-        units, ms_max = job_throughput(converged(infos), ms, world)
-        return units / (ms_max / 1e3), ms_max
-
-    value, ms_warm = rate(info_warm, ms_warm)
-    cold_value, ms_cold = rate(info_cold, ms_cold)
-    e2e_value, ms_e2e = rate(info_e2e, ms_e2e)
-    pw_value, ms_pw = rate(info_pw, ms_pw)
-    pc_value, ms_pc = rate(info_pc, ms_pc)
-    iters_w = [r["iters"] for inf in info_warm for r in inf]
-    iters_c = [r["iters"] for inf in info_cold for r in inf]
-    rrel = [r["r_rel"] for inf in info_warm + info_cold for r in inf]
-    status = [r["status"] for inf in info_warm + info_cold for r in inf]
+    value, ms_warm_max = rate(info_warm, ms_warm)
+    cold_value, ms_cold_max = rate(info_cold, ms_cold)
+    e2e_value, _ = rate(info_e2e, ms_e2e)
+    pc_name = {psfd.PC_LAYERED: "layered-background preconditioner P (per-mode TE/TM inverse of the "
+                                "laterally averaged operator; not in the paper)",
+               psfd.PC_DAMPING: "spectral damping M (the paper's preconditioner)"}[pc_main]
     out = {
         "metric": "PSFD solves/s to rel. residual 1e-6 (warm start; cold alongside)",
         "value": value,
@@ -297,42 +340,41 @@ def run_ours(args, rank, world):
         "n_gpus": world,
         "steps": K,
         "warmup": args.warmup,
-        "ms_per_step": ms_warm / K,
+        "ms_per_step": ms_warm_max / K,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64 (FP64 reductions, bf16 FNO mixing)",
+        "dtype": "c64 (FP64 reductions and refinement residual, bf16 FNO mixing)",
         "data": "synthetic: seeded random Manhattan masks (4-24 rectangles, edges 4-40 px), "
                 "seed-initialised FNO weights",
         "config": {"workload": args.workload, "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
                    "rhs_per_step": nrhs, "pols": ["TE", "TM"][:nrhs], "theta_deg": prob.theta_deg, "tol": TOL,
-                   "solver": f"{args.method}({args.restart}) in complex64 with FP64 outer residual and field "
-                             "(mixed-precision refinement, inner tol 1e-2), spectral-damping right preconditioner, "
-                             "affine warm start",
-                   "damping": {"m_min": prob.m_min, "gamma": prob.gamma, "k_ref": "k0"},
-                   "l2": "working set (>= 9 vectors x 25 MB) exceeds the 126 MB L2; no flush",
+                   "preconditioner": pc_name,
+                   "solver": f"{args.method}({args.restart}) in complex64 inside FP64 iterative refinement "
+                             "(FP64 residual and field, inner tol 1e-2), right preconditioning, affine warm start",
+                   "step": "mask -> fill -> FP64 TMM + source -> preconditioner set-up -> FNO warm start -> "
+                           "solve -> FP64 true residual",
+                   "l2": "working set (2.7 GB of blocks + >= 9 vectors x 25 MB) exceeds the 126 MB L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "solve": {"iters_warm": iters_w, "iters_cold": iters_c, "r_rel_fp64_warm": [r["r_rel"] for inf in info_warm for r in inf],
+        "solve": {"iters_warm": [r["iters"] for inf in info_warm for r in inf],
+                  "iters_cold": [r["iters"] for inf in info_cold for r in inf],
+                  "outer_steps_warm": [r["outer"] for inf in info_warm for r in inf],
+                  "r_rel_fp64_warm": [r["r_rel"] for inf in info_warm for r in inf],
                   "r_rel_fp64_cold": [r["r_rel"] for inf in info_cold for r in inf],
                   "r_rel_output_c64": [r["r_rel_output"] for inf in info_warm + info_cold for r in inf],
-                  "status": status, "converged": f"{converged(info_warm) + converged(info_cold)} of {len(status)}",
-                  "maxit": args.maxit, "outer_steps": [r["outer"] for inf in info_warm for r in inf],
-                  "r_rel_initial_warm": [r["r_rel_initial"] for inf in info_warm for r in inf]},
-        "cold": {"value": cold_value, "unit": "solves/s", "ms_per_step": ms_cold / K},
-        "practical_5e-2": {"warm": {"value": pw_value, "ms_per_step": ms_pw / K,
-                                    "iters": [r["iters"] for inf in info_pw for r in inf]},
-                           "cold": {"value": pc_value, "ms_per_step": ms_pc / K,
-                                    "iters": [r["iters"] for inf in info_pc for r in inf]},
-                           "unit": "solves/s"},
+                  "r_rel_initial_warm": [r["r_rel_initial"] for inf in info_warm for r in inf],
+                  "converged": f"{converged(info_warm) + converged(info_cold)} of "
+                               f"{sum(len(x) for x in info_warm + info_cold)}", "maxit": args.maxit},
+        "cold": {"value": cold_value, "unit": "solves/s", "ms_per_step": ms_cold_max / K},
+        "paper_configurations": paper,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "matvec": {"ms": ms_apply, "algorithmic_bytes": apply_bytes, "GBps_algorithmic": apply_bytes / ms_apply / 1e6,
-                   "frac_of_peak": apply_bytes / ms_apply / 1e6 / peak, "stages_ms_per_apply":
-                       {k: v["ms"] / nap for k, v in stages.items() if v["calls"]}},
-        "roofline": {"kernel": kernels[dom], "stage": dom, "bound": "hbm", "achieved": d["GBps"], "peak": peak,
-                     "unit": "GB/s", "frac": d["frac"], "traffic": None, "peak_kind": peak_kind,
-                     "ms_per_launch": d["ms_per_call"], "algorithmic_bytes_per_launch": d["bytes_per_call"],
-                     "share_of_step": d["share"]},
+        "matvec": {"ms_per_A_P_apply": ms_apply, "stages_ms_per_apply":
+                   {k: v["ms"] / nap for k, v in mv_stages.items() if v["calls"]},
+                   "GBps_algorithmic": {k: v["bytes"] / (v["ms"] / 1e3) / 1e9 for k, v in mv_stages.items()
+                                        if v["calls"] and v["bytes"] > 0},
+                   "A_bytes_per_point_rhs": BYTES_PER_POINT, "points_x_rhs": npts},
+        "roofline": roof,
         "roofline_by_stage": by_stage,
         "solve_stage_ms": {k: v["ms"] for k, v in solve_stages.items() if v["calls"]},
         "clocks": clocks,
@@ -341,7 +383,7 @@ def run_ours(args, rank, world):
 
 
 def run_profile_apply(args):
-    """N applies of A M in the HYBRID domain on one mask (for kernel captures)."""
+    """N applies of A P (layered) or A M (damping) in the HYBRID domain on one mask (kernel captures)."""
     import torch
     from paper_2607_25330_b300 import inputs as I
     from paper_2607_25330_b300 import psfd
@@ -350,23 +392,28 @@ def run_profile_apply(args):
     plan = psfd.Plan(prob, nrhs=nrhs)
     fill = plan.mask_fill(torch.from_numpy(I.mask_for(prob, 0)).cuda(), prob.zprofile())
     plan.background(prob.stack(), fill, prob.pols[:nrhs] if nrhs <= len(prob.pols) else [0] * nrhs)
+    flags = psfd.PSFD_HYBRID | psfd.PSFD_PRECOND
+    if args.precond == "layered" and plan.layered_bytes() > 0:
+        plan.layered_build()
+        flags = psfd.PSFD_HYBRID | psfd.PSFD_LAYERED
     x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.profile_apply):
-        plan.apply(x, flags=psfd.PSFD_PRECOND | psfd.PSFD_HYBRID, out=y)
+        plan.apply(x, flags=flags, out=y)
     e1.record()
     torch.cuda.synchronize()
-    return {"profile_apply": args.profile_apply, "workload": args.workload, "nrhs": nrhs,
+    return {"profile_apply": args.profile_apply, "workload": args.workload, "nrhs": nrhs, "flags": flags,
             "ms_per_apply": e0.elapsed_time(e1) / max(1, args.profile_apply)}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(prob, seed, n_iter, method="gmres"):
-    """Time the FP64 oracle: setup + a fixed number of Krylov iterations of the bench's method."""
+def oracle_sample(prob, seed):
+    """Time the FP64 oracle's pieces of one solve with the layered preconditioner on one mask and
+    one polarisation: set-up (fill, TMM tables, b), one operator apply, and one application of
+    the per-mode block inverses (torch.linalg.solve on blocks of the true size)."""
     import torch
-    from oracle import krylov as K
     from oracle import psfd as O
     from paper_2607_25330_b300 import inputs as I
     a = I.mask_for(prob, seed)
@@ -375,41 +422,55 @@ def oracle_sample(prob, seed, n_iter, method="gmres"):
     fill = O.fill_fraction(a, prob.zprofile(), prob.sigma_px)
     b = O.source_b(g, fill, prob.pols[0])
     t_setup = time.perf_counter() - t0
-    A = lambda E: O.apply_A(g, E, fill)
-    M = lambda x: O.apply_M(g, x)
     t1 = time.perf_counter()
-    K.solve(A, M, b, tol=1e-30, maxit=n_iter, method=method, restart=30)
-    t_it = (time.perf_counter() - t1) / n_iter
-    return t_setup, t_it
+    O.apply_A(g, b, fill)
+    t_apply = time.perf_counter() - t1
+    # the block solves of one P application, timed on 1/16 of the lateral modes (host memory) and
+    # scaled by 16: torch.linalg.solve on (modes, 3 nz, 3 nz) complex128 blocks, as apply_P_layered does
+    n = 3 * g.nz
+    nsub = max(1, g.ny * g.nx // 16)
+    gen = torch.Generator().manual_seed(seed)
+    mats = torch.eye(n, dtype=torch.complex128).expand(nsub, n, n) + 0.01 * torch.randn(
+        nsub, n, n, dtype=torch.complex128, generator=gen)
+    rhs = torch.randn(nsub, n, 1, dtype=torch.complex128, generator=gen)
+    t2 = time.perf_counter()
+    torch.linalg.solve(mats, rhs)
+    t_p = (time.perf_counter() - t2) * (g.ny * g.nx / nsub)
+    return t_setup, t_apply, t_p, n
+
+
+def oracle_seconds_per_solve(t_setup, t_apply, t_p, n, iters):
+    # set-up + block build (one apply per unit source: 3 nz of them) + per iteration one A and one P
+    return t_setup + n * t_apply + iters * (t_apply + t_p)
 
 
 def cpu_baseline(args, iters_per_solve):
     import torch
     from paper_2607_25330_b300 import inputs as I
     prob = I.preset(args.workload)
-    n_iter = 6
-    t_setup, t_it = oracle_sample(prob, 0, n_iter, args.method)
-    s_per_solve = t_setup + t_it * iters_per_solve
-    return {"value": 1.0 / s_per_solve, "unit": "solves/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle on one {args.workload} mask, one polarisation: setup + {n_iter} "
-                      f"{args.method} iterations timed ({t_it:.2f} s/iteration, {t_setup:.2f} s setup), scaled to "
-                      f"{iters_per_solve:.0f} iterations per solve (the GPU solve's mean count)"}
+    t_setup, t_apply, t_p, n = oracle_sample(prob, 0)
+    s = oracle_seconds_per_solve(t_setup, t_apply, t_p, n, iters_per_solve)
+    return {"value": 1.0 / s, "unit": "solves/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle on one {args.workload} mask, one polarisation: set-up {t_setup:.2f} s, "
+                      f"one A apply {t_apply:.2f} s, one P application {t_p:.2f} s (blocks of the true size); "
+                      f"solve = set-up + {n} applies for the blocks + {iters_per_solve:.0f} iterations "
+                      f"(the GPU solve's mean count) x (A + P)"}
 
 
 def run_reference(args):
     import torch
     from paper_2607_25330_b300 import inputs as I
     prob = I.preset(args.workload)
-    iters_per_solve = float(MAXIT)   # the GPU arm's iteration cap per solve; stated, not measured here
+    iters_per_solve = 20.0   # typical GPU iteration count of this workload's layered solve; stated
     times = []
     for s in range(args.warmup + args.steps):
-        t_setup, t_it = oracle_sample(prob, s, 2, args.method)
+        t_setup, t_apply, t_p, n = oracle_sample(prob, s)
         if s >= args.warmup:
-            times.append(t_setup + t_it * iters_per_solve)
+            times.append(oracle_seconds_per_solve(t_setup, t_apply, t_p, n, iters_per_solve))
     value = 1.0 / (sum(times) / len(times))
     cb = {"value": value, "unit": "solves/s", "cores": torch.get_num_threads(), "kind": "oracle",
-          "sample": f"per step: FP64 oracle setup + 2 {args.method} iterations on one {args.workload} mask, "
-                    f"scaled to {iters_per_solve:.0f} iterations per solve"}
+          "sample": f"per step: FP64 oracle set-up, one A apply and one P application on one {args.workload} "
+                    f"mask; solve = set-up + 3 nz applies for the blocks + {iters_per_solve:.0f} iterations x (A + P)"}
     return {"impl": "reference", "metric": "PSFD solves/s to rel. residual 1e-6 (warm start; cold alongside)",
             "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
@@ -436,7 +497,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = out["solve"]["iters_warm"]
-            out["cpu_baseline"] = cpu_baseline(args, float(np.mean(iters)) if iters else 1000.0)
+            out["cpu_baseline"] = cpu_baseline(args, float(np.mean(iters)) if iters else 20.0)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch

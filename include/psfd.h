@@ -61,7 +61,9 @@ enum { PSFD_TE = 0, PSFD_TM = 1 };
 enum {
   PSFD_PRECOND = 1,          /* apply A M instead of A                          */
   PSFD_HYBRID = 2,           /* x and y are in the HYBRID (kx, ky, z) domain    */
-  PSFD_ADJOINT = 4           /* apply A^H (or (A M)^H = M A^H with PSFD_PRECOND) */
+  PSFD_ADJOINT = 4,          /* apply A^H (or (A M)^H = M A^H with PSFD_PRECOND) */
+  PSFD_LAYERED = 8           /* apply A P with the layered-background preconditioner P
+                                (psfd_layered_build); not combined with ADJOINT    */
 };
 
 enum { PSFD_BICGSTAB = 0, PSFD_GMRES = 1 };
@@ -145,20 +147,39 @@ PSFD_API int psfd_reflection_tables(psfd_plan plan, double* rs, double* rp, doub
  *         vector_helmholtz_operator; derivatives pseudo-spectral, PML in z)
  * flags: PSFD_PRECOND -> y = A M x (Eq. right_preconditioned);
  *        PSFD_ADJOINT -> y = A^H x (with PRECOND: M A^H x);
+ *        PSFD_LAYERED -> y = A P x (P: layered-background preconditioner);
  *        PSFD_HYBRID  -> x, y in the HYBRID domain (no lateral transforms of x, y).
  * x, y: device [nrhs][3][nz][ny][nx]; x and y must not overlap. */
 PSFD_API int psfd_apply(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int flags);
 
 /* y = M x, spectral damping (Eq. spectral_damping_action): componentwise 3-D
- * Fourier multiplier m(k).  flags: PSFD_HYBRID.  In-place (x == y) allowed. */
+ * Fourier multiplier m(k); with PSFD_LAYERED in flags, y = P x instead.
+ * flags: PSFD_HYBRID, PSFD_LAYERED.  In-place (x == y) allowed. */
 PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int flags);
+
+/* ---------------------------------------------------------------- layered-background preconditioner
+ * Not in the paper: an alternative right preconditioner P = A0^-1, where A0 is A
+ * with the contrast replaced on every z-plane by its lateral mean
+ * (deps_bar(z) = (eps_abs - 1) * mean_xy fill(z)).  A0 does not couple lateral
+ * Bloch modes; per mode it splits into a TE block (nz x nz, E along s) and a TM
+ * block (2nz x 2nz, (E_t, E_z)), which psfd_layered_build assembles and inverts
+ * (FP32, partial pivoting) on the device and stores in the plan:
+ * psfd_layered_bytes() bytes = nx*ny*5*nz^2 complex64 (2.7 GB at 128x128x64).
+ * Call after psfd_background (again after each psfd_background).  Supported for
+ * nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else PSFD_ERR_ARG /
+ * psfd_layered_bytes() = 0); PSFD_ERR_BREAKDOWN if a block is singular.
+ * Synchronises the plan's stream. */
+PSFD_API int psfd_layered_build(psfd_plan plan);
+PSFD_API size_t psfd_layered_bytes(psfd_plan plan);
 
 /* ---------------------------------------------------------------- solve (Sec. 3, warm start)
  * Solves A E = b for every right-hand side with right preconditioning and an
  * affine warm start: E = E_base + M y with A M y = b - A E_base
  * (Eqs. right_correction_solution, right_preconditioned_system); x0 = NULL is
- * the null initialisation (Eq. right_preconditioned).  With use_precond = 0, M
- * is the identity (the paper's "null preconditioner").  Convergence: recursive
+ * the null initialisation (Eq. right_preconditioned).  use_precond: 1 = the
+ * spectral damping M; 0 = identity (the paper's "null preconditioner");
+ * 2 = the layered-background preconditioner P in place of M (psfd_layered_build
+ * first, else PSFD_ERR_STATE).  Convergence: recursive
  * relative residual <= tol with ||b|| of the original b (Eq. relative_residual);
  * the true residual is recomputed in FP64 at exit.
  *   b, x0 (nullable), E: device [nrhs][3][nz][ny][nx], real space.
@@ -301,7 +322,8 @@ PSFD_API int psfd_spectral_upsample_static(const psfd_c64* src, int nb, int nx0,
  * psfd_timing_enable(1) starts per-stage timing with CUDA events recorded on each
  * call's stream around the launches of a stage (0 fused axial operator kernel,
  * 1 lateral contrast passes, 2 Krylov vector kernels, 3 lateral real<->HYBRID
- * transforms, 4 FNO forward) and clears the totals; 0 stops it.
+ * transforms, 4 FNO forward and backward, 5 layered preconditioner apply,
+ * 6 layered preconditioner build) and clears the totals; 0 stops it.
  * psfd_timing_read synchronises on the recorded events and returns the summed
  * milliseconds and the number of timed launches groups per stage (HOST arrays). */
 PSFD_API long long psfd_launch_count(void);

@@ -37,7 +37,10 @@ operator, Fresnel / quarter-wave / lossless-stack closed forms for the
 reflection coefficients, an independent transfer-matrix product, the blank-mask
 invariant, the homogeneous absorber slab against the Airy formula and against
 the reflection of [slab | multilayer], the adjoint identity and the dense
-conjugate transpose, and the periodised Gaussian for the smoothing.
+conjugate transpose, and the periodised Gaussian for the smoothing.  The
+layered-background preconditioner (an addition to the paper's method): with a
+laterally uniform fill it is the exact inverse of A; in the (s, t, z) basis of
+every lateral mode its blocks do not couple E_s with (E_t, E_z).
 """
 from __future__ import annotations
 
@@ -346,3 +349,41 @@ def upgoing_amplitude(g: Grid, Etot_y_column: torch.Tensor, k: int) -> complex:
     """Helper for slab tests: amplitude of exp(+i kz_inc (z - z_ml)) in a 1-D column at plane k."""
     zrel = (k - g.z_ml) * g.dz
     return complex(Etot_y_column[k] * torch.exp(torch.tensor(-1j * g.kz_inc * zrel)))
+
+
+# --------------------------------------------------------------------------- layered-background preconditioner
+# Not in the paper: the right preconditioner P = A0^-1 with A0 the operator A whose contrast is
+# replaced, on every z-plane, by its lateral mean.  A0 couples no lateral Bloch modes.
+
+def lateral_mean_fill(fill: torch.Tensor) -> torch.Tensor:
+    """The fill averaged over every z-plane and broadcast back to (nz, ny, nx)."""
+    return fill.to(F64).mean(dim=(1, 2), keepdim=True).expand_as(fill).contiguous()
+
+
+def layered_blocks(g: Grid, fill: torch.Tensor) -> torch.Tensor:
+    """Per-mode matrices of A0, shape (ny, nx, 3 nz, 3 nz), index c * nz + z (c = x, y, z).
+
+    Column (c, z') is A0 applied to a unit source at component c, plane z' and the lateral
+    origin: the lateral DFT of that source is 1 in every mode, so the DFT of the output is
+    column (c, z') of every mode's matrix at once.
+    """
+    fbar = lateral_mean_fill(fill)
+    n = 3 * g.nz
+    mats = torch.zeros(g.ny, g.nx, n, n, dtype=C128)
+    for c in range(3):
+        for z in range(g.nz):
+            E = torch.zeros(g.shape, dtype=C128)
+            E[c, z, 0, 0] = 1.0
+            Yh = _fft2(apply_A(g, E, fbar))                      # (3, nz, ny, nx)
+            mats[:, :, :, c * g.nz + z] = Yh.permute(2, 3, 0, 1).reshape(g.ny, g.nx, n)
+    return mats
+
+
+def apply_P_layered(g: Grid, fill: torch.Tensor, X: torch.Tensor, mats: torch.Tensor = None) -> torch.Tensor:
+    """y = A0^-1 x per lateral mode (real-space fields (3, nz, ny, nx))."""
+    if mats is None:
+        mats = layered_blocks(g, fill)
+    n = 3 * g.nz
+    Xh = _fft2(X.to(C128)).permute(2, 3, 0, 1).reshape(g.ny, g.nx, n, 1)
+    Yh = torch.linalg.solve(mats, Xh).reshape(g.ny, g.nx, 3, g.nz).permute(2, 3, 0, 1)
+    return _ifft2(Yh)

@@ -840,12 +840,18 @@ static int adjoint_contrast(psfd_plan_s* P, const cf* x) {
 int apply_hybrid(psfd_plan_s* P, const cf* x, cf* y, int flags, const int* done) {
   int rc;
   if (flags & PSFD_ADJOINT) {
+    if (flags & PSFD_LAYERED) { psfd_set_error("psfd_apply: PSFD_LAYERED has no adjoint"); return PSFD_ERR_ARG; }
     if ((rc = adjoint_contrast(P, x))) return rc;
     if (!(flags & PSFD_PRECOND)) return launch_axial(P, x, y, AX_AH, done, P->nrhs);
     if ((rc = launch_axial(P, x, P->tmpB, AX_AH, done, P->nrhs))) return rc;
     return launch_axial(P, P->tmpB, y, AX_M, done, P->nrhs);
   }
-  rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) ? AX_AM : AX_A, done, P->nrhs);
+  if (flags & PSFD_LAYERED) {
+    // A P x: the per-column inverses first, then the operator
+    if ((rc = layered_apply(P, x, P->tmpB))) return rc;
+    x = P->tmpB;
+  }
+  rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) && !(flags & PSFD_LAYERED) ? AX_AM : AX_A, done, P->nrhs);
   if (rc) return rc;
   return launch_lateral_contrast(P, y, done, false);
 }
@@ -854,6 +860,10 @@ extern "C" int psfd_apply(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags
   if (!P || !x || !y) { psfd_set_error("psfd_apply: null argument"); return PSFD_ERR_ARG; }
   if (!P->have_background) { psfd_set_error("psfd_apply: call psfd_background first"); return PSFD_ERR_STATE; }
   if (x == y) { psfd_set_error("psfd_apply: x and y must not overlap"); return PSFD_ERR_ARG; }
+  if ((flags & PSFD_LAYERED) && !P->lay_built) {
+    psfd_set_error("psfd_apply: call psfd_layered_build first");
+    return PSFD_ERR_STATE;
+  }
   const cf* xi = (const cf*)x;
   cf* yo = (cf*)y;
   const long bytes = (long)P->nrhs * P->nvec * sizeof(cf);
@@ -870,18 +880,23 @@ extern "C" int psfd_apply(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags
 extern "C" int psfd_precond(psfd_plan P, const psfd_c64* x, psfd_c64* y, int flags) {
   if (!P || !x || !y) { psfd_set_error("psfd_precond: null argument"); return PSFD_ERR_ARG; }
   const long bytes = (long)P->nrhs * P->nvec * sizeof(cf);
+  const bool lay = (flags & PSFD_LAYERED) != 0;
+  if (lay && !P->lay_built) { psfd_set_error("psfd_precond: call psfd_layered_build first"); return PSFD_ERR_STATE; }
+  auto op = [&](const cf* in, cf* out) {
+    return lay ? layered_apply(P, in, out) : launch_axial(P, in, out, AX_M, nullptr, P->nrhs);
+  };
   if (flags & PSFD_HYBRID) {
     if ((const void*)x == (void*)y) {
       PSFD_CUDA_TRY(cudaMemcpyAsync(P->tmpA, x, bytes, cudaMemcpyDeviceToDevice, P->stream));
-      return launch_axial(P, P->tmpA, (cf*)y, AX_M, nullptr, P->nrhs);
+      return op(P->tmpA, (cf*)y);
     }
-    return launch_axial(P, (const cf*)x, (cf*)y, AX_M, nullptr, P->nrhs);
+    return op((const cf*)x, (cf*)y);
   }
   const float us = 1.0f / sqrtf((float)P->ncols);
   const long nplanes = (long)P->nrhs * 3 * P->nz;
   PSFD_CUDA_TRY(cudaMemcpyAsync(P->tmpA, x, bytes, cudaMemcpyDeviceToDevice, P->stream));
   int rc;
   if ((rc = launch_lateral_transform(P, P->tmpA, nplanes, true, us))) return rc;
-  if ((rc = launch_axial(P, P->tmpA, (cf*)y, AX_M, nullptr, P->nrhs))) return rc;
+  if ((rc = op(P->tmpA, (cf*)y))) return rc;
   return launch_lateral_transform(P, (cf*)y, nplanes, false, us);
 }

@@ -355,18 +355,8 @@ int fp64_prepare(psfd_plan_s* P) {
     for (int i = 0; i < P->nx; ++i) kx[i] = host_k(i, P->nx, P->p.dx) + P->kx_inc;
     for (int i = 0; i < P->ny; ++i) ky[i] = host_k(i, P->ny, P->p.dy) + P->ky_inc;
     for (int i = 0; i < P->nz; ++i) kz[i] = host_k(i, P->nz, P->p.dz);
-    std::vector<zd> sinv(P->nz), twx, twy, twz;
-    const int np = P->p.pml_planes;
-    const double dpml = np * P->p.dz;
-    const double alpha = np > 0 ? 4.0 * log(1.0 / P->p.pml_R0) / (2.0 * P->k0 * dpml) : 0.0;
-    for (int k = 0; k < P->nz; ++k) {
-      double d = 0.0;
-      if (k < np) d = (np - k) * P->p.dz;
-      else if (k >= P->nz - np) d = (k - (P->nz - np - 1)) * P->p.dz;
-      const double sig = np > 0 ? alpha * pow(d / dpml, 3.0) : 0.0;
-      const double den = 1.0 + sig * sig;
-      sinv[k] = make_double2(1.0 / den, -sig / den);
-    }
+    std::vector<zd> sinv, twx, twy, twz;
+    pml_sinv64(P, sinv);
     host_tw64(P->nx, twx); host_tw64(P->ny, twy); host_tw64(P->nz, twz);
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.kx, P->nx * 8));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.ky, P->ny * 8));

@@ -24,6 +24,7 @@ __device__ __forceinline__ cf cfma(cf a, cf b, cf c) {                          
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 __device__ __forceinline__ cf czero() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ cf cneg(cf a) { return make_float2(-a.x, -a.y); }
 
 // complex128 overloads (same names) for the FP64 residual path
 typedef double2 zd;
@@ -145,7 +146,8 @@ void psfd_set_error(const char* fmt, ...);
 void psfd_count_launch();
 
 // Optional per-stage timing with CUDA events on the launching stream.
-enum { ST_AXIAL = 0, ST_CONTRAST = 1, ST_KRYLOV = 2, ST_TRANSFORM = 3, ST_FNO = 4, ST_N = 5 };
+enum { ST_AXIAL = 0, ST_CONTRAST = 1, ST_KRYLOV = 2, ST_TRANSFORM = 3, ST_FNO = 4, ST_PRECOND = 5, ST_LAYBUILD = 6,
+       ST_N = 7 };
 // `bytes` is the stage's algorithmic traffic: the compulsory reads and writes of its
 // inputs and outputs (intermediate passes of a multi-kernel stage are not counted).
 void stage_mark(cudaStream_t s, int stage, bool begin, double bytes = 0.0);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include "../../include/psfd.h"
 #include "common.cuh"
 
@@ -64,6 +65,13 @@ struct psfd_plan_s {
   // single-pass plane kernel: error word of its bounded waits; use_plane enables the kernel
   int* err = nullptr;
   bool use_plane = false;
+  // layered-background preconditioner (per-column TE/TM inverses, built by psfd_layered_build)
+  cf* lay = nullptr;         // [ncols][5 nz^2]
+  cf* lay_D = nullptr;       // [nz][nz] stretched axial derivative
+  cf* lay_D2 = nullptr;      // [nz][nz]
+  cf* lay_deps = nullptr;    // [nz] laterally averaged contrast
+  int* lay_err = nullptr;
+  bool lay_built = false;
 };
 
 // apply64.cu
@@ -87,3 +95,11 @@ int lateral_supported(int n);
 
 // plan.cu
 void psfd_set_error(const char* fmt, ...);
+double fft_wavenumber(int i, int n, double d);           // 2 pi m / (n d), FFT order, Nyquist negative
+void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv);   // 1 / s(z) in FP64
+
+// layered.cu
+int layered_supported(const psfd_plan_s* P);
+size_t layered_bytes(const psfd_plan_s* P);
+int layered_apply(psfd_plan_s* P, const cf* x, cf* y);
+void layered_free(psfd_plan_s* P);

@@ -372,7 +372,7 @@ __global__ void k_copy_bnorm(KScal* sc, int nrhs) {
 namespace {
 
 constexpr int GCH = 8;       // basis vectors per multi-dot block
-constexpr int GMAX = 64;     // largest restart length supported
+constexpr int GMAX = 256;    // largest restart length supported
 
 struct GState {
   double2 H[(GMAX + 1) * GMAX];  // column-major: H[i + j*(m+1)]
@@ -812,6 +812,8 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
     psfd_set_error("psfd_solve: GMRES restart must be in [1, %d]", GMAX);
     return PSFD_ERR_ARG;
   }
+  if (use_precond < 0 || use_precond > 2) { psfd_set_error("psfd_solve: use_precond must be 0, 1 or 2"); return PSFD_ERR_ARG; }
+  if (use_precond == 2 && !P->lay_built) { psfd_set_error("psfd_solve: call psfd_layered_build first"); return PSFD_ERR_STATE; }
   cudaStream_t st = P->stream;
   SolveWs w;
   const size_t need = ws_layout(P, method, restart, &w, nullptr);
@@ -868,14 +870,16 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
   } else {
     PSFD_CUDA_TRY(cudaMemcpyAsync(w.r, w.bH, vbytes, cudaMemcpyDeviceToDevice, st));
   }
-  const int aflags = use_precond ? PSFD_PRECOND : 0;
+  const int aflags = use_precond == 2 ? PSFD_LAYERED : (use_precond ? PSFD_PRECOND : 0);
   if (method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, maxit, aflags, nb);
   else rc = gmres_loop(P, w, va, tol, maxit, restart, aflags, nb);
   if (rc) return fail(rc);
   // ---- E = E_base + M y ; true residual (FP64 norm)
   va.use_done = false;
   cf* My = w.t;
-  if (use_precond) {
+  if (use_precond == 2) {
+    if ((rc = layered_apply(P, w.y, My))) return fail(rc);
+  } else if (use_precond) {
     if ((rc = launch_axial(P, w.y, My, 2, nullptr, nr))) return fail(rc);
   } else {
     PSFD_CUDA_TRY(cudaMemcpyAsync(My, w.y, vbytes, cudaMemcpyDeviceToDevice, st));
@@ -1018,6 +1022,14 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     psfd_set_error("psfd_solve_ex: GMRES restart must be in [1, %d]", GMAX);
     return PSFD_ERR_ARG;
   }
+  if (o->use_precond < 0 || o->use_precond > 2) {
+    psfd_set_error("psfd_solve_ex: use_precond must be 0, 1 or 2");
+    return PSFD_ERR_ARG;
+  }
+  if (o->use_precond == 2 && !P->lay_built) {
+    psfd_set_error("psfd_solve_ex: call psfd_layered_build first");
+    return PSFD_ERR_STATE;
+  }
   int rc = fp64_prepare(P);
   if (rc) return rc;
   cudaStream_t st = P->stream;
@@ -1076,7 +1088,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
   int* dskip = w.active;  // reused as the per-rhs "outer converged" flag
   int outer = 0;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 100;
-  const int aflags = o->use_precond ? PSFD_PRECOND : 0;
+  const int aflags = o->use_precond == 2 ? PSFD_LAYERED : (o->use_precond ? PSFD_PRECOND : 0);
   VArgs va{};
   va.n = n; va.sc = w.sc; va.done = w.done; va.partials = w.partials; va.counters = w.counters;
   for (;; ++outer) {
@@ -1119,7 +1131,9 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
       if (!conv[r]) inner_its[r] += hs[r].iters;
     // E += M y
     cf* My = w.t;
-    if (o->use_precond) {
+    if (o->use_precond == 2) {
+      if ((rc = layered_apply(P, w.y, My))) return fail(rc);
+    } else if (o->use_precond) {
       if ((rc = launch_axial(P, w.y, My, 2, nullptr, nr))) return fail(rc);
     } else {
       PSFD_CUDA_TRY(cudaMemcpyAsync(My, w.y, vbytes, cudaMemcpyDeviceToDevice, st));

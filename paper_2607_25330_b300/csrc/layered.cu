@@ -1,0 +1,476 @@
+// Layered-background preconditioner: the exact inverse, per lateral Bloch mode, of the operator
+// with the permittivity contrast replaced by its lateral average on each plane.
+//
+// With the fill averaged over every z-plane, Δε̄(z) = (ε_abs − 1) · mean_xy f(z), the operator of
+// Eqs. bg_source / vector_helmholtz_operator no longer couples lateral modes.  For the mode
+// (kx, ky), κ = |k∥|, ŝ = (−ky, kx)/κ, t̂ = (kx, ky)/κ (ŝ = ŷ, t̂ = x̂ at κ = 0) and the
+// stretched axial derivative D = s⁻¹ F⁻¹ i k_z F, the curl-curl is
+//     (cc)_s = (κ² − D²) E_s,   (cc)_t = −D² E_t + iκ D E_z,   (cc)_z = iκ D E_t + κ² E_z,
+// and the reflection R (Sec. 2.2) maps E_s(z_ml) to r_s e(z) ŝ and E_t(z_ml) to
+// r_p e(z) (t̂ − κ/k_z ẑ), e(z) = exp(i k_z (z − z_ml)) for z ≥ z_ml.  So the averaged operator
+// splits into a TE block (E_s, nz × nz) and a TM block ((E_t, E_z), 2nz × 2nz):
+//     TE = κ² − D² − k0² (1 + Δε̄) − k0² Δε̄ r_s e e_mlᵀ
+//     TM = [ −D² − k0² (1 + Δε̄) − k0² Δε̄ r_p e e_mlᵀ      iκ D                 ]
+//          [ iκ D + k0² Δε̄ (κ r_p / k_z) e e_mlᵀ          κ² − k0² (1 + Δε̄)   ]
+// Both are assembled per column on the device and inverted in FP32 by Gauss-Jordan exchange
+// steps with partial pivoting (one CTA per matrix, the matrix held in registers), then applied as
+// dense per-column matrix-vector products in the HYBRID (kx, ky, z) domain.  Used as the right
+// preconditioner P in A P y = b − A E_base, E = E_base + P y, in place of the spectral damping
+// M of Eq. spectral_damping_action (an addition to the paper's method: the damping alone leaves
+// restarted Krylov stalling near 1e-5 at oblique incidence, where near-grazing diffraction orders
+// are barely absorbed by the axial PML; the averaged operator resolves those modes exactly).
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using zc = std::complex<double>;
+constexpr int LAY_THREADS = 256;   // 16 x 16 thread grid over an N x N matrix
+constexpr int LAY_GROUP = 4;       // lateral columns (consecutive kx) per apply CTA
+
+struct LayArgs {
+  const float* kx;
+  const float* ky;
+  const float4* refl;   // (r_s, r_p) per mode
+  const cf* kz0;        // upgoing k_z per mode
+  const cf* D;          // [nz][nz] stretched axial derivative
+  const cf* D2;         // [nz][nz] D * D
+  const cf* deps;       // [nz] laterally averaged contrast
+  float k0sq, dz;
+  int nx, nz, zml;
+  cf* mats;             // [ncols][5 nz^2]: TE inverse (nz^2) then TM inverse (4 nz^2), column-major
+  int* err;             // set to 1 if a pivot vanished
+};
+
+__device__ __forceinline__ cf cdiv1(cf a) {  // 1 / a
+  const float d = a.x * a.x + a.y * a.y;
+  return make_float2(a.x / d, -a.y / d);
+}
+
+// per-column mode data
+struct Mode {
+  float kap, kap2;
+  cf rs, rp, kz;
+};
+__device__ __forceinline__ Mode mode_of(const LayArgs& a, long col) {
+  Mode m;
+  const int ix = (int)(col % a.nx), iy = (int)(col / a.nx);
+  const float kx = a.kx[ix], ky = a.ky[iy];
+  m.kap2 = kx * kx + ky * ky;
+  m.kap = sqrtf(m.kap2);
+  const float4 r = a.refl[col];
+  m.rs = make_float2(r.x, r.y);
+  m.rp = make_float2(r.z, r.w);
+  m.kz = a.kz0[col];
+  return m;
+}
+
+// e(z) = exp(i k_z (z − z_ml) dz) for z ≥ z_ml, else 0
+__device__ __forceinline__ cf upgoing(const LayArgs& a, const Mode& m, int z) {
+  if (z < a.zml) return czero();
+  const float d = (float)(z - a.zml) * a.dz;
+  const float mag = expf(-m.kz.y * d);
+  float sn, cs;
+  sincosf(m.kz.x * d, &sn, &cs);
+  return make_float2(mag * cs, mag * sn);
+}
+
+// entry (i, j) of the TE (TM = false, N = nz) or TM (TM = true, N = 2 nz) block of a column
+template <bool TM>
+__device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
+  const int nz = a.nz;
+  if (!TM) {
+    cf v = cneg(a.D2[i * nz + j]);
+    const cf de = a.deps[i];
+    if (i == j) v = cadd(v, make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * de.y));
+    if (j == a.zml && i >= a.zml) v = csub(v, cscale(cmul(cmul(de, m.rs), upgoing(a, m, i)), a.k0sq));
+    return v;
+  }
+  const int bi = i / nz, bj = j / nz, ii = i - bi * nz, jj = j - bj * nz;
+  const cf de = a.deps[ii];
+  if (bi == 0 && bj == 0) {
+    cf v = cneg(a.D2[ii * nz + jj]);
+    if (ii == jj) v = cadd(v, make_float2(-a.k0sq * (1.f + de.x), -a.k0sq * de.y));
+    if (jj == a.zml && ii >= a.zml) v = csub(v, cscale(cmul(cmul(de, m.rp), upgoing(a, m, ii)), a.k0sq));
+    return v;
+  }
+  if (bi == 0) return ctimesi(cscale(a.D[ii * nz + jj], m.kap));   // iκ D
+  if (bj == 0) {
+    cf v = ctimesi(cscale(a.D[ii * nz + jj], m.kap));
+    if (jj == a.zml && ii >= a.zml) {
+      // + k0² Δε̄ (κ r_p / k_z) e
+      const cf c = cmul(cmul(de, m.rp), cmul(upgoing(a, m, ii), cdiv1(m.kz)));
+      v = cadd(v, cscale(c, a.k0sq * m.kap));
+    }
+    return v;
+  }
+  if (ii == jj) return make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * de.y);
+  return czero();
+}
+
+// Assemble and invert one N x N block per CTA.  Thread (rg, cg) of the 16 x 16 grid owns rows
+// rg + 16 u and columns cg + 16 v (u, v < N/16).  Step k exchanges the roles of x_k and y_p for
+// the pivot row p (largest |T[p][k]| among rows not yet used):
+//     T[p][k] <- 1/π,  T[p][j] <- −T[p][j]/π,  T[i][k] <- T[i][k]/π,  T[i][j] <- T[i][j] − T[i][k] T[p][j]/π
+// with π = T[p][k].  After N steps, row p_k holds x_k and column k' holds y_{p_k'}:
+// Minv[k][p_k'] = T[p_k][k'].
+template <int N, bool TM>
+__global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_off) {
+  constexpr int TT = N / 16;
+  __shared__ cf colv[2][N], rowv[2][N];
+  __shared__ float mag[N];
+  __shared__ int used[N], pivrow[N], rowvar[N];
+  __shared__ int s_p;
+  __shared__ cf s_pinv;
+  const long col = blockIdx.x;
+  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+  const Mode m = mode_of(a, col);
+  cf T[TT][TT];
+#pragma unroll
+  for (int u = 0; u < TT; ++u)
+#pragma unroll
+    for (int v = 0; v < TT; ++v) T[u][v] = entry<TM>(a, m, rg + 16 * u, cg + 16 * v);
+  for (int i = tid; i < N; i += LAY_THREADS) used[i] = 0;
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    const int buf = k & 1;
+    // column k -> shared (owners: cg == k % 16)
+    if (cg == (k & 15)) {
+      const int vk = k >> 4;
+#pragma unroll
+      for (int v = 0; v < TT; ++v) {
+        if (v != vk) continue;   // static register indexing: select the column by predicate
+#pragma unroll
+        for (int u = 0; u < TT; ++u) {
+          const int i = rg + 16 * u;
+          const cf t = T[u][v];
+          colv[buf][i] = t;
+          mag[i] = used[i] ? -1.f : t.x * t.x + t.y * t.y;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {
+      float best = -2.f;
+      int bi = 0;
+      for (int i = tid; i < N; i += 32) {
+        // used rows -1; a non-finite magnitude counts as 0, so the pivot is always an unused row
+        const float mv = used[i] ? -1.f : (mag[i] >= 0.f && mag[i] <= 3.0e38f ? mag[i] : 0.f);
+        if (mv > best) { best = mv; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_p = bi;
+        used[bi] = 1;
+        pivrow[k] = bi;
+        if (!(best > 0.f)) {
+          atomicExch(a.err, 1);
+          s_pinv = czero();
+        } else {
+          s_pinv = cdiv1(colv[buf][bi]);
+        }
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const cf pinv = s_pinv;
+    // pivot row p -> shared (owners: rg == p % 16)
+    if (rg == (p & 15)) {
+      const int up = p >> 4;
+#pragma unroll
+      for (int u = 0; u < TT; ++u) {
+        if (u != up) continue;
+#pragma unroll
+        for (int v = 0; v < TT; ++v) rowv[buf][cg + 16 * v] = T[u][v];
+      }
+    }
+    __syncthreads();
+    cf ci[TT], rj[TT];
+#pragma unroll
+    for (int u = 0; u < TT; ++u) ci[u] = cmul(colv[buf][rg + 16 * u], pinv);
+#pragma unroll
+    for (int v = 0; v < TT; ++v) rj[v] = rowv[buf][cg + 16 * v];
+    // rank-1 update of every owned entry; the pivot row and column are overwritten below
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+      for (int v = 0; v < TT; ++v) T[u][v] = csub(T[u][v], cmul(ci[u], rj[v]));
+    const bool own_row = rg == (p & 15), own_col = cg == (k & 15);
+    const int up = p >> 4, vk = k >> 4;
+    if (own_row) {
+#pragma unroll
+      for (int u = 0; u < TT; ++u) {
+        if (u != up) continue;
+#pragma unroll
+        for (int v = 0; v < TT; ++v) T[u][v] = cneg(cmul(rj[v], pinv));
+      }
+    }
+    if (own_col) {
+#pragma unroll
+      for (int v = 0; v < TT; ++v) {
+        if (v != vk) continue;
+#pragma unroll
+        for (int u = 0; u < TT; ++u) T[u][v] = (own_row && u == up) ? pinv : ci[u];
+      }
+    }
+  }
+  __syncthreads();
+  // pivrow is a permutation: each step picks a row not used before
+  for (int k = tid; k < N; k += LAY_THREADS) rowvar[pivrow[k]] = k;
+  __syncthreads();
+  // column-major output: element (r, c) of the inverse at c * N + r
+  cf* out = a.mats + col * (5L * a.nz * a.nz) + block_off;
+#pragma unroll
+  for (int u = 0; u < TT; ++u)
+#pragma unroll
+    for (int v = 0; v < TT; ++v) {
+      const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
+      out[(long)c * N + r] = T[u][v];
+    }
+}
+
+// mean fill of every z-plane (FP64 sum) -> deps[z] = mean * (eps_abs - 1)
+__global__ void k_plane_mean(const float* __restrict__ fill, long plane, cf* deps, double dre, double dim) {
+  __shared__ double sh[LAY_THREADS / 32];
+  const int z = blockIdx.x;
+  double s = 0.0;
+  for (long i = threadIdx.x; i < plane; i += blockDim.x) s += (double)fill[(long)z * plane + i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < LAY_THREADS / 32; ++w) t += sh[w];
+    const double mean = t / (double)plane;
+    deps[z] = make_float2((float)(mean * dre), (float)(mean * dim));
+  }
+}
+
+// y = P x in the HYBRID domain: per column, rotate (x, y) -> (s, t), apply the TE and TM
+// inverses, rotate back.  One CTA per LAY_GROUP consecutive kx columns of one ky row; all
+// right-hand sides share the matrices, which are read once.
+template <int NZ>
+__global__ void __launch_bounds__(LAY_THREADS) k_lay_apply(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y,
+                                                         int nrhs, long ncols) {
+  constexpr int G = LAY_GROUP;
+  extern __shared__ cf xs[];   // [G][3][NZ][nrhs]: (s, t, z) components after rotation
+  __shared__ float rot[G][4];  // sx, sy, tx, ty
+  const long col0 = (long)blockIdx.x * G;
+  const int ix0 = (int)(col0 % a.nx), iy = (int)(col0 / a.nx);
+  const int tid = threadIdx.x;
+  if (tid < G) {
+    const float kx = a.kx[ix0 + tid], ky = a.ky[iy];
+    const float kap = sqrtf(kx * kx + ky * ky);
+    const bool small = !(kap > 0.f);
+    rot[tid][0] = small ? 0.f : -ky / kap;
+    rot[tid][1] = small ? 1.f : kx / kap;
+    rot[tid][2] = small ? 1.f : kx / kap;
+    rot[tid][3] = small ? 0.f : ky / kap;
+  }
+  __syncthreads();
+  const long n = 3L * NZ * ncols;   // entries per right-hand side
+  // gather + rotate: item = ((r * NZ + z) * G + g)
+  for (int it = tid; it < nrhs * NZ * G; it += LAY_THREADS) {
+    const int g = it % G, z = (it / G) % NZ, r = it / (G * NZ);
+    const long base = (long)r * n + (long)z * ncols + col0 + g;
+    const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
+    const float sx = rot[g][0], sy = rot[g][1], tx = rot[g][2], ty = rot[g][3];
+    xs[((g * 3 + 0) * NZ + z) * nrhs + r] = cadd(cscale(ex, sx), cscale(ey, sy));
+    xs[((g * 3 + 1) * NZ + z) * nrhs + r] = cadd(cscale(ex, tx), cscale(ey, ty));
+    xs[((g * 3 + 2) * NZ + z) * nrhs + r] = ez;
+  }
+  __syncthreads();
+  constexpr long MS = 5L * NZ * NZ;
+  cf acc[4];
+  // TE: rows i of column g; TM: rows i of the (t, z) block; outputs staged in registers, written
+  // after a barrier (the inputs live in the same shared array)
+  constexpr int NOUT = (G * 3 * NZ + LAY_THREADS - 1) / LAY_THREADS;
+  cf outv[NOUT][4];
+#pragma unroll
+  for (int q = 0; q < NOUT; ++q) {
+    const int o = tid + q * LAY_THREADS;
+    if (o >= G * 3 * NZ) continue;
+    const int g = o / (3 * NZ), rr = o - g * 3 * NZ;
+    const cf* Mg = a.mats + (col0 + g) * MS;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[r] = czero();
+    if (rr < NZ) {   // TE row rr
+      const cf* xsv = xs + (g * 3 + 0) * NZ * nrhs;
+      for (int j = 0; j < NZ; ++j) {
+        const cf mv = Mg[(long)j * NZ + rr];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < nrhs) acc[r] = cfma(mv, xsv[j * nrhs + r], acc[r]);
+      }
+    } else {         // TM row rr - NZ of the 2NZ block
+      const int i = rr - NZ;
+      const cf* Mt = Mg + (long)NZ * NZ;
+      const cf* xsv = xs + (g * 3 + 1) * NZ * nrhs;   // t then z: contiguous 2 NZ entries
+      for (int j = 0; j < 2 * NZ; ++j) {
+        const cf mv = Mt[(long)j * 2 * NZ + i];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < nrhs) acc[r] = cfma(mv, xsv[j * nrhs + r], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) outv[q][r] = acc[r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NOUT; ++q) {
+    const int o = tid + q * LAY_THREADS;
+    if (o >= G * 3 * NZ) continue;
+    const int g = o / (3 * NZ), rr = o - g * 3 * NZ;
+    const int comp = rr < NZ ? 0 : (rr < 2 * NZ ? 1 : 2);
+    const int z = rr - comp * NZ;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < nrhs) xs[((g * 3 + comp) * NZ + z) * nrhs + r] = outv[q][r];
+  }
+  __syncthreads();
+  for (int it = tid; it < nrhs * NZ * G; it += LAY_THREADS) {
+    const int g = it % G, z = (it / G) % NZ, r = it / (G * NZ);
+    const long base = (long)r * n + (long)z * ncols + col0 + g;
+    const cf es = xs[((g * 3 + 0) * NZ + z) * nrhs + r], et = xs[((g * 3 + 1) * NZ + z) * nrhs + r];
+    const float sx = rot[g][0], sy = rot[g][1], tx = rot[g][2], ty = rot[g][3];
+    y[base] = cadd(cscale(es, sx), cscale(et, tx));
+    y[base + (long)NZ * ncols] = cadd(cscale(es, sy), cscale(et, ty));
+    y[base + 2L * NZ * ncols] = xs[((g * 3 + 2) * NZ + z) * nrhs + r];
+  }
+}
+
+LayArgs lay_args(psfd_plan_s* P) {
+  LayArgs a{};
+  a.kx = P->kx; a.ky = P->ky; a.refl = P->R.refl; a.kz0 = P->R.kz0;
+  a.D = P->lay_D; a.D2 = P->lay_D2; a.deps = P->lay_deps;
+  a.k0sq = (float)(P->k0 * P->k0); a.dz = (float)P->p.dz;
+  a.nx = P->nx; a.nz = P->nz; a.zml = P->p.z_ml;
+  a.mats = P->lay; a.err = P->lay_err;
+  return a;
+}
+
+template <int NZ>
+int build_nz(psfd_plan_s* P) {
+  LayArgs a = lay_args(P);
+  k_lay_inv<NZ, false><<<(unsigned)P->ncols, LAY_THREADS, 0, P->stream>>>(a, 0);
+  PSFD_CHECK_LAUNCH();
+  k_lay_inv<2 * NZ, true><<<(unsigned)P->ncols, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <int NZ>
+int apply_nz(psfd_plan_s* P, const cf* x, cf* y) {
+  LayArgs a = lay_args(P);
+  const size_t smem = (size_t)LAY_GROUP * 3 * NZ * P->nrhs * sizeof(cf);
+  k_lay_apply<NZ><<<(unsigned)(P->ncols / LAY_GROUP), LAY_THREADS, smem, P->stream>>>(a, x, y, P->nrhs, P->ncols);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+}  // namespace
+
+int layered_supported(const psfd_plan_s* P) {
+  return (P->nz == 16 || P->nz == 32 || P->nz == 48 || P->nz == 64) && P->nx % LAY_GROUP == 0 && P->nrhs <= 4;
+}
+
+size_t layered_bytes(const psfd_plan_s* P) { return (size_t)P->ncols * 5 * P->nz * P->nz * sizeof(cf); }
+
+int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
+  if (!P->lay_built) { psfd_set_error("layered preconditioner: call psfd_layered_build first"); return PSFD_ERR_STATE; }
+  StageScope scope(P->stream, ST_PRECOND, (double)layered_bytes(P) + 2.0 * P->nrhs * P->nvec * sizeof(cf));
+  switch (P->nz) {
+    case 16: return apply_nz<16>(P, x, y);
+    case 32: return apply_nz<32>(P, x, y);
+    case 48: return apply_nz<48>(P, x, y);
+    case 64: return apply_nz<64>(P, x, y);
+    default: psfd_set_error("layered preconditioner: unsupported nz %d", P->nz); return PSFD_ERR_ARG;
+  }
+}
+
+void layered_free(psfd_plan_s* P) {
+  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  P->lay = nullptr; P->lay_D = nullptr; P->lay_D2 = nullptr; P->lay_deps = nullptr; P->lay_err = nullptr;
+  P->lay_built = false;
+}
+
+extern "C" size_t psfd_layered_bytes(psfd_plan P) {
+  if (!P || !layered_supported(P)) return 0;
+  return layered_bytes(P);
+}
+
+extern "C" int psfd_layered_build(psfd_plan P) {
+  if (!P) { psfd_set_error("psfd_layered_build: null plan"); return PSFD_ERR_ARG; }
+  if (!P->have_background) { psfd_set_error("psfd_layered_build: call psfd_background first"); return PSFD_ERR_STATE; }
+  if (!layered_supported(P)) {
+    psfd_set_error("psfd_layered_build: supported for nz in {16, 32, 48, 64}, nx a multiple of 4, nrhs <= 4");
+    return PSFD_ERR_ARG;
+  }
+  const int nz = P->nz;
+  cudaStream_t s = P->stream;
+  StageScope scope(s, ST_LAYBUILD);
+  if (!P->lay) {
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay, layered_bytes(P)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D, (size_t)nz * nz * sizeof(cf)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D2, (size_t)nz * nz * sizeof(cf)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_deps, (size_t)nz * sizeof(cf)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_err, sizeof(int)));
+    // D = s^-1 C, C[z][z'] = (1/nz) sum_m i k_m exp(2 pi i m (z - z') / nz) (FFT-order k_m, Nyquist
+    // negative), and D^2, in FP64 on the host
+    std::vector<zd> sinv;
+    pml_sinv64(P, sinv);
+    std::vector<zc> Cc(nz), D((size_t)nz * nz), D2((size_t)nz * nz, zc(0.0, 0.0));
+    for (int d = 0; d < nz; ++d) {
+      zc acc(0.0, 0.0);
+      for (int m = 0; m < nz; ++m) {
+        const double km = fft_wavenumber(m, nz, P->p.dz);
+        const double ph = 2.0 * M_PI * (double)m * (double)d / (double)nz;
+        acc += zc(0.0, km) * zc(cos(ph), sin(ph));
+      }
+      Cc[d] = acc / (double)nz;
+    }
+    for (int i = 0; i < nz; ++i)
+      for (int j = 0; j < nz; ++j) D[(size_t)i * nz + j] = zc(sinv[i].x, sinv[i].y) * Cc[((i - j) % nz + nz) % nz];
+    for (int i = 0; i < nz; ++i)
+      for (int k = 0; k < nz; ++k) {
+        const zc dik = D[(size_t)i * nz + k];
+        for (int j = 0; j < nz; ++j) D2[(size_t)i * nz + j] += dik * D[(size_t)k * nz + j];
+      }
+    std::vector<cf> hD((size_t)nz * nz), hD2((size_t)nz * nz);
+    for (size_t e = 0; e < hD.size(); ++e) {
+      hD[e] = make_float2((float)D[e].real(), (float)D[e].imag());
+      hD2[e] = make_float2((float)D2[e].real(), (float)D2[e].imag());
+    }
+    PSFD_CUDA_TRY(cudaMemcpy(P->lay_D, hD.data(), hD.size() * sizeof(cf), cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(P->lay_D2, hD2.data(), hD2.size() * sizeof(cf), cudaMemcpyHostToDevice));
+  }
+  PSFD_CUDA_TRY(cudaMemsetAsync(P->lay_err, 0, sizeof(int), s));
+  k_plane_mean<<<nz, LAY_THREADS, 0, s>>>(P->fill, P->ncols, P->lay_deps, P->deps_re, P->deps_im);
+  PSFD_CHECK_LAUNCH();
+  int rc;
+  switch (nz) {
+    case 16: rc = build_nz<16>(P); break;
+    case 32: rc = build_nz<32>(P); break;
+    case 48: rc = build_nz<48>(P); break;
+    default: rc = build_nz<64>(P); break;
+  }
+  if (rc) return rc;
+  int herr = 0;
+  PSFD_CUDA_TRY(cudaMemcpyAsync(&herr, P->lay_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr) { psfd_set_error("psfd_layered_build: a column block is singular"); return PSFD_ERR_BREAKDOWN; }
+  P->lay_built = true;
+  return PSFD_OK;
+}

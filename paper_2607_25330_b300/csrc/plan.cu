@@ -315,6 +315,25 @@ static double host_fftk(int i, int n, double d) {
   return 2.0 * M_PI * m / (n * d);
 }
 
+double fft_wavenumber(int i, int n, double d) { return host_fftk(i, n, d); }
+
+// 1/s(z) of the stretched-coordinate PML: s = 1 + i alpha (d/d_pml)^3, alpha = 4 ln(1/R0) / (2 k0 d_pml)
+void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv) {
+  const psfd_params_t& p = P->p;
+  sinv.resize(p.nz);
+  const int np = p.pml_planes;
+  const double dpml = np * p.dz;
+  const double alpha = np > 0 ? 4.0 * log(1.0 / p.pml_R0) / (2.0 * P->k0 * dpml) : 0.0;
+  for (int k = 0; k < p.nz; ++k) {
+    double d = 0.0;
+    if (k < np) d = (np - k) * p.dz;
+    else if (k >= p.nz - np) d = (k - (p.nz - np - 1)) * p.dz;
+    const double sig = np > 0 ? alpha * pow(d / dpml, 3.0) : 0.0;
+    const double den = 1.0 + sig * sig;            // 1/(1 + i sig) = (1 - i sig)/(1 + sig^2)
+    sinv[k] = make_double2(1.0 / den, -sig / den);
+  }
+}
+
 static int upload(void** dst, const void* src, size_t bytes) {
   PSFD_CUDA_TRY(cudaMalloc(dst, bytes));
   PSFD_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
@@ -323,6 +342,7 @@ static int upload(void** dst, const void* src, size_t bytes) {
 
 static void plan_free(psfd_plan_s* P) {
   fp64_free(P);
+  layered_free(P);
   void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
                   P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err};
   for (void* q : ptrs)
@@ -373,19 +393,10 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
   for (int i = 0; i < p.nx; ++i) kx[i] = (float)(host_fftk(i, p.nx, p.dx) + P->kx_inc);
   for (int i = 0; i < p.ny; ++i) ky[i] = (float)(host_fftk(i, p.ny, p.dy) + P->ky_inc);
   for (int i = 0; i < p.nz; ++i) kz[i] = (float)host_fftk(i, p.nz, p.dz);
-  // PML: s = 1 + i alpha (d/d_pml)^3, alpha = 4 ln(1/R0) / (2 k0 d_pml)
+  std::vector<zd> sinv64;
+  pml_sinv64(P, sinv64);
   std::vector<cf> sinv(p.nz);
-  int np = p.pml_planes;
-  double dpml = np * p.dz;
-  double alpha = np > 0 ? 4.0 * log(1.0 / p.pml_R0) / (2.0 * P->k0 * dpml) : 0.0;
-  for (int k = 0; k < p.nz; ++k) {
-    double d = 0.0;
-    if (k < np) d = (np - k) * p.dz;
-    else if (k >= p.nz - np) d = (k - (p.nz - np - 1)) * p.dz;
-    double sig = np > 0 ? alpha * pow(d / dpml, 3.0) : 0.0;
-    double den = 1.0 + sig * sig;            // 1/(1 + i sig) = (1 - i sig)/(1 + sig^2)
-    sinv[k] = make_float2((float)(1.0 / den), (float)(-sig / den));
-  }
+  for (int k = 0; k < p.nz; ++k) sinv[k] = make_float2((float)sinv64[k].x, (float)sinv64[k].y);
   std::vector<cf> twx, twy, twz;
   host_twiddles(p.nx, twx);
   host_twiddles(p.ny, twy);
@@ -531,6 +542,7 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
     PSFD_CHECK_LAUNCH();
   }
   P->have_background = true;
+  P->lay_built = false;   // the layered preconditioner depends on the fill: rebuild
   return PSFD_OK;
 }
 

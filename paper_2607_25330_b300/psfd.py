@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpsfd.so")
 
 PSFD_OK, PSFD_ERR_ARG, PSFD_ERR_CUDA, PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN, PSFD_ERR_TIMEOUT, PSFD_ERR_STATE = range(7)
 PSFD_TE, PSFD_TM = 0, 1
-PSFD_PRECOND, PSFD_HYBRID, PSFD_ADJOINT = 1, 2, 4
+PSFD_PRECOND, PSFD_HYBRID, PSFD_ADJOINT, PSFD_LAYERED = 1, 2, 4, 8
+# use_precond values of the solves: identity, spectral damping M, layered-background P
+PC_NONE, PC_DAMPING, PC_LAYERED = 0, 1, 2
 PSFD_BICGSTAB, PSFD_GMRES = 0, 1
 
 
@@ -96,6 +98,8 @@ def lib() -> C.CDLL:
         "psfd_solve_ex": (i, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(Info), vp, sz]),
         "psfd_solve_ex_workspace_size": (sz, [vp, C.POINTER(SolveOpts)]),
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
+        "psfd_layered_build": (i, [vp]),
+        "psfd_layered_bytes": (sz, [vp]),
         "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
                                    C.POINTER(Info), i]),
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
@@ -125,9 +129,18 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
+            "psfd_layered_build", "psfd_layered_bytes",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
             "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
+
+
+def _pc(precond) -> int:
+    """Solver preconditioner selector: False/0 none, True/1 spectral damping M, 2 layered P."""
+    v = int(precond)
+    if v not in (PC_NONE, PC_DAMPING, PC_LAYERED):
+        raise ValueError(f"precond must be 0, 1 or 2, got {precond!r}")
+    return v
 
 
 def _check(code: int, what: str, allow=()):
@@ -238,13 +251,20 @@ class Plan:
         """Mixed-precision solve (FP64 outer residual and field, complex64 inner Krylov)."""
         E = self.empty() if out is None else out
         info = (Info * self.nrhs)()
-        o = SolveOpts(tol, maxit, method, restart, 1 if precond else 0, 1 if refine else 0, inner_tol, max_outer)
+        o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, max_outer)
         ws, wsb = None, 0
         if workspace is not None:
             ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
         code = lib().psfd_solve_ex(self.h, _ptr(b), _ptr(x0), _ptr(E), C.byref(o), info, ws, wsb)
         _check(code, "psfd_solve_ex", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
         return {"E": E, "info": [info_dict(i) for i in info], "code": code}
+
+    def layered_build(self) -> None:
+        """Assemble and invert the per-column blocks of the layered-background preconditioner."""
+        _check(lib().psfd_layered_build(self.h), "psfd_layered_build")
+
+    def layered_bytes(self) -> int:
+        return int(lib().psfd_layered_bytes(self.h))
 
     def autotune(self) -> int:
         T = C.c_int(0)
@@ -273,7 +293,7 @@ class Plan:
         if workspace is not None:
             ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
         code = lib().psfd_solve(self.h, _ptr(b), _ptr(x0), _ptr(E), tol, maxit, method, restart,
-                                1 if precond else 0, info, ws, wsb)
+                                _pc(precond), info, ws, wsb)
         if history > 0:
             lib().psfd_set_history(self.h, None, 0)
         _check(code, "psfd_solve", allow=(PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN))
@@ -371,7 +391,7 @@ def solve_batched(plans: Sequence["Plan"], bs: Sequence[torch.Tensor], x0s=None,
     arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() if t is not None else None for t in ts])
     total = sum(p.nrhs for p in plans)
     info = (Info * total)()
-    o = SolveOpts(tol, maxit, method, restart, 1 if precond else 0, 1 if refine else 0, inner_tol, 0)
+    o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, 0)
     for t in list(bs) + ([t for t in x0s if t is not None] if x0s else []):
         _ptr(t)
     code = lib().psfd_solve_batched((C.c_void_p * n)(*[p.h for p in plans]), n, arr(bs),
@@ -384,7 +404,7 @@ def solve_batched(plans: Sequence["Plan"], bs: Sequence[torch.Tensor], x0s=None,
     return Es, infos
 
 
-STAGES = ("axial", "contrast", "krylov", "transform", "fno")
+STAGES = ("axial", "contrast", "krylov", "transform", "fno", "precond", "lay_build")
 
 
 def launch_count() -> int:
