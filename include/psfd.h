@@ -165,11 +165,18 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * block (2nz x 2nz, (E_t, E_z)), which psfd_layered_build assembles and inverts
  * (FP32, partial pivoting) on the device and stores in the plan:
  * psfd_layered_bytes() bytes = nx*ny*5*nz^2 complex64 (2.7 GB at 128x128x64).
- * Call after psfd_background (again after each psfd_background).  Supported for
- * nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else PSFD_ERR_ARG /
- * psfd_layered_bytes() = 0); PSFD_ERR_BREAKDOWN if a block is singular.
- * Synchronises the plan's stream. */
+ * psfd_layered_build makes the blocks exact for the fill registered by the last
+ * psfd_background.  They stay usable as a preconditioner after later
+ * psfd_background calls on the same plan (any fill): P only changes how fast the
+ * solve converges, never the solution.  psfd_layered_refresh rebuilds them only
+ * when some plane's mean fill moved by more than max_shift (fill fraction units)
+ * since the last build, and sets *rebuilt (nullable) to 1 if it did.
+ * Supported for nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else
+ * PSFD_ERR_ARG / psfd_layered_bytes() = 0); PSFD_ERR_STATE before
+ * psfd_background; PSFD_ERR_BREAKDOWN if a block is singular.  Both synchronise
+ * the plan's stream. */
 PSFD_API int psfd_layered_build(psfd_plan plan);
+PSFD_API int psfd_layered_refresh(psfd_plan plan, double max_shift, int* rebuilt);
 PSFD_API size_t psfd_layered_bytes(psfd_plan plan);
 
 /* ---------------------------------------------------------------- solve (Sec. 3, warm start)
@@ -179,7 +186,7 @@ PSFD_API size_t psfd_layered_bytes(psfd_plan plan);
  * the null initialisation (Eq. right_preconditioned).  use_precond: 1 = the
  * spectral damping M; 0 = identity (the paper's "null preconditioner");
  * 2 = the layered-background preconditioner P in place of M (psfd_layered_build
- * first, else PSFD_ERR_STATE).  Convergence: recursive
+ * at least once on the plan, else PSFD_ERR_STATE).  Convergence: recursive
  * relative residual <= tol with ||b|| of the original b (Eq. relative_residual);
  * the true residual is recomputed in FP64 at exit.
  *   b, x0 (nullable), E: device [nrhs][3][nz][ny][nx], real space.

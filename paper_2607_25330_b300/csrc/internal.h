@@ -71,6 +71,8 @@ struct psfd_plan_s {
   cf* lay_D2 = nullptr;      // [nz][nz]
   cf* lay_deps = nullptr;    // [nz] laterally averaged contrast
   int* lay_err = nullptr;
+  double* lay_fmean = nullptr;          // [nz] device scratch for plane means
+  std::vector<double> lay_mean;         // plane means of the fill the blocks were built for
   bool lay_built = false;
 };
 

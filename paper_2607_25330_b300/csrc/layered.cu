@@ -19,6 +19,7 @@
 // M of Eq. spectral_damping_action (an addition to the paper's method: the damping alone leaves
 // restarted Krylov stalling near 1e-5 at oblique incidence, where near-grazing diffraction orders
 // are barely absorbed by the axial PML; the averaged operator resolves those modes exactly).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
     }
 }
 
-// mean fill of every z-plane (FP64 sum) -> deps[z] = mean * (eps_abs - 1)
-__global__ void k_plane_mean(const float* __restrict__ fill, long plane, cf* deps, double dre, double dim) {
+// mean fill of every z-plane (FP64 sum)
+__global__ void k_plane_mean(const float* __restrict__ fill, long plane, double* mean) {
   __shared__ double sh[LAY_THREADS / 32];
   const int z = blockIdx.x;
   double s = 0.0;
@@ -250,18 +251,22 @@ __global__ void k_plane_mean(const float* __restrict__ fill, long plane, cf* dep
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < LAY_THREADS / 32; ++w) t += sh[w];
-    const double mean = t / (double)plane;
-    deps[z] = make_float2((float)(mean * dre), (float)(mean * dim));
+    mean[z] = t / (double)plane;
   }
 }
 
 // y = P x in the HYBRID domain: per column, rotate (x, y) -> (s, t), apply the TE and TM
 // inverses, rotate back.  One CTA per LAY_GROUP consecutive kx columns of one ky row; all
-// right-hand sides share the matrices, which are read once.
+// right-hand sides share the matrices, which are read once.  Each thread produces two adjacent
+// output rows of one block, so every matrix load is a 16-byte (two-entry) load of a column of the
+// column-major block; a CTA has LAY_GROUP * 3 NZ / 2 threads.
 template <int NZ>
-__global__ void __launch_bounds__(LAY_THREADS) k_lay_apply(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y,
-                                                         int nrhs, long ncols) {
-  constexpr int G = LAY_GROUP;
+constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / 2; }
+
+template <int NZ>
+__global__ void __launch_bounds__(apply_threads<NZ>()) k_lay_apply(LayArgs a, const cf* __restrict__ x,
+                                                                  cf* __restrict__ y, int nrhs, long ncols) {
+  constexpr int G = LAY_GROUP, NT = apply_threads<NZ>();
   extern __shared__ cf xs[];   // [G][3][NZ][nrhs]: (s, t, z) components after rotation
   __shared__ float rot[G][4];  // sx, sy, tx, ty
   const long col0 = (long)blockIdx.x * G;
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_apply(LayArgs a, const cf* 
   __syncthreads();
   const long n = 3L * NZ * ncols;   // entries per right-hand side
   // gather + rotate: item = ((r * NZ + z) * G + g)
-  for (int it = tid; it < nrhs * NZ * G; it += LAY_THREADS) {
+  for (int it = tid; it < nrhs * NZ * G; it += NT) {
     const int g = it % G, z = (it / G) % NZ, r = it / (G * NZ);
     const long base = (long)r * n + (long)z * ncols + col0 + g;
     const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
@@ -290,62 +295,48 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_apply(LayArgs a, const cf* 
   }
   __syncthreads();
   constexpr long MS = 5L * NZ * NZ;
-  cf acc[4];
-  // TE: rows i of column g; TM: rows i of the (t, z) block; outputs staged in registers, written
-  // after a barrier (the inputs live in the same shared array)
-  constexpr int NOUT = (G * 3 * NZ + LAY_THREADS - 1) / LAY_THREADS;
-  cf outv[NOUT][4];
+  // thread -> (column g, row pair rr, rr + 1) of the 3 NZ stacked rows (TE rows, then TM rows)
+  const int g = tid / (3 * NZ / 2), rr = 2 * (tid - g * (3 * NZ / 2));
+  const bool te = rr < NZ;
+  const int nb = te ? NZ : 2 * NZ;                         // block size
+  const int i = te ? rr : rr - NZ;                         // row inside the block
+  const cf* Mb = a.mats + (col0 + g) * MS + (te ? 0 : (long)NZ * NZ);
+  const cf* xsv = xs + (g * 3 + (te ? 0 : 1)) * NZ * nrhs;  // TE: s; TM: t then z (contiguous)
+  cf acc0[4], acc1[4];
 #pragma unroll
-  for (int q = 0; q < NOUT; ++q) {
-    const int o = tid + q * LAY_THREADS;
-    if (o >= G * 3 * NZ) continue;
-    const int g = o / (3 * NZ), rr = o - g * 3 * NZ;
-    const cf* Mg = a.mats + (col0 + g) * MS;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r] = czero();
-    if (rr < NZ) {   // TE row rr
-      const cf* xsv = xs + (g * 3 + 0) * NZ * nrhs;
-      for (int j = 0; j < NZ; ++j) {
-        const cf mv = Mg[(long)j * NZ + rr];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (r < nrhs) acc[r] = cfma(mv, xsv[j * nrhs + r], acc[r]);
-      }
-    } else {         // TM row rr - NZ of the 2NZ block
-      const int i = rr - NZ;
-      const cf* Mt = Mg + (long)NZ * NZ;
-      const cf* xsv = xs + (g * 3 + 1) * NZ * nrhs;   // t then z: contiguous 2 NZ entries
-      for (int j = 0; j < 2 * NZ; ++j) {
-        const cf mv = Mt[(long)j * 2 * NZ + i];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (r < nrhs) acc[r] = cfma(mv, xsv[j * nrhs + r], acc[r]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) outv[q][r] = acc[r];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NOUT; ++q) {
-    const int o = tid + q * LAY_THREADS;
-    if (o >= G * 3 * NZ) continue;
-    const int g = o / (3 * NZ), rr = o - g * 3 * NZ;
-    const int comp = rr < NZ ? 0 : (rr < 2 * NZ ? 1 : 2);
-    const int z = rr - comp * NZ;
+  for (int r = 0; r < 4; ++r) { acc0[r] = czero(); acc1[r] = czero(); }
+#pragma unroll 4
+  for (int j = 0; j < nb; ++j) {
+    const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
+    const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (r < nrhs) xs[((g * 3 + comp) * NZ + z) * nrhs + r] = outv[q][r];
+      if (r < nrhs) {
+        const cf xv = xsv[j * nrhs + r];
+        acc0[r] = cfma(m0, xv, acc0[r]);
+        acc1[r] = cfma(m1, xv, acc1[r]);
+      }
+  }
+  __syncthreads();   // every thread has read its inputs: the outputs overwrite xs in place
+  {
+    const int comp = te ? 0 : (i < NZ ? 1 : 2);
+    const int z = te ? rr : (i < NZ ? i : i - NZ);          // rows z, z + 1 of component comp
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < nrhs) {
+        xs[((g * 3 + comp) * NZ + z) * nrhs + r] = acc0[r];
+        xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = acc1[r];
+      }
   }
   __syncthreads();
-  for (int it = tid; it < nrhs * NZ * G; it += LAY_THREADS) {
-    const int g = it % G, z = (it / G) % NZ, r = it / (G * NZ);
-    const long base = (long)r * n + (long)z * ncols + col0 + g;
-    const cf es = xs[((g * 3 + 0) * NZ + z) * nrhs + r], et = xs[((g * 3 + 1) * NZ + z) * nrhs + r];
-    const float sx = rot[g][0], sy = rot[g][1], tx = rot[g][2], ty = rot[g][3];
+  for (int it = tid; it < nrhs * NZ * G; it += NT) {
+    const int gg = it % G, z = (it / G) % NZ, r = it / (G * NZ);
+    const long base = (long)r * n + (long)z * ncols + col0 + gg;
+    const cf es = xs[((gg * 3 + 0) * NZ + z) * nrhs + r], et = xs[((gg * 3 + 1) * NZ + z) * nrhs + r];
+    const float sx = rot[gg][0], sy = rot[gg][1], tx = rot[gg][2], ty = rot[gg][3];
     y[base] = cadd(cscale(es, sx), cscale(et, tx));
     y[base + (long)NZ * ncols] = cadd(cscale(es, sy), cscale(et, ty));
-    y[base + 2L * NZ * ncols] = xs[((g * 3 + 2) * NZ + z) * nrhs + r];
+    y[base + 2L * NZ * ncols] = xs[((gg * 3 + 2) * NZ + z) * nrhs + r];
   }
 }
 
@@ -373,7 +364,8 @@ template <int NZ>
 int apply_nz(psfd_plan_s* P, const cf* x, cf* y) {
   LayArgs a = lay_args(P);
   const size_t smem = (size_t)LAY_GROUP * 3 * NZ * P->nrhs * sizeof(cf);
-  k_lay_apply<NZ><<<(unsigned)(P->ncols / LAY_GROUP), LAY_THREADS, smem, P->stream>>>(a, x, y, P->nrhs, P->ncols);
+  k_lay_apply<NZ><<<(unsigned)(P->ncols / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(a, x, y, P->nrhs,
+                                                                                           P->ncols);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -399,11 +391,25 @@ int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
 }
 
 void layered_free(psfd_plan_s* P) {
-  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err};
+  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err, P->lay_fmean};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   P->lay = nullptr; P->lay_D = nullptr; P->lay_D2 = nullptr; P->lay_deps = nullptr; P->lay_err = nullptr;
+  P->lay_fmean = nullptr;
   P->lay_built = false;
+  P->lay_mean.clear();
+}
+
+// per-plane mean of the registered fill, copied to the host (synchronises the plan's stream)
+static int plane_means(psfd_plan_s* P, std::vector<double>& mean) {
+  cudaStream_t s = P->stream;
+  if (!P->lay_fmean) PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_fmean, (size_t)P->nz * sizeof(double)));
+  k_plane_mean<<<P->nz, LAY_THREADS, 0, s>>>(P->fill, P->ncols, P->lay_fmean);
+  PSFD_CHECK_LAUNCH();
+  mean.resize(P->nz);
+  PSFD_CUDA_TRY(cudaMemcpyAsync(mean.data(), P->lay_fmean, P->nz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  return PSFD_OK;
 }
 
 extern "C" size_t psfd_layered_bytes(psfd_plan P) {
@@ -456,10 +462,14 @@ extern "C" int psfd_layered_build(psfd_plan P) {
     PSFD_CUDA_TRY(cudaMemcpy(P->lay_D, hD.data(), hD.size() * sizeof(cf), cudaMemcpyHostToDevice));
     PSFD_CUDA_TRY(cudaMemcpy(P->lay_D2, hD2.data(), hD2.size() * sizeof(cf), cudaMemcpyHostToDevice));
   }
+  std::vector<double> mean;
+  int rc = plane_means(P, mean);
+  if (rc) return rc;
+  std::vector<cf> deps(nz);
+  for (int z = 0; z < nz; ++z)
+    deps[z] = make_float2((float)(mean[z] * P->deps_re), (float)(mean[z] * P->deps_im));
+  PSFD_CUDA_TRY(cudaMemcpyAsync(P->lay_deps, deps.data(), nz * sizeof(cf), cudaMemcpyHostToDevice, s));
   PSFD_CUDA_TRY(cudaMemsetAsync(P->lay_err, 0, sizeof(int), s));
-  k_plane_mean<<<nz, LAY_THREADS, 0, s>>>(P->fill, P->ncols, P->lay_deps, P->deps_re, P->deps_im);
-  PSFD_CHECK_LAUNCH();
-  int rc;
   switch (nz) {
     case 16: rc = build_nz<16>(P); break;
     case 32: rc = build_nz<32>(P); break;
@@ -472,5 +482,22 @@ extern "C" int psfd_layered_build(psfd_plan P) {
   PSFD_CUDA_TRY(cudaStreamSynchronize(s));
   if (herr) { psfd_set_error("psfd_layered_build: a column block is singular"); return PSFD_ERR_BREAKDOWN; }
   P->lay_built = true;
+  P->lay_mean = mean;
   return PSFD_OK;
+}
+
+extern "C" int psfd_layered_refresh(psfd_plan P, double max_shift, int* rebuilt) {
+  if (rebuilt) *rebuilt = 0;
+  if (!P) { psfd_set_error("psfd_layered_refresh: null plan"); return PSFD_ERR_ARG; }
+  if (!P->have_background) { psfd_set_error("psfd_layered_refresh: call psfd_background first"); return PSFD_ERR_STATE; }
+  if (P->lay_built && (int)P->lay_mean.size() == P->nz) {
+    std::vector<double> mean;
+    int rc = plane_means(P, mean);
+    if (rc) return rc;
+    double shift = 0.0;
+    for (int z = 0; z < P->nz; ++z) shift = std::max(shift, fabs(mean[z] - P->lay_mean[z]));
+    if (shift <= max_shift) return PSFD_OK;
+  }
+  if (rebuilt) *rebuilt = 1;
+  return psfd_layered_build(P);
 }

@@ -542,7 +542,6 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
     PSFD_CHECK_LAUNCH();
   }
   P->have_background = true;
-  P->lay_built = false;   // the layered preconditioner depends on the fill: rebuild
   return PSFD_OK;
 }
 

@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
         "psfd_solve_ex_workspace_size": (sz, [vp, C.POINTER(SolveOpts)]),
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
         "psfd_layered_build": (i, [vp]),
+        "psfd_layered_refresh": (i, [vp, d, C.POINTER(C.c_int)]),
         "psfd_layered_bytes": (sz, [vp]),
         "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
                                    C.POINTER(Info), i]),
@@ -129,7 +130,7 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
-            "psfd_layered_build", "psfd_layered_bytes",
+            "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
             "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
@@ -262,6 +263,12 @@ class Plan:
     def layered_build(self) -> None:
         """Assemble and invert the per-column blocks of the layered-background preconditioner."""
         _check(lib().psfd_layered_build(self.h), "psfd_layered_build")
+
+    def layered_refresh(self, max_shift: float) -> bool:
+        """Rebuild the blocks only if a plane's mean fill moved by more than max_shift; True if rebuilt."""
+        r = C.c_int(0)
+        _check(lib().psfd_layered_refresh(self.h, max_shift, C.byref(r)), "psfd_layered_refresh")
+        return bool(r.value)
 
     def layered_bytes(self) -> int:
         return int(lib().psfd_layered_bytes(self.h))

@@ -88,20 +88,35 @@ def test_layered_solve_matches_oracle_and_converges_fast():
         assert rel_l2(res["E"][r].cpu(), ref["E"]) < 1e-4
 
 
-def test_layered_warm_start_and_state_errors():
+def test_layered_warm_start_refresh_and_state_errors():
     from paper_2607_25330_b300 import psfd
-    prob, g, fill_o, plan, b = setup(16, 16, 16, 6.0, 0.0, 1, seed=2)
+    prob = problem(16, 16, 16, theta=6.0, pols=[0])
+    plan = psfd.Plan(prob, nrhs=1)
+    x = torch.zeros(plan.shape, dtype=torch.complex64, device="cuda")
+    with pytest.raises(psfd.PsfdError):
+        plan.layered_build()                       # no background yet
+    fill = plan.mask_fill(torch.from_numpy(I.mask_for(prob, 2, "manhattan")), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    with pytest.raises(psfd.PsfdError):
+        plan.solve_ex(b, tol=1e-6, maxit=10, precond=psfd.PC_LAYERED)   # blocks never built
+    assert plan.layered_refresh(0.25)              # first call builds
+    assert not plan.layered_refresh(0.25)          # same fill: nothing to do
     cold = plan.solve_ex(b, tol=1e-6, maxit=200, precond=psfd.PC_LAYERED)
+    assert cold["code"] == 0
     # the exact solution as warm start needs no inner iteration
     warm = plan.solve_ex(b, x0=cold["E"].clone(), tol=1e-5, maxit=200, precond=psfd.PC_LAYERED)
     assert warm["info"][0]["iters"] == 0
-    # a new background invalidates the blocks until they are rebuilt
-    fill = plan.mask_fill(torch.from_numpy(I.mask_for(prob, 9, "manhattan")), prob.zprofile())
-    b2 = plan.background(prob.stack(), fill, prob.pols)
-    with pytest.raises(psfd.PsfdError):
-        plan.solve_ex(b2, tol=1e-6, maxit=10, precond=psfd.PC_LAYERED)
-    plan.layered_build()
-    assert plan.solve_ex(b2, tol=1e-6, maxit=200, precond=psfd.PC_LAYERED)["code"] == 0
+    # another mask: the old blocks remain a valid preconditioner; refresh decides on the shift
+    a2 = I.mask_for(prob, 9, "manhattan")
+    fill2 = plan.mask_fill(torch.from_numpy(a2), prob.zprofile())
+    b2 = plan.background(prob.stack(), fill2, prob.pols)
+    stale = plan.solve_ex(b2, tol=1e-6, maxit=200, precond=psfd.PC_LAYERED)
+    assert stale["code"] == 0
+    shift = abs(float(np.mean(a2)) - float(np.mean(I.mask_for(prob, 2, "manhattan"))))
+    assert plan.layered_refresh(0.0) == (shift > 0)
+    fresh = plan.solve_ex(b2, tol=1e-6, maxit=200, precond=psfd.PC_LAYERED)
+    assert fresh["code"] == 0
+    assert rel_l2(fresh["E"].cpu(), stale["E"].cpu()) < 1e-4
 
 
 def test_layered_full_size_128x128x64_reaches_1e6():

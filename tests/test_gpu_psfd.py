@@ -160,7 +160,11 @@ def test_manhattan_128x128x64_full_size_apply_and_solve():
     for r in range(2):
         ref = O.apply_A(g, O.apply_M(g, x[r].to(torch.complex128)), fill_o)
         assert rel_l2(y[r], ref) < TOL_C64
-    res = plan.solve(b, tol=1e-6, maxit=3000)
+    # at 6 deg the spectral damping alone stalls near 1e-5 (near-grazing orders); the layered
+    # preconditioner reaches the tolerance.  The returned complex64 field carries the rounding
+    # residual of complex64 storage (about 1.4e-6 here) on top of the FP64 field's 1e-6.
+    plan.layered_build()
+    res = plan.solve_ex(b, tol=1e-6, maxit=600, precond=psfd.PC_LAYERED)
     for r, pol in enumerate(prob.pols):
         assert res["info"][r]["status"] == 0
         bo = O.source_b(g, fill_o, pol)
