@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--maxit-paper", type=int, default=2000,
                     help="iteration cap of the paper-configuration arms at 1e-6 and of the null arm")
     ap.add_argument("--skip-paper-arms", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=1e-2,
+                    help="relative tolerance of each complex64 inner solve of the FP64 refinement")
+    ap.add_argument("--train-step", action="store_true",
+                    help="time the physics-informed FNO training step (16 masks 128x128x48) and exit")
+    ap.add_argument("--train-batch", type=int, default=16)
     ap.add_argument("--lay-shift", type=float, default=0.25,
                     help="rebuild the layered blocks when a plane's mean fill moved by more than this")
     return ap.parse_args()
@@ -201,7 +206,8 @@ def run_ours(args, rank, world):
             for r, m in enumerate(models):
                 psfd.fno_forward(m, a, out=x0[r:r + 1])
         return plan.solve_ex(b, x0=x0 if warm else None, tol=tol, maxit=maxit, method=method,
-                             restart=args.restart, precond=pc, refine=True, inner_tol=1e-2, out=E, workspace=ws)
+                             restart=args.restart, precond=pc, refine=True, inner_tol=args.inner_tol, out=E,
+                             workspace=ws)
 
     # warm-up (also exercises every kernel once)
     for i in range(args.warmup):
@@ -383,7 +389,8 @@ def run_ours(args, rank, world):
                    "rhs_per_step": nrhs, "pols": ["TE", "TM"][:nrhs], "theta_deg": prob.theta_deg, "tol": TOL,
                    "preconditioner": pc_name,
                    "solver": f"{args.method}({args.restart}) in complex64 inside FP64 iterative refinement "
-                             "(FP64 residual and field, inner tol 1e-2), right preconditioning, affine warm start",
+                             f"(FP64 residual and field, inner tol {args.inner_tol:g}), right preconditioning, "
+                             "affine warm start",
                    "step": "mask -> fill -> FP64 TMM + source -> preconditioner set-up -> FNO warm start -> "
                            "solve -> FP64 true residual",
                    "l2": "working set (2.7 GB of blocks + >= 9 vectors x 25 MB) exceeds the 126 MB L2; no flush",
@@ -442,6 +449,60 @@ def run_profile_apply(args):
     torch.cuda.synchronize()
     return {"profile_apply": args.profile_apply, "workload": args.workload, "nrhs": nrhs, "flags": flags,
             "ms_per_apply": e0.elapsed_time(e1) / max(1, args.profile_apply)}
+
+
+def run_train_step(args):
+    """Physics-informed training step of the factorised FNO (config 4): 16 masks 128x128x48,
+    E = G_theta(a) for the batch, J = mean over masks of Eq. loss through the PSFD operator
+    (hand-written adjoint), reverse pass of the FNO (checkpointed), Adam update."""
+    import torch
+    from paper_2607_25330_b300 import inputs as I
+    from paper_2607_25330_b300 import psfd
+    from paper_2607_25330_b300.autograd import fno_apply, physics_loss
+    prob = I.preset("fno_train_128x128x48")
+    B = args.train_batch
+    S = I.FNOShape()
+    w = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda().requires_grad_(True)
+         for k, v in I.fno_weights(S, 91, spectral_scale=1.0).items()}
+    trainer = psfd.FnoTrainer(psfd.fno_struct(w, S), B, prob.nz, prob.ny, prob.nx, checkpoint=True)
+    plans, bs, fills = [], [], []
+    for s in range(B):
+        pl = psfd.Plan(prob, nrhs=1)
+        fill = pl.mask_fill(torch.from_numpy(I.mask_for(prob, 500 + s)), prob.zprofile())
+        bs.append(pl.background(prob.stack(), fill, prob.pols))
+        plans.append(pl)
+        fills.append(fill)
+    a = torch.stack(fills).contiguous()
+    opt = torch.optim.Adam(list(w.values()), lr=1e-3)
+
+    def train_step():
+        opt.zero_grad(set_to_none=True)
+        E = fno_apply(trainer, w, a)
+        J = sum(physics_loss(plans[s], E[s:s + 1], bs[s]) for s in range(B)) / B
+        J.backward()
+        opt.step()
+        return J
+
+    for _ in range(args.warmup):
+        train_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psfd.timing_enable(True)
+    e0.record()
+    losses = [train_step() for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    st = psfd.timing_read()
+    psfd.timing_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    mem = torch.cuda.max_memory_allocated() / 2 ** 30
+    return {"mode": "train_step", "workload": "fno_train_128x128x48", "batch": B, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "masks_per_s": B / (ms / 1e3),
+            "loss": [float(l) for l in losses], "fno_ms_per_step": st["fno"]["ms"] / args.steps,
+            "psfd_ms_per_step": (st["axial"]["ms"] + st["contrast"]["ms"]) / args.steps,
+            "workspace_GiB": trainer.n / 2 ** 30, "max_allocated_GiB": mem,
+            "note": "forward + physics loss (PSFD apply and adjoint per mask) + checkpointed FNO reverse pass + "
+                    "Adam; the high-frequency term of the loss uses torch.fft"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -525,6 +586,9 @@ def main():
         return
     if args.profile_apply:
         print(json.dumps(run_profile_apply(args)), flush=True)
+        return
+    if args.train_step:
+        print(json.dumps(run_train_step(args)), flush=True)
         return
     if world > 1:
         import torch

@@ -129,7 +129,9 @@ PSFD_API int psfd_mask_fill(psfd_plan plan, const uint8_t* a_bin, const float* z
 /* ---------------------------------------------------------------- background (Eq. bg_source)
  * Computes in FP64 on the device the reflection coefficients r_s, r_p (ratios of
  * reflected to incident tangential E) of the stack for every lateral Bloch mode
- * (transfer-matrix method), registers `fill` (device [nz][ny][nx], kept by
+ * (transfer-matrix method; recomputed only when the stack differs from the
+ * previous call's, since they do not depend on the mask), registers `fill`
+ * (device [nz][ny][nx], kept by
  * pointer: it must stay alive while the plan is used), and writes the source
  *   b = k0^2 deps (E_inc + R E_inc)
  * for each right-hand side r with polarisation pol[r] (HOST int array [nrhs],
@@ -323,6 +325,20 @@ PSFD_API int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny
  * capture. */
 PSFD_API int psfd_spectral_upsample_static(const psfd_c64* src, int nb, int nx0, int ny0, int nz0,
                                            psfd_c64* dst, int nx, int ny, int nz, void* stream);
+
+/* ---------------------------------------------------------------- threshold-width metric (Sec. 4)
+ * Practical convergence measure of the paper: intensity I = |E_comp|^2 on plane z
+ * of right-hand side rhs; contour I = I_th (the S = 0.5 level of the logistic map
+ * of Eq. logistic_sigmoid); min(n_lines, ny) rows and min(n_lines, nx) columns of
+ * the periodic grid; threshold-bounded segment widths by linear interpolation of
+ * the crossings; every segment of E_ref (the converged field) matched to the
+ * segment of E whose centre lies inside it.  out (HOST double[6]) = mean, std and
+ * max of |d_ref - d| * pixel / demag (nm; demag = 4 for wafer units), matched
+ * count, unresolved reference segments, fraction with deviation > 1 nm.
+ * E, E_ref: device real-space fields [nrhs][3][nz][ny][nx].  Synchronises the
+ * plan's stream.  PSFD_ERR_ARG on bad indices. */
+PSFD_API int psfd_width_metric(psfd_plan plan, const psfd_c64* E, const psfd_c64* E_ref, int rhs, int comp, int z,
+                               float I_th, int n_lines, double demag, double* out);
 
 /* ---------------------------------------------------------------- observability
  * psfd_launch_count: number of kernels this library has launched in the process.

@@ -48,6 +48,7 @@ struct psfd_plan_s {
   const float* fill = nullptr;
   int za0 = 0, za1 = 0;      // planes with nonzero fill: [za0, za1)
   bool have_background = false;
+  std::vector<double> stack_sig;   // stack the reflection tables were computed for
   // damping
   float m_min = 0, kref2 = 0, gamma = 1, damp_eps = 0;
   // scratch (plan-owned)

@@ -702,6 +702,9 @@ static int bicgstab_loop(psfd_plan_s* P, SolveWs& w, VArgs va, int maxit, int af
 }
 
 static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxit, int m, int aflags, int nb) {
+  // the multi-dot and update kernels stream (j + 2) vectors per launch: about two CTAs per SM over
+  // all right-hand sides measured best (fewer end-of-block reductions, one wave)
+  const int nbg = std::max(1, std::min(nb, 2 * 148 / std::max(1, P->nrhs)));
   const int nr = P->nrhs;
   cudaStream_t st = P->stream;
   const long n = P->nvec;
@@ -758,10 +761,10 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         StageScope sc(st, ST_KRYLOV, (2.0 * (j + 1) + 3.0) * nr * n * sizeof(cf));
         g.hout = w.h1;
         g.save_norm = true;
-        k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
+        k_gdot<<<dim3(nbg, nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
         g.save_norm = false;
-        k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+        k_gupd<false><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
       }
       k_greorth<<<1, tpb, 0, st>>>(w.sc, w.active, w.skip2, nr);
@@ -771,9 +774,9 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         const int* keep = g.mask;
         g.mask = w.skip2;
         g.hout = w.h2;
-        k_gdot<<<dim3(nb, nr, nch), kThreads, 0, st>>>(g);
+        k_gdot<<<dim3(nbg, nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
-        k_gupd<false><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+        k_gupd<false><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
         g.mask = keep;
       }
@@ -793,7 +796,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
     k_gtri<<<1, tpb, 0, st>>>(w.gs, nr);
     PSFD_CHECK_LAUNCH();
     g.mask = nullptr;  // every rhs with jd > 0 updates y
-    k_gupd<true><<<dim3(nb, nr), kThreads, 0, st>>>(g);
+    k_gupd<true><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
     PSFD_CHECK_LAUNCH();
   }
   k_gfinish<<<1, tpb, 0, st>>>(w.gs, w.sc, nr);

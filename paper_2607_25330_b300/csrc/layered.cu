@@ -122,23 +122,21 @@ template <int N, bool TM>
 __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_off) {
   constexpr int TT = N / 16;
   __shared__ cf colv[2][N], rowv[2][N];
-  __shared__ float mag[N];
-  __shared__ int used[N], pivrow[N], rowvar[N];
-  __shared__ int s_p;
-  __shared__ cf s_pinv;
+  __shared__ float mag[2][N];
+  __shared__ int pivrow[N], rowvar[N];
   const long col = blockIdx.x;
-  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15, lane = tid & 31;
   const Mode m = mode_of(a, col);
   cf T[TT][TT];
 #pragma unroll
   for (int u = 0; u < TT; ++u)
 #pragma unroll
     for (int v = 0; v < TT; ++v) T[u][v] = entry<TM>(a, m, rg + 16 * u, cg + 16 * v);
-  for (int i = tid; i < N; i += LAY_THREADS) used[i] = 0;
-  __syncthreads();
+  unsigned used = 0;   // bit u: owned row rg + 16 u has been a pivot row
   for (int k = 0; k < N; ++k) {
     const int buf = k & 1;
-    // column k -> shared (owners: cg == k % 16)
+    // column k -> shared (owners: cg == k % 16); used rows get magnitude -1 and a non-finite
+    // magnitude counts as 0, so the pivot is always a row not used before
     if (cg == (k & 15)) {
       const int vk = k >> 4;
 #pragma unroll
@@ -148,44 +146,36 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
         for (int u = 0; u < TT; ++u) {
           const int i = rg + 16 * u;
           const cf t = T[u][v];
+          const float mg = t.x * t.x + t.y * t.y;
           colv[buf][i] = t;
-          mag[i] = used[i] ? -1.f : t.x * t.x + t.y * t.y;
+          mag[buf][i] = ((used >> u) & 1u) ? -1.f : (mg <= 3.0e38f ? mg : 0.f);
         }
       }
     }
     __syncthreads();
-    if (tid < 32) {
-      float best = -2.f;
-      int bi = 0;
-      for (int i = tid; i < N; i += 32) {
-        // used rows -1; a non-finite magnitude counts as 0, so the pivot is always an unused row
-        const float mv = used[i] ? -1.f : (mag[i] >= 0.f && mag[i] <= 3.0e38f ? mag[i] : 0.f);
-        if (mv > best) { best = mv; bi = i; }
-      }
+    // every warp finds the pivot itself (no broadcast barrier): argmax, ties to the lower row
+    float best = -2.f;
+    int p = 0;
+    for (int i = lane; i < N; i += 32) {
+      const float mv = mag[buf][i];
+      if (mv > best) { best = mv; p = i; }
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        s_p = bi;
-        used[bi] = 1;
-        pivrow[k] = bi;
-        if (!(best > 0.f)) {
-          atomicExch(a.err, 1);
-          s_pinv = czero();
-        } else {
-          s_pinv = cdiv1(colv[buf][bi]);
-        }
-      }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, p, off);
+      if (ob > best || (ob == best && oi < p)) { best = ob; p = oi; }
     }
-    __syncthreads();
-    const int p = s_p;
-    const cf pinv = s_pinv;
+    const bool ok = best > 0.f;
+    const cf pinv = ok ? cdiv1(colv[buf][p]) : czero();
+    if (tid == 0) {
+      pivrow[k] = p;
+      if (!ok) atomicExch(a.err, 1);
+    }
     // pivot row p -> shared (owners: rg == p % 16)
     if (rg == (p & 15)) {
       const int up = p >> 4;
+      used |= 1u << up;
 #pragma unroll
       for (int u = 0; u < TT; ++u) {
         if (u != up) continue;
@@ -263,9 +253,10 @@ __global__ void k_plane_mean(const float* __restrict__ fill, long plane, double*
 template <int NZ>
 constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / 2; }
 
-template <int NZ>
-__global__ void __launch_bounds__(apply_threads<NZ>()) k_lay_apply(LayArgs a, const cf* __restrict__ x,
-                                                                  cf* __restrict__ y, int nrhs, long ncols) {
+template <int NZ, int NR>
+__global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 4 : 3)) k_lay_apply(LayArgs a, const cf* __restrict__ x,
+                                                                     cf* __restrict__ y, long ncols) {
+  constexpr int nrhs = NR;
   constexpr int G = LAY_GROUP, NT = apply_threads<NZ>();
   extern __shared__ cf xs[];   // [G][3][NZ][nrhs]: (s, t, z) components after rotation
   __shared__ float rot[G][4];  // sx, sy, tx, ty
@@ -302,31 +293,29 @@ __global__ void __launch_bounds__(apply_threads<NZ>()) k_lay_apply(LayArgs a, co
   const int i = te ? rr : rr - NZ;                         // row inside the block
   const cf* Mb = a.mats + (col0 + g) * MS + (te ? 0 : (long)NZ * NZ);
   const cf* xsv = xs + (g * 3 + (te ? 0 : 1)) * NZ * nrhs;  // TE: s; TM: t then z (contiguous)
-  cf acc0[4], acc1[4];
+  cf acc0[NR], acc1[NR];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) { acc0[r] = czero(); acc1[r] = czero(); }
-#pragma unroll 4
+  for (int r = 0; r < NR; ++r) { acc0[r] = czero(); acc1[r] = czero(); }
+#pragma unroll 8
   for (int j = 0; j < nb; ++j) {
     const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
     const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-      if (r < nrhs) {
-        const cf xv = xsv[j * nrhs + r];
-        acc0[r] = cfma(m0, xv, acc0[r]);
-        acc1[r] = cfma(m1, xv, acc1[r]);
-      }
+    for (int r = 0; r < NR; ++r) {
+      const cf xv = xsv[j * NR + r];
+      acc0[r] = cfma(m0, xv, acc0[r]);
+      acc1[r] = cfma(m1, xv, acc1[r]);
+    }
   }
   __syncthreads();   // every thread has read its inputs: the outputs overwrite xs in place
   {
     const int comp = te ? 0 : (i < NZ ? 1 : 2);
     const int z = te ? rr : (i < NZ ? i : i - NZ);          // rows z, z + 1 of component comp
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-      if (r < nrhs) {
-        xs[((g * 3 + comp) * NZ + z) * nrhs + r] = acc0[r];
-        xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = acc1[r];
-      }
+    for (int r = 0; r < NR; ++r) {
+      xs[((g * 3 + comp) * NZ + z) * nrhs + r] = acc0[r];
+      xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = acc1[r];
+    }
   }
   __syncthreads();
   for (int it = tid; it < nrhs * NZ * G; it += NT) {
@@ -360,14 +349,24 @@ int build_nz(psfd_plan_s* P) {
   return PSFD_OK;
 }
 
+template <int NZ, int NR>
+int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
+  const size_t smem = (size_t)LAY_GROUP * 3 * NZ * NR * sizeof(cf);
+  k_lay_apply<NZ, NR><<<(unsigned)(P->ncols / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(a, x, y,
+                                                                                               P->ncols);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
 template <int NZ>
 int apply_nz(psfd_plan_s* P, const cf* x, cf* y) {
   LayArgs a = lay_args(P);
-  const size_t smem = (size_t)LAY_GROUP * 3 * NZ * P->nrhs * sizeof(cf);
-  k_lay_apply<NZ><<<(unsigned)(P->ncols / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(a, x, y, P->nrhs,
-                                                                                           P->ncols);
-  PSFD_CHECK_LAUNCH();
-  return PSFD_OK;
+  switch (P->nrhs) {
+    case 1: return apply_nr<NZ, 1>(P, a, x, y);
+    case 2: return apply_nr<NZ, 2>(P, a, x, y);
+    case 3: return apply_nr<NZ, 3>(P, a, x, y);
+    default: return apply_nr<NZ, 4>(P, a, x, y);
+  }
 }
 
 }  // namespace

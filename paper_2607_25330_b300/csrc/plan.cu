@@ -491,19 +491,30 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
   cudaStream_t s = P->stream;
   int nl = stack->n_layers;
   double* dstack = nullptr;
-  if (nl > 0) {
-    PSFD_CUDA_TRY(cudaMalloc((void**)&dstack, 3 * nl * sizeof(double)));
-    PSFD_CUDA_TRY(cudaMemcpy(dstack, stack->n_re, nl * 8, cudaMemcpyHostToDevice));
-    PSFD_CUDA_TRY(cudaMemcpy(dstack + nl, stack->n_im, nl * 8, cudaMemcpyHostToDevice));
-    PSFD_CUDA_TRY(cudaMemcpy(dstack + 2 * nl, stack->d, nl * 8, cudaMemcpyHostToDevice));
-  }
-  StackDev st{nl, dstack, dstack ? dstack + nl : nullptr, dstack ? dstack + 2 * nl : nullptr, stack->sub_re,
-              stack->sub_im};
-  double dkx = 2.0 * M_PI / (P->nx * P->p.dx), dky = 2.0 * M_PI / (P->ny * P->p.dy);
   long nm = P->ncols;
-  k_tmm<<<(unsigned)((nm + 127) / 128), 128, 0, s>>>(P->nx, P->ny, dkx, dky, P->kx_inc, P->ky_inc, P->k0, st,
-                                                     P->R.rs64, P->R.rp64, P->R.kz064, P->R.refl, P->R.kz0);
-  PSFD_CHECK_LAUNCH();
+  // the reflection tables depend on the grid, the illumination and the stack, not on the mask:
+  // recompute them only when the stack differs from the one they were built for
+  std::vector<double> sig;
+  sig.reserve(3 * nl + 3);
+  sig.push_back((double)nl);
+  for (int l = 0; l < nl; ++l) { sig.push_back(stack->n_re[l]); sig.push_back(stack->n_im[l]); sig.push_back(stack->d[l]); }
+  sig.push_back(stack->sub_re);
+  sig.push_back(stack->sub_im);
+  if (!P->have_background || sig != P->stack_sig) {
+    if (nl > 0) {
+      PSFD_CUDA_TRY(cudaMalloc((void**)&dstack, 3 * nl * sizeof(double)));
+      PSFD_CUDA_TRY(cudaMemcpy(dstack, stack->n_re, nl * 8, cudaMemcpyHostToDevice));
+      PSFD_CUDA_TRY(cudaMemcpy(dstack + nl, stack->n_im, nl * 8, cudaMemcpyHostToDevice));
+      PSFD_CUDA_TRY(cudaMemcpy(dstack + 2 * nl, stack->d, nl * 8, cudaMemcpyHostToDevice));
+    }
+    StackDev st{nl, dstack, dstack ? dstack + nl : nullptr, dstack ? dstack + 2 * nl : nullptr, stack->sub_re,
+                stack->sub_im};
+    double dkx = 2.0 * M_PI / (P->nx * P->p.dx), dky = 2.0 * M_PI / (P->ny * P->p.dy);
+    k_tmm<<<(unsigned)((nm + 127) / 128), 128, 0, s>>>(P->nx, P->ny, dkx, dky, P->kx_inc, P->ky_inc, P->k0, st,
+                                                       P->R.rs64, P->R.rp64, P->R.kz064, P->R.refl, P->R.kz0);
+    PSFD_CHECK_LAUNCH();
+    P->stack_sig = sig;
+  }
   // absorber plane range
   int* zr = nullptr;
   int hz[2] = {P->nz, 0};
