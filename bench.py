@@ -181,9 +181,11 @@ def run_ours(args, rank, world):
         models.append(psfd.fno_struct(wd, shape))
     plan = psfd.Plan(prob, nrhs=nrhs)
     ws = torch.empty(plan.workspace_size_ex(method, args.restart, True), dtype=torch.uint8, device="cuda")
-    E = plan.empty()
+    # the FP64 field is returned (complex128): its own residual is the one checked against 1e-6
+    # (its complex64 rounding alone would carry about 1.3e-6 on this grid)
+    E = torch.empty(plan.shape, dtype=torch.complex128, device="cuda")
     x0 = plan.empty()
-    E_host = torch.empty(plan.shape, dtype=torch.complex64).pin_memory()
+    E_host = torch.empty(plan.shape, dtype=torch.complex128).pin_memory()
     stream = torch.cuda.current_stream()
 
     rebuilds = [0]
@@ -207,7 +209,7 @@ def run_ours(args, rank, world):
                 psfd.fno_forward(m, a, out=x0[r:r + 1])
         return plan.solve_ex(b, x0=x0 if warm else None, tol=tol, maxit=maxit, method=method,
                              restart=args.restart, precond=pc, refine=True, inner_tol=args.inner_tol, out=E,
-                             workspace=ws)
+                             workspace=ws, out_c128=True)
 
     # warm-up (also exercises every kernel once)
     for i in range(args.warmup):
@@ -285,6 +287,42 @@ def run_ours(args, rank, world):
             paper[k]["maxit"] = args.maxit_paper
         paper["note"] = ("the paper's spectral damping M and null configuration on the same masks and solver; "
                          "only right-hand sides that reached the tolerance within maxit count")
+
+    # the paper's practical criterion (Sec. 4): iterations until the threshold-contour widths of
+    # |E_y|^2 on the plane above the absorber are within 1 nm (wafer units, /4) of the converged
+    # field's, on one mask, rhs 0 (TE)
+    width = {}
+    if not args.skip_paper_arms:
+        i0 = args.warmup
+        fill = plan.mask_fill(masks[i0], zprof)
+        b0 = plan.background(stack, fill, prob.pols)
+        if pc_main == psfd.PC_LAYERED:
+            plan.layered_build()
+        a0 = fill.unsqueeze(0).contiguous()
+        for r, m in enumerate(models):
+            psfd.fno_forward(m, a0, out=x0[r:r + 1])
+        ref = plan.solve_ex(b0, tol=1e-7, maxit=args.maxit, precond=pc_main)["E"].clone()   # complex64
+        zp = np.asarray(zprof)
+        ztop = int(np.nonzero(zp > 0)[0].max()) + 1
+        grids = {"layered": [1, 2, 3, 4, 6, 8, 12, 16, 24, 32], "damping": [10, 20, 40, 80, 160, 320, 640]}
+        for name, pc in (("layered", psfd.PC_LAYERED), ("damping", psfd.PC_DAMPING)):
+            if name == "layered" and pc_main != psfd.PC_LAYERED:
+                continue
+            for warm in (True, False):
+                hit, trace = None, []
+                for k in grids[name]:
+                    E_k = plan.solve(b0, x0=x0 if warm else None, tol=1e-12, maxit=k, method=method,
+                                     restart=args.restart, precond=pc)["E"]
+                    mtr = plan.width_metric(E_k, ref, ztop, rhs=0, comp=1, I_th=0.15, n_lines=100, demag=4.0)
+                    trace.append([k, round(mtr["mean"], 4), mtr["matched"], mtr["unresolved"]])
+                    if hit is None and mtr["matched"] > 0 and mtr["mean"] <= 1.0:
+                        hit = k
+                        break
+                width[f"{name}_{'warm' if warm else 'cold'}"] = {"iters_to_mean_below_1nm": hit, "trace": trace}
+        width["definition"] = ("I = |E_y|^2 on the first plane above the absorber, I_th = 0.15, 100 + 100 scan "
+                               "lines, widths of threshold-bounded segments, |d_ref - d| / 4 against the 1e-7 "
+                               "solution; criterion: mean <= 1 nm (the paper's sub-nanometre level); "
+                               "trace = [iterations, mean nm, matched, unresolved reference segments]")
 
     # per-stage CUDA-event timing inside one headline step (stage byte counts are algorithmic)
     psfd.timing_enable(True)
@@ -382,7 +420,8 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64 (FP64 reductions and refinement residual, bf16 FNO mixing)",
+        "dtype": "c64 (Krylov, operator, preconditioner; FP64 reductions, refinement residual and returned field; "
+                 "bf16 FNO mixing)",
         "data": "synthetic: seeded random Manhattan masks (4-24 rectangles, edges 4-40 px), "
                 "seed-initialised FNO weights",
         "config": {"workload": args.workload, "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
@@ -400,7 +439,8 @@ def run_ours(args, rank, world):
                   "outer_steps_warm": [r["outer"] for inf in info_warm for r in inf],
                   "r_rel_fp64_warm": [r["r_rel"] for inf in info_warm for r in inf],
                   "r_rel_fp64_cold": [r["r_rel"] for inf in info_cold for r in inf],
-                  "r_rel_output_c64": [r["r_rel_output"] for inf in info_warm + info_cold for r in inf],
+                  "r_rel_output_field": [r["r_rel_output"] for inf in info_warm + info_cold for r in inf],
+                  "output": "FP64 field (complex128)",
                   "r_rel_initial_warm": [r["r_rel_initial"] for inf in info_warm for r in inf],
                   "converged": f"{converged(info_warm) + converged(info_cold)} of "
                                f"{sum(len(x) for x in info_warm + info_cold)}", "maxit": args.maxit},
@@ -410,6 +450,7 @@ def run_ours(args, rank, world):
                            "rebuilds_in_timed_warm_steps": rebuilds_warm,
                            "warm_with_rebuild_every_mask": layered_always},
         "paper_configurations": paper,
+        "practical_width_criterion": width,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "matvec": {"ms_per_A_P_apply": ms_apply, "stages_ms_per_apply":

@@ -208,9 +208,11 @@ PSFD_API size_t psfd_solve_workspace_size(psfd_plan plan, int method, int restar
  * as above) to the relative tolerance inner_tol, then E += M d.  Convergence is
  * the FP64 relative residual <= tol (Eq. relative_residual); maxit bounds the
  * total number of inner iterations, max_outer (0 = 100) the outer steps.  The
- * returned field is the complex64 rounding of the FP64 field; info.r_rel_output
- * is its own FP64 relative residual (rounding a field to complex64 leaves a
- * residual of the order of 1e-6 on these grids).  refine = 0 is psfd_solve.
+ * returned field is the complex64 rounding of the FP64 field, or with out_c128
+ * the FP64 field itself; info.r_rel_output is the returned field's own FP64
+ * relative residual (rounding a field to complex64 leaves a residual of about
+ * 1.3e-6 at 128x128x64, so a 1e-6 target needs out_c128 to hold in the
+ * output).  refine = 0 is psfd_solve.
  * Workspace: psfd_solve_ex_workspace_size() bytes or NULL (allocated inside). */
 typedef struct {
   double tol;
@@ -221,6 +223,8 @@ typedef struct {
   int refine;
   double inner_tol;
   int max_outer;
+  int out_c128;   /* 1: E receives the FP64 field as complex128 (double re, im) [nrhs][3][nz][ny][nx]
+                     (pass a buffer of that size, cast to psfd_c64*); needs refine = 1.  0: complex64 */
 } psfd_solve_opts_t;
 PSFD_API int psfd_solve_ex(psfd_plan plan, const psfd_c64* b, const psfd_c64* x0, psfd_c64* E,
                            const psfd_solve_opts_t* opts, psfd_info_t* info, void* workspace,

@@ -19,6 +19,10 @@ PyTorch CPU ops (library FFTs, matmuls and dense LU serve as steps):
                       (Eq. relative_residual), dense assembly + LU.
 * ``oracle.fno``    - factorised FNO forward (Sec. 2.1, Eqs. 1-4) and the
                       physics-informed loss (Eq. loss).
+* ``oracle.metric`` - threshold-contour widths of the scattered-field
+                      intensity along scan lines and their deviation from a
+                      reference solution (Sec. 4, practical assessment,
+                      Eq. logistic_sigmoid).
 
 Parity status of each function is stated in its module header.
 """

@@ -1009,6 +1009,10 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
                              const psfd_solve_opts_t* o, psfd_info_t* info, void* workspace,
                              size_t workspace_bytes) {
   if (!P || !b || !E || !info || !o) { psfd_set_error("psfd_solve_ex: null argument"); return PSFD_ERR_ARG; }
+  if (o->out_c128 && !o->refine) {
+    psfd_set_error("psfd_solve_ex: out_c128 needs refine = 1 (the FP64 field)");
+    return PSFD_ERR_ARG;
+  }
   if (!o->refine) {
     int rc = psfd_solve(P, b, x0, E, o->tol, o->maxit, o->method, o->restart, o->use_precond, info, workspace,
                         workspace_bytes);
@@ -1144,19 +1148,27 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     a64.a32 = My; a64.o64 = E64;
     if ((rc = launch_v64<V64_ADD>(a64, nr, st, nb))) return fail(rc);
   }
-  // output: E = complex64(F^-1 E64), transformed in FP64
-  PSFD_CUDA_TRY(cudaMemcpyAsync(r64, E64, (size_t)nr * n * sizeof(zd), cudaMemcpyDeviceToDevice, st));
-  if ((rc = transform64(P, r64, nplanes, false, us))) return fail(rc);
-  a64.a64 = r64; a64.o32 = (cf*)E; a64.skip = nullptr;
-  if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
-  // FP64 residual of the returned complex64 field
-  a64.a32 = (const cf*)E; a64.o64 = r64;
-  if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
-  if ((rc = transform64(P, r64, nplanes, true, us))) return fail(rc);
-  if ((rc = apply64_hybrid(P, r64, E64))) return fail(rc);
-  a64.b64 = b64; a64.a64 = E64; a64.o64 = E64;
-  if ((rc = launch_v64<V64_RES>(a64, nr, st, nb))) return fail(rc);
-  PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+  if (o->out_c128) {
+    // output: E = F^-1 E64 in FP64 (complex128); its residual is the last outer residual
+    zd* E128 = (zd*)E;
+    PSFD_CUDA_TRY(cudaMemcpyAsync(E128, E64, (size_t)nr * n * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+    if ((rc = transform64(P, E128, nplanes, false, us))) return fail(rc);
+    for (int r = 0; r < nr; ++r) hs[r].res1 = rr[r];
+  } else {
+    // output: E = complex64(F^-1 E64), transformed in FP64
+    PSFD_CUDA_TRY(cudaMemcpyAsync(r64, E64, (size_t)nr * n * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+    if ((rc = transform64(P, r64, nplanes, false, us))) return fail(rc);
+    a64.a64 = r64; a64.o32 = (cf*)E; a64.skip = nullptr;
+    if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
+    // FP64 residual of the returned complex64 field
+    a64.a32 = (const cf*)E; a64.o64 = r64;
+    if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
+    if ((rc = transform64(P, r64, nplanes, true, us))) return fail(rc);
+    if ((rc = apply64_hybrid(P, r64, E64))) return fail(rc);
+    a64.b64 = b64; a64.a64 = E64; a64.o64 = E64;
+    if ((rc = launch_v64<V64_RES>(a64, nr, st, nb))) return fail(rc);
+    PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
+  }
   PSFD_CUDA_TRY(cudaStreamSynchronize(st));
   int worst = PSFD_OK;
   for (int r = 0; r < nr; ++r) {

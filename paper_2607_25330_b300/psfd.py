@@ -54,7 +54,8 @@ class Info(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("method", C.c_int), ("restart", C.c_int),
-                ("use_precond", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int)]
+                ("use_precond", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
+                ("out_c128", C.c_int)]
 
 
 class FnoWeights(C.Structure):
@@ -99,6 +100,7 @@ def lib() -> C.CDLL:
         "psfd_solve_ex_workspace_size": (sz, [vp, C.POINTER(SolveOpts)]),
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
         "psfd_layered_build": (i, [vp]),
+        "psfd_width_metric": (i, [vp, vp, vp, i, i, i, C.c_float, i, d, C.POINTER(C.c_double)]),
         "psfd_layered_refresh": (i, [vp, d, C.POINTER(C.c_int)]),
         "psfd_layered_bytes": (sz, [vp]),
         "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
@@ -130,7 +132,7 @@ def declared_symbols() -> List[str]:
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
-            "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes",
+            "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
             "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
@@ -248,11 +250,18 @@ class Plan:
     def solve_ex(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-6, maxit: int = 20000,
                  method: int = PSFD_GMRES, restart: int = 30, precond: bool = True, refine: bool = True,
                  inner_tol: float = 1e-2, max_outer: int = 0, out: Optional[torch.Tensor] = None,
-                 workspace: Optional[torch.Tensor] = None):
-        """Mixed-precision solve (FP64 outer residual and field, complex64 inner Krylov)."""
-        E = self.empty() if out is None else out
+                 workspace: Optional[torch.Tensor] = None, out_c128: bool = False):
+        """Mixed-precision solve (FP64 outer residual and field, complex64 inner Krylov).
+
+        out_c128: return the FP64 field as complex128 instead of its complex64 rounding."""
+        if out is None:
+            E = torch.empty(self.shape, dtype=torch.complex128 if out_c128 else torch.complex64, device="cuda")
+        else:
+            E = out
+            assert E.dtype == (torch.complex128 if out_c128 else torch.complex64)
         info = (Info * self.nrhs)()
-        o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, max_outer)
+        o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, max_outer,
+                      1 if out_c128 else 0)
         ws, wsb = None, 0
         if workspace is not None:
             ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
@@ -270,6 +279,15 @@ class Plan:
         _check(lib().psfd_layered_refresh(self.h, max_shift, C.byref(r)), "psfd_layered_refresh")
         return bool(r.value)
 
+    def width_metric(self, E: torch.Tensor, E_ref: torch.Tensor, z: int, rhs: int = 0, comp: int = 1,
+                     I_th: float = 0.15, n_lines: int = 100, demag: float = 4.0) -> Dict:
+        """Threshold-contour width deviation of E from E_ref on plane z (Sec. 4), wafer units (nm)."""
+        out = (C.c_double * 6)()
+        _check(lib().psfd_width_metric(self.h, _ptr(E.contiguous()), _ptr(E_ref.contiguous()), rhs, comp, z, I_th,
+                                       n_lines, demag, out), "psfd_width_metric")
+        return {"mean": out[0], "std": out[1], "max": out[2], "matched": int(out[3]), "unresolved": int(out[4]),
+                "frac_above_1nm": out[5]}
+
     def layered_bytes(self) -> int:
         return int(lib().psfd_layered_bytes(self.h))
 
@@ -279,7 +297,7 @@ class Plan:
         return T.value
 
     def workspace_size_ex(self, method: int = PSFD_GMRES, restart: int = 30, refine: bool = True) -> int:
-        o = SolveOpts(1e-6, 1, method, restart, 1, 1 if refine else 0, 1e-2, 0)
+        o = SolveOpts(1e-6, 1, method, restart, 1, 1 if refine else 0, 1e-2, 0, 0)
         return int(lib().psfd_solve_ex_workspace_size(self.h, C.byref(o)))
 
     def workspace_size(self, method: int = PSFD_BICGSTAB, restart: int = 30) -> int:
@@ -398,7 +416,7 @@ def solve_batched(plans: Sequence["Plan"], bs: Sequence[torch.Tensor], x0s=None,
     arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() if t is not None else None for t in ts])
     total = sum(p.nrhs for p in plans)
     info = (Info * total)()
-    o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, 0)
+    o = SolveOpts(tol, maxit, method, restart, _pc(precond), 1 if refine else 0, inner_tol, 0, 0)
     for t in list(bs) + ([t for t in x0s if t is not None] if x0s else []):
         _ptr(t)
     code = lib().psfd_solve_batched((C.c_void_p * n)(*[p.h for p in plans]), n, arr(bs),

@@ -128,7 +128,13 @@ def test_layered_full_size_128x128x64_reaches_1e6():
     fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
     b = plan.background(prob.stack(), fill, prob.pols)
     plan.layered_build()
-    res = plan.solve_ex(b, tol=1e-6, maxit=600, method=psfd.PSFD_GMRES, restart=30, precond=psfd.PC_LAYERED)
+    res = plan.solve_ex(b, tol=1e-6, maxit=600, method=psfd.PSFD_GMRES, restart=30, precond=psfd.PC_LAYERED,
+                        out_c128=True)
     assert res["code"] == 0, res["info"]
-    for inf in res["info"]:
-        assert inf["r_rel"] <= 1e-6 and inf["iters"] <= 200, inf
+    assert res["E"].dtype == torch.complex128
+    g, fill_o = oracle_setup(prob, a)
+    for r, inf in enumerate(res["info"]):
+        assert inf["r_rel"] <= 1e-6 and inf["r_rel_output"] <= 1e-6 and inf["iters"] <= 200, inf
+        # the returned FP64 field meets the tolerance in the oracle's own residual too
+        bo = O.source_b(g, fill_o, prob.pols[r])
+        assert O.rel_residual(g, res["E"][r].cpu(), fill_o, bo) <= 1.01e-6
