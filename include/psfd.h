@@ -139,6 +139,23 @@ PSFD_API int psfd_mask_fill(psfd_plan plan, const uint8_t* a_bin, const float* z
 PSFD_API int psfd_background(psfd_plan plan, const psfd_stack_t* stack, const float* fill,
                     const int* pol, psfd_c64* b);
 
+/* Per-plane material contrast: deps(x, y, z) = fill(x, y, z) * c[z] with c[z] =
+ * re[z] + i im[z] (HOST double arrays [nz]); NULL, NULL restores c[z] = eps_abs - 1
+ * (the absorber of psfd_params_t).  With fill = 1 on the planes of a layered
+ * structure and c[z] its cell-averaged eps - 1, and an empty stack (r = 0, so
+ * R = 0), the operator is the standard full-domain scattered-field PSFD with
+ * that structure meshed (e.g. a bare multilayer, whose specular reflection can
+ * be compared with the transfer-matrix result).  Call psfd_background again
+ * afterwards (the source depends on c); PSFD_ERR_ARG on a non-finite entry. */
+PSFD_API int psfd_set_plane_contrast(psfd_plan plan, const double* re, const double* im);
+/* The per-plane table of a layer stack meshed in the domain: layers (top to
+ * bottom, refractive indices and thicknesses in nm) with the top face at height
+ * z_top (nm, plane k at k dz), the stack's substrate below it down through the
+ * bottom PML, vacuum above; c[z] = cell average of eps - 1 over
+ * [z dz - dz/2, z dz + dz/2].  zmask (HOST float [nz], nullable) receives 1 on
+ * planes with nonzero contrast (the zprof of psfd_mask_fill for fill = 1). */
+PSFD_API int psfd_set_layer_stack_contrast(psfd_plan plan, const psfd_stack_t* layers, double z_top, float* zmask);
+
 /* Copy the FP64 reflection tables to host: rs, rp, kz0 as [ny][nx] complex
  * double pairs (re, im), each array 2*nx*ny doubles.  Synchronous. */
 PSFD_API int psfd_reflection_tables(psfd_plan plan, double* rs, double* rp, double* kz0);

@@ -44,6 +44,7 @@ every lateral mode its blocks do not couple E_s with (E_t, E_z).
 """
 from __future__ import annotations
 
+import cmath
 import math
 from typing import Dict, Optional, Sequence
 
@@ -89,6 +90,8 @@ class Grid:
         self.z_ml = int(p["z_ml"])
         self.eps_abs = complex(p["n_abs"]) ** 2
         self.deps_abs = self.eps_abs - 1.0
+        # per-plane material contrast c[z] (deps = fill * c[z]); None: c[z] = eps_abs - 1
+        self.plane_contrast = None
         # PML (stretched coordinate, cubic grading, both ends of the z box)
         npml = int(p["pml_planes"])
         self.sigma = torch.zeros(self.nz, dtype=F64)
@@ -274,8 +277,12 @@ def reflect_adjoint(g: Grid, U: torch.Tensor) -> torch.Tensor:
 
 
 def deps_field(g: Grid, fill: torch.Tensor) -> torch.Tensor:
-    """Permittivity contrast deps = eps - eps_bg = f * (eps_abs - 1) (Sec. 2.2)."""
-    return fill.to(C128) * g.deps_abs
+    """Permittivity contrast deps = eps - eps_bg = f * (eps_abs - 1) (Sec. 2.2), or f * c[z] with a
+    per-plane material table (a layered structure meshed in the domain)."""
+    if g.plane_contrast is None:
+        return fill.to(C128) * g.deps_abs
+    c = torch.as_tensor(g.plane_contrast, dtype=C128)
+    return fill.to(C128) * c[:, None, None]
 
 
 def apply_A(g: Grid, E: torch.Tensor, fill: torch.Tensor) -> torch.Tensor:
@@ -387,3 +394,40 @@ def apply_P_layered(g: Grid, fill: torch.Tensor, X: torch.Tensor, mats: torch.Te
     Xh = _fft2(X.to(C128)).permute(2, 3, 0, 1).reshape(g.ny, g.nx, n, 1)
     Yh = torch.linalg.solve(mats, Xh).reshape(g.ny, g.nx, 3, g.nz).permute(2, 3, 0, 1)
     return _ifft2(Yh)
+
+
+# --------------------------------------------------------------------------- meshed layered structures
+def layered_cell_contrast(g: Grid, layers, z_top: float, eps_below: complex) -> torch.Tensor:
+    """Cell-averaged eps - 1 of a layer stack meshed on the planes: layers = [(eps, thickness), ...]
+    listed top to bottom, the top face at height z_top (nm, plane k at k dz), eps_below under the
+    last layer (down into the bottom PML), vacuum above.  Cell k covers [k dz - dz/2, k dz + dz/2]."""
+    bounds = [(float("inf"), z_top, 1.0 + 0j)]
+    z = z_top
+    for eps, d in layers:
+        bounds.append((z, z - d, complex(eps)))
+        z -= d
+    bounds.append((z, -float("inf"), complex(eps_below)))
+    c = torch.zeros(g.nz, dtype=C128)
+    for k in range(g.nz):
+        lo, hi = k * g.dz - 0.5 * g.dz, k * g.dz + 0.5 * g.dz
+        acc = 0j
+        for top, bot, eps in bounds:
+            ov = max(0.0, min(hi, top) - max(lo, bot))
+            acc += ov * (eps - 1.0)
+        c[k] = acc / g.dz
+    return c
+
+
+def specular_reflection(g: Grid, E: torch.Tensor, z_obs: int, z_top: float, pol: int) -> complex:
+    """Reflection coefficient of the tangential field at the stack top from the scattered field in
+    the vacuum above it: E_s = r E_inc(z_top) exp(i k_z (z - z_top)) in the incident Bloch mode."""
+    Eh = _fft2(E.to(C128)) / (g.nx * g.ny)                        # mode (0, 0) = incident Bloch mode
+    kz = g.kz_inc
+    einc_top = cmath.exp(-1j * kz * (z_top - g.z_ml * g.dz))       # incident phase at the stack top
+    if pol == 0:
+        e_t = -math.sin(g.phi) * Eh[0, z_obs, 0, 0] + math.cos(g.phi) * Eh[1, z_obs, 0, 0]
+        amp = 1.0
+    else:
+        e_t = math.cos(g.phi) * Eh[0, z_obs, 0, 0] + math.sin(g.phi) * Eh[1, z_obs, 0, 0]
+        amp = math.cos(g.theta)                                    # tangential part of the TM field
+    return complex(e_t) / (amp * einc_top * cmath.exp(1j * kz * (z_obs * g.dz - z_top)))

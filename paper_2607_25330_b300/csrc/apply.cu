@@ -423,7 +423,9 @@ struct ColArgs {
   const cf* tw;
   // COL_CONTRAST
   const float* fill;
-  float dre, dim;  // scale * deps (complex)
+  const cf* pc;    // per-plane contrast c[z]; the multiplier is cs * c[z] (conjugated if pc_conj)
+  float cs;
+  int pc_conj;
   int nab, za0;
   long plane_elems;  // nx * ny
   const int* done;
@@ -465,13 +467,15 @@ __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
     // IFFT_y -> * scale * deps * fill(x, y, z) -> FFT_y
     const long zz = plane % a.nab;
     const float* __restrict__ f = a.fill + (a.za0 + zz) * a.plane_elems + ix;
+    const cf c0 = a.pc[a.za0 + zz];
+    const float dre = a.cs * c0.x, dim = a.cs * (a.pc_conj ? -c0.y : c0.y);
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : czero();
     PY::template to_time<true>(v, t, a.tw);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const float fv = act ? __ldg(f + (long)(t + T * m) * sx) : 0.f;
-      v[m] = cmul(v[m], make_float2(a.dre * fv, a.dim * fv));
+      v[m] = cmul(v[m], make_float2(dre * fv, dim * fv));
     }
     PY::template to_freq<false>(v, t, a.tw);
 #pragma unroll
@@ -628,7 +632,9 @@ struct PlaneArgs {
   const int* done;
   int* err;
   int nz, nab, za0;
-  float dre, dim;
+  const cf* pc;     // per-plane contrast; multiplier cs * c[z] (conjugated if pc_conj)
+  float cs;
+  int pc_conj;
   bool to_y;   // true: y -= result (forward); false: G <- result (adjoint preparation)
 };
 
@@ -649,6 +655,8 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(PlaneArgs a) {
   if (a.done && a.done[rhs]) return;
   const int c = (int)((plane / a.nab) % 3);
   const int zz = (int)(plane % a.nab);
+  const cf c0 = a.pc[a.za0 + zz];
+  const float dre = a.cs * c0.x, dim = a.cs * (a.pc_conj ? -c0.y : c0.y);
   cf* Gp = a.G + plane * (long)N * N;
   const float* Fp = a.fill + (long)(a.za0 + zz) * N * N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -709,7 +717,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(PlaneArgs a) {
 #pragma unroll
     for (int m = 0; m < RC; ++m) {
       const float fv = F[(t + TC * m) * N + col];
-      v[m] = cmul(v[m], make_float2(a.dre * fv, a.dim * fv));
+      v[m] = cmul(v[m], make_float2(dre * fv, dim * fv));
     }
     PY::template to_freq<false>(v, t, a.twy);
 #pragma unroll
@@ -760,9 +768,9 @@ static int plane_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint, 
   PlaneArgs a;
   a.G = P->G; a.y = y; a.fill = P->fill; a.twx = P->tw_x; a.twy = P->tw_y; a.done = done; a.err = P->err;
   a.nz = P->nz; a.nab = nab; a.za0 = P->za0;
-  const double sc = P->k0 * P->k0 / (double)P->ncols;
-  a.dre = (float)(sc * P->deps_re);
-  a.dim = (float)(sc * (adjoint ? -P->deps_im : P->deps_im));
+  a.pc = P->pc;
+  a.cs = (float)(P->k0 * P->k0 / (double)P->ncols);
+  a.pc_conj = adjoint ? 1 : 0;
   a.to_y = to_y;
   const long nplanes = (long)P->nrhs * 3 * nab;
   int rc = PSFD_OK;
@@ -798,7 +806,7 @@ int launch_lateral_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint
   ColArgs c{};
   const double sc = P->k0 * P->k0 / (double)P->ncols;
   c.buf = P->G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.f; c.tw = P->tw_y;
-  c.fill = P->fill; c.dre = (float)(sc * P->deps_re); c.dim = (float)(sc * (adjoint ? -P->deps_im : P->deps_im));
+  c.fill = P->fill; c.pc = P->pc; c.cs = (float)sc; c.pc_conj = adjoint ? 1 : 0;
   c.nab = nab; c.za0 = P->za0; c.plane_elems = P->ncols; c.done = done; c.planes_per_rhs = 3L * nab;
   if ((rc = cols_dispatch(P->ny, c, COL_CONTRAST, P->stream))) return rc;
   RowArgs w{};
@@ -830,7 +838,7 @@ static int adjoint_contrast(psfd_plan_s* P, const cf* x) {
   ColArgs c{};
   const double sc = P->k0 * P->k0 / (double)P->ncols;
   c.buf = P->G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.f; c.tw = P->tw_y;
-  c.fill = P->fill; c.dre = (float)(sc * P->deps_re); c.dim = (float)(-sc * P->deps_im);
+  c.fill = P->fill; c.pc = P->pc; c.cs = (float)sc; c.pc_conj = 1;
   c.nab = nab; c.za0 = P->za0; c.plane_elems = P->ncols; c.planes_per_rhs = 3L * nab;
   if ((rc = cols_dispatch(P->ny, c, COL_CONTRAST, P->stream))) return rc;
   return rows_dispatch(P->nx, r, ROW_FWD, P->stream);

@@ -206,7 +206,8 @@ struct Col64 {
   double scale;
   const zd* tw;
   const float* fill;
-  double dre, dim;
+  const zd* pc;   // per-plane contrast; multiplier cs * c[z]
+  double cs;
   int nab, za0;
   long plane_elems;
 };
@@ -242,13 +243,15 @@ __global__ void __launch_bounds__(64) k_cols64(Col64 a) {
   } else {
     const long zz = plane % a.nab;
     const float* f = a.fill + (a.za0 + zz) * a.plane_elems + ix;
+    const zd c0 = a.pc[a.za0 + zz];
+    const double dre = a.cs * c0.x, dim = a.cs * c0.y;
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : make_double2(0.0, 0.0);
     PY::template to_time<true>(v, t, a.tw);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const double fv = act ? (double)f[(long)(t + T * m) * sx] : 0.0;
-      v[m] = cmul(v[m], make_double2(a.dre * fv, a.dim * fv));
+      v[m] = cmul(v[m], make_double2(dre * fv, dim * fv));
     }
     PY::template to_freq<false>(v, t, a.tw);
 #pragma unroll
@@ -417,7 +420,7 @@ int apply64_hybrid(psfd_plan_s* P, const zd* x, zd* y) {
   Col64 c{};
   const double scl = P->k0 * P->k0 / (double)P->ncols;
   c.buf = P->F.G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.0; c.tw = P->F.twy;
-  c.fill = P->fill; c.dre = scl * P->deps_re; c.dim = scl * P->deps_im; c.nab = nab; c.za0 = P->za0;
+  c.fill = P->fill; c.pc = P->pc64; c.cs = scl; c.nab = nab; c.za0 = P->za0;
   c.plane_elems = P->ncols;
   if ((rc = cols64(P->ny, c, C64_CONTRAST, P->stream))) return rc;
   Row64 w{};

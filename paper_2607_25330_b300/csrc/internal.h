@@ -34,7 +34,11 @@ struct psfd_plan_s {
   long ncols = 0;            // nx * ny
   long nvec = 0;             // 3 * nz * ncols (complex entries per right-hand side)
   double k0 = 0, kx_inc = 0, ky_inc = 0, kz_inc = 0;
-  double deps_re = 0, deps_im = 0;
+  double deps_re = 0, deps_im = 0;  // eps_abs - 1 (default per-plane contrast)
+  // per-plane material contrast c[z]: deps(x, y, z) = fill(x, y, z) * c[z]; defaults to eps_abs - 1
+  cf* pc = nullptr;                  // [nz] complex64
+  zd* pc64 = nullptr;                // [nz] FP64
+  std::vector<zd> pc_host;
   // device tables
   float* kx = nullptr;       // [nx] Bloch-shifted lateral wavenumbers
   float* ky = nullptr;       // [ny]

@@ -1,7 +1,8 @@
 // Layered-background preconditioner: the exact inverse, per lateral Bloch mode, of the operator
 // with the permittivity contrast replaced by its lateral average on each plane.
 //
-// With the fill averaged over every z-plane, Δε̄(z) = (ε_abs − 1) · mean_xy f(z), the operator of
+// With the fill averaged over every z-plane, Δε̄(z) = c(z) · mean_xy f(z) (c = ε_abs − 1 unless a
+// per-plane contrast table is set), the operator of
 // Eqs. bg_source / vector_helmholtz_operator no longer couples lateral modes.  For the mode
 // (kx, ky), κ = |k∥|, ŝ = (−ky, kx)/κ, t̂ = (kx, ky)/κ (ŝ = ŷ, t̂ = x̂ at κ = 0) and the
 // stretched axial derivative D = s⁻¹ F⁻¹ i k_z F, the curl-curl is
@@ -466,7 +467,7 @@ extern "C" int psfd_layered_build(psfd_plan P) {
   if (rc) return rc;
   std::vector<cf> deps(nz);
   for (int z = 0; z < nz; ++z)
-    deps[z] = make_float2((float)(mean[z] * P->deps_re), (float)(mean[z] * P->deps_im));
+    deps[z] = make_float2((float)(mean[z] * P->pc_host[z].x), (float)(mean[z] * P->pc_host[z].y));
   PSFD_CUDA_TRY(cudaMemcpyAsync(P->lay_deps, deps.data(), nz * sizeof(cf), cudaMemcpyHostToDevice, s));
   PSFD_CUDA_TRY(cudaMemsetAsync(P->lay_err, 0, sizeof(int), s));
   switch (nz) {

@@ -1,6 +1,8 @@
 // Plan set-up, geometry (mask -> fill), FP64 multilayer reflection and the
 // background source b (Sec. 2.2, Eq. bg_source).
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <atomic>
@@ -224,7 +226,8 @@ struct SourceArgs {
   cf* b;
   int nx, ny, nz, z_ml;
   long ncols;
-  double dz, k0, theta, phi, deps_re, deps_im;
+  double dz, k0, theta, phi;
+  const double2* pc64;     // per-plane contrast c[z]
   const double2* rs64;
   const double2* rp64;
   const double2* kz064;
@@ -268,7 +271,7 @@ __global__ void k_source(SourceArgs a) {
   const long i = (long)z * a.ncols + xy;
   const double f = a.fill[i];
   const double k02 = a.k0 * a.k0;
-  const cd de = {f * a.deps_re * k02, f * a.deps_im * k02};
+  const cd de = {f * a.pc64[z].x * k02, f * a.pc64[z].y * k02};
   const long plane = a.ncols * a.nz;
   for (int c = 0; c < 3; ++c) {
     const cd v = de * cd_(f_tot[2 * c], f_tot[2 * c + 1]);
@@ -334,6 +337,14 @@ void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv) {
   }
 }
 
+static int upload_pc32(psfd_plan_s* P) {
+  std::vector<cf> h(P->pc_host.size());
+  for (size_t z = 0; z < h.size(); ++z) h[z] = make_float2((float)P->pc_host[z].x, (float)P->pc_host[z].y);
+  if (!P->pc) PSFD_CUDA_TRY(cudaMalloc((void**)&P->pc, h.size() * sizeof(cf)));
+  PSFD_CUDA_TRY(cudaMemcpy(P->pc, h.data(), h.size() * sizeof(cf), cudaMemcpyHostToDevice));
+  return PSFD_OK;
+}
+
 static int upload(void** dst, const void* src, size_t bytes) {
   PSFD_CUDA_TRY(cudaMalloc(dst, bytes));
   PSFD_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
@@ -344,7 +355,7 @@ static void plan_free(psfd_plan_s* P) {
   fp64_free(P);
   layered_free(P);
   void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
-                  P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err};
+                  P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err, P->pc, P->pc64};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -393,6 +404,7 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
   for (int i = 0; i < p.nx; ++i) kx[i] = (float)(host_fftk(i, p.nx, p.dx) + P->kx_inc);
   for (int i = 0; i < p.ny; ++i) ky[i] = (float)(host_fftk(i, p.ny, p.dy) + P->ky_inc);
   for (int i = 0; i < p.nz; ++i) kz[i] = (float)host_fftk(i, p.nz, p.dz);
+  P->pc_host.assign(p.nz, make_double2(P->deps_re, P->deps_im));
   std::vector<zd> sinv64;
   pml_sinv64(P, sinv64);
   std::vector<cf> sinv(p.nz);
@@ -406,9 +418,11 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
       (rc = upload((void**)&P->ky, ky.data(), ky.size() * 4)) ||
       (rc = upload((void**)&P->kz, kz.data(), kz.size() * 4)) ||
       (rc = upload((void**)&P->sinv, sinv.data(), sinv.size() * 8)) ||
+      (rc = upload((void**)&P->pc64, P->pc_host.data(), P->pc_host.size() * sizeof(zd))) ||
       (rc = upload((void**)&P->tw_x, twx.data(), twx.size() * 8)) ||
       (rc = upload((void**)&P->tw_y, twy.data(), twy.size() * 8)) ||
-      (rc = upload((void**)&P->tw_z, twz.data(), twz.size() * 8))) {
+      (rc = upload((void**)&P->tw_z, twz.data(), twz.size() * 8)) ||
+      (rc = upload_pc32(P))) {
     plan_free(P);
     delete P;
     return rc;
@@ -545,7 +559,7 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
     a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.z_ml = P->p.z_ml; a.ncols = nm;
     a.dz = P->p.dz; a.k0 = P->k0;
     a.theta = P->p.theta_deg * M_PI / 180.0; a.phi = P->p.phi_deg * M_PI / 180.0;
-    a.deps_re = P->deps_re; a.deps_im = P->deps_im;
+    a.pc64 = P->pc64;
     a.rs64 = P->R.rs64; a.rp64 = P->R.rp64; a.kz064 = P->R.kz064;
     a.pol = pol[r];
     dim3 grid((unsigned)((nm + 255) / 256), (unsigned)P->nz);
@@ -554,6 +568,62 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
   }
   P->have_background = true;
   return PSFD_OK;
+}
+
+extern "C" int psfd_set_plane_contrast(psfd_plan P, const double* re, const double* im) {
+  if (!P) { psfd_set_error("psfd_set_plane_contrast: null plan"); return PSFD_ERR_ARG; }
+  if ((re == nullptr) != (im == nullptr)) {
+    psfd_set_error("psfd_set_plane_contrast: give both re and im, or neither");
+    return PSFD_ERR_ARG;
+  }
+  for (int z = 0; z < P->nz; ++z) {
+    P->pc_host[z] = re ? make_double2(re[z], im[z]) : make_double2(P->deps_re, P->deps_im);
+    if (!std::isfinite(P->pc_host[z].x) || !std::isfinite(P->pc_host[z].y)) {
+      psfd_set_error("psfd_set_plane_contrast: non-finite entry at plane %d", z);
+      return PSFD_ERR_ARG;
+    }
+  }
+  PSFD_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  PSFD_CUDA_TRY(cudaMemcpy(P->pc64, P->pc_host.data(), P->nz * sizeof(zd), cudaMemcpyHostToDevice));
+  int rc = upload_pc32(P);
+  if (rc) return rc;
+  P->have_background = false;   // b and the registered fill must be set again with psfd_background
+  return PSFD_OK;
+}
+
+extern "C" int psfd_set_layer_stack_contrast(psfd_plan P, const psfd_stack_t* layers, double z_top, float* zmask) {
+  if (!P || !layers) { psfd_set_error("psfd_set_layer_stack_contrast: null argument"); return PSFD_ERR_ARG; }
+  if (layers->n_layers < 0 || (layers->n_layers > 0 && (!layers->n_re || !layers->n_im || !layers->d))) {
+    psfd_set_error("psfd_set_layer_stack_contrast: bad stack");
+    return PSFD_ERR_ARG;
+  }
+  // layer k occupies [top_k - d_k, top_k] (top to bottom from z_top), the substrate everything
+  // below, vacuum everything above; cell z covers [z dz - dz/2, z dz + dz/2]
+  struct Slab { double top, bot; std::complex<double> eps; };
+  std::vector<Slab> slabs;
+  double zc = z_top;
+  for (int l = 0; l < layers->n_layers; ++l) {
+    const std::complex<double> n(layers->n_re[l], layers->n_im[l]);
+    slabs.push_back({zc, zc - layers->d[l], n * n});
+    zc -= layers->d[l];
+  }
+  const std::complex<double> ns(layers->sub_re, layers->sub_im);
+  slabs.push_back({zc, -1e300, ns * ns});
+  const double dz = P->p.dz;
+  std::vector<double> re(P->nz), im(P->nz);
+  for (int z = 0; z < P->nz; ++z) {
+    const double lo = z * dz - 0.5 * dz, hi = z * dz + 0.5 * dz;
+    std::complex<double> acc(0.0, 0.0);
+    for (const Slab& s : slabs) {
+      const double ov = std::max(0.0, std::min(hi, s.top) - std::max(lo, s.bot));
+      acc += ov * (s.eps - 1.0);
+    }
+    acc /= dz;
+    re[z] = acc.real();
+    im[z] = acc.imag();
+    if (zmask) zmask[z] = (acc != std::complex<double>(0.0, 0.0)) ? 1.f : 0.f;
+  }
+  return psfd_set_plane_contrast(P, re.data(), im.data());
 }
 
 extern "C" int psfd_reflection_tables(psfd_plan P, double* rs, double* rp, double* kz0) {

@@ -101,6 +101,8 @@ def lib() -> C.CDLL:
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
         "psfd_layered_build": (i, [vp]),
         "psfd_width_metric": (i, [vp, vp, vp, i, i, i, C.c_float, i, d, C.POINTER(C.c_double)]),
+        "psfd_set_plane_contrast": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "psfd_set_layer_stack_contrast": (i, [vp, C.POINTER(Stack), d, C.POINTER(C.c_float)]),
         "psfd_layered_refresh": (i, [vp, d, C.POINTER(C.c_int)]),
         "psfd_layered_bytes": (sz, [vp]),
         "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
@@ -133,6 +135,7 @@ def declared_symbols() -> List[str]:
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
             "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
+            "psfd_set_plane_contrast", "psfd_set_layer_stack_contrast",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
             "psfd_spectral_upsample_static", "psfd_launch_count", "psfd_timing_enable", "psfd_timing_read", "psfd_timing_read_bytes", "psfd_last_error", "psfd_version"]
@@ -287,6 +290,27 @@ class Plan:
                                        n_lines, demag, out), "psfd_width_metric")
         return {"mean": out[0], "std": out[1], "max": out[2], "matched": int(out[3]), "unresolved": int(out[4]),
                 "frac_above_1nm": out[5]}
+
+    def set_plane_contrast(self, c: Optional[Sequence[complex]]) -> None:
+        """deps = fill * c[z] per plane (None restores eps_abs - 1); call background() afterwards."""
+        if c is None:
+            _check(lib().psfd_set_plane_contrast(self.h, None, None), "psfd_set_plane_contrast")
+            return
+        c = np.asarray(c, dtype=np.complex128)
+        assert c.shape == (self.prob.nz,)
+        re = np.ascontiguousarray(c.real)
+        im = np.ascontiguousarray(c.imag)
+        _check(lib().psfd_set_plane_contrast(self.h, re.ctypes.data_as(C.POINTER(C.c_double)),
+                                             im.ctypes.data_as(C.POINTER(C.c_double))), "psfd_set_plane_contrast")
+
+    def set_layer_stack_contrast(self, stack: Dict, z_top: float) -> np.ndarray:
+        """Mesh a layer stack (top face at z_top nm) into the per-plane contrast; returns the plane mask."""
+        st = make_stack(stack)
+        zm = np.zeros(self.prob.nz, dtype=np.float32)
+        _check(lib().psfd_set_layer_stack_contrast(self.h, C.byref(st), z_top,
+                                                   zm.ctypes.data_as(C.POINTER(C.c_float))),
+               "psfd_set_layer_stack_contrast")
+        return zm
 
     def layered_bytes(self) -> int:
         return int(lib().psfd_layered_bytes(self.h))
