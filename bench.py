@@ -126,6 +126,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from
+# one ncu capture of the current kernel version on this workload (profiles/k_lay_apply_*.md):
+# reported as roofline.traffic when the bench runs the same kernel on the same workload
+NCU_TRAFFIC = {}
+
+
 def fp32_peak_tflops():
     """FP32 FMA peak of a B300 from its unit counts: 148 SMs x 128 lanes x 2 flop x 2.032 GHz."""
     return 148 * 128 * 2 * 2.032e9 / 1e12
@@ -363,7 +369,9 @@ def run_ours(args, rank, world):
     fp32_peak = fp32_peak_tflops()
     # Gauss-Jordan inversion of the TE (nz) and TM (2 nz) blocks of every lateral column:
     # N^3 complex multiply-adds (8 real flops each) per N x N block
-    lay_flops = prob.nx * prob.ny * 8.0 * (prob.nz ** 3 + (2 * prob.nz) ** 3)
+    # (ky and -ky share their blocks when there is no Bloch shift along y: ny/2 + 1 stored rows)
+    lay_rows = prob.ny // 2 + 1 if (prob.phi_deg == 0.0 or prob.theta_deg == 0.0) and prob.ny % 2 == 0 else prob.ny
+    lay_flops = prob.nx * lay_rows * 8.0 * (prob.nz ** 3 + (2 * prob.nz) ** 3)
     kernels = {"axial": "k_axial (fused curl-curl + R column kernel)",
                "contrast": "k_rows/k_cols contrast passes (absorber planes)",
                "krylov": "Krylov vector kernels (k_vec, k_gdot, k_gupd, k_v64)",
@@ -401,8 +409,10 @@ def run_ours(args, rank, world):
                 "ms_per_launch": d["ms_per_call"], "algorithmic_flops_per_launch": lay_flops,
                 "share_of_step": d["share"]}
     else:
+        traffic = NCU_TRAFFIC.get((dom, args.workload, nrhs))
         roof = {"kernel": kernels[dom], "stage": dom, "bound": "hbm", "achieved": d["GBps"], "peak": peak,
-                "unit": "GB/s", "frac": d["frac"], "traffic": None, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": d["frac"], "traffic": traffic, "peak_kind": peak_kind,
+                "traffic_source": "ncu capture in profiles/ (dram read + write per launch)" if traffic else None,
                 "ms_per_launch": d["ms_per_call"], "algorithmic_bytes_per_launch": d["bytes_per_call"],
                 "share_of_step": d["share"]}
     K = args.steps

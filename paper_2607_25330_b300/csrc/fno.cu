@@ -804,12 +804,20 @@ static size_t mix_smem_bytes(int C) { return (2 * C * C + 2 * C * MIX_TN) * size
 // per-mode mixing of a branch; xy modes: grid (n-tiles, mx*my); z modes: grid (n-tiles, mz) with mx = MX = 1
 static void mix_xy(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, cudaStream_t s) {
   const long NB = (long)d.B * d.nz;
+  if (!adjoint && fno_mix_tc_enabled(d.C)) {
+    fno_mix_tc(V, U, K, NB, d.mx * d.my, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2, s);
+    return;
+  }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)(d.mx * d.my));
   k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2,
                                            adjoint, !adjoint);
 }
 static void mix_z(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, cudaStream_t s) {
   const long NB = (long)d.B * d.nx * d.ny;
+  if (!adjoint && fno_mix_tc_enabled(d.C)) {
+    fno_mix_tc(V, U, K, NB, d.mz, 1, 1, (d.MZ - d.mz) / 2, 0, s);
+    return;
+  }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)d.mz);
   k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, adjoint, !adjoint);
 }

@@ -105,8 +105,16 @@ void psfd_set_error(const char* fmt, ...);
 double fft_wavenumber(int i, int n, double d);           // 2 pi m / (n d), FFT order, Nyquist negative
 void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv);   // 1 / s(z) in FP64
 
+// fno_tc.cu: forward per-mode mixing on the tensor cores (C = 32)
+bool fno_mix_tc_enabled(int C);
+int fno_mix_tc(const cf* V, cf* U, const cf* K, long NB, int modes, int mx, int MX, int offy, int offx,
+               cudaStream_t s);
+int fno_mix_tc_error(int* host_flag);
+
 // layered.cu
 int layered_supported(const psfd_plan_s* P);
+bool layered_pairs(const psfd_plan_s* P);
+long layered_columns(const psfd_plan_s* P);
 size_t layered_bytes(const psfd_plan_s* P);
 int layered_apply(psfd_plan_s* P, const cf* x, cf* y);
 void layered_free(psfd_plan_s* P);

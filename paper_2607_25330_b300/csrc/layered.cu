@@ -42,7 +42,8 @@ struct LayArgs {
   const cf* D2;         // [nz][nz] D * D
   const cf* deps;       // [nz] laterally averaged contrast
   float k0sq, dz;
-  int nx, nz, zml;
+  int nx, ny, nz, zml;
+  int pair;             // 1: blocks stored for rows 0 .. ny/2 only (ky and -ky share them)
   cf* mats;             // [ncols][5 nz^2]: TE inverse (nz^2) then TM inverse (4 nz^2), column-major
   int* err;             // set to 1 if a pivot vanished
 };
@@ -247,25 +248,32 @@ __global__ void k_plane_mean(const float* __restrict__ fill, long plane, double*
 }
 
 // y = P x in the HYBRID domain: per column, rotate (x, y) -> (s, t), apply the TE and TM
-// inverses, rotate back.  One CTA per LAY_GROUP consecutive kx columns of one ky row; all
-// right-hand sides share the matrices, which are read once.  Each thread produces two adjacent
-// output rows of one block, so every matrix load is a 16-byte (two-entry) load of a column of the
-// column-major block; a CTA has LAY_GROUP * 3 NZ / 2 threads.
+// inverses, rotate back.  The blocks depend on a column only through kappa = |k_par|; with no
+// Bloch shift along y the columns ky and -ky share them, so blocks are stored for the rows
+// h = 0 .. ny/2 only and a CTA serves LAY_GROUP consecutive kx columns of row h and of its partner
+// row ny - h, reading each block once for both rows and all right-hand sides.  Each thread
+// produces two adjacent output rows of one block (16-byte loads of the column-major blocks); a
+// CTA has LAY_GROUP * 3 NZ / 2 threads.
 template <int NZ>
 constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / 2; }
 
 template <int NZ, int NR>
-__global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 4 : 3)) k_lay_apply(LayArgs a, const cf* __restrict__ x,
+__global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 3 : 2)) k_lay_apply(LayArgs a, const cf* __restrict__ x,
                                                                      cf* __restrict__ y, long ncols) {
   constexpr int nrhs = NR;
   constexpr int G = LAY_GROUP, NT = apply_threads<NZ>();
-  extern __shared__ cf xs[];   // [G][3][NZ][nrhs]: (s, t, z) components after rotation
-  __shared__ float rot[G][4];  // sx, sy, tx, ty
-  const long col0 = (long)blockIdx.x * G;
-  const int ix0 = (int)(col0 % a.nx), iy = (int)(col0 / a.nx);
+  extern __shared__ cf xs[];       // [2G][3][NZ][nrhs]: (s, t, z) components after rotation
+  __shared__ float rot[2 * G][4];  // sx, sy, tx, ty per virtual column
+  const long hc0 = (long)blockIdx.x * G;               // first block column: row h, kx index ix0
+  const int ix0 = (int)(hc0 % a.nx), h = (int)(hc0 / a.nx);
+  const int ny = a.ny;
+  const int iyB = a.pair ? (ny - h) % ny : h;
+  const bool two = a.pair && iyB != h;                 // a partner row exists
+  const int nv = two ? 2 * G : G;                      // virtual columns: row h, then row iyB
   const int tid = threadIdx.x;
-  if (tid < G) {
-    const float kx = a.kx[ix0 + tid], ky = a.ky[iy];
+  if (tid < nv) {
+    const int iy = tid < G ? h : iyB;
+    const float kx = a.kx[ix0 + (tid % G)], ky = a.ky[iy];
     const float kap = sqrtf(kx * kx + ky * ky);
     const bool small = !(kap > 0.f);
     rot[tid][0] = small ? 0.f : -ky / kap;
@@ -275,37 +283,56 @@ __global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 4 : 3)) k_lay_
   }
   __syncthreads();
   const long n = 3L * NZ * ncols;   // entries per right-hand side
-  // gather + rotate: item = ((r * NZ + z) * G + g)
-  for (int it = tid; it < nrhs * NZ * G; it += NT) {
-    const int g = it % G, z = (it / G) % NZ, r = it / (G * NZ);
-    const long base = (long)r * n + (long)z * ncols + col0 + g;
+  auto colof = [&](int v) -> long { return (long)(v < G ? h : iyB) * a.nx + ix0 + (v % G); };
+  // gather + rotate: item = ((r * NZ + z) * nv + v)
+  for (int it = tid; it < nrhs * NZ * nv; it += NT) {
+    const int v = it % nv, z = (it / nv) % NZ, r = it / (nv * NZ);
+    const long base = (long)r * n + (long)z * ncols + colof(v);
     const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
-    const float sx = rot[g][0], sy = rot[g][1], tx = rot[g][2], ty = rot[g][3];
-    xs[((g * 3 + 0) * NZ + z) * nrhs + r] = cadd(cscale(ex, sx), cscale(ey, sy));
-    xs[((g * 3 + 1) * NZ + z) * nrhs + r] = cadd(cscale(ex, tx), cscale(ey, ty));
-    xs[((g * 3 + 2) * NZ + z) * nrhs + r] = ez;
+    const float sx = rot[v][0], sy = rot[v][1], tx = rot[v][2], ty = rot[v][3];
+    xs[((v * 3 + 0) * NZ + z) * nrhs + r] = cadd(cscale(ex, sx), cscale(ey, sy));
+    xs[((v * 3 + 1) * NZ + z) * nrhs + r] = cadd(cscale(ex, tx), cscale(ey, ty));
+    xs[((v * 3 + 2) * NZ + z) * nrhs + r] = ez;
   }
   __syncthreads();
   constexpr long MS = 5L * NZ * NZ;
-  // thread -> (column g, row pair rr, rr + 1) of the 3 NZ stacked rows (TE rows, then TM rows)
+  // thread -> (block column g, row pair rr, rr + 1) of the 3 NZ stacked rows (TE rows, then TM rows)
   const int g = tid / (3 * NZ / 2), rr = 2 * (tid - g * (3 * NZ / 2));
   const bool te = rr < NZ;
   const int nb = te ? NZ : 2 * NZ;                         // block size
   const int i = te ? rr : rr - NZ;                         // row inside the block
-  const cf* Mb = a.mats + (col0 + g) * MS + (te ? 0 : (long)NZ * NZ);
-  const cf* xsv = xs + (g * 3 + (te ? 0 : 1)) * NZ * nrhs;  // TE: s; TM: t then z (contiguous)
-  cf acc0[NR], acc1[NR];
+  const cf* Mb = a.mats + (hc0 + g) * MS + (te ? 0 : (long)NZ * NZ);
+  const int comp0 = te ? 0 : 1;                            // TE: s; TM: t then z (contiguous)
+  const cf* xa = xs + (g * 3 + comp0) * NZ * nrhs;
+  const cf* xb = xs + ((g + G) * 3 + comp0) * NZ * nrhs;
+  cf a0[NR], a1[NR], b0[NR], b1[NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) { acc0[r] = czero(); acc1[r] = czero(); }
+  for (int r = 0; r < NR; ++r) { a0[r] = czero(); a1[r] = czero(); b0[r] = czero(); b1[r] = czero(); }
+  if (two) {
 #pragma unroll 8
-  for (int j = 0; j < nb; ++j) {
-    const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
-    const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
+    for (int j = 0; j < nb; ++j) {
+      const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
+      const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const cf xv = xsv[j * NR + r];
-      acc0[r] = cfma(m0, xv, acc0[r]);
-      acc1[r] = cfma(m1, xv, acc1[r]);
+      for (int r = 0; r < NR; ++r) {
+        const cf xv = xa[j * NR + r], xw = xb[j * NR + r];
+        a0[r] = cfma(m0, xv, a0[r]);
+        a1[r] = cfma(m1, xv, a1[r]);
+        b0[r] = cfma(m0, xw, b0[r]);
+        b1[r] = cfma(m1, xw, b1[r]);
+      }
+    }
+  } else {
+#pragma unroll 8
+    for (int j = 0; j < nb; ++j) {
+      const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
+      const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const cf xv = xa[j * NR + r];
+        a0[r] = cfma(m0, xv, a0[r]);
+        a1[r] = cfma(m1, xv, a1[r]);
+      }
     }
   }
   __syncthreads();   // every thread has read its inputs: the outputs overwrite xs in place
@@ -314,19 +341,23 @@ __global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 4 : 3)) k_lay_
     const int z = te ? rr : (i < NZ ? i : i - NZ);          // rows z, z + 1 of component comp
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      xs[((g * 3 + comp) * NZ + z) * nrhs + r] = acc0[r];
-      xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = acc1[r];
+      xs[((g * 3 + comp) * NZ + z) * nrhs + r] = a0[r];
+      xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = a1[r];
+      if (two) {
+        xs[(((g + G) * 3 + comp) * NZ + z) * nrhs + r] = b0[r];
+        xs[(((g + G) * 3 + comp) * NZ + z + 1) * nrhs + r] = b1[r];
+      }
     }
   }
   __syncthreads();
-  for (int it = tid; it < nrhs * NZ * G; it += NT) {
-    const int gg = it % G, z = (it / G) % NZ, r = it / (G * NZ);
-    const long base = (long)r * n + (long)z * ncols + col0 + gg;
-    const cf es = xs[((gg * 3 + 0) * NZ + z) * nrhs + r], et = xs[((gg * 3 + 1) * NZ + z) * nrhs + r];
-    const float sx = rot[gg][0], sy = rot[gg][1], tx = rot[gg][2], ty = rot[gg][3];
+  for (int it = tid; it < nrhs * NZ * nv; it += NT) {
+    const int v = it % nv, z = (it / nv) % NZ, r = it / (nv * NZ);
+    const long base = (long)r * n + (long)z * ncols + colof(v);
+    const cf es = xs[((v * 3 + 0) * NZ + z) * nrhs + r], et = xs[((v * 3 + 1) * NZ + z) * nrhs + r];
+    const float sx = rot[v][0], sy = rot[v][1], tx = rot[v][2], ty = rot[v][3];
     y[base] = cadd(cscale(es, sx), cscale(et, tx));
     y[base + (long)NZ * ncols] = cadd(cscale(es, sy), cscale(et, ty));
-    y[base + 2L * NZ * ncols] = xs[((gg * 3 + 2) * NZ + z) * nrhs + r];
+    y[base + 2L * NZ * ncols] = xs[((v * 3 + 2) * NZ + z) * nrhs + r];
   }
 }
 
@@ -335,7 +366,8 @@ LayArgs lay_args(psfd_plan_s* P) {
   a.kx = P->kx; a.ky = P->ky; a.refl = P->R.refl; a.kz0 = P->R.kz0;
   a.D = P->lay_D; a.D2 = P->lay_D2; a.deps = P->lay_deps;
   a.k0sq = (float)(P->k0 * P->k0); a.dz = (float)P->p.dz;
-  a.nx = P->nx; a.nz = P->nz; a.zml = P->p.z_ml;
+  a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.zml = P->p.z_ml;
+  a.pair = layered_pairs(P) ? 1 : 0;
   a.mats = P->lay; a.err = P->lay_err;
   return a;
 }
@@ -343,18 +375,19 @@ LayArgs lay_args(psfd_plan_s* P) {
 template <int NZ>
 int build_nz(psfd_plan_s* P) {
   LayArgs a = lay_args(P);
-  k_lay_inv<NZ, false><<<(unsigned)P->ncols, LAY_THREADS, 0, P->stream>>>(a, 0);
+  const unsigned nblk = (unsigned)layered_columns(P);
+  k_lay_inv<NZ, false><<<nblk, LAY_THREADS, 0, P->stream>>>(a, 0);
   PSFD_CHECK_LAUNCH();
-  k_lay_inv<2 * NZ, true><<<(unsigned)P->ncols, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+  k_lay_inv<2 * NZ, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
 
 template <int NZ, int NR>
 int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
-  const size_t smem = (size_t)LAY_GROUP * 3 * NZ * NR * sizeof(cf);
-  k_lay_apply<NZ, NR><<<(unsigned)(P->ncols / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(a, x, y,
-                                                                                               P->ncols);
+  const size_t smem = (size_t)2 * LAY_GROUP * 3 * NZ * NR * sizeof(cf);
+  k_lay_apply<NZ, NR><<<(unsigned)(layered_columns(P) / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(
+      a, x, y, P->ncols);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -376,7 +409,15 @@ int layered_supported(const psfd_plan_s* P) {
   return (P->nz == 16 || P->nz == 32 || P->nz == 48 || P->nz == 64) && P->nx % LAY_GROUP == 0 && P->nrhs <= 4;
 }
 
-size_t layered_bytes(const psfd_plan_s* P) { return (size_t)P->ncols * 5 * P->nz * P->nz * sizeof(cf); }
+// ky and -ky share their blocks when there is no Bloch shift along y (the blocks depend on kappa)
+bool layered_pairs(const psfd_plan_s* P) { return P->ky_inc == 0.0 && P->ny % 2 == 0; }
+
+// number of stored block columns
+long layered_columns(const psfd_plan_s* P) {
+  return layered_pairs(P) ? (long)(P->ny / 2 + 1) * P->nx : P->ncols;
+}
+
+size_t layered_bytes(const psfd_plan_s* P) { return (size_t)layered_columns(P) * 5 * P->nz * P->nz * sizeof(cf); }
 
 int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
   if (!P->lay_built) { psfd_set_error("layered preconditioner: call psfd_layered_build first"); return PSFD_ERR_STATE; }

@@ -63,3 +63,21 @@ def test_spectral_upsample_matches_oracle(shapes):
     out = psfd.spectral_upsample(src.cuda(), nz, ny, nx).cpu()
     ref = F.spectral_upsample(src.to(torch.complex128), nz, ny, nx)
     assert rel_l2(out, ref) < 1e-5
+
+
+@pytest.mark.parametrize("dims", [(2, 32, 32, 16), (1, 128, 128, 64), (3, 16, 64, 48)])
+def test_tensor_core_mixing_equals_simt_mixing(dims, monkeypatch):
+    """The forward mode mixing on tcgen05 (bf16 operands, FP32 accumulation in tensor memory)
+    against the SIMT kernel with the same bf16 operands: only the summation order differs."""
+    from paper_2607_25330_b300 import psfd
+    B, nx, ny, nz = dims
+    S = I.FNOShape()
+    w = I.fno_weights(S, 23, spectral_scale=4.0)
+    ws = psfd.fno_struct(device_weights(w), S)
+    a = torch.from_numpy(np.random.default_rng(6).random((B, nz, ny, nx)).astype(np.float32)).cuda()
+    monkeypatch.setenv("PSFD_MIX_SIMT", "0")
+    E_tc = psfd.fno_forward(ws, a)
+    monkeypatch.setenv("PSFD_MIX_SIMT", "1")
+    E_simt = psfd.fno_forward(ws, a)
+    torch.cuda.synchronize()
+    assert rel_l2(E_tc.cpu(), E_simt.cpu()) < 1e-5
