@@ -6,7 +6,7 @@ with capping layer, TE + TM at 6 deg = 2 right-hand sides sharing one operator):
   mask -> smoothed fill (psfd_mask_fill) -> FP64 multilayer reflection and source
   b (psfd_background) -> layered-background preconditioner blocks (psfd_layered_build)
   -> factorised-FNO warm start for each polarisation (fno_forward, seed-initialised
-  weights) -> right-preconditioned GMRES(30) inside FP64 iterative refinement to
+  weights) -> right-preconditioned BiCGSTAB inside FP64 iterative refinement to
   ||b - A E|| / ||b|| <= 1e-6 (psfd_solve_ex with x0) -> FP64 true residual.
 `value` counts solved right-hand sides per second over the timed steps.  The same
 step without the warm start (null initialisation) is reported as `cold`; the
@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--method", default="gmres", choices=["bicgstab", "gmres"])
+    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "gmres"],
+                    help="inner Krylov method (BiCGSTAB is the paper's; GMRES(m) alongside)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--maxit", type=int, default=MAXIT,
                     help="iteration cap per solve (lower it only for profiling runs)")
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--train-step", action="store_true",
                     help="time the physics-informed FNO training step (16 masks 128x128x48) and exit")
     ap.add_argument("--train-batch", type=int, default=16)
+    ap.add_argument("--lay-half", type=int, default=1,
+                    help="store the layered blocks in half precision with per-block scales (1) or complex64 (0)")
     ap.add_argument("--lay-shift", type=float, default=0.25,
                     help="rebuild the layered blocks when a plane's mean fill moved by more than this")
     return ap.parse_args()
@@ -129,7 +132,7 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from
 # one ncu capture of the current kernel version on this workload (profiles/k_lay_apply_*.md):
 # reported as roofline.traffic when the bench runs the same kernel on the same workload
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("precond", "manhattan_128x128x64", 2, True): 735.125504e6 + 45.432064e6}
 
 
 def fp32_peak_tflops():
@@ -186,7 +189,11 @@ def run_ours(args, rank, world):
         wd = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in w.items()}
         models.append(psfd.fno_struct(wd, shape))
     plan = psfd.Plan(prob, nrhs=nrhs)
-    ws = torch.empty(plan.workspace_size_ex(method, args.restart, True), dtype=torch.uint8, device="cuda")
+    if args.lay_half:
+        plan.layered_storage(True)
+    # sized for both methods: the paper-configuration arms run GMRES(30)
+    ws_bytes = max(plan.workspace_size_ex(m, args.restart, True) for m in (psfd.PSFD_BICGSTAB, psfd.PSFD_GMRES))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     # the FP64 field is returned (complex128): its own residual is the one checked against 1e-6
     # (its complex64 rounding alone would carry about 1.3e-6 on this grid)
     E = torch.empty(plan.shape, dtype=torch.complex128, device="cuda")
@@ -196,7 +203,7 @@ def run_ours(args, rank, world):
 
     rebuilds = [0]
 
-    def step(i, warm=True, mask=None, pc=pc_main, tol=TOL, maxit=args.maxit, rebuild="refresh"):
+    def step(i, warm=True, mask=None, pc=pc_main, tol=TOL, maxit=args.maxit, rebuild="refresh", meth=None):
         """The whole hot path for mask i: fill, background, preconditioner set-up, warm start, solve.
 
         The layered blocks depend on the mask only through each plane's mean fill; they are rebuilt
@@ -213,7 +220,7 @@ def run_ours(args, rank, world):
             a = fill.unsqueeze(0).contiguous()
             for r, m in enumerate(models):
                 psfd.fno_forward(m, a, out=x0[r:r + 1])
-        return plan.solve_ex(b, x0=x0 if warm else None, tol=tol, maxit=maxit, method=method,
+        return plan.solve_ex(b, x0=x0 if warm else None, tol=tol, maxit=maxit, method=method if meth is None else meth,
                              restart=args.restart, precond=pc, refine=True, inner_tol=args.inner_tol, out=E,
                              workspace=ws, out_c128=True)
 
@@ -283,16 +290,19 @@ def run_ours(args, rank, world):
     # configuration (no preconditioner, cold), at 1e-6 and at the practical 5e-2
     paper = {}
     if not args.skip_paper_arms:
-        pd = psfd.PC_DAMPING
-        paper["damping_warm_1e-6"] = arm(timed(warm=True, pc=pd, maxit=args.maxit_paper))
-        paper["damping_cold_1e-6"] = arm(timed(warm=False, pc=pd, maxit=args.maxit_paper))
-        paper["damping_warm_5e-2"] = arm(timed(warm=True, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
-        paper["damping_cold_5e-2"] = arm(timed(warm=False, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
-        paper["null_cold_5e-2"] = arm(timed(warm=False, pc=psfd.PC_NONE, tol=PRACTICAL_TOL, maxit=args.maxit_paper))
+        # GMRES(30): complex64 BiCGSTAB with the damping M alone diverges on this workload at 6 deg
+        pd, gm = psfd.PC_DAMPING, psfd.PSFD_GMRES
+        paper["damping_warm_1e-6"] = arm(timed(warm=True, pc=pd, maxit=args.maxit_paper, meth=gm))
+        paper["damping_cold_1e-6"] = arm(timed(warm=False, pc=pd, maxit=args.maxit_paper, meth=gm))
+        paper["damping_warm_5e-2"] = arm(timed(warm=True, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper, meth=gm))
+        paper["damping_cold_5e-2"] = arm(timed(warm=False, pc=pd, tol=PRACTICAL_TOL, maxit=args.maxit_paper, meth=gm))
+        paper["null_cold_5e-2"] = arm(timed(warm=False, pc=psfd.PC_NONE, tol=PRACTICAL_TOL, maxit=args.maxit_paper,
+                                            meth=gm))
         for k in paper:
             paper[k]["maxit"] = args.maxit_paper
-        paper["note"] = ("the paper's spectral damping M and null configuration on the same masks and solver; "
-                         "only right-hand sides that reached the tolerance within maxit count")
+        paper["note"] = ("the paper's spectral damping M and null configuration on the same masks with GMRES(30) "
+                         "in the same FP64 refinement (complex64 BiCGSTAB with M alone diverges here); only "
+                         "right-hand sides that reached the tolerance within maxit count")
 
     # the paper's practical criterion (Sec. 4): iterations until the threshold-contour widths of
     # |E_y|^2 on the plane above the absorber are within 1 nm (wafer units, /4) of the converged
@@ -317,7 +327,8 @@ def run_ours(args, rank, world):
             for warm in (True, False):
                 hit, trace = None, []
                 for k in grids[name]:
-                    E_k = plan.solve(b0, x0=x0 if warm else None, tol=1e-12, maxit=k, method=method,
+                    E_k = plan.solve(b0, x0=x0 if warm else None, tol=1e-12, maxit=k,
+                                     method=method if pc == psfd.PC_LAYERED else psfd.PSFD_GMRES,
                                      restart=args.restart, precond=pc)["E"]
                     mtr = plan.width_metric(E_k, ref, ztop, rhs=0, comp=1, I_th=0.15, n_lines=100, demag=4.0)
                     trace.append([k, round(mtr["mean"], 4), mtr["matched"], mtr["unresolved"]])
@@ -409,7 +420,7 @@ def run_ours(args, rank, world):
                 "ms_per_launch": d["ms_per_call"], "algorithmic_flops_per_launch": lay_flops,
                 "share_of_step": d["share"]}
     else:
-        traffic = NCU_TRAFFIC.get((dom, args.workload, nrhs))
+        traffic = NCU_TRAFFIC.get((dom, args.workload, nrhs, bool(args.lay_half)))
         roof = {"kernel": kernels[dom], "stage": dom, "bound": "hbm", "achieved": d["GBps"], "peak": peak,
                 "unit": "GB/s", "frac": d["frac"], "traffic": traffic, "peak_kind": peak_kind,
                 "traffic_source": "ncu capture in profiles/ (dram read + write per launch)" if traffic else None,
@@ -440,7 +451,8 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
                    "rhs_per_step": nrhs, "pols": ["TE", "TM"][:nrhs], "theta_deg": prob.theta_deg, "tol": TOL,
                    "preconditioner": pc_name,
-                   "solver": f"{args.method}({args.restart}) in complex64 inside FP64 iterative refinement "
+                   "solver": (f"{args.method}({args.restart})" if args.method == "gmres" else args.method) +
+                             " in complex64 inside FP64 iterative refinement "
                              f"(FP64 residual and field, inner tol {args.inner_tol:g}), right preconditioning, "
                              "affine warm start",
                    "step": "mask -> fill -> FP64 TMM + source -> preconditioner set-up -> FNO warm start -> "
@@ -460,6 +472,8 @@ def run_ours(args, rank, world):
         "cold": {"value": cold_value, "unit": "solves/s", "ms_per_step": ms_cold_max / K},
         "layered_blocks": {"reuse_rule": f"rebuilt when a plane's mean fill moved by > {args.lay_shift} "
                                          "since the last build (psfd_layered_refresh)",
+                           "storage": "half precision, power-of-two scale per block" if args.lay_half else "complex64",
+                           "bytes": plan.layered_bytes(),
                            "rebuilds_in_timed_warm_steps": rebuilds_warm,
                            "warm_with_rebuild_every_mask": layered_always},
         "paper_configurations": paper,
@@ -491,6 +505,8 @@ def run_profile_apply(args):
     plan.background(prob.stack(), fill, prob.pols[:nrhs] if nrhs <= len(prob.pols) else [0] * nrhs)
     flags = psfd.PSFD_HYBRID | psfd.PSFD_PRECOND
     if args.precond == "layered" and plan.layered_bytes() > 0:
+        if args.lay_half:
+            plan.layered_storage(True)
         plan.layered_build()
         flags = psfd.PSFD_HYBRID | psfd.PSFD_LAYERED
     x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")

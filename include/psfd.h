@@ -183,7 +183,9 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * Bloch modes; per mode it splits into a TE block (nz x nz, E along s) and a TM
  * block (2nz x 2nz, (E_t, E_z)), which psfd_layered_build assembles and inverts
  * (FP32, partial pivoting) on the device and stores in the plan:
- * psfd_layered_bytes() bytes = nx*ny*5*nz^2 complex64 (2.7 GB at 128x128x64).
+ * psfd_layered_bytes() bytes = columns * 5 nz^2 entries, where columns = nx*ny, or
+ * nx*(ny/2+1) without a Bloch shift along y (the blocks depend on |k_par| only,
+ * so ky and -ky share them): 1.36 GB at 128x128x64 at 6 deg in complex64.
  * psfd_layered_build makes the blocks exact for the fill registered by the last
  * psfd_background.  They stay usable as a preconditioner after later
  * psfd_background calls on the same plan (any fill): P only changes how fast the
@@ -195,6 +197,15 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * psfd_background; PSFD_ERR_BREAKDOWN if a block is singular.  Both synchronise
  * the plan's stream. */
 PSFD_API int psfd_layered_build(psfd_plan plan);
+/* Storage of the blocks, taking effect at the next build (the current blocks are
+ * released): PSFD_LAY_C64 (default) complex64; PSFD_LAY_HALF complex half
+ * precision, each block divided by the power of two at or above its largest
+ * |re|, |im| (the scale is kept per block and applied in FP32 after the
+ * product).  Half storage halves the bytes of every P apply; P changes only the
+ * convergence, never the solution, and the iteration counts measured with it
+ * match complex64 storage.  PSFD_ERR_ARG for an unknown storage. */
+enum { PSFD_LAY_C64 = 0, PSFD_LAY_HALF = 1 };
+PSFD_API int psfd_layered_storage(psfd_plan plan, int storage);
 PSFD_API int psfd_layered_refresh(psfd_plan plan, double max_shift, int* rebuilt);
 PSFD_API size_t psfd_layered_bytes(psfd_plan plan);
 

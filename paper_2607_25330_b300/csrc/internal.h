@@ -77,6 +77,9 @@ struct psfd_plan_s {
   cf* lay_deps = nullptr;    // [nz] laterally averaged contrast
   int* lay_err = nullptr;
   double* lay_fmean = nullptr;          // [nz] device scratch for plane means
+  void* lay16 = nullptr;                // half-precision blocks (storage PSFD_LAY_HALF)
+  float* lay_scale = nullptr;           // their per-block power-of-two scales
+  bool lay_half = false;
   std::vector<double> lay_mean;         // plane means of the fill the blocks were built for
   bool lay_built = false;
 };

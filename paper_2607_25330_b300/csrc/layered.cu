@@ -25,6 +25,8 @@
 #include <complex>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace {
@@ -45,6 +47,9 @@ struct LayArgs {
   int nx, ny, nz, zml;
   int pair;             // 1: blocks stored for rows 0 .. ny/2 only (ky and -ky share them)
   cf* mats;             // [ncols][5 nz^2]: TE inverse (nz^2) then TM inverse (4 nz^2), column-major
+  __half2* mats16;      // the same in half precision (storage 1), entries divided by the block's scale
+  float* scales;        // [ncols][2] power-of-two scale of the TE and TM block (storage 1)
+  int half;             // 1: half-precision storage
   int* err;             // set to 1 if a pivot vanished
 };
 
@@ -220,13 +225,42 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
   for (int k = tid; k < N; k += LAY_THREADS) rowvar[pivrow[k]] = k;
   __syncthreads();
   // column-major output: element (r, c) of the inverse at c * N + r
-  cf* out = a.mats + col * (5L * a.nz * a.nz) + block_off;
+  if (!a.half) {
+    cf* out = a.mats + col * (5L * a.nz * a.nz) + block_off;
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+      for (int v = 0; v < TT; ++v) {
+        const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
+        out[(long)c * N + r] = T[u][v];
+      }
+    return;
+  }
+  // half precision: divide by the power of two at or above the block's largest |re|, |im| (the
+  // entries then lie in [-1, 1], where half keeps 11 significant bits)
+  float mx = 0.f;
+#pragma unroll
+  for (int u = 0; u < TT; ++u)
+#pragma unroll
+    for (int v = 0; v < TT; ++v) mx = fmaxf(mx, fmaxf(fabsf(T[u][v].x), fabsf(T[u][v].y)));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  __shared__ float wmax[LAY_THREADS / 32];
+  if (lane == 0) wmax[tid >> 5] = mx;
+  __syncthreads();
+  mx = 0.f;
+  for (int w = 0; w < LAY_THREADS / 32; ++w) mx = fmaxf(mx, wmax[w]);
+  int e = 0;
+  if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &e);   // mx = f 2^e with f in [0.5, 1)
+  const float scale = ldexpf(1.f, e), inv = ldexpf(1.f, -e);
+  if (tid == 0) a.scales[col * 2 + (TM ? 1 : 0)] = scale;
+  __half2* out = a.mats16 + col * (5L * a.nz * a.nz) + block_off;
 #pragma unroll
   for (int u = 0; u < TT; ++u)
 #pragma unroll
     for (int v = 0; v < TT; ++v) {
       const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
-      out[(long)c * N + r] = T[u][v];
+      out[(long)c * N + r] = __floats2half2_rn(T[u][v].x * inv, T[u][v].y * inv);
     }
 }
 
@@ -254,14 +288,18 @@ __global__ void k_plane_mean(const float* __restrict__ fill, long plane, double*
 // row ny - h, reading each block once for both rows and all right-hand sides.  Each thread
 // produces two adjacent output rows of one block (16-byte loads of the column-major blocks); a
 // CTA has LAY_GROUP * 3 NZ / 2 threads.
-template <int NZ>
-constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / 2; }
+// rows of a block per thread: 2 for complex64 blocks (16-byte loads of two entries), 4 for half
+// blocks (16-byte loads of four entries)
+template <bool HALF>
+constexpr int apply_rpt() { return HALF ? 4 : 2; }
+template <int NZ, bool HALF>
+constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / apply_rpt<HALF>(); }
 
-template <int NZ, int NR>
-__global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 3 : 2)) k_lay_apply(LayArgs a, const cf* __restrict__ x,
-                                                                     cf* __restrict__ y, long ncols) {
+template <int NZ, int NR, bool HALF>
+__global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 2 ? 3 : 2)))
+    k_lay_apply(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
   constexpr int nrhs = NR;
-  constexpr int G = LAY_GROUP, NT = apply_threads<NZ>();
+  constexpr int G = LAY_GROUP, NT = apply_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
   extern __shared__ cf xs[];       // [2G][3][NZ][nrhs]: (s, t, z) components after rotation
   __shared__ float rot[2 * G][4];  // sx, sy, tx, ty per virtual column
   const long hc0 = (long)blockIdx.x * G;               // first block column: row h, kx index ix0
@@ -296,58 +334,82 @@ __global__ void __launch_bounds__(apply_threads<NZ>(), (NR <= 2 ? 3 : 2)) k_lay_
   }
   __syncthreads();
   constexpr long MS = 5L * NZ * NZ;
-  // thread -> (block column g, row pair rr, rr + 1) of the 3 NZ stacked rows (TE rows, then TM rows)
-  const int g = tid / (3 * NZ / 2), rr = 2 * (tid - g * (3 * NZ / 2));
+  // thread -> (block column g, rows rr .. rr + RPT - 1) of the 3 NZ stacked rows (TE, then TM)
+  constexpr int TPC = 3 * NZ / RPT;                         // threads per block column
+  const int g = tid / TPC, rr = RPT * (tid - g * TPC);
   const bool te = rr < NZ;
   const int nb = te ? NZ : 2 * NZ;                         // block size
-  const int i = te ? rr : rr - NZ;                         // row inside the block
+  const int i = te ? rr : rr - NZ;                         // first row inside the block
   const cf* Mb = a.mats + (hc0 + g) * MS + (te ? 0 : (long)NZ * NZ);
+  const __half2* Mh = a.mats16 + (hc0 + g) * MS + (te ? 0 : (long)NZ * NZ);
   const int comp0 = te ? 0 : 1;                            // TE: s; TM: t then z (contiguous)
   const cf* xa = xs + (g * 3 + comp0) * NZ * nrhs;
   const cf* xb = xs + ((g + G) * 3 + comp0) * NZ * nrhs;
-  cf a0[NR], a1[NR], b0[NR], b1[NR];
+  cf A[RPT][NR], Bv[RPT][NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) { a0[r] = czero(); a1[r] = czero(); b0[r] = czero(); b1[r] = czero(); }
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) { A[q][r] = czero(); Bv[q][r] = czero(); }
+  auto load = [&](int j, cf (&m)[RPT]) {
+    if constexpr (HALF) {
+      const uint4 hv = __ldg(reinterpret_cast<const uint4*>(Mh + (long)j * nb + i));
+      m[0] = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+      m[1] = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+      m[2] = __half22float2(*reinterpret_cast<const __half2*>(&hv.z));
+      m[3] = __half22float2(*reinterpret_cast<const __half2*>(&hv.w));
+    } else {
+      const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
+      m[0] = make_float2(mv.x, mv.y);
+      m[1] = make_float2(mv.z, mv.w);
+    }
+  };
   if (two) {
 #pragma unroll 8
     for (int j = 0; j < nb; ++j) {
-      const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
-      const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
+      cf m[RPT];
+      load(j, m);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const cf xv = xa[j * NR + r], xw = xb[j * NR + r];
-        a0[r] = cfma(m0, xv, a0[r]);
-        a1[r] = cfma(m1, xv, a1[r]);
-        b0[r] = cfma(m0, xw, b0[r]);
-        b1[r] = cfma(m1, xw, b1[r]);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          A[q][r] = cfma(m[q], xv, A[q][r]);
+          Bv[q][r] = cfma(m[q], xw, Bv[q][r]);
+        }
       }
     }
   } else {
 #pragma unroll 8
     for (int j = 0; j < nb; ++j) {
-      const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * nb + i));
-      const cf m0 = make_float2(mv.x, mv.y), m1 = make_float2(mv.z, mv.w);
+      cf m[RPT];
+      load(j, m);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const cf xv = xa[j * NR + r];
-        a0[r] = cfma(m0, xv, a0[r]);
-        a1[r] = cfma(m1, xv, a1[r]);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) A[q][r] = cfma(m[q], xv, A[q][r]);
       }
     }
   }
+  if constexpr (HALF) {
+    const float s = a.scales[(hc0 + g) * 2 + (te ? 0 : 1)];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) { A[q][r] = cscale(A[q][r], s); Bv[q][r] = cscale(Bv[q][r], s); }
+  }
   __syncthreads();   // every thread has read its inputs: the outputs overwrite xs in place
   {
+    // rows i .. i + RPT - 1 never straddle the t / z boundary (NZ is a multiple of RPT)
     const int comp = te ? 0 : (i < NZ ? 1 : 2);
-    const int z = te ? rr : (i < NZ ? i : i - NZ);          // rows z, z + 1 of component comp
+    const int z = te ? rr : (i < NZ ? i : i - NZ);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      xs[((g * 3 + comp) * NZ + z) * nrhs + r] = a0[r];
-      xs[((g * 3 + comp) * NZ + z + 1) * nrhs + r] = a1[r];
-      if (two) {
-        xs[(((g + G) * 3 + comp) * NZ + z) * nrhs + r] = b0[r];
-        xs[(((g + G) * 3 + comp) * NZ + z + 1) * nrhs + r] = b1[r];
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        xs[((g * 3 + comp) * NZ + z + q) * nrhs + r] = A[q][r];
+        if (two) xs[(((g + G) * 3 + comp) * NZ + z + q) * nrhs + r] = Bv[q][r];
       }
-    }
   }
   __syncthreads();
   for (int it = tid; it < nrhs * NZ * nv; it += NT) {
@@ -369,6 +431,7 @@ LayArgs lay_args(psfd_plan_s* P) {
   a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.zml = P->p.z_ml;
   a.pair = layered_pairs(P) ? 1 : 0;
   a.mats = P->lay; a.err = P->lay_err;
+  a.mats16 = (__half2*)P->lay16; a.scales = P->lay_scale; a.half = P->lay_half ? 1 : 0;
   return a;
 }
 
@@ -386,8 +449,11 @@ int build_nz(psfd_plan_s* P) {
 template <int NZ, int NR>
 int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
   const size_t smem = (size_t)2 * LAY_GROUP * 3 * NZ * NR * sizeof(cf);
-  k_lay_apply<NZ, NR><<<(unsigned)(layered_columns(P) / LAY_GROUP), apply_threads<NZ>(), smem, P->stream>>>(
-      a, x, y, P->ncols);
+  const unsigned grid = (unsigned)(layered_columns(P) / LAY_GROUP);
+  if (a.half)
+    k_lay_apply<NZ, NR, true><<<grid, apply_threads<NZ, true>(), smem, P->stream>>>(a, x, y, P->ncols);
+  else
+    k_lay_apply<NZ, NR, false><<<grid, apply_threads<NZ, false>(), smem, P->stream>>>(a, x, y, P->ncols);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -417,7 +483,10 @@ long layered_columns(const psfd_plan_s* P) {
   return layered_pairs(P) ? (long)(P->ny / 2 + 1) * P->nx : P->ncols;
 }
 
-size_t layered_bytes(const psfd_plan_s* P) { return (size_t)layered_columns(P) * 5 * P->nz * P->nz * sizeof(cf); }
+size_t layered_bytes(const psfd_plan_s* P) {
+  const size_t per = (size_t)5 * P->nz * P->nz * (P->lay_half ? sizeof(__half2) : sizeof(cf));
+  return (size_t)layered_columns(P) * per;
+}
 
 int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
   if (!P->lay_built) { psfd_set_error("layered preconditioner: call psfd_layered_build first"); return PSFD_ERR_STATE; }
@@ -432,11 +501,11 @@ int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
 }
 
 void layered_free(psfd_plan_s* P) {
-  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err, P->lay_fmean};
+  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err, P->lay_fmean, P->lay16, P->lay_scale};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   P->lay = nullptr; P->lay_D = nullptr; P->lay_D2 = nullptr; P->lay_deps = nullptr; P->lay_err = nullptr;
-  P->lay_fmean = nullptr;
+  P->lay_fmean = nullptr; P->lay16 = nullptr; P->lay_scale = nullptr;
   P->lay_built = false;
   P->lay_mean.clear();
 }
@@ -450,6 +519,20 @@ static int plane_means(psfd_plan_s* P, std::vector<double>& mean) {
   mean.resize(P->nz);
   PSFD_CUDA_TRY(cudaMemcpyAsync(mean.data(), P->lay_fmean, P->nz * sizeof(double), cudaMemcpyDeviceToHost, s));
   PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  return PSFD_OK;
+}
+
+extern "C" int psfd_layered_storage(psfd_plan P, int storage) {
+  if (!P || (storage != PSFD_LAY_C64 && storage != PSFD_LAY_HALF)) {
+    psfd_set_error("psfd_layered_storage: null plan or unknown storage");
+    return PSFD_ERR_ARG;
+  }
+  const bool half = storage == PSFD_LAY_HALF;
+  if (half != P->lay_half) {
+    PSFD_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    layered_free(P);   // blocks are rebuilt in the new storage by the next psfd_layered_build
+    P->lay_half = half;
+  }
   return PSFD_OK;
 }
 
@@ -468,8 +551,15 @@ extern "C" int psfd_layered_build(psfd_plan P) {
   const int nz = P->nz;
   cudaStream_t s = P->stream;
   StageScope scope(s, ST_LAYBUILD);
-  if (!P->lay) {
-    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay, layered_bytes(P)));
+  if (P->lay_half ? !P->lay16 : !P->lay) {
+    if (P->lay_half) {
+      PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay16, layered_bytes(P)));
+      PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_scale, (size_t)layered_columns(P) * 2 * sizeof(float)));
+    } else {
+      PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay, layered_bytes(P)));
+    }
+  }
+  if (!P->lay_D) {
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D2, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_deps, (size_t)nz * sizeof(cf)));

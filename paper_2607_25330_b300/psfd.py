@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpsfd.so")
 PSFD_OK, PSFD_ERR_ARG, PSFD_ERR_CUDA, PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN, PSFD_ERR_TIMEOUT, PSFD_ERR_STATE = range(7)
 PSFD_TE, PSFD_TM = 0, 1
 PSFD_PRECOND, PSFD_HYBRID, PSFD_ADJOINT, PSFD_LAYERED = 1, 2, 4, 8
+LAY_C64, LAY_HALF = 0, 1
 # use_precond values of the solves: identity, spectral damping M, layered-background P
 PC_NONE, PC_DAMPING, PC_LAYERED = 0, 1, 2
 PSFD_BICGSTAB, PSFD_GMRES = 0, 1
@@ -100,6 +101,7 @@ def lib() -> C.CDLL:
         "psfd_solve_ex_workspace_size": (sz, [vp, C.POINTER(SolveOpts)]),
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
         "psfd_layered_build": (i, [vp]),
+        "psfd_layered_storage": (i, [vp, i]),
         "psfd_width_metric": (i, [vp, vp, vp, i, i, i, C.c_float, i, d, C.POINTER(C.c_double)]),
         "psfd_set_plane_contrast": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "psfd_set_layer_stack_contrast": (i, [vp, C.POINTER(Stack), d, C.POINTER(C.c_float)]),
@@ -135,6 +137,7 @@ def declared_symbols() -> List[str]:
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
             "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
+            "psfd_layered_storage",
             "psfd_set_plane_contrast", "psfd_set_layer_stack_contrast",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
@@ -311,6 +314,10 @@ class Plan:
                                                    zm.ctypes.data_as(C.POINTER(C.c_float))),
                "psfd_set_layer_stack_contrast")
         return zm
+
+    def layered_storage(self, half: bool) -> None:
+        """Store the layered blocks in half precision (True) or complex64 (False) from the next build."""
+        _check(lib().psfd_layered_storage(self.h, LAY_HALF if half else LAY_C64), "psfd_layered_storage")
 
     def layered_bytes(self) -> int:
         return int(lib().psfd_layered_bytes(self.h))

@@ -140,3 +140,30 @@ def test_layered_full_size_128x128x64_reaches_1e6():
         # the returned FP64 field meets the tolerance in the oracle's own residual too
         bo = O.source_b(g, fill_o, prob.pols[r])
         assert O.rel_residual(g, res["E"][r].cpu(), fill_o, bo) <= 1.01e-6
+
+
+@pytest.mark.parametrize("grid", [GRIDS[1], GRIDS[3]])
+def test_half_storage_of_the_blocks(grid):
+    """Blocks stored in half precision with a power-of-two scale per block: P x within the half
+    rounding of its entries (2^-11 relative, amplified by cancellation in the sums: 2e-3) of the
+    oracle's, half the bytes, and the same solve result."""
+    from paper_2607_25330_b300 import psfd
+    from oracle import krylov as K
+    prob, g, fill_o, plan, b = setup(*grid)
+    full = plan.layered_bytes()
+    plan.layered_storage(True)
+    plan.layered_build()
+    assert plan.layered_bytes() * 2 == full
+    x = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64)
+    y = plan.precond(x.cuda(), flags=psfd.PSFD_LAYERED).cpu()
+    mats = O.layered_blocks(g, fill_o)
+    for r in range(plan.nrhs):
+        ref = O.apply_P_layered(g, fill_o, x[r].to(torch.complex128), mats)
+        assert rel_l2(y[r], ref) < 2e-3
+    res = plan.solve_ex(b, tol=1e-6, maxit=400, precond=psfd.PC_LAYERED, out_c128=True)
+    assert res["code"] == 0
+    bo = O.source_b(g, fill_o, prob.pols[0])
+    assert O.rel_residual(g, res["E"][0].cpu(), fill_o, bo) <= 1.01e-6
+    plan.layered_storage(False)
+    with pytest.raises(psfd.PsfdError):
+        plan.precond(x.cuda(), flags=psfd.PSFD_LAYERED)    # released until rebuilt
