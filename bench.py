@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--maxit-paper", type=int, default=2000,
                     help="iteration cap of the paper-configuration arms at 1e-6 and of the null arm")
     ap.add_argument("--skip-paper-arms", action="store_true")
-    ap.add_argument("--inner-tol", type=float, default=1e-2,
+    ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative tolerance of each complex64 inner solve of the FP64 refinement")
     ap.add_argument("--train-step", action="store_true",
                     help="time the physics-informed FNO training step (16 masks 128x128x48) and exit")
