@@ -233,7 +233,9 @@ PSFD_API size_t psfd_solve_workspace_size(psfd_plan plan, int method, int restar
 /* Solve with options; refine = 1 selects mixed precision: the field is kept in
  * FP64, the outer residual b - A E is computed with an FP64 operator apply, and
  * each outer step solves A M d = r in complex64 (method, restart, preconditioner
- * as above) to the relative tolerance inner_tol, then E += M d.  Convergence is
+ * as above) to the relative tolerance inner_tol (or only to 0.5 tol ||b|| / ||r||
+ * when that is looser: the correction is not solved more accurately than the
+ * final tolerance needs), then E += M d.  Convergence is
  * the FP64 relative residual <= tol (Eq. relative_residual); maxit bounds the
  * total number of inner iterations, max_outer (0 = 100) the outer steps.  The
  * returned field is the complex64 rounding of the FP64 field, or with out_c128

@@ -1120,9 +1120,14 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     PSFD_CUDA_TRY(cudaMemcpyAsync(dskip, conv.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
     a64.a64 = r64; a64.o32 = w.r; a64.skip = dskip;
     if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
-    // inner complex64 solve of A M y = r to inner_tol (relative to ||r||)
+    // inner complex64 solve of A M y = r to inner_tol (relative to ||r||), or only as far as the
+    // final tolerance needs: 0.5 tol ||b|| / ||r|| when that is looser (strictest over the rhs)
     const int inner_max = std::max(1, o->maxit - total_max);
-    k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, o->inner_tol * o->inner_tol, inner_max);
+    double itol = 0.5;
+    for (int r = 0; r < nr; ++r)
+      if (!conv[r] && rr[r] > 0) itol = std::min(itol, 0.5 * o->tol * sqrt(bnorm2[r] / rr[r]));
+    itol = std::max(itol, o->inner_tol);
+    k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, itol * itol, inner_max);
     PSFD_CHECK_LAUNCH();
     va.use_done = false;
     va.v0 = w.r;
@@ -1130,7 +1135,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     k_copy_bnorm<<<1, tpb, 0, st>>>(w.sc, nr);
     PSFD_CHECK_LAUNCH();
     if (o->method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, inner_max, aflags, nb);
-    else rc = gmres_loop(P, w, va, o->inner_tol, inner_max, o->restart, aflags, nb);
+    else rc = gmres_loop(P, w, va, itol, inner_max, o->restart, aflags, nb);
     if (rc) return fail(rc);
     PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
     PSFD_CUDA_TRY(cudaStreamSynchronize(st));
