@@ -391,6 +391,15 @@ PSFD_API int psfd_timing_read(double* ms, long long* calls, int nstages);
 PSFD_API int psfd_timing_read_bytes(double* ms, long long* calls, double* bytes, int nstages);
 
 /* ---------------------------------------------------------------- misc */
+/* Every wait of a kernel on its own bulk copies or tensor-core products (the
+ * operator's single-pass plane kernel, the FNO mode mixing) gives up after a
+ * bounded time instead of hanging, and records that in a device flag.
+ * psfd_device_status reads and clears the flags: PSFD_ERR_TIMEOUT (with a
+ * message naming the kernel) if a wait gave up since the last call, else
+ * PSFD_OK.  Synchronises the plan's stream.  psfd_solve and psfd_solve_ex call
+ * it before they return; callers of psfd_apply, psfd_precond and fno_forward
+ * call it themselves. */
+PSFD_API int psfd_device_status(psfd_plan plan);
 PSFD_API const char* psfd_last_error(void);
 PSFD_API const char* psfd_version(void);
 

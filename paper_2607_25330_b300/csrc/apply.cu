@@ -763,7 +763,10 @@ static int run_plane(psfd_plan_s* P, const PlaneArgs& a, long nplanes) {
 static int plane_contrast(psfd_plan_s* P, cf* y, const int* done, bool adjoint, bool to_y, bool* handled) {
   *handled = false;
   if (P->nx != P->ny || P->nx > 128 || !P->use_plane) return PSFD_OK;
-  if (!P->err) PSFD_CUDA_TRY(cudaMalloc((void**)&P->err, sizeof(int)));
+  if (!P->err) {
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->err, sizeof(int)));
+    PSFD_CUDA_TRY(cudaMemset(P->err, 0, sizeof(int)));
+  }
   const int nab = P->za1 - P->za0;
   PlaneArgs a;
   a.G = P->G; a.y = y; a.fill = P->fill; a.twx = P->tw_x; a.twy = P->tw_y; a.done = done; a.err = P->err;

@@ -202,5 +202,6 @@ int fno_mix_tc_error(int* host_flag) {
   *host_flag = 0;
   if (!g_tc_err) return PSFD_OK;
   PSFD_CUDA_TRY(cudaMemcpy(host_flag, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*host_flag) PSFD_CUDA_TRY(cudaMemset(g_tc_err, 0, sizeof(int)));
   return PSFD_OK;
 }

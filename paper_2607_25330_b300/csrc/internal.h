@@ -112,7 +112,8 @@ void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv);   // 1 / s(z) in F
 bool fno_mix_tc_enabled(int C);
 int fno_mix_tc(const cf* V, cf* U, const cf* K, long NB, int modes, int mx, int MX, int offy, int offx,
                cudaStream_t s);
-int fno_mix_tc_error(int* host_flag);
+int fno_mix_tc_error(int* host_flag);   // reads and clears the flag
+int plan_wait_status(psfd_plan_s* P);   // PSFD_ERR_TIMEOUT if a bounded device wait gave up
 
 // layered.cu
 int layered_supported(const psfd_plan_s* P);

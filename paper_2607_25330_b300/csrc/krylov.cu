@@ -919,6 +919,7 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
     if (info[r].status != PSFD_OK && worst == PSFD_OK) worst = info[r].status;
   }
   if (own) PSFD_CUDA_TRY(cudaFreeAsync(base, st));
+  if ((rc = plan_wait_status(P))) return rc;
   return worst;
 }
 
@@ -1187,5 +1188,6 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     if (status[r] != PSFD_OK && worst == PSFD_OK) worst = status[r];
   }
   if (own) PSFD_CUDA_TRY(cudaFreeAsync(base, st));
+  if ((rc = plan_wait_status(P))) return rc;
   return worst;
 }

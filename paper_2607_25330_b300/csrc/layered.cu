@@ -50,7 +50,7 @@ struct LayArgs {
   __half2* mats16;      // the same in half precision (storage 1), entries divided by the block's scale
   float* scales;        // [ncols][2] power-of-two scale of the TE and TM block (storage 1)
   int half;             // 1: half-precision storage
-  int* err;             // set to 1 if a pivot vanished
+  int* err;             // [0] set to 1 if a pivot vanished, [1] if an apply gave up waiting for its blocks
 };
 
 __device__ __forceinline__ cf cdiv1(cf a) {  // 1 / a
@@ -563,7 +563,8 @@ extern "C" int psfd_layered_build(psfd_plan P) {
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D2, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_deps, (size_t)nz * sizeof(cf)));
-    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_err, sizeof(int)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_err, 2 * sizeof(int)));   // [0] singular pivot, [1] apply wait
+    PSFD_CUDA_TRY(cudaMemset(P->lay_err, 0, 2 * sizeof(int)));
     // D = s^-1 C, C[z][z'] = (1/nz) sum_m i k_m exp(2 pi i m (z - z') / nz) (FFT-order k_m, Nyquist
     // negative), and D^2, in FP64 on the host
     std::vector<zd> sinv;

@@ -113,6 +113,31 @@ void psfd_set_error(const char* fmt, ...) {
 extern "C" const char* psfd_last_error(void) { return g_err; }
 extern "C" const char* psfd_version(void) { return "psfd-b300 0.1 (sm_103a)"; }
 
+// The bounded device-side waits record a timeout instead of hanging: the operator's plane kernel
+// in P->err, the layered apply in P->lay_err[1], the FNO mode mixing in a global flag.  Read and
+// clear them (synchronises the plan's stream).
+int plan_wait_status(psfd_plan_s* P) {
+  int h[2] = {0, 0}, tc = 0;
+  cudaStream_t s = P->stream;
+  if (P->err) PSFD_CUDA_TRY(cudaMemcpyAsync(&h[0], P->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (P->lay_err) PSFD_CUDA_TRY(cudaMemcpyAsync(&h[1], P->lay_err + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  int rc = fno_mix_tc_error(&tc);
+  if (rc) return rc;
+  if (!h[0] && !h[1] && !tc) return PSFD_OK;
+  if (h[0]) PSFD_CUDA_TRY(cudaMemsetAsync(P->err, 0, sizeof(int), s));
+  if (h[1]) PSFD_CUDA_TRY(cudaMemsetAsync(P->lay_err + 1, 0, sizeof(int), s));
+  PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+  psfd_set_error("a bounded device-side wait gave up (%s)",
+                 h[0] ? "operator plane kernel" : h[1] ? "layered preconditioner apply" : "FNO mode mixing");
+  return PSFD_ERR_TIMEOUT;
+}
+
+extern "C" int psfd_device_status(psfd_plan P) {
+  if (!P) { psfd_set_error("psfd_device_status: null plan"); return PSFD_ERR_ARG; }
+  return plan_wait_status(P);
+}
+
 extern "C" int psfd_supported(int nx, int ny, int nz) {
   return lateral_supported(nx) && lateral_supported(ny) && axial_supported(nz) ? 1 : 0;
 }

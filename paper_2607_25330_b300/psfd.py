@@ -107,6 +107,7 @@ def lib() -> C.CDLL:
         "psfd_set_layer_stack_contrast": (i, [vp, C.POINTER(Stack), d, C.POINTER(C.c_float)]),
         "psfd_layered_refresh": (i, [vp, d, C.POINTER(C.c_int)]),
         "psfd_layered_bytes": (sz, [vp]),
+        "psfd_device_status": (i, [vp]),
         "psfd_solve_batched": (i, [C.POINTER(vp), i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
                                    C.POINTER(Info), i]),
         "fno_workspace_size": (sz, [C.POINTER(FnoWeights), i, i, i, i]),
@@ -137,7 +138,7 @@ def declared_symbols() -> List[str]:
             "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
             "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
-            "psfd_layered_storage",
+            "psfd_layered_storage", "psfd_device_status",
             "psfd_set_plane_contrast", "psfd_set_layer_stack_contrast",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
@@ -278,6 +279,10 @@ class Plan:
     def layered_build(self) -> None:
         """Assemble and invert the per-column blocks of the layered-background preconditioner."""
         _check(lib().psfd_layered_build(self.h), "psfd_layered_build")
+
+    def device_status(self) -> None:
+        """Raise PsfdError (PSFD_ERR_TIMEOUT) if a bounded device-side wait gave up since the last check."""
+        _check(lib().psfd_device_status(self.h), "psfd_device_status")
 
     def layered_refresh(self, max_shift: float) -> bool:
         """Rebuild the blocks only if a plane's mean fill moved by more than max_shift; True if rebuilt."""
