@@ -192,6 +192,12 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * solve converges, never the solution.  psfd_layered_refresh rebuilds them only
  * when some plane's mean fill moved by more than max_shift (fill fraction units)
  * since the last build, and sets *rebuilt (nullable) to 1 if it did.
+ * With half storage and nz a multiple of 32 (nz = 64: nrhs <= 2) P is applied on
+ * the tensor cores: each column's blocks are copied to shared memory in bulk and
+ * multiplied as f16 matrices with FP32 accumulation, the vector entering as a
+ * two-term f16 split with a power-of-two scale per column (about 22 bits), so P
+ * stays linear to FP32 level; PSFD_LAY_SIMT=1 in the environment selects the
+ * FP32 SIMT kernel instead.
  * Supported for nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else
  * PSFD_ERR_ARG / psfd_layered_bytes() = 0); PSFD_ERR_STATE before
  * psfd_background; PSFD_ERR_BREAKDOWN if a block is singular.  Both synchronise
@@ -392,7 +398,8 @@ PSFD_API int psfd_timing_read_bytes(double* ms, long long* calls, double* bytes,
 
 /* ---------------------------------------------------------------- misc */
 /* Every wait of a kernel on its own bulk copies or tensor-core products (the
- * operator's single-pass plane kernel, the FNO mode mixing) gives up after a
+ * operator's single-pass plane kernel, the tensor-core apply of the layered P,
+ * the FNO mode mixing) gives up after a
  * bounded time instead of hanging, and records that in a device flag.
  * psfd_device_status reads and clears the flags: PSFD_ERR_TIMEOUT (with a
  * message naming the kernel) if a wait gave up since the last call, else

@@ -35,6 +35,13 @@ using zc = std::complex<double>;
 constexpr int LAY_THREADS = 256;   // 16 x 16 thread grid over an N x N matrix
 constexpr int LAY_GROUP = 4;       // lateral columns (consecutive kx) per apply CTA
 
+// the half-precision blocks are applied on the tensor cores when nz is a multiple of 32 and two
+// CTAs fit an SM (PSFD_LAY_SIMT=1 selects the SIMT kernel)
+bool lay_apply_tc_enabled() {
+  const char* e = getenv("PSFD_LAY_SIMT");
+  return !(e && e[0] == '1');
+}
+
 struct LayArgs {
   const float* kx;
   const float* ky;
@@ -51,6 +58,7 @@ struct LayArgs {
   float* scales;        // [ncols][2] power-of-two scale of the TE and TM block (storage 1)
   int half;             // 1: half-precision storage
   int* err;             // [0] set to 1 if a pivot vanished, [1] if an apply gave up waiting for its blocks
+  int no_copy;          // test of the bounded wait: the tensor-core apply requests no blocks
 };
 
 __device__ __forceinline__ cf cdiv1(cf a) {  // 1 / a
@@ -423,6 +431,242 @@ __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tensor-core apply of the half-precision blocks.  For one stored block column the V vectors
+// (right-hand sides x rows ky, -ky) form an nb x V complex panel, and M X is, in real arithmetic,
+// A' (nb x 2nb) times B' (2nb x 2V) with the entries of M as (re, im) pairs along k -- exactly the
+// stored half2 layout -- and the columns of vector v holding (Re x, -Im x) and (Im x, Re x) along
+// k.  That is an f16 matrix product with FP32 accumulation (mma.sync m16n8k16, N = 8 = two output
+// columns for each of four vectors).  The vector enters as a two-term f16 split: with s a power of
+// two putting the column's largest entry in [2^13, 2^14), hi = f16(s x) and lo = f16(s x - hi)
+// carry about 22 bits, so P stays linear to about FP32 rounding (the Krylov solvers need a fixed
+// linear P) while every stored entry costs a quarter of an instruction instead of the SIMT
+// kernel's four complex FMAs.
+//
+// One CTA per stored block column.  Its 20 nz^2 bytes of blocks are requested at once with bulk
+// asynchronous copies into shared memory, so the gather, rotation and split of the vectors
+// overlap the transfer, and two CTAs per SM keep up to 160 KB in flight.  One warp per (slab of
+// 32 block rows, k range of nz): nz / 32 TE slabs and nz / 16 TM slabs x two k halves (the TM
+// input's t and z parts, summed in the output).  Lane (g, t) reads 16 B = rows 4g .. 4g + 3 of the
+// slab at k columns j and j + 4; the MMA row order is permuted so that those four rows are the
+// fragment rows g, g + 8 of the slab's two 16-row tiles, and the k order within an 8-column step
+// is the stored one.
+__device__ __forceinline__ void mma_f16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                        unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned h2bits(__half2 h) { return *reinterpret_cast<unsigned*>(&h); }
+
+// 2^e for e in [-126, 127]
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+__device__ __forceinline__ unsigned smem_u32a(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// wait for phase `parity` of an mbarrier, giving up after about max_cycles SM clocks
+__device__ __forceinline__ bool mbar_wait_cycles(unsigned mb, unsigned parity, long long max_cycles) {
+  const long long t0 = clock64();
+  unsigned ok = 0;
+  while (!ok) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+    if (!ok && clock64() - t0 > max_cycles) return false;
+  }
+  return true;
+}
+
+template <int NZ, int NR>
+struct MmaCfg {
+  static constexpr int V = 2 * NR;            // vector slots: rhs r of row h is r, of row ny - h is NR + r
+  static constexpr int NT = (V + 3) / 4;      // n8 tiles (four vectors each)
+  static constexpr int TES = NZ / 32;         // TE slabs
+  static constexpr int TMS = NZ / 16;         // TM slabs
+  static constexpr int W = TES + 2 * TMS;     // warps
+  static constexpr int THREADS = 32 * W;
+  static constexpr int KT = NZ / 8;           // 8-column k steps per warp
+  static constexpr int R3 = 3 * NZ;           // stacked (s, t, z) rows
+  static constexpr size_t M_BYTES = (size_t)5 * NZ * NZ * sizeof(__half2);  // the column's blocks
+  static constexpr size_t S_BYTES = (size_t)NT * R3 * 8 * sizeof(uint2);    // B' fragments (hi, lo)
+  static constexpr size_t X_BYTES = (size_t)V * R3 * sizeof(cf);             // rotated x, FP32
+  static constexpr size_t O_BYTES = (size_t)V * 5 * NZ * sizeof(cf);         // outputs, in the block area
+  static constexpr size_t SMEM = M_BYTES + S_BYTES + X_BYTES + (size_t)V * sizeof(float);
+  static_assert(O_BYTES <= M_BYTES, "outputs reuse the block area");
+};
+
+// used where two CTAs fit an SM (up to 113 KB of shared memory each)
+template <int NZ, int NR>
+constexpr bool mma_fits() { return MmaCfg<NZ, NR>::SMEM <= 113 * 1024; }
+
+template <int NZ, int NR>
+__global__ void __launch_bounds__(MmaCfg<NZ, NR>::THREADS, 2)
+    k_lay_apply_mma(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
+  using C = MmaCfg<NZ, NR>;
+  constexpr int V = C::V, NT = C::NT, R3 = C::R3;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __half2* Mt = reinterpret_cast<__half2*>(smem);                           // [5 NZ^2], as stored
+  uint2* S = reinterpret_cast<uint2*>(smem + C::M_BYTES);                   // [NT][R3][8]
+  cf* X = reinterpret_cast<cf*>(smem + C::M_BYTES + C::S_BYTES);            // [V][R3]
+  float* isv = reinterpret_cast<float*>(smem + C::M_BYTES + C::S_BYTES + C::X_BYTES);   // [V] 1 / s
+  cf* O = reinterpret_cast<cf*>(smem);                                      // [V][5 NZ], after the MMAs
+  __shared__ float rot[2][4];
+  __shared__ __align__(8) unsigned long long bar;
+  const long hc = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned mb = smem_u32a(&bar);
+  // 0. request the column's blocks
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid == 0 && !a.no_copy) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"((unsigned)C::M_BYTES)
+                 : "memory");
+    const __half2* src = a.mats16 + hc * (5L * NZ * NZ);
+    constexpr unsigned PART = (unsigned)(C::M_BYTES / 5);   // TE block, then the TM block in four parts
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   :: "r"(smem_u32a(smem + q * PART)), "l"(reinterpret_cast<const char*>(src) + q * PART),
+                      "r"(PART), "r"(mb)
+                   : "memory");
+  }
+  const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
+  const int iyB = a.pair ? (a.ny - h) % a.ny : h;
+  const bool two = a.pair && iyB != h;
+  if (tid < 2) {   // p = 0: row h, p = 1: row iyB
+    const float kx = a.kx[ix], ky = a.ky[tid == 0 ? h : iyB];
+    const float kap = sqrtf(kx * kx + ky * ky);
+    const bool small = !(kap > 0.f);
+    rot[tid][0] = small ? 0.f : -ky / kap;
+    rot[tid][1] = small ? 1.f : kx / kap;
+    rot[tid][2] = small ? 1.f : kx / kap;
+    rot[tid][3] = small ? 0.f : ky / kap;
+  }
+  __syncthreads();
+  const long n = 3L * NZ * ncols;
+  constexpr int ITEMS = NR * NZ * 2;    // (p fastest, then z, r)
+  // 1. gather + rotate into X
+  for (int it = tid; it < ITEMS; it += C::THREADS) {
+    const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+    cf* Xv = X + (p * NR + r) * R3;
+    if (p && !two) {
+      Xv[z] = czero(); Xv[NZ + z] = czero(); Xv[2 * NZ + z] = czero();
+      continue;
+    }
+    const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
+    const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
+    const float* q = rot[p];
+    Xv[z] = cadd(cscale(ex, q[0]), cscale(ey, q[1]));
+    Xv[NZ + z] = cadd(cscale(ex, q[2]), cscale(ey, q[3]));
+    Xv[2 * NZ + z] = ez;
+  }
+  __syncthreads();
+  // 2. per-vector power-of-two scale (one warp per vector)
+  for (int v = w; v < V; v += C::W) {
+    const cf* Xv = X + v * R3;
+    float m = 0.f;
+    for (int i = lane; i < R3; i += 32) m = fmaxf(m, fmaxf(fabsf(Xv[i].x), fabsf(Xv[i].y)));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      int e = 0;
+      if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+      const int es = min(120, max(-120, 14 - e));    // s m in [2^13, 2^14)
+      isv[v] = pow2f(-es);
+    }
+  }
+  __syncthreads();
+  // 3. B' fragments: S[nt][jj][n], n = 2 (v mod 4) + o; (hi, lo) half2 pairs along k
+  for (int it = tid; it < NT * R3 * 8; it += C::THREADS) {
+    const int nn = it & 7, jj = (it >> 3) % R3, nt = (it >> 3) / R3;
+    const int v = 4 * nt + (nn >> 1);
+    float p0 = 0.f, p1 = 0.f;
+    if (v < V) {
+      const float s = 1.f / isv[v];
+      const cf xv = X[v * R3 + jj];
+      if (nn & 1) { p0 = xv.y * s; p1 = xv.x * s; }
+      else { p0 = xv.x * s; p1 = -xv.y * s; }
+    }
+    const __half2 hi = __floats2half2_rn(p0, p1);
+    const __half2 lo = __floats2half2_rn(p0 - __low2float(hi), p1 - __high2float(hi));
+    S[it] = make_uint2(h2bits(hi), h2bits(lo));
+  }
+  __syncthreads();
+  // 4. wait for the blocks (bounded: about a second), then the MMAs
+  const bool arrived = mbar_wait_cycles(mb, 0, 2000000000LL);
+  if (__syncthreads_or(!arrived)) {
+    // the copies did not complete in time: report, give them one more bounded wait, leave together
+    if (tid == 0) {
+      atomicExch(a.err + 1, 1);
+      if (!a.no_copy) mbar_wait_cycles(mb, 0, 2000000000LL);
+    }
+    __syncthreads();
+    return;
+  }
+  const int g = lane >> 2, t = lane & 3;
+  const bool te = w < C::TES;
+  const int slab = te ? w : (w - C::TES) % C::TMS, kh = te ? 0 : (w - C::TES) / C::TMS;
+  const int nb = te ? NZ : 2 * NZ;
+  const int jjb = te ? 0 : NZ + kh * NZ;                       // first stacked input row of the k range
+  const uint4* Ab = reinterpret_cast<const uint4*>(
+      Mt + (te ? 0 : NZ * NZ) + (kh * NZ + t) * nb + slab * 32 + 4 * g);
+  const uint2* Sb = S + (jjb + t) * 8 + g;
+  float acc[NT][2][4];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[nt][m][q] = 0.f;
+#pragma unroll
+  for (int kt = 0; kt < C::KT; ++kt) {
+    const uint4 aj = Ab[kt * 2 * nb];          // k column j = 8 kt + t
+    const uint4 aj4 = Ab[kt * 2 * nb + nb];    // k column j + 4
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const uint2 b0 = Sb[(nt * R3 + 8 * kt) * 8], b1 = Sb[(nt * R3 + 8 * kt + 4) * 8];
+      mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.x, b1.x);
+      mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.y, b1.y);
+      mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.x, b1.x);
+      mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.y, b1.y);
+    }
+  }
+  __syncthreads();   // every warp is done with the blocks: the outputs reuse their area
+  // epilogue: lane (g, t) holds vector 4 nt + t at slab rows 4g + 2m (c0, c1) and 4g + 2m + 1 (c2, c3)
+  {
+    const float bs = a.scales[hc * 2 + (te ? 0 : 1)];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int v = 4 * nt + t;
+      if (v >= V) continue;
+      const float sc = bs * isv[v];
+      cf* Ov = O + v * 5 * NZ + (te ? 0 : (kh == 0 ? NZ : 3 * NZ)) + slab * 32 + 4 * g;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        Ov[2 * m] = make_float2(acc[nt][m][0] * sc, acc[nt][m][1] * sc);
+        Ov[2 * m + 1] = make_float2(acc[nt][m][2] * sc, acc[nt][m][3] * sc);
+      }
+    }
+  }
+  __syncthreads();
+  // 5. rotate back and scatter
+  for (int it = tid; it < ITEMS; it += C::THREADS) {
+    const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+    if (p && !two) continue;
+    const cf* Ov = O + (p * NR + r) * 5 * NZ;
+    const cf es = Ov[z], et = cadd(Ov[NZ + z], Ov[3 * NZ + z]), ez = cadd(Ov[2 * NZ + z], Ov[4 * NZ + z]);
+    const float* q = rot[p];
+    const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
+    y[base] = cadd(cscale(es, q[0]), cscale(et, q[2]));
+    y[base + (long)NZ * ncols] = cadd(cscale(es, q[1]), cscale(et, q[3]));
+    y[base + 2L * NZ * ncols] = ez;
+  }
+}
+
 LayArgs lay_args(psfd_plan_s* P) {
   LayArgs a{};
   a.kx = P->kx; a.ky = P->ky; a.refl = P->R.refl; a.kz0 = P->R.kz0;
@@ -432,6 +676,8 @@ LayArgs lay_args(psfd_plan_s* P) {
   a.pair = layered_pairs(P) ? 1 : 0;
   a.mats = P->lay; a.err = P->lay_err;
   a.mats16 = (__half2*)P->lay16; a.scales = P->lay_scale; a.half = P->lay_half ? 1 : 0;
+  const char* e = getenv("PSFD_TEST_LAY_NO_COPY");
+  a.no_copy = (e && e[0] == '1') ? 1 : 0;
   return a;
 }
 
@@ -448,6 +694,21 @@ int build_nz(psfd_plan_s* P) {
 
 template <int NZ, int NR>
 int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
+  if constexpr (NZ % 32 == 0 && mma_fits<NZ, NR>()) {
+    if (a.half && lay_apply_tc_enabled()) {
+      using C = MmaCfg<NZ, NR>;
+      static bool attr = false;
+      if (!attr) {
+        PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_mma<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::SMEM));
+        attr = true;
+      }
+      const unsigned grid = (unsigned)layered_columns(P);
+      k_lay_apply_mma<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, x, y, P->ncols);
+      PSFD_CHECK_LAUNCH();
+      return PSFD_OK;
+    }
+  }
   const size_t smem = (size_t)2 * LAY_GROUP * 3 * NZ * NR * sizeof(cf);
   const unsigned grid = (unsigned)(layered_columns(P) / LAY_GROUP);
   if (a.half)

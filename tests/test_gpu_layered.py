@@ -167,3 +167,68 @@ def test_half_storage_of_the_blocks(grid):
     plan.layered_storage(False)
     with pytest.raises(psfd.PsfdError):
         plan.precond(x.cuda(), flags=psfd.PSFD_LAYERED)    # released until rebuilt
+
+
+TC_GRIDS = [  # nz a multiple of 32: the half-precision blocks are applied on the tensor cores
+    (32, 16, 32, 8.0, 30.0, 2),   # no ky / -ky pairing (Bloch shift along y)
+    (32, 32, 64, 6.0, 0.0, 2),
+    (16, 16, 32, 0.0, 0.0, 4),
+    (16, 16, 64, 6.0, 0.0, 1),
+    (32, 16, 32, 6.0, 0.0, 3),
+]
+
+
+@pytest.mark.parametrize("grid", TC_GRIDS)
+def test_tensor_core_apply_of_half_blocks(grid, monkeypatch):
+    """The tensor-core apply (f16 blocks, two-term f16 split of the vector, FP32 accumulation)
+    against the SIMT apply of the same stored blocks (FP32 FMAs): the split keeps about 22 bits of
+    the vector, so the two agree to a few FP32 roundings (1e-5), and P stays linear and
+    scale-covariant to that level over 50 decades of input magnitude."""
+    from paper_2607_25330_b300 import psfd
+    prob, g, fill_o, plan, b = setup(*grid)
+    plan.layered_storage(True)
+    plan.layered_build()
+    x1 = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64).cuda()
+    x2 = torch.from_numpy(I.random_field(plan.shape, 4)).to(torch.complex64).cuda()
+    monkeypatch.setenv("PSFD_LAY_SIMT", "1")
+    y_simt = plan.precond(x1, flags=psfd.PSFD_LAYERED).cpu()
+    monkeypatch.setenv("PSFD_LAY_SIMT", "0")
+    y1 = plan.precond(x1, flags=psfd.PSFD_LAYERED).cpu()
+    for r in range(plan.nrhs):
+        assert rel_l2(y1[r], y_simt[r]) < 1e-5
+    y2 = plan.precond(x2, flags=psfd.PSFD_LAYERED).cpu()
+    y12 = plan.precond(x1 + 3.0 * x2, flags=psfd.PSFD_LAYERED).cpu()
+    assert rel_l2(y12, y1 + 3.0 * y2) < 1e-5
+    for s in (1e-25, 1e25):
+        ys = plan.precond(x1 * s, flags=psfd.PSFD_LAYERED).cpu()
+        assert rel_l2(ys / s, y1) < 1e-5
+    # a zero right-hand side stays zero (the scale of an all-zero column is finite)
+    x0 = x1.clone()
+    x0[0] = 0
+    y0 = plan.precond(x0, flags=psfd.PSFD_LAYERED).cpu()
+    assert torch.count_nonzero(y0[0]) == 0 and bool(torch.isfinite(torch.view_as_real(y0)).all())
+    plan.device_status()
+
+
+def test_tensor_core_apply_wait_gives_up_and_reports(monkeypatch):
+    """The apply's wait for its bulk block copies is bounded: with no copy requested (a test hook;
+    nothing else completes the barrier) every CTA gives up after about a second, records it, and
+    leaves; psfd_device_status reports PSFD_ERR_TIMEOUT once, and the context stays usable."""
+    from paper_2607_25330_b300 import psfd
+    prob, g, fill_o, plan, b = setup(16, 16, 32, 0.0, 0.0, 2)
+    plan.layered_storage(True)
+    plan.layered_build()
+    plan.device_status()
+    x = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64).cuda()
+    y_ref = plan.precond(x, flags=psfd.PSFD_LAYERED).cpu()
+    monkeypatch.setenv("PSFD_TEST_LAY_NO_COPY", "1")
+    plan.precond(x, flags=psfd.PSFD_LAYERED)
+    monkeypatch.delenv("PSFD_TEST_LAY_NO_COPY")
+    with pytest.raises(psfd.PsfdError) as e:
+        plan.device_status()
+    assert e.value.code == psfd.PSFD_ERR_TIMEOUT and "layered" in str(e.value)
+    plan.device_status()                                   # cleared
+    y = plan.precond(x, flags=psfd.PSFD_LAYERED).cpu()     # and the next apply is complete again
+    assert rel_l2(y, y_ref) == 0.0
+    res = plan.solve_ex(b, tol=1e-6, maxit=400, precond=psfd.PC_LAYERED)
+    assert res["code"] == 0
