@@ -193,8 +193,8 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * when some plane's mean fill moved by more than max_shift (fill fraction units)
  * since the last build, and sets *rebuilt (nullable) to 1 if it did.
  * With half storage and nz a multiple of 32 (nz = 64: nrhs <= 2) P is applied on
- * the tensor cores: each column's blocks are copied to shared memory in bulk and
- * multiplied as f16 matrices with FP32 accumulation, the vector entering as a
+ * the tensor cores: the columns' blocks stream through shared memory in bulk
+ * copies and are multiplied as f16 matrices with FP32 accumulation, the vector entering as a
  * two-term f16 split with a power-of-two scale per column (about 22 bits), so P
  * stays linear to FP32 level; PSFD_LAY_SIMT=1 in the environment selects the
  * FP32 SIMT kernel instead.

@@ -35,8 +35,8 @@ using zc = std::complex<double>;
 constexpr int LAY_THREADS = 256;   // 16 x 16 thread grid over an N x N matrix
 constexpr int LAY_GROUP = 4;       // lateral columns (consecutive kx) per apply CTA
 
-// the half-precision blocks are applied on the tensor cores when nz is a multiple of 32 and two
-// CTAs fit an SM (PSFD_LAY_SIMT=1 selects the SIMT kernel)
+// the half-precision blocks are applied on the tensor cores when nz is a multiple of 32
+// (PSFD_LAY_SIMT=1 selects the SIMT kernel)
 bool lay_apply_tc_enabled() {
   const char* e = getenv("PSFD_LAY_SIMT");
   return !(e && e[0] == '1');
@@ -443,14 +443,11 @@ __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 
 // linear P) while every stored entry costs a quarter of an instruction instead of the SIMT
 // kernel's four complex FMAs.
 //
-// One CTA per stored block column.  Its 20 nz^2 bytes of blocks are requested at once with bulk
-// asynchronous copies into shared memory, so the gather, rotation and split of the vectors
-// overlap the transfer, and two CTAs per SM keep up to 160 KB in flight.  One warp per (slab of
-// 32 block rows, k range of nz): nz / 32 TE slabs and nz / 16 TM slabs x two k halves (the TM
-// input's t and z parts, summed in the output).  Lane (g, t) reads 16 B = rows 4g .. 4g + 3 of the
-// slab at k columns j and j + 4; the MMA row order is permuted so that those four rows are the
-// fragment rows g, g + 8 of the slab's two 16-row tiles, and the k order within an 8-column step
-// is the stored one.
+// One warp per (slab of 32 block rows, k range of nz): nz / 32 TE slabs and nz / 16 TM slabs x two
+// k halves (the TM input's t and z parts, summed in the output).  Lane (g, t) reads 16 B = rows
+// 4g .. 4g + 3 of the slab at k columns j and j + 4; the MMA row order is permuted so that those
+// four rows are the fragment rows g, g + 8 of the slab's two 16-row tiles, and the k order within
+// an 8-column step is the stored one.
 __device__ __forceinline__ void mma_f16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
                                         unsigned b0, unsigned b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
@@ -486,184 +483,274 @@ struct MmaCfg {
   static constexpr int TES = NZ / 32;         // TE slabs
   static constexpr int TMS = NZ / 16;         // TM slabs
   static constexpr int W = TES + 2 * TMS;     // warps
-  static constexpr int THREADS = 32 * W;
   static constexpr int KT = NZ / 8;           // 8-column k steps per warp
   static constexpr int R3 = 3 * NZ;           // stacked (s, t, z) rows
-  static constexpr size_t M_BYTES = (size_t)5 * NZ * NZ * sizeof(__half2);  // the column's blocks
   static constexpr size_t S_BYTES = (size_t)NT * R3 * 8 * sizeof(uint2);    // B' fragments (hi, lo)
   static constexpr size_t X_BYTES = (size_t)V * R3 * sizeof(cf);             // rotated x, FP32
-  static constexpr size_t O_BYTES = (size_t)V * 5 * NZ * sizeof(cf);         // outputs, in the block area
-  static constexpr size_t SMEM = M_BYTES + S_BYTES + X_BYTES + (size_t)V * sizeof(float);
-  static_assert(O_BYTES <= M_BYTES, "outputs reuse the block area");
+  static constexpr size_t O_BYTES = (size_t)V * 5 * NZ * sizeof(cf);         // outputs (s, t, z + upper-k t, z)
 };
 
-// used where two CTAs fit an SM (up to 113 KB of shared memory each)
+// Persistent, pipelined form of the tensor-core apply.  One CTA per SM walks the stored block
+// columns blockIdx.x, + gridDim.x, ...; the column's blocks stream through a ring of shared-memory
+// slots of 4 nz^2 bytes (the TE block, then the TM block in four quarters of nz/2 columns each),
+// filled by bulk asynchronous copies that one producer lane issues as soon as a slot is released,
+// so the HBM stream never waits for the per-column work.  Two groups of worker warps take
+// alternate columns: while one gathers, splits and scatters, the other multiplies.  Each worker
+// warp passes every chunk of its column in order (waits until it has landed, uses it if it holds
+// the warp's k range, then releases it), and prefetches the vectors of its group's next column
+// into registers before the multiplications.  Every wait is bounded (about a second); the first
+// that gives up sets a CTA-wide abort flag, after which nothing waits any more, no copy is issued,
+// the producer waits (bounded) for the copies it issued, and the flag err[1] reports it.
 template <int NZ, int NR>
-constexpr bool mma_fits() { return MmaCfg<NZ, NR>::SMEM <= 113 * 1024; }
+struct PipeCfg {
+  using M = MmaCfg<NZ, NR>;
+  static constexpr int W = M::W;                                      // worker warps per group
+  static constexpr int GT = 32 * W;                                   // worker threads per group
+  static constexpr int THREADS = 32 + 2 * GT;                         // producer warp + two groups
+  static constexpr size_t CH = (size_t)4 * NZ * NZ;                   // bytes per chunk (nz^2 half2)
+  static constexpr size_t G_BYTES = M::S_BYTES + M::O_BYTES + 16 * ((M::V * sizeof(float) + 15) / 16);
+  // two columns of chunks: slot 5 g + q only ever holds chunk q of group g's columns, so every
+  // wait on a slot's barriers follows the same warps' wait on the previous round (the parity
+  // of a phase identifies it only within one phase)
+  static constexpr int RING = 10;
+  static constexpr size_t SMEM = RING * CH + 2 * G_BYTES;
+  static constexpr int ITEMS = NR * NZ * 2;                           // gather items per column
+  static constexpr int IPT = (ITEMS + GT - 1) / GT;                   // per worker thread
+  static_assert(M::X_BYTES <= M::O_BYTES, "the rotated vectors reuse the output area");
+};
 
 template <int NZ, int NR>
-__global__ void __launch_bounds__(MmaCfg<NZ, NR>::THREADS, 2)
-    k_lay_apply_mma(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
-  using C = MmaCfg<NZ, NR>;
-  constexpr int V = C::V, NT = C::NT, R3 = C::R3;
+constexpr bool pipe_fits() { return PipeCfg<NZ, NR>::SMEM <= (size_t)227 * 1024; }
+
+__device__ __forceinline__ void group_sync(int grp, int nthreads) {
+  asm volatile("bar.sync %0, %1;" :: "r"(1 + grp), "r"(nthreads) : "memory");
+}
+
+template <int NZ, int NR>
+__global__ void __maxnreg__(96)
+    k_lay_apply_pipe(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols, long ncolsB) {
+  using P = PipeCfg<NZ, NR>;
+  using M = MmaCfg<NZ, NR>;
+  constexpr int V = M::V, NT = M::NT, R3 = M::R3, W = P::W, RING = P::RING;
+  constexpr long long WAIT = 2000000000LL;   // SM clocks, about a second
   extern __shared__ __align__(128) unsigned char smem[];
-  __half2* Mt = reinterpret_cast<__half2*>(smem);                           // [5 NZ^2], as stored
-  uint2* S = reinterpret_cast<uint2*>(smem + C::M_BYTES);                   // [NT][R3][8]
-  cf* X = reinterpret_cast<cf*>(smem + C::M_BYTES + C::S_BYTES);            // [V][R3]
-  float* isv = reinterpret_cast<float*>(smem + C::M_BYTES + C::S_BYTES + C::X_BYTES);   // [V] 1 / s
-  cf* O = reinterpret_cast<cf*>(smem);                                      // [V][5 NZ], after the MMAs
-  __shared__ float rot[2][4];
-  __shared__ __align__(8) unsigned long long bar;
-  const long hc = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const unsigned mb = smem_u32a(&bar);
-  // 0. request the column's blocks
+  __shared__ __align__(8) unsigned long long full[RING], empty[RING];
+  __shared__ int abort_flag;
+  __shared__ float rot[2][2][4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long ncta = blockIdx.x < ncolsB ? (ncolsB - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // columns here
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    for (int s = 0; s < RING; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32a(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32a(&empty[s])), "r"(W) : "memory");
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (tid == 0 && !a.no_copy) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"((unsigned)C::M_BYTES)
-                 : "memory");
-    const __half2* src = a.mats16 + hc * (5L * NZ * NZ);
-    constexpr unsigned PART = (unsigned)(C::M_BYTES / 5);   // TE block, then the TM block in four parts
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   :: "r"(smem_u32a(smem + q * PART)), "l"(reinterpret_cast<const char*>(src) + q * PART),
-                      "r"(PART), "r"(mb)
-                   : "memory");
-  }
-  const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
-  const int iyB = a.pair ? (a.ny - h) % a.ny : h;
-  const bool two = a.pair && iyB != h;
-  if (tid < 2) {   // p = 0: row h, p = 1: row iyB
-    const float kx = a.kx[ix], ky = a.ky[tid == 0 ? h : iyB];
-    const float kap = sqrtf(kx * kx + ky * ky);
-    const bool small = !(kap > 0.f);
-    rot[tid][0] = small ? 0.f : -ky / kap;
-    rot[tid][1] = small ? 1.f : kx / kap;
-    rot[tid][2] = small ? 1.f : kx / kap;
-    rot[tid][3] = small ? 0.f : ky / kap;
   }
   __syncthreads();
   const long n = 3L * NZ * ncols;
-  constexpr int ITEMS = NR * NZ * 2;    // (p fastest, then z, r)
-  // 1. gather + rotate into X
-  for (int it = tid; it < ITEMS; it += C::THREADS) {
-    const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
-    cf* Xv = X + (p * NR + r) * R3;
-    if (p && !two) {
-      Xv[z] = czero(); Xv[NZ + z] = czero(); Xv[2 * NZ + z] = czero();
-      continue;
-    }
-    const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
-    const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
-    const float* q = rot[p];
-    Xv[z] = cadd(cscale(ex, q[0]), cscale(ey, q[1]));
-    Xv[NZ + z] = cadd(cscale(ex, q[2]), cscale(ey, q[3]));
-    Xv[2 * NZ + z] = ez;
-  }
-  __syncthreads();
-  // 2. per-vector power-of-two scale (one warp per vector)
-  for (int v = w; v < V; v += C::W) {
-    const cf* Xv = X + v * R3;
-    float m = 0.f;
-    for (int i = lane; i < R3; i += 32) m = fmaxf(m, fmaxf(fabsf(Xv[i].x), fabsf(Xv[i].y)));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  auto give_up = [&]() {
+    if (atomicExch(&abort_flag, 1) == 0) atomicExch(a.err + 1, 1);
+  };
+  // ------------------------------------------------------------------ producer
+  if (warp == 0) {
     if (lane == 0) {
-      int e = 0;
-      if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
-      const int es = min(120, max(-120, 14 - e));    // s m in [2^13, 2^14)
-      isv[v] = pow2f(-es);
+      long issued = 0;
+      for (long k = 0; k < ncta; ++k) {
+        const char* src = reinterpret_cast<const char*>(a.mats16 + (blockIdx.x + k * gridDim.x) * (5L * NZ * NZ));
+        for (int q = 0; q < 5; ++q) {
+          const long c = 5 * k + q;
+          const int slot = (int)(c % RING);
+          if (c >= RING && !mbar_wait_cycles(smem_u32a(&empty[slot]), (unsigned)(((c / RING) - 1) & 1), WAIT))
+            give_up();
+          if (*(volatile int*)&abort_flag) break;
+          if (!a.no_copy) {
+            const unsigned fb = smem_u32a(&full[slot]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"((unsigned)P::CH)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32a(smem + (size_t)slot * P::CH)), "l"(src + q * P::CH), "r"((unsigned)P::CH),
+                            "r"(fb)
+                         : "memory");
+            issued = c + 1;
+          }
+        }
+        if (*(volatile int*)&abort_flag) break;
+      }
+      // leave only when every copy issued has landed (bounded)
+      for (long c = issued > RING ? issued - RING : 0; c < issued; ++c)
+        mbar_wait_cycles(smem_u32a(&full[c % RING]), (unsigned)((c / RING) & 1), WAIT);
     }
-  }
-  __syncthreads();
-  // 3. B' fragments: S[nt][jj][n], n = 2 (v mod 4) + o; (hi, lo) half2 pairs along k
-  for (int it = tid; it < NT * R3 * 8; it += C::THREADS) {
-    const int nn = it & 7, jj = (it >> 3) % R3, nt = (it >> 3) / R3;
-    const int v = 4 * nt + (nn >> 1);
-    float p0 = 0.f, p1 = 0.f;
-    if (v < V) {
-      const float s = 1.f / isv[v];
-      const cf xv = X[v * R3 + jj];
-      if (nn & 1) { p0 = xv.y * s; p1 = xv.x * s; }
-      else { p0 = xv.x * s; p1 = -xv.y * s; }
-    }
-    const __half2 hi = __floats2half2_rn(p0, p1);
-    const __half2 lo = __floats2half2_rn(p0 - __low2float(hi), p1 - __high2float(hi));
-    S[it] = make_uint2(h2bits(hi), h2bits(lo));
-  }
-  __syncthreads();
-  // 4. wait for the blocks (bounded: about a second), then the MMAs
-  const bool arrived = mbar_wait_cycles(mb, 0, 2000000000LL);
-  if (__syncthreads_or(!arrived)) {
-    // the copies did not complete in time: report, give them one more bounded wait, leave together
-    if (tid == 0) {
-      atomicExch(a.err + 1, 1);
-      if (!a.no_copy) mbar_wait_cycles(mb, 0, 2000000000LL);
-    }
-    __syncthreads();
     return;
   }
+  // ------------------------------------------------------------------ workers
+  const int grp = (warp - 1) / W, w = (warp - 1) % W, gt = tid - 32 - grp * P::GT;
+  unsigned char* gbase = smem + (size_t)RING * P::CH + (size_t)grp * P::G_BYTES;
+  uint2* S = reinterpret_cast<uint2*>(gbase);                                  // [NT][R3][8]
+  cf* O = reinterpret_cast<cf*>(gbase + M::S_BYTES);                           // [V][5 NZ]
+  cf* X = O;                                                                   // [V][R3], before the MMAs
+  float* isv = reinterpret_cast<float*>(gbase + M::S_BYTES + M::O_BYTES);      // [V]
   const int g = lane >> 2, t = lane & 3;
-  const bool te = w < C::TES;
-  const int slab = te ? w : (w - C::TES) % C::TMS, kh = te ? 0 : (w - C::TES) / C::TMS;
+  const bool te = w < M::TES;
+  const int slab = te ? w : (w - M::TES) % M::TMS, kh = te ? 0 : (w - M::TES) / M::TMS;
   const int nb = te ? NZ : 2 * NZ;
-  const int jjb = te ? 0 : NZ + kh * NZ;                       // first stacked input row of the k range
-  const uint4* Ab = reinterpret_cast<const uint4*>(
-      Mt + (te ? 0 : NZ * NZ) + (kh * NZ + t) * nb + slab * 32 + 4 * g);
-  const uint2* Sb = S + (jjb + t) * 8 + g;
-  float acc[NT][2][4];
+  const int jjb = te ? 0 : NZ + kh * NZ;
+  // the warp's chunks: TE -> chunk 0 (all KT k steps); TM (slab, kh) -> chunks 1 + 2 kh, 2 + 2 kh
+  // (KT / 2 k steps each, over the chunk's nz/2 columns of the 2nz x 2nz block)
+  const int qa = te ? 0 : 1 + 2 * kh;
+  constexpr int KT = M::KT;
+  // prefetched vector entries of the group's next column: item it = gt + i GT -> (p, z, r)
+  cf pre[P::IPT][3];
+  auto fetch = [&](long k) {
+    const long hc = blockIdx.x + k * gridDim.x;
+    const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
+    const int iyB = a.pair ? (a.ny - h) % a.ny : h;
+    const bool two = a.pair && iyB != h;
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[nt][m][q] = 0.f;
-#pragma unroll
-  for (int kt = 0; kt < C::KT; ++kt) {
-    const uint4 aj = Ab[kt * 2 * nb];          // k column j = 8 kt + t
-    const uint4 aj4 = Ab[kt * 2 * nb + nb];    // k column j + 4
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const uint2 b0 = Sb[(nt * R3 + 8 * kt) * 8], b1 = Sb[(nt * R3 + 8 * kt + 4) * 8];
-      mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.x, b1.x);
-      mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.y, b1.y);
-      mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.x, b1.x);
-      mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.y, b1.y);
-    }
-  }
-  __syncthreads();   // every warp is done with the blocks: the outputs reuse their area
-  // epilogue: lane (g, t) holds vector 4 nt + t at slab rows 4g + 2m (c0, c1) and 4g + 2m + 1 (c2, c3)
-  {
-    const float bs = a.scales[hc * 2 + (te ? 0 : 1)];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int v = 4 * nt + t;
-      if (v >= V) continue;
-      const float sc = bs * isv[v];
-      cf* Ov = O + v * 5 * NZ + (te ? 0 : (kh == 0 ? NZ : 3 * NZ)) + slab * 32 + 4 * g;
-#pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        Ov[2 * m] = make_float2(acc[nt][m][0] * sc, acc[nt][m][1] * sc);
-        Ov[2 * m + 1] = make_float2(acc[nt][m][2] * sc, acc[nt][m][3] * sc);
+    for (int i = 0; i < P::IPT; ++i) {
+      const int it = gt + i * P::GT;
+      const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+      if (it < P::ITEMS && !(p && !two)) {
+        const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
+        pre[i][0] = x[base]; pre[i][1] = x[base + (long)NZ * ncols]; pre[i][2] = x[base + 2L * NZ * ncols];
+      } else {
+        pre[i][0] = czero(); pre[i][1] = czero(); pre[i][2] = czero();
       }
     }
-  }
-  __syncthreads();
-  // 5. rotate back and scatter
-  for (int it = tid; it < ITEMS; it += C::THREADS) {
-    const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
-    if (p && !two) continue;
-    const cf* Ov = O + (p * NR + r) * 5 * NZ;
-    const cf es = Ov[z], et = cadd(Ov[NZ + z], Ov[3 * NZ + z]), ez = cadd(Ov[2 * NZ + z], Ov[4 * NZ + z]);
-    const float* q = rot[p];
-    const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
-    y[base] = cadd(cscale(es, q[0]), cscale(et, q[2]));
-    y[base + (long)NZ * ncols] = cadd(cscale(es, q[1]), cscale(et, q[3]));
-    y[base + 2L * NZ * ncols] = ez;
+  };
+  if (grp < ncta) fetch(grp);
+  for (long k = grp; k < ncta; k += 2) {
+    const long hc = blockIdx.x + k * gridDim.x;
+    const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
+    const int iyB = a.pair ? (a.ny - h) % a.ny : h;
+    const bool two = a.pair && iyB != h;
+    if (gt < 2) {
+      const float kx = a.kx[ix], ky = a.ky[gt == 0 ? h : iyB];
+      const float kap = sqrtf(kx * kx + ky * ky);
+      const bool small = !(kap > 0.f);
+      rot[grp][gt][0] = small ? 0.f : -ky / kap;
+      rot[grp][gt][1] = small ? 1.f : kx / kap;
+      rot[grp][gt][2] = small ? 1.f : kx / kap;
+      rot[grp][gt][3] = small ? 0.f : ky / kap;
+    }
+    group_sync(grp, P::GT);
+    // 1. rotate the prefetched entries into X
+#pragma unroll
+    for (int i = 0; i < P::IPT; ++i) {
+      const int it = gt + i * P::GT;
+      if (it < P::ITEMS) {
+        const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+        cf* Xv = X + (p * NR + r) * R3;
+        const float* q = rot[grp][p];
+        Xv[z] = cadd(cscale(pre[i][0], q[0]), cscale(pre[i][1], q[1]));
+        Xv[NZ + z] = cadd(cscale(pre[i][0], q[2]), cscale(pre[i][1], q[3]));
+        Xv[2 * NZ + z] = pre[i][2];
+      }
+    }
+    group_sync(grp, P::GT);
+    // 2. per-vector power-of-two scale
+    for (int v = w; v < V; v += W) {
+      const cf* Xv = X + v * R3;
+      float m = 0.f;
+      for (int i = lane; i < R3; i += 32) m = fmaxf(m, fmaxf(fabsf(Xv[i].x), fabsf(Xv[i].y)));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (lane == 0) {
+        int e = 0;
+        if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);
+        isv[v] = pow2f(-min(120, max(-120, 14 - e)));
+      }
+    }
+    group_sync(grp, P::GT);
+    // 3. B' fragments
+    for (int it = gt; it < NT * R3 * 8; it += P::GT) {
+      const int nn = it & 7, jj = (it >> 3) % R3, nt = (it >> 3) / R3;
+      const int v = 4 * nt + (nn >> 1);
+      float p0 = 0.f, p1 = 0.f;
+      if (v < V) {
+        const float s = 1.f / isv[v];
+        const cf xv = X[v * R3 + jj];
+        if (nn & 1) { p0 = xv.y * s; p1 = xv.x * s; }
+        else { p0 = xv.x * s; p1 = -xv.y * s; }
+      }
+      const __half2 hi = __floats2half2_rn(p0, p1);
+      const __half2 lo = __floats2half2_rn(p0 - __low2float(hi), p1 - __high2float(hi));
+      S[it] = make_uint2(h2bits(hi), h2bits(lo));
+    }
+    group_sync(grp, P::GT);
+    // prefetch the group's next column while this one is multiplied
+    if (k + 2 < ncta) fetch(k + 2);
+    // 4. the chunks of this column, in order
+    float acc[NT][2][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[nt][m][q] = 0.f;
+    const uint2* Sb = S + (jjb + t) * 8 + g;
+    for (int q = 0; q < 5; ++q) {
+      const long c = 5 * k + q;
+      const int slot = (int)(c % RING);
+      bool ok = !*(volatile int*)&abort_flag;
+      if (ok) ok = mbar_wait_cycles(smem_u32a(&full[slot]), (unsigned)((c / RING) & 1), WAIT);
+      if (!ok && lane == 0) give_up();
+      ok = __all_sync(0xffffffffu, ok) && !*(volatile int*)&abort_flag;
+      if (ok && (q == qa || (!te && q == qa + 1))) {
+        // k steps of this chunk: TE all KT from column 0; TM KT / 2 from the chunk's first column
+        const int k0 = te ? 0 : (q - qa) * (KT / 2);
+        const int nk = te ? KT : KT / 2;
+        const uint4* Ab = reinterpret_cast<const uint4*>(
+            reinterpret_cast<const __half2*>(smem + (size_t)slot * P::CH) + t * nb + slab * 32 + 4 * g);
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+          if (kk >= nk) break;
+          const uint4 aj = Ab[kk * 2 * nb];
+          const uint4 aj4 = Ab[kk * 2 * nb + nb];
+          const int kt = k0 + kk;
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const uint2 b0 = Sb[(nt * R3 + 8 * kt) * 8], b1 = Sb[(nt * R3 + 8 * kt + 4) * 8];
+            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.x, b1.x);
+            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.y, b1.y);
+            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.x, b1.x);
+            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.y, b1.y);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32a(&empty[slot])) : "memory");
+    }
+    group_sync(grp, P::GT);   // X (under O) and S are no longer read
+    // 5. epilogue into O, then rotate back and scatter
+    {
+      const float bs = a.scales[hc * 2 + (te ? 0 : 1)];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int v = 4 * nt + t;
+        if (v >= V) continue;
+        const float sc = bs * isv[v];
+        cf* Ov = O + v * 5 * NZ + (te ? 0 : (kh == 0 ? NZ : 3 * NZ)) + slab * 32 + 4 * g;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          Ov[2 * m] = make_float2(acc[nt][m][0] * sc, acc[nt][m][1] * sc);
+          Ov[2 * m + 1] = make_float2(acc[nt][m][2] * sc, acc[nt][m][3] * sc);
+        }
+      }
+    }
+    group_sync(grp, P::GT);
+    for (int it = gt; it < P::ITEMS; it += P::GT) {
+      const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+      if (p && !two) continue;
+      const cf* Ov = O + (p * NR + r) * 5 * NZ;
+      const cf es = Ov[z], et = cadd(Ov[NZ + z], Ov[3 * NZ + z]), ez = cadd(Ov[2 * NZ + z], Ov[4 * NZ + z]);
+      const float* rq = rot[grp][p];
+      const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
+      y[base] = cadd(cscale(es, rq[0]), cscale(et, rq[2]));
+      y[base + (long)NZ * ncols] = cadd(cscale(es, rq[1]), cscale(et, rq[3]));
+      y[base + 2L * NZ * ncols] = ez;
+    }
+    group_sync(grp, P::GT);   // O and rot are free for the next column
   }
 }
 
@@ -694,17 +781,20 @@ int build_nz(psfd_plan_s* P) {
 
 template <int NZ, int NR>
 int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
-  if constexpr (NZ % 32 == 0 && mma_fits<NZ, NR>()) {
-    if (a.half && lay_apply_tc_enabled()) {
-      using C = MmaCfg<NZ, NR>;
-      static bool attr = false;
-      if (!attr) {
-        PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_mma<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if constexpr (NZ % 32 == 0) {
+    if (pipe_fits<NZ, NR>() && a.half && lay_apply_tc_enabled()) {
+      using C = PipeCfg<NZ, NR>;
+      static int nsm = 0;
+      if (!nsm) {
+        int dev = 0;
+        PSFD_CUDA_TRY(cudaGetDevice(&dev));
+        PSFD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_pipe<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)C::SMEM));
-        attr = true;
       }
-      const unsigned grid = (unsigned)layered_columns(P);
-      k_lay_apply_mma<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, x, y, P->ncols);
+      const long cols = layered_columns(P);
+      const unsigned grid = (unsigned)std::min<long>(cols, nsm);
+      k_lay_apply_pipe<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, x, y, P->ncols, cols);
       PSFD_CHECK_LAUNCH();
       return PSFD_OK;
     }
