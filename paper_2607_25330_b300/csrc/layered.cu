@@ -527,7 +527,7 @@ __device__ __forceinline__ void group_sync(int grp, int nthreads) {
 }
 
 template <int NZ, int NR>
-__global__ void __maxnreg__(96)
+__global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     k_lay_apply_pipe(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols, long ncolsB) {
   using P = PipeCfg<NZ, NR>;
   using M = MmaCfg<NZ, NR>;
