@@ -190,9 +190,9 @@ def test_tensor_core_apply_of_half_blocks(grid, monkeypatch):
     plan.layered_build()
     x1 = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64).cuda()
     x2 = torch.from_numpy(I.random_field(plan.shape, 4)).to(torch.complex64).cuda()
-    monkeypatch.setenv("PSFD_LAY_SIMT", "1")
+    monkeypatch.setenv("PSFD_LAY_TC", "0")
     y_simt = plan.precond(x1, flags=psfd.PSFD_LAYERED).cpu()
-    monkeypatch.setenv("PSFD_LAY_SIMT", "0")
+    monkeypatch.setenv("PSFD_LAY_TC", "1")
     y1 = plan.precond(x1, flags=psfd.PSFD_LAYERED).cpu()
     for r in range(plan.nrhs):
         assert rel_l2(y1[r], y_simt[r]) < 1e-5
@@ -219,6 +219,7 @@ def test_tensor_core_apply_wait_gives_up_and_reports(monkeypatch):
     plan.layered_storage(True)
     plan.layered_build()
     plan.device_status()
+    monkeypatch.setenv("PSFD_LAY_TC", "1")
     x = torch.from_numpy(I.random_field(plan.shape, 3)).to(torch.complex64).cuda()
     y_ref = plan.precond(x, flags=psfd.PSFD_LAYERED).cpu()
     monkeypatch.setenv("PSFD_TEST_LAY_NO_COPY", "1")
