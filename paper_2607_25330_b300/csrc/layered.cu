@@ -25,6 +25,7 @@
 #include <complex>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -54,12 +55,21 @@ struct LayArgs {
   int nx, ny, nz, zml;
   int pair;             // 1: blocks stored for rows 0 .. ny/2 only (ky and -ky share them)
   cf* mats;             // [ncols][5 nz^2]: TE inverse (nz^2) then TM inverse (4 nz^2), column-major
-  __half2* mats16;      // the same in half precision (storage 1), entries divided by the block's scale
+  __half2* mats16;      // the same in half precision (storage 1), entries divided by the block's scale,
+                        // each block laid out by half_pos
   float* scales;        // [ncols][2] power-of-two scale of the TE and TM block (storage 1)
   int half;             // 1: half-precision storage
   int* err;             // [0] set to 1 if a pivot vanished, [1] if an apply gave up waiting for its blocks
   int no_copy;          // test of the bounded wait: the tensor-core apply requests no blocks
 };
+
+// Half-precision block layout: column-major, with the 16-byte chunks of four rows permuted
+// within each column by an XOR with 2 (j mod 4) when the block size is a multiple of 32, so
+// that the tensor-core apply's fragment reads (lanes at columns j .. j + 3, same row chunk) fall
+// in distinct shared-memory banks.  Half2 index of entry (i, j) of an nb x nb block:
+__host__ __device__ __forceinline__ int half_pos(int i, int j, int nb) {
+  return (nb % 32 == 0) ? j * nb + ((((i >> 2) ^ (2 * (j & 3))) << 2) | (i & 3)) : j * nb + i;
+}
 
 __device__ __forceinline__ cf cdiv1(cf a) {  // 1 / a
   const float d = a.x * a.x + a.y * a.y;
@@ -268,7 +278,7 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
 #pragma unroll
     for (int v = 0; v < TT; ++v) {
       const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
-      out[(long)c * N + r] = __floats2half2_rn(T[u][v].x * inv, T[u][v].y * inv);
+      out[half_pos(r, c, N)] = __floats2half2_rn(T[u][v].x * inv, T[u][v].y * inv);
     }
 }
 
@@ -360,7 +370,7 @@ __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 
     for (int r = 0; r < NR; ++r) { A[q][r] = czero(); Bv[q][r] = czero(); }
   auto load = [&](int j, cf (&m)[RPT]) {
     if constexpr (HALF) {
-      const uint4 hv = __ldg(reinterpret_cast<const uint4*>(Mh + (long)j * nb + i));
+      const uint4 hv = __ldg(reinterpret_cast<const uint4*>(Mh + half_pos(i, j, nb)));   // rows i .. i + 3
       m[0] = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
       m[1] = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
       m[2] = __half22float2(*reinterpret_cast<const __half2*>(&hv.z));
@@ -480,102 +490,101 @@ template <int NZ, int NR>
 struct MmaCfg {
   static constexpr int V = 2 * NR;            // vector slots: rhs r of row h is r, of row ny - h is NR + r
   static constexpr int NT = (V + 3) / 4;      // n8 tiles (four vectors each)
-  static constexpr int TES = NZ / 32;         // TE slabs
-  static constexpr int TMS = NZ / 16;         // TM slabs
-  static constexpr int W = TES + 2 * TMS;     // warps
-  static constexpr int KT = NZ / 8;           // 8-column k steps per warp
+  static constexpr int TES = NZ / 32;         // TE slabs (warps) per column
+  static constexpr int TMS = NZ / 16;         // TM slabs (warps) per column
+  static constexpr int CW = TES + TMS;        // warps per column
+  static constexpr int KT = NZ / 8;           // 8-column k steps of a TE block
   static constexpr int R3 = 3 * NZ;           // stacked (s, t, z) rows
-  static constexpr size_t S_BYTES = (size_t)NT * R3 * 8 * sizeof(uint2);    // B' fragments (hi, lo)
-  static constexpr size_t X_BYTES = (size_t)V * R3 * sizeof(cf);             // rotated x, FP32
-  static constexpr size_t O_BYTES = (size_t)V * 5 * NZ * sizeof(cf);         // outputs (s, t, z + upper-k t, z)
+  static constexpr int R3P = R3 + 4;          // padded row count of the FP32 vectors in shared memory
 };
 
-// Persistent, pipelined form of the tensor-core apply.  One CTA per SM walks the stored block
-// columns blockIdx.x, + gridDim.x, ...; the column's blocks stream through a ring of shared-memory
-// slots of 4 nz^2 bytes (the TE block, then the TM block in four quarters of nz/2 columns each),
-// filled by bulk asynchronous copies that one producer lane issues as soon as a slot is released,
-// so the HBM stream never waits for the per-column work.  Two groups of worker warps take
-// alternate columns: while one gathers, splits and scatters, the other multiplies.  Each worker
-// warp passes every chunk of its column in order (waits until it has landed, uses it if it holds
-// the warp's k range, then releases it), and prefetches the vectors of its group's next column
-// into registers before the multiplications.  Every wait is bounded (about a second); the first
-// that gives up sets a CTA-wide abort flag, after which nothing waits any more, no copy is issued,
-// the producer waits (bounded) for the copies it issued, and the flag err[1] reports it.
+// Persistent, pipelined form of the tensor-core apply.  One CTA per SM walks pairs of stored
+// block columns (kx, kx + 1 of one row; blockIdx.x, + gridDim.x, ...).  The blocks stream through
+// a ring of ten shared-memory slots of 4 nz^2 bytes (per column: the TE block, then the TM block
+// in four quarters of nz/2 columns), filled by bulk asynchronous copies that one producer lane
+// issues as soon as a slot is released, so the HBM stream never waits for the per-pair work.
+// The vectors move as tensor-memory-access boxes (2 kx x 1 row x nz x 3 components x nrhs, 16 B
+// rows): the next pair's boxes are loaded while this pair is multiplied, and the result box is
+// stored from the same buffer, so neither touches the load/store pipe that the fragment reads
+// use.  Six warps per column (nz = 64: two TE slabs over 8 k steps, four TM slabs over 16): both
+// columns of a pair are multiplied at once, and slot 5 c + q only ever holds chunk q of column c
+// of a pair, consumed by the same warps every round (the parity of a phase identifies it only
+// within one phase).  Every wait is bounded (about a second); the first that gives up sets a
+// CTA-wide abort flag, after which nothing waits any more and no copy is issued, every copy
+// issued is waited for (bounded) before its issuer leaves, and err[1] reports it.
 template <int NZ, int NR>
 struct PipeCfg {
   using M = MmaCfg<NZ, NR>;
-  static constexpr int W = M::W;                                      // worker warps per group
-  static constexpr int GT = 32 * W;                                   // worker threads per group
-  static constexpr int THREADS = 32 + 2 * GT;                         // producer warp + two groups
+  static constexpr int WW = 2 * M::CW;                                // worker warps
+  static constexpr int WT = 32 * WW;                                  // worker threads
+  static constexpr int THREADS = 32 + WT;                             // + producer warp
   static constexpr size_t CH = (size_t)4 * NZ * NZ;                   // bytes per chunk (nz^2 half2)
-  static constexpr size_t G_BYTES = M::S_BYTES + M::O_BYTES + 16 * ((M::V * sizeof(float) + 15) / 16);
-  // two columns of chunks: slot 5 g + q only ever holds chunk q of group g's columns, so every
-  // wait on a slot's barriers follows the same warps' wait on the previous round (the parity
-  // of a phase identifies it only within one phase)
-  static constexpr int RING = 10;
-  static constexpr size_t SMEM = RING * CH + 2 * G_BYTES;
-  static constexpr int ITEMS = NR * NZ * 2;                           // gather items per column
-  static constexpr int IPT = (ITEMS + GT - 1) / GT;                   // per worker thread
-  static_assert(M::X_BYTES <= M::O_BYTES, "the rotated vectors reuse the output area");
+  static constexpr int RING = 10;                                     // one pair of columns
+  static constexpr size_t BOX = (size_t)2 * NZ * 3 * NR * sizeof(cf); // one row's vector box
+  static constexpr size_t XT_OFF = RING * CH;                         // [2 buffers][2 rows] boxes
+  static constexpr size_t X_OFF = XT_OFF + 4 * BOX;                   // [2 cols][V][R3P] FP32
+  static constexpr size_t O_OFF = X_OFF + (size_t)2 * M::V * M::R3P * sizeof(cf);   // [2][V][R3]
+  static constexpr size_t IS_OFF = O_OFF + (size_t)2 * M::V * M::R3 * sizeof(cf);   // [2][V] 1 / s
+  static constexpr size_t SMEM = IS_OFF + 2 * M::V * sizeof(float);
+  static constexpr int ITEMS = 2 * 2 * NR * NZ;                       // (col, row, rhs, z) per pair
 };
 
 template <int NZ, int NR>
 constexpr bool pipe_fits() { return PipeCfg<NZ, NR>::SMEM <= (size_t)227 * 1024; }
 
-__device__ __forceinline__ void group_sync(int grp, int nthreads) {
-  asm volatile("bar.sync %0, %1;" :: "r"(1 + grp), "r"(nthreads) : "memory");
+__device__ __forceinline__ void group_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
 }
 
 template <int NZ, int NR>
 __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
-    k_lay_apply_pipe(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols, long ncolsB) {
+    k_lay_apply_pipe(LayArgs a, const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ty,
+                     long npairs) {
   using P = PipeCfg<NZ, NR>;
   using M = MmaCfg<NZ, NR>;
-  constexpr int V = M::V, NT = M::NT, R3 = M::R3, W = P::W, RING = P::RING;
+  constexpr int V = M::V, NT = M::NT, R3 = M::R3, R3P = M::R3P, CW = M::CW, RING = P::RING;
   constexpr long long WAIT = 2000000000LL;   // SM clocks, about a second
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long full[RING], empty[RING];
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[RING], empty[RING], xfull[2];
   __shared__ int abort_flag;
-  __shared__ float rot[2][2][4];
+  __shared__ float rot[2][2][4];   // [col][row] sx, sy, tx, ty
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long ncta = blockIdx.x < ncolsB ? (ncolsB - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // columns here
+  const long npc = blockIdx.x < npairs ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // pairs here
   if (tid == 0) {
     for (int s = 0; s < RING; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32a(&full[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32a(&empty[s])), "r"(W) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32a(&empty[s])), "r"(CW) : "memory");
     }
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32a(&xfull[b])) : "memory");
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const long n = 3L * NZ * ncols;
+  auto aborted = [&]() { return *(volatile int*)&abort_flag != 0; };
   auto give_up = [&]() {
     if (atomicExch(&abort_flag, 1) == 0) atomicExch(a.err + 1, 1);
   };
   // ------------------------------------------------------------------ producer
   if (warp == 0) {
     if (lane == 0) {
-      long issued = 0;
-      for (long k = 0; k < ncta; ++k) {
-        const char* src = reinterpret_cast<const char*>(a.mats16 + (blockIdx.x + k * gridDim.x) * (5L * NZ * NZ));
-        for (int q = 0; q < 5; ++q) {
-          const long c = 5 * k + q;
-          const int slot = (int)(c % RING);
-          if (c >= RING && !mbar_wait_cycles(smem_u32a(&empty[slot]), (unsigned)(((c / RING) - 1) & 1), WAIT))
-            give_up();
-          if (*(volatile int*)&abort_flag) break;
+      long issued = 0;   // chunks c = 10 k + 5 col + q
+      for (long k = 0; k < npc && !aborted(); ++k) {
+        const char* src = reinterpret_cast<const char*>(a.mats16 + 2 * (blockIdx.x + k * gridDim.x) * (5L * NZ * NZ));
+        for (int sl = 0; sl < RING; ++sl) {
+          if (k > 0 && !mbar_wait_cycles(smem_u32a(&empty[sl]), (unsigned)((k - 1) & 1), WAIT)) give_up();
+          if (aborted()) break;
           if (!a.no_copy) {
-            const unsigned fb = smem_u32a(&full[slot]);
+            const unsigned fb = smem_u32a(&full[sl]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"((unsigned)P::CH)
                          : "memory");
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         :: "r"(smem_u32a(smem + (size_t)slot * P::CH)), "l"(src + q * P::CH), "r"((unsigned)P::CH),
+                         :: "r"(smem_u32a(smem + (size_t)sl * P::CH)), "l"(src + sl * P::CH), "r"((unsigned)P::CH),
                             "r"(fb)
                          : "memory");
-            issued = c + 1;
+            issued = 10 * k + sl + 1;
           }
         }
-        if (*(volatile int*)&abort_flag) break;
       }
       // leave only when every copy issued has landed (bounded)
       for (long c = issued > RING ? issued - RING : 0; c < issued; ++c)
@@ -584,153 +593,162 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     return;
   }
   // ------------------------------------------------------------------ workers
-  const int grp = (warp - 1) / W, w = (warp - 1) % W, gt = tid - 32 - grp * P::GT;
-  unsigned char* gbase = smem + (size_t)RING * P::CH + (size_t)grp * P::G_BYTES;
-  uint2* S = reinterpret_cast<uint2*>(gbase);                                  // [NT][R3][8]
-  cf* O = reinterpret_cast<cf*>(gbase + M::S_BYTES);                           // [V][5 NZ]
-  cf* X = O;                                                                   // [V][R3], before the MMAs
-  float* isv = reinterpret_cast<float*>(gbase + M::S_BYTES + M::O_BYTES);      // [V]
-  const int g = lane >> 2, t = lane & 3;
-  const bool te = w < M::TES;
-  const int slab = te ? w : (w - M::TES) % M::TMS, kh = te ? 0 : (w - M::TES) / M::TMS;
-  const int nb = te ? NZ : 2 * NZ;
-  const int jjb = te ? 0 : NZ + kh * NZ;
-  // the warp's chunks: TE -> chunk 0 (all KT k steps); TM (slab, kh) -> chunks 1 + 2 kh, 2 + 2 kh
-  // (KT / 2 k steps each, over the chunk's nz/2 columns of the 2nz x 2nz block)
-  const int qa = te ? 0 : 1 + 2 * kh;
-  constexpr int KT = M::KT;
-  // prefetched vector entries of the group's next column: item it = gt + i GT -> (p, z, r)
-  cf pre[P::IPT][3];
-  auto fetch = [&](long k) {
-    const long hc = blockIdx.x + k * gridDim.x;
-    const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
-    const int iyB = a.pair ? (a.ny - h) % a.ny : h;
-    const bool two = a.pair && iyB != h;
-#pragma unroll
-    for (int i = 0; i < P::IPT; ++i) {
-      const int it = gt + i * P::GT;
-      const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
-      if (it < P::ITEMS && !(p && !two)) {
-        const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
-        pre[i][0] = x[base]; pre[i][1] = x[base + (long)NZ * ncols]; pre[i][2] = x[base + 2L * NZ * ncols];
-      } else {
-        pre[i][0] = czero(); pre[i][1] = czero(); pre[i][2] = czero();
-      }
-    }
+  const int wt = tid - 32, ww = warp - 1;
+  const bool leader = wt == 0;
+  cf* X = reinterpret_cast<cf*>(smem + P::X_OFF);       // [2][V][R3P] rotated vectors
+  cf* O = reinterpret_cast<cf*>(smem + P::O_OFF);       // [2][V][R3] products
+  float* isv = reinterpret_cast<float*>(smem + P::IS_OFF);
+  auto xtile = [&](int b, int p) { return reinterpret_cast<cf*>(smem + P::XT_OFF + (size_t)(2 * b + p) * P::BOX); };
+  auto pair_rows = [&](long k, int& ix0, int& h, int& iyB, bool& two) {
+    const long hc = 2 * (blockIdx.x + k * gridDim.x);
+    ix0 = (int)(hc % a.nx); h = (int)(hc / a.nx);
+    iyB = a.pair ? (a.ny - h) % a.ny : h;
+    two = a.pair && iyB != h;
   };
-  if (grp < ncta) fetch(grp);
-  for (long k = grp; k < ncta; k += 2) {
-    const long hc = blockIdx.x + k * gridDim.x;
-    const int ix = (int)(hc % a.nx), h = (int)(hc / a.nx);
-    const int iyB = a.pair ? (a.ny - h) % a.ny : h;
-    const bool two = a.pair && iyB != h;
-    if (gt < 2) {
-      const float kx = a.kx[ix], ky = a.ky[gt == 0 ? h : iyB];
+  // the leader loads pair k's vector boxes into buffer k % 2
+  long xissued = 0;   // boxes requested: pair index + 1
+  auto load_boxes = [&](long k) {
+    int ix0, h, iyB; bool two;
+    pair_rows(k, ix0, h, iyB, two);
+    const int b = (int)(k & 1);
+    const unsigned mb = smem_u32a(&xfull[b]);
+    const unsigned bytes = (unsigned)((two ? 2 : 1) * P::BOX);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+    for (int p = 0; p < (two ? 2 : 1); ++p)
+      asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                   " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                   :: "r"(smem_u32a(xtile(b, p))), "l"(reinterpret_cast<const void*>(&tx)), "r"(ix0),
+                      "r"(p ? iyB : h), "r"(0), "r"(0), "r"(0), "r"(mb)
+                   : "memory");
+    xissued = k + 1;
+  };
+  if (leader && npc > 0 && !a.no_copy) load_boxes(0);
+  // this warp's column and slab
+  const int col = ww / CW, cw = ww % CW;
+  const bool te = cw < M::TES;
+  const int slab = te ? cw : cw - M::TES;
+  const int nb = te ? NZ : 2 * NZ;
+  const int g = lane >> 2, t = lane & 3;
+  const int q0 = te ? 0 : 1, nq = te ? 1 : 4;               // chunks: TE 0; TM 1 .. 4
+  constexpr int KQ_TE = NZ / 8, KQ_TM = NZ / 16;            // 8-column k steps per chunk
+  for (long k = 0; k < npc; ++k) {
+    int ix0, h, iyB; bool two;
+    pair_rows(k, ix0, h, iyB, two);
+    const int b = (int)(k & 1);
+    if (wt < 4) {   // rotation of (col, row) = (wt & 1, wt >> 1)
+      const int c = wt & 1, p = wt >> 1;
+      const float kx = a.kx[ix0 + c], ky = a.ky[p ? iyB : h];
       const float kap = sqrtf(kx * kx + ky * ky);
       const bool small = !(kap > 0.f);
-      rot[grp][gt][0] = small ? 0.f : -ky / kap;
-      rot[grp][gt][1] = small ? 1.f : kx / kap;
-      rot[grp][gt][2] = small ? 1.f : kx / kap;
-      rot[grp][gt][3] = small ? 0.f : ky / kap;
+      rot[c][p][0] = small ? 0.f : -ky / kap;
+      rot[c][p][1] = small ? 1.f : kx / kap;
+      rot[c][p][2] = small ? 1.f : kx / kap;
+      rot[c][p][3] = small ? 0.f : ky / kap;
     }
-    group_sync(grp, P::GT);
-    // 1. rotate the prefetched entries into X
-#pragma unroll
-    for (int i = 0; i < P::IPT; ++i) {
-      const int it = gt + i * P::GT;
-      if (it < P::ITEMS) {
-        const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
-        cf* Xv = X + (p * NR + r) * R3;
-        const float* q = rot[grp][p];
-        Xv[z] = cadd(cscale(pre[i][0], q[0]), cscale(pre[i][1], q[1]));
-        Xv[NZ + z] = cadd(cscale(pre[i][0], q[2]), cscale(pre[i][1], q[3]));
-        Xv[2 * NZ + z] = pre[i][2];
-      }
+    // this pair's boxes
+    bool ok = !aborted() && !a.no_copy;
+    if (ok) ok = mbar_wait_cycles(smem_u32a(&xfull[b]), (unsigned)((k >> 1) & 1), WAIT);
+    if (!ok && !a.no_copy && !aborted()) give_up();
+    group_sync(P::WT);
+    // the next pair's boxes go to the other buffer (its last store has been read: see below)
+    if (leader && k + 1 < npc && !aborted() && !a.no_copy) {
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      load_boxes(k + 1);
     }
-    group_sync(grp, P::GT);
+    // 1. rotate into X: item (c, p, r, z)
+    for (int it = wt; it < P::ITEMS; it += P::WT) {
+      const int z = it % NZ, r = (it / NZ) % NR, p = (it / (NZ * NR)) & 1, c = it / (NZ * NR * 2);
+      cf* Xv = X + (c * V + p * NR + r) * R3P;
+      if (p && !two) { Xv[z] = czero(); Xv[NZ + z] = czero(); Xv[2 * NZ + z] = czero(); continue; }
+      const cf* bx = xtile(b, p);
+      const cf ex = bx[((r * 3 + 0) * NZ + z) * 2 + c], ey = bx[((r * 3 + 1) * NZ + z) * 2 + c];
+      const cf ez = bx[((r * 3 + 2) * NZ + z) * 2 + c];
+      const float* q = rot[c][p];
+      Xv[z] = cadd(cscale(ex, q[0]), cscale(ey, q[1]));
+      Xv[NZ + z] = cadd(cscale(ex, q[2]), cscale(ey, q[3]));
+      Xv[2 * NZ + z] = ez;
+    }
+    group_sync(P::WT);
     // 2. per-vector power-of-two scale
-    for (int v = w; v < V; v += W) {
-      const cf* Xv = X + v * R3;
+    for (int cv = ww; cv < 2 * V; cv += P::WW) {
+      const cf* Xv = X + cv * R3P;
       float m = 0.f;
       for (int i = lane; i < R3; i += 32) m = fmaxf(m, fmaxf(fabsf(Xv[i].x), fabsf(Xv[i].y)));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
       if (lane == 0) {
         int e = 0;
-        if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);
-        isv[v] = pow2f(-min(120, max(-120, 14 - e)));
+        if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+        isv[cv] = pow2f(-min(120, max(-120, 14 - e)));   // s m in [2^13, 2^14)
       }
     }
-    group_sync(grp, P::GT);
-    // 3. B' fragments
-    for (int it = gt; it < NT * R3 * 8; it += P::GT) {
-      const int nn = it & 7, jj = (it >> 3) % R3, nt = (it >> 3) / R3;
-      const int v = 4 * nt + (nn >> 1);
-      float p0 = 0.f, p1 = 0.f;
-      if (v < V) {
-        const float s = 1.f / isv[v];
-        const cf xv = X[v * R3 + jj];
-        if (nn & 1) { p0 = xv.y * s; p1 = xv.x * s; }
-        else { p0 = xv.x * s; p1 = -xv.y * s; }
-      }
-      const __half2 hi = __floats2half2_rn(p0, p1);
-      const __half2 lo = __floats2half2_rn(p0 - __low2float(hi), p1 - __high2float(hi));
-      S[it] = make_uint2(h2bits(hi), h2bits(lo));
-    }
-    group_sync(grp, P::GT);
-    // prefetch the group's next column while this one is multiplied
-    if (k + 2 < ncta) fetch(k + 2);
-    // 4. the chunks of this column, in order
+    group_sync(P::WT);
+    // 3. multiply this warp's slab of its column: chunks q0 .. q0 + nq - 1 of slots 5 col + q
     float acc[NT][2][4];
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
       for (int m = 0; m < 2; ++m)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[nt][m][q] = 0.f;
-    const uint2* Sb = S + (jjb + t) * 8 + g;
-    for (int q = 0; q < 5; ++q) {
-      const long c = 5 * k + q;
-      const int slot = (int)(c % RING);
-      bool ok = !*(volatile int*)&abort_flag;
-      if (ok) ok = mbar_wait_cycles(smem_u32a(&full[slot]), (unsigned)((c / RING) & 1), WAIT);
-      if (!ok && lane == 0) give_up();
-      ok = __all_sync(0xffffffffu, ok) && !*(volatile int*)&abort_flag;
-      if (ok && (q == qa || (!te && q == qa + 1))) {
-        // k steps of this chunk: TE all KT from column 0; TM KT / 2 from the chunk's first column
-        const int k0 = te ? 0 : (q - qa) * (KT / 2);
-        const int nk = te ? KT : KT / 2;
-        const uint4* Ab = reinterpret_cast<const uint4*>(
-            reinterpret_cast<const __half2*>(smem + (size_t)slot * P::CH) + t * nb + slab * 32 + 4 * g);
+        for (int e = 0; e < 4; ++e) acc[nt][m][e] = 0.f;
+    // B' columns of lane (g, t): n = g -> vector 4 nt + g / 2, (re, im) part g & 1
+    float sv[NT];
+    const cf* Xg[NT];
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) {
-          if (kk >= nk) break;
+    for (int nt = 0; nt < NT; ++nt) {
+      const int v = 4 * nt + (g >> 1);
+      sv[nt] = v < V ? 1.f / isv[col * V + v] : 0.f;
+      Xg[nt] = X + (col * V + (v < V ? v : 0)) * R3P + (te ? 0 : NZ) + t;
+    }
+    auto bfrag = [&](const cf* xp, float s, unsigned& hi, unsigned& lo) {
+      const cf xv = *xp;
+      const float p0 = (g & 1) ? xv.y * s : xv.x * s, p1 = (g & 1) ? xv.x * s : -xv.y * s;
+      const __half2 h2 = __floats2half2_rn(p0, p1);
+      hi = h2bits(h2);
+      lo = h2bits(__floats2half2_rn(p0 - __low2float(h2), p1 - __high2float(h2)));
+    };
+    for (int qq = 0; qq < 5; ++qq) {
+      const int sl = col * 5 + qq;
+      bool okc = !aborted();
+      if (okc) okc = mbar_wait_cycles(smem_u32a(&full[sl]), (unsigned)(k & 1), WAIT);
+      if (!okc && lane == 0) give_up();
+      okc = __all_sync(0xffffffffu, okc) && !aborted();
+      if (okc && qq >= q0 && qq < q0 + nq) {
+        const int kq = te ? KQ_TE : KQ_TM;
+        const int kbase = te ? 0 : (qq - 1) * KQ_TM;         // first 8-column step of this chunk
+        // lane (g, t): rows 4g .. 4g + 3 of the slab (chunk g ^ 2t of 4 rows), columns 8 kk + t, + 4
+        const uint4* Ab = reinterpret_cast<const uint4*>(
+            reinterpret_cast<const __half2*>(smem + (size_t)sl * P::CH) + t * nb + slab * 32 + 4 * (g ^ (2 * t)));
+#pragma unroll 4
+        for (int kk = 0; kk < kq; ++kk) {
           const uint4 aj = Ab[kk * 2 * nb];
           const uint4 aj4 = Ab[kk * 2 * nb + nb];
-          const int kt = k0 + kk;
+          const int j = 8 * (kbase + kk);
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
-            const uint2 b0 = Sb[(nt * R3 + 8 * kt) * 8], b1 = Sb[(nt * R3 + 8 * kt + 4) * 8];
-            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.x, b1.x);
-            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, b0.y, b1.y);
-            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.x, b1.x);
-            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, b0.y, b1.y);
+            unsigned h0, l0, h1, l1;
+            bfrag(Xg[nt] + j, sv[nt], h0, l0);
+            bfrag(Xg[nt] + j + 4, sv[nt], h1, l1);
+            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, h0, h1);
+            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, l0, l1);
+            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, h0, h1);
+            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, l0, l1);
           }
         }
       }
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32a(&empty[slot])) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32a(&empty[sl])) : "memory");
     }
-    group_sync(grp, P::GT);   // X (under O) and S are no longer read
-    // 5. epilogue into O, then rotate back and scatter
+    // 4. products into O (rows of the stacked s, t, z vector): lane (g, t) holds vector 4 nt + t
+    //    at slab rows 4g + 2m (c0, c1) and 4g + 2m + 1 (c2, c3)
     {
-      const float bs = a.scales[hc * 2 + (te ? 0 : 1)];
+      const float bs = a.scales[(2 * (blockIdx.x + k * gridDim.x) + col) * 2 + (te ? 0 : 1)];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int v = 4 * nt + t;
         if (v >= V) continue;
-        const float sc = bs * isv[v];
-        cf* Ov = O + v * 5 * NZ + (te ? 0 : (kh == 0 ? NZ : 3 * NZ)) + slab * 32 + 4 * g;
+        const float sc = bs * isv[col * V + v];
+        cf* Ov = O + (col * V + v) * R3 + (te ? 0 : NZ) + slab * 32 + 4 * g;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
           Ov[2 * m] = make_float2(acc[nt][m][0] * sc, acc[nt][m][1] * sc);
@@ -738,20 +756,63 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
         }
       }
     }
-    group_sync(grp, P::GT);
-    for (int it = gt; it < P::ITEMS; it += P::GT) {
-      const int p = it & 1, z = (it >> 1) % NZ, r = (it >> 1) / NZ;
+    group_sync(P::WT);
+    // 5. rotate back into the box buffer b (its input was consumed in step 1) and store it
+    for (int it = wt; it < P::ITEMS; it += P::WT) {
+      const int z = it % NZ, r = (it / NZ) % NR, p = (it / (NZ * NR)) & 1, c = it / (NZ * NR * 2);
       if (p && !two) continue;
-      const cf* Ov = O + (p * NR + r) * 5 * NZ;
-      const cf es = Ov[z], et = cadd(Ov[NZ + z], Ov[3 * NZ + z]), ez = cadd(Ov[2 * NZ + z], Ov[4 * NZ + z]);
-      const float* rq = rot[grp][p];
-      const long base = (long)r * n + (long)z * ncols + (long)(p ? iyB : h) * a.nx + ix;
-      y[base] = cadd(cscale(es, rq[0]), cscale(et, rq[2]));
-      y[base + (long)NZ * ncols] = cadd(cscale(es, rq[1]), cscale(et, rq[3]));
-      y[base + 2L * NZ * ncols] = ez;
+      const cf* Ov = O + (c * V + p * NR + r) * R3;
+      const cf es = Ov[z], et = Ov[NZ + z], ez = Ov[2 * NZ + z];
+      const float* q = rot[c][p];
+      cf* by = xtile(b, p);
+      by[((r * 3 + 0) * NZ + z) * 2 + c] = cadd(cscale(es, q[0]), cscale(et, q[2]));
+      by[((r * 3 + 1) * NZ + z) * 2 + c] = cadd(cscale(es, q[1]), cscale(et, q[3]));
+      by[((r * 3 + 2) * NZ + z) * 2 + c] = ez;
     }
-    group_sync(grp, P::GT);   // O and rot are free for the next column
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor store
+    group_sync(P::WT);
+    if (leader && !aborted()) {
+      for (int p = 0; p < (two ? 2 : 1); ++p)
+        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];"
+                     :: "l"(reinterpret_cast<const void*>(&ty)), "r"(ix0), "r"(p ? iyB : h), "r"(0), "r"(0), "r"(0),
+                        "r"(smem_u32a(xtile(b, p)))
+                     : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
   }
+  if (leader) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete before the CTA leaves
+    // boxes requested but not consumed (abort): wait for them (bounded)
+    if (xissued > 0) mbar_wait_cycles(smem_u32a(&xfull[(xissued - 1) & 1]), (unsigned)(((xissued - 1) >> 1) & 1), WAIT);
+  }
+}
+
+// Tensor map of a vector [nrhs][3][nz][ny][nx] (complex64, as 8-byte elements) with boxes of
+// 2 kx x 1 row x nz x 3 x nrhs; false if the driver entry point is missing or the encoding is
+// refused (an address not 16-byte aligned), in which case the SIMT apply runs.
+bool vector_box_map(const psfd_plan_s* P, int nz, int nrhs, const void* base, CUtensorMap* m) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<Encode>(fn);
+  }
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t e = sizeof(cf);
+  const cuuint64_t dims[5] = {(cuuint64_t)P->nx, (cuuint64_t)P->ny, (cuuint64_t)nz, 3, (cuuint64_t)nrhs};
+  const cuuint64_t strides[4] = {e * P->nx, e * P->ncols, e * P->ncols * nz, e * P->ncols * nz * 3};
+  const cuuint32_t box[5] = {2, 1, (cuuint32_t)nz, 3, (cuuint32_t)nrhs};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 LayArgs lay_args(psfd_plan_s* P) {
@@ -784,19 +845,22 @@ int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
   if constexpr (NZ % 32 == 0) {
     if (pipe_fits<NZ, NR>() && a.half && lay_apply_tc_enabled()) {
       using C = PipeCfg<NZ, NR>;
-      static int nsm = 0;
-      if (!nsm) {
-        int dev = 0;
-        PSFD_CUDA_TRY(cudaGetDevice(&dev));
-        PSFD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_pipe<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::SMEM));
+      CUtensorMap tx, ty;
+      if (vector_box_map(P, NZ, NR, x, &tx) && vector_box_map(P, NZ, NR, y, &ty)) {
+        static int nsm = 0;
+        if (!nsm) {
+          int dev = 0;
+          PSFD_CUDA_TRY(cudaGetDevice(&dev));
+          PSFD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+          PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_pipe<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM));
+        }
+        const long npairs = layered_columns(P) / 2;
+        const unsigned grid = (unsigned)std::min<long>(npairs, nsm);
+        k_lay_apply_pipe<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, tx, ty, npairs);
+        PSFD_CHECK_LAUNCH();
+        return PSFD_OK;
       }
-      const long cols = layered_columns(P);
-      const unsigned grid = (unsigned)std::min<long>(cols, nsm);
-      k_lay_apply_pipe<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, x, y, P->ncols, cols);
-      PSFD_CHECK_LAUNCH();
-      return PSFD_OK;
     }
   }
   const size_t smem = (size_t)2 * LAY_GROUP * 3 * NZ * NR * sizeof(cf);
