@@ -192,12 +192,12 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * solve converges, never the solution.  psfd_layered_refresh rebuilds them only
  * when some plane's mean fill moved by more than max_shift (fill fraction units)
  * since the last build, and sets *rebuilt (nullable) to 1 if it did.
- * With half storage, nz a multiple of 32 (nz = 64: nrhs <= 2) and PSFD_LAY_TC=1
- * in the environment, P is applied on the tensor cores: the columns' blocks
- * stream through shared memory in bulk copies and are multiplied as f16
- * matrices with FP32 accumulation, the vector entering as a two-term f16 split
- * with a power-of-two scale per column (about 22 bits), so P stays linear to
- * FP32 level.  The default is the FP32 SIMT kernel.
+ * With half storage and nz a multiple of 32 (nz = 64: nrhs <= 2) P is applied on
+ * the tensor cores: the columns' blocks stream through shared memory in bulk
+ * copies and are multiplied as f16 matrices with FP32 accumulation, the vector
+ * entering as a two-term f16 split with a power-of-two scale per column (about
+ * 22 bits), so P stays linear to FP32 level.  PSFD_LAY_TC=0 in the environment
+ * selects the FP32 SIMT kernel.
  * Supported for nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else
  * PSFD_ERR_ARG / psfd_layered_bytes() = 0); PSFD_ERR_STATE before
  * psfd_background; PSFD_ERR_BREAKDOWN if a block is singular.  Both synchronise

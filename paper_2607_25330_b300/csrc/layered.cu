@@ -36,11 +36,11 @@ using zc = std::complex<double>;
 constexpr int LAY_THREADS = 256;   // 16 x 16 thread grid over an N x N matrix
 constexpr int LAY_GROUP = 4;       // lateral columns (consecutive kx) per apply CTA
 
-// PSFD_LAY_TC=1 applies the half-precision blocks on the tensor cores (nz a multiple of 32);
-// the default is the SIMT kernel, measured faster on 128x128x64 (0.20 vs 0.30 ms per apply)
+// the half-precision blocks are applied on the tensor cores where the pipeline fits (nz a multiple
+// of 32); PSFD_LAY_TC=0 selects the SIMT kernel
 bool lay_apply_tc_enabled() {
   const char* e = getenv("PSFD_LAY_TC");
-  return e && e[0] == '1';
+  return !(e && e[0] == '0');
 }
 
 struct LayArgs {
@@ -521,8 +521,9 @@ struct PipeCfg {
   static constexpr size_t CH = (size_t)4 * NZ * NZ;                   // bytes per chunk (nz^2 half2)
   static constexpr int RING = 10;                                     // one pair of columns
   static constexpr size_t BOX = (size_t)2 * NZ * 3 * NR * sizeof(cf); // one row's vector box
-  static constexpr size_t XT_OFF = RING * CH;                         // [2 buffers][2 rows] boxes
-  static constexpr size_t X_OFF = XT_OFF + 4 * BOX;                   // [2 cols][V][R3P] FP32
+  static constexpr int NBUF = 3;                                      // box buffers (pairs k, k + 1, k - 1's store)
+  static constexpr size_t XT_OFF = RING * CH;                         // [NBUF][2 rows] boxes
+  static constexpr size_t X_OFF = XT_OFF + 2 * NBUF * BOX;            // [2 cols][V][R3P] FP32
   static constexpr size_t O_OFF = X_OFF + (size_t)2 * M::V * M::R3P * sizeof(cf);   // [2][V][R3]
   static constexpr size_t IS_OFF = O_OFF + (size_t)2 * M::V * M::R3 * sizeof(cf);   // [2][V] 1 / s
   static constexpr size_t SMEM = IS_OFF + 2 * M::V * sizeof(float);
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
   constexpr int V = M::V, NT = M::NT, R3 = M::R3, R3P = M::R3P, CW = M::CW, RING = P::RING;
   constexpr long long WAIT = 2000000000LL;   // SM clocks, about a second
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long full[RING], empty[RING], xfull[2];
+  __shared__ __align__(8) unsigned long long full[RING], empty[RING], xfull[P::NBUF];
   __shared__ int abort_flag;
   __shared__ float rot[2][2][4];   // [col][row] sx, sy, tx, ty
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -555,7 +556,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32a(&full[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32a(&empty[s])), "r"(CW) : "memory");
     }
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < P::NBUF; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32a(&xfull[b])) : "memory");
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -605,12 +606,12 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     iyB = a.pair ? (a.ny - h) % a.ny : h;
     two = a.pair && iyB != h;
   };
-  // the leader loads pair k's vector boxes into buffer k % 2
+  // the leader loads pair k's vector boxes into buffer k % NBUF
   long xissued = 0;   // boxes requested: pair index + 1
   auto load_boxes = [&](long k) {
     int ix0, h, iyB; bool two;
     pair_rows(k, ix0, h, iyB, two);
-    const int b = (int)(k & 1);
+    const int b = (int)(k % P::NBUF);
     const unsigned mb = smem_u32a(&xfull[b]);
     const unsigned bytes = (unsigned)((two ? 2 : 1) * P::BOX);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
   for (long k = 0; k < npc; ++k) {
     int ix0, h, iyB; bool two;
     pair_rows(k, ix0, h, iyB, two);
-    const int b = (int)(k & 1);
+    const int b = (int)(k % P::NBUF);
     if (wt < 4) {   // rotation of (col, row) = (wt & 1, wt >> 1)
       const int c = wt & 1, p = wt >> 1;
       const float kx = a.kx[ix0 + c], ky = a.ky[p ? iyB : h];
@@ -647,12 +648,13 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     }
     // this pair's boxes
     bool ok = !aborted() && !a.no_copy;
-    if (ok) ok = mbar_wait_cycles(smem_u32a(&xfull[b]), (unsigned)((k >> 1) & 1), WAIT);
+    if (ok) ok = mbar_wait_cycles(smem_u32a(&xfull[b]), (unsigned)((k / P::NBUF) & 1), WAIT);
     if (!ok && !a.no_copy && !aborted()) give_up();
     group_sync(P::WT);
-    // the next pair's boxes go to the other buffer (its last store has been read: see below)
+    // the next pair's boxes go to buffer (k + 1) % NBUF, last used by pair k - 2, whose store
+    // (all but the most recent group) has been read
     if (leader && k + 1 < npc && !aborted() && !a.no_copy) {
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
       load_boxes(k + 1);
     }
     // 1. rotate into X: item (c, p, r, z)
@@ -684,13 +686,17 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     }
     group_sync(P::WT);
     // 3. multiply this warp's slab of its column: chunks q0 .. q0 + nq - 1 of slots 5 col + q
-    float acc[NT][2][4];
+    // four independent accumulations per tile (hi and lo products, even and odd k steps), summed
+    // at the end, so consecutive MMAs do not wait on each other
+    float acc[NT][2][4][4];
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
       for (int m = 0; m < 2; ++m)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[nt][m][e] = 0.f;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[nt][m][u][e] = 0.f;
     // B' columns of lane (g, t): n = g -> vector 4 nt + g / 2, (re, im) part g & 1
     float sv[NT];
     const cf* Xg[NT];
@@ -719,20 +725,24 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
         // lane (g, t): rows 4g .. 4g + 3 of the slab (chunk g ^ 2t of 4 rows), columns 8 kk + t, + 4
         const uint4* Ab = reinterpret_cast<const uint4*>(
             reinterpret_cast<const __half2*>(smem + (size_t)sl * P::CH) + t * nb + slab * 32 + 4 * (g ^ (2 * t)));
-#pragma unroll 4
-        for (int kk = 0; kk < kq; ++kk) {
-          const uint4 aj = Ab[kk * 2 * nb];
-          const uint4 aj4 = Ab[kk * 2 * nb + nb];
-          const int j = 8 * (kbase + kk);
+#pragma unroll 2
+        for (int k2 = 0; k2 < kq; k2 += 2) {
 #pragma unroll
-          for (int nt = 0; nt < NT; ++nt) {
-            unsigned h0, l0, h1, l1;
-            bfrag(Xg[nt] + j, sv[nt], h0, l0);
-            bfrag(Xg[nt] + j + 4, sv[nt], h1, l1);
-            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, h0, h1);
-            mma_f16(acc[nt][0], aj.x, aj.y, aj4.x, aj4.y, l0, l1);
-            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, h0, h1);
-            mma_f16(acc[nt][1], aj.z, aj.w, aj4.z, aj4.w, l0, l1);
+          for (int par = 0; par < 2; ++par) {
+            const int kk = k2 + par;
+            const uint4 aj = Ab[kk * 2 * nb];
+            const uint4 aj4 = Ab[kk * 2 * nb + nb];
+            const int j = 8 * (kbase + kk);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              unsigned h0, l0, h1, l1;
+              bfrag(Xg[nt] + j, sv[nt], h0, l0);
+              bfrag(Xg[nt] + j + 4, sv[nt], h1, l1);
+              mma_f16(acc[nt][0][2 * par], aj.x, aj.y, aj4.x, aj4.y, h0, h1);
+              mma_f16(acc[nt][0][2 * par + 1], aj.x, aj.y, aj4.x, aj4.y, l0, l1);
+              mma_f16(acc[nt][1][2 * par], aj.z, aj.w, aj4.z, aj4.w, h0, h1);
+              mma_f16(acc[nt][1][2 * par + 1], aj.z, aj.w, aj4.z, aj4.w, l0, l1);
+            }
           }
         }
       }
@@ -751,8 +761,12 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
         cf* Ov = O + (col * V + v) * R3 + (te ? 0 : NZ) + slab * 32 + 4 * g;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
-          Ov[2 * m] = make_float2(acc[nt][m][0] * sc, acc[nt][m][1] * sc);
-          Ov[2 * m + 1] = make_float2(acc[nt][m][2] * sc, acc[nt][m][3] * sc);
+          float f[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            f[e] = (acc[nt][m][0][e] + acc[nt][m][2][e]) + (acc[nt][m][1][e] + acc[nt][m][3][e]);
+          Ov[2 * m] = make_float2(f[0] * sc, f[1] * sc);
+          Ov[2 * m + 1] = make_float2(f[2] * sc, f[3] * sc);
         }
       }
     }
@@ -783,7 +797,8 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
   if (leader) {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete before the CTA leaves
     // boxes requested but not consumed (abort): wait for them (bounded)
-    if (xissued > 0) mbar_wait_cycles(smem_u32a(&xfull[(xissued - 1) & 1]), (unsigned)(((xissued - 1) >> 1) & 1), WAIT);
+    if (xissued > 0)
+      mbar_wait_cycles(smem_u32a(&xfull[(xissued - 1) % P::NBUF]), (unsigned)(((xissued - 1) / P::NBUF) & 1), WAIT);
   }
 }
 
