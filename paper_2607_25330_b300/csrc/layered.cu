@@ -495,7 +495,9 @@ struct MmaCfg {
   static constexpr int CW = TES + TMS;        // warps per column
   static constexpr int KT = NZ / 8;           // 8-column k steps of a TE block
   static constexpr int R3 = 3 * NZ;           // stacked (s, t, z) rows
-  static constexpr int R3P = R3 + 4;          // padded row count of the FP32 vectors in shared memory
+  static constexpr int VS = 4 * NT;           // vector slots of the B' operand (unused ones zero)
+  static constexpr int R3S = R3 + 4;          // row stride of the split vectors (16 B rows; 64 mod 128 B)
+  static constexpr int R3O = R3 + 1;          // row stride of the products (8 B rows; 8 mod 128 B)
 };
 
 // Persistent, pipelined form of the tensor-core apply.  One CTA per SM walks pairs of stored
@@ -521,11 +523,11 @@ struct PipeCfg {
   static constexpr size_t CH = (size_t)4 * NZ * NZ;                   // bytes per chunk (nz^2 half2)
   static constexpr int RING = 10;                                     // one pair of columns
   static constexpr size_t BOX = (size_t)2 * NZ * 3 * NR * sizeof(cf); // one row's vector box
-  static constexpr int NBUF = 3;                                      // box buffers (pairs k, k + 1, k - 1's store)
+  static constexpr int NBUF = 2;                                      // box buffers (pairs k, k + 1)
   static constexpr size_t XT_OFF = RING * CH;                         // [NBUF][2 rows] boxes
-  static constexpr size_t X_OFF = XT_OFF + 2 * NBUF * BOX;            // [2 cols][V][R3P] FP32
-  static constexpr size_t O_OFF = X_OFF + (size_t)2 * M::V * M::R3P * sizeof(cf);   // [2][V][R3]
-  static constexpr size_t IS_OFF = O_OFF + (size_t)2 * M::V * M::R3 * sizeof(cf);   // [2][V] 1 / s
+  static constexpr size_t XS_OFF = XT_OFF + 2 * NBUF * BOX;           // [2 cols][VS][R3S] uint4
+  static constexpr size_t O_OFF = XS_OFF + (size_t)2 * M::VS * M::R3S * sizeof(uint4);   // [2][V][R3O]
+  static constexpr size_t IS_OFF = O_OFF + (size_t)2 * M::V * M::R3O * sizeof(cf);       // [2][V] 1 / s
   static constexpr size_t SMEM = IS_OFF + 2 * M::V * sizeof(float);
   static constexpr int ITEMS = 2 * 2 * NR * NZ;                       // (col, row, rhs, z) per pair
 };
@@ -543,7 +545,8 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
                      long npairs) {
   using P = PipeCfg<NZ, NR>;
   using M = MmaCfg<NZ, NR>;
-  constexpr int V = M::V, NT = M::NT, R3 = M::R3, R3P = M::R3P, CW = M::CW, RING = P::RING;
+  constexpr int V = M::V, NT = M::NT, R3 = M::R3, VS = M::VS, R3S = M::R3S, R3O = M::R3O, CW = M::CW;
+  constexpr int RING = P::RING;
   constexpr long long WAIT = 2000000000LL;   // SM clocks, about a second
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full[RING], empty[RING], xfull[P::NBUF];
@@ -596,8 +599,10 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
   // ------------------------------------------------------------------ workers
   const int wt = tid - 32, ww = warp - 1;
   const bool leader = wt == 0;
-  cf* X = reinterpret_cast<cf*>(smem + P::X_OFF);       // [2][V][R3P] rotated vectors
-  cf* O = reinterpret_cast<cf*>(smem + P::O_OFF);       // [2][V][R3] products
+  // split vectors: entry (col, v, jj) = {hi, lo} of (Re w, -Im w), then {hi, lo} of (Im w, Re w),
+  // w = s x the rotated, scaled entry; lane (g, t) of an MMA warp reads the half with o = g & 1
+  uint4* XS = reinterpret_cast<uint4*>(smem + P::XS_OFF);
+  cf* O = reinterpret_cast<cf*>(smem + P::O_OFF);       // [2][V][R3O] products
   float* isv = reinterpret_cast<float*>(smem + P::IS_OFF);
   auto xtile = [&](int b, int p) { return reinterpret_cast<cf*>(smem + P::XT_OFF + (size_t)(2 * b + p) * P::BOX); };
   auto pair_rows = [&](long k, int& ix0, int& h, int& iyB, bool& two) {
@@ -624,6 +629,10 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     xissued = k + 1;
   };
   if (leader && npc > 0 && !a.no_copy) load_boxes(0);
+  for (int i = wt; i < 2 * (VS - V) * R3S; i += P::WT) {   // slots past the vectors stay zero
+    const int c = i / ((VS - V) * R3S), e = i % ((VS - V) * R3S);
+    XS[(c * VS + V) * R3S + e] = make_uint4(0u, 0u, 0u, 0u);
+  }
   // this warp's column and slab
   const int col = ww / CW, cw = ww % CW;
   const bool te = cw < M::TES;
@@ -651,37 +660,57 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     if (ok) ok = mbar_wait_cycles(smem_u32a(&xfull[b]), (unsigned)((k / P::NBUF) & 1), WAIT);
     if (!ok && !a.no_copy && !aborted()) give_up();
     group_sync(P::WT);
-    // the next pair's boxes go to buffer (k + 1) % NBUF, last used by pair k - 2, whose store
-    // (all but the most recent group) has been read
+    // the next pair's boxes go to the other buffer, once pair k - 1's store has read it
     if (leader && k + 1 < npc && !aborted() && !a.no_copy) {
-      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       load_boxes(k + 1);
     }
-    // 1. rotate into X: item (c, p, r, z)
+    // 1. per-vector power-of-two scale from the raw entries: a rotated entry is at most sqrt 2
+    //    times the largest raw one (|sx| + |sy| <= sqrt 2), so s puts the rotated vector below
+    //    2^14 and its largest entry at or above 2^12 (one bit of the split at most is lost)
+    for (int cv = ww; cv < 2 * V; cv += P::WW) {
+      const int c = cv / V, v = cv % V, p = v / NR, r = v % NR;
+      float m = 0.f;
+      if (!(p && !two)) {
+        const cf* bx = xtile(b, p);
+        for (int i = lane; i < R3; i += 32) {
+          const cf e = bx[((r * 3 + i / NZ) * NZ + i % NZ) * 2 + c];
+          m = fmaxf(m, fmaxf(fabsf(e.x), fabsf(e.y)));
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (lane == 0) {
+        const float mb = m * 1.41421356f;
+        int e = 0;
+        if (mb > 0.f && mb <= 3.0e38f) frexpf(mb, &e);   // mb = f 2^e, f in [0.5, 1)
+        isv[cv] = pow2f(-min(120, max(-120, 14 - e)));     // s mb in [2^13, 2^14)
+      }
+    }
+    group_sync(P::WT);
+    // 2. rotate, scale and split into XS: item (c, p, r, z)
     for (int it = wt; it < P::ITEMS; it += P::WT) {
       const int z = it % NZ, r = (it / NZ) % NR, p = (it / (NZ * NR)) & 1, c = it / (NZ * NR * 2);
-      cf* Xv = X + (c * V + p * NR + r) * R3P;
-      if (p && !two) { Xv[z] = czero(); Xv[NZ + z] = czero(); Xv[2 * NZ + z] = czero(); continue; }
+      const int v = p * NR + r;
+      uint4* Xv = XS + (c * VS + v) * R3S;
+      if (p && !two) {
+        Xv[z] = Xv[NZ + z] = Xv[2 * NZ + z] = make_uint4(0u, 0u, 0u, 0u);
+        continue;
+      }
       const cf* bx = xtile(b, p);
       const cf ex = bx[((r * 3 + 0) * NZ + z) * 2 + c], ey = bx[((r * 3 + 1) * NZ + z) * 2 + c];
       const cf ez = bx[((r * 3 + 2) * NZ + z) * 2 + c];
       const float* q = rot[c][p];
-      Xv[z] = cadd(cscale(ex, q[0]), cscale(ey, q[1]));
-      Xv[NZ + z] = cadd(cscale(ex, q[2]), cscale(ey, q[3]));
-      Xv[2 * NZ + z] = ez;
-    }
-    group_sync(P::WT);
-    // 2. per-vector power-of-two scale
-    for (int cv = ww; cv < 2 * V; cv += P::WW) {
-      const cf* Xv = X + cv * R3P;
-      float m = 0.f;
-      for (int i = lane; i < R3; i += 32) m = fmaxf(m, fmaxf(fabsf(Xv[i].x), fabsf(Xv[i].y)));
+      const float sc = 1.f / isv[c * V + v];
+      const cf w[3] = {cscale(cadd(cscale(ex, q[0]), cscale(ey, q[1])), sc),
+                       cscale(cadd(cscale(ex, q[2]), cscale(ey, q[3])), sc), cscale(ez, sc)};
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-      if (lane == 0) {
-        int e = 0;
-        if (m > 0.f && m <= 3.0e38f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
-        isv[cv] = pow2f(-min(120, max(-120, 14 - e)));   // s m in [2^13, 2^14)
+      for (int comp = 0; comp < 3; ++comp) {
+        const __half hr = __float2half_rn(w[comp].x), hm = __float2half_rn(w[comp].y);
+        const __half lr = __float2half_rn(w[comp].x - __half2float(hr));
+        const __half lm = __float2half_rn(w[comp].y - __half2float(hm));
+        Xv[comp * NZ + z] = make_uint4(h2bits(__halves2half2(hr, __hneg(hm))), h2bits(__halves2half2(lr, __hneg(lm))),
+                                       h2bits(__halves2half2(hm, hr)), h2bits(__halves2half2(lm, lr)));
       }
     }
     group_sync(P::WT);
@@ -697,22 +726,12 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int e = 0; e < 4; ++e) acc[nt][m][u][e] = 0.f;
-    // B' columns of lane (g, t): n = g -> vector 4 nt + g / 2, (re, im) part g & 1
-    float sv[NT];
-    const cf* Xg[NT];
+    // B' columns of lane (g, t): n = g -> vector 4 nt + g / 2, (re, im) part g & 1: the (hi, lo)
+    // pair at uint2 2 (row index) + (g & 1) of XS
+    const uint2* Xg[NT];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int v = 4 * nt + (g >> 1);
-      sv[nt] = v < V ? 1.f / isv[col * V + v] : 0.f;
-      Xg[nt] = X + (col * V + (v < V ? v : 0)) * R3P + (te ? 0 : NZ) + t;
-    }
-    auto bfrag = [&](const cf* xp, float s, unsigned& hi, unsigned& lo) {
-      const cf xv = *xp;
-      const float p0 = (g & 1) ? xv.y * s : xv.x * s, p1 = (g & 1) ? xv.x * s : -xv.y * s;
-      const __half2 h2 = __floats2half2_rn(p0, p1);
-      hi = h2bits(h2);
-      lo = h2bits(__floats2half2_rn(p0 - __low2float(h2), p1 - __high2float(h2)));
-    };
+    for (int nt = 0; nt < NT; ++nt)
+      Xg[nt] = reinterpret_cast<const uint2*>(XS + (col * VS + 4 * nt + (g >> 1)) * R3S + (te ? 0 : NZ) + t) + (g & 1);
     for (int qq = 0; qq < 5; ++qq) {
       const int sl = col * 5 + qq;
       bool okc = !aborted();
@@ -735,13 +754,11 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
             const int j = 8 * (kbase + kk);
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-              unsigned h0, l0, h1, l1;
-              bfrag(Xg[nt] + j, sv[nt], h0, l0);
-              bfrag(Xg[nt] + j + 4, sv[nt], h1, l1);
-              mma_f16(acc[nt][0][2 * par], aj.x, aj.y, aj4.x, aj4.y, h0, h1);
-              mma_f16(acc[nt][0][2 * par + 1], aj.x, aj.y, aj4.x, aj4.y, l0, l1);
-              mma_f16(acc[nt][1][2 * par], aj.z, aj.w, aj4.z, aj4.w, h0, h1);
-              mma_f16(acc[nt][1][2 * par + 1], aj.z, aj.w, aj4.z, aj4.w, l0, l1);
+              const uint2 b0 = Xg[nt][2 * j], b1 = Xg[nt][2 * (j + 4)];
+              mma_f16(acc[nt][0][2 * par], aj.x, aj.y, aj4.x, aj4.y, b0.x, b1.x);
+              mma_f16(acc[nt][0][2 * par + 1], aj.x, aj.y, aj4.x, aj4.y, b0.y, b1.y);
+              mma_f16(acc[nt][1][2 * par], aj.z, aj.w, aj4.z, aj4.w, b0.x, b1.x);
+              mma_f16(acc[nt][1][2 * par + 1], aj.z, aj.w, aj4.z, aj4.w, b0.y, b1.y);
             }
           }
         }
@@ -758,7 +775,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
         const int v = 4 * nt + t;
         if (v >= V) continue;
         const float sc = bs * isv[col * V + v];
-        cf* Ov = O + (col * V + v) * R3 + (te ? 0 : NZ) + slab * 32 + 4 * g;
+        cf* Ov = O + (col * V + v) * R3O + (te ? 0 : NZ) + slab * 32 + 4 * g;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
           float f[4];
@@ -775,7 +792,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     for (int it = wt; it < P::ITEMS; it += P::WT) {
       const int z = it % NZ, r = (it / NZ) % NR, p = (it / (NZ * NR)) & 1, c = it / (NZ * NR * 2);
       if (p && !two) continue;
-      const cf* Ov = O + (c * V + p * NR + r) * R3;
+      const cf* Ov = O + (c * V + p * NR + r) * R3O;
       const cf es = Ov[z], et = Ov[NZ + z], ez = Ov[2 * NZ + z];
       const float* q = rot[c][p];
       cf* by = xtile(b, p);
