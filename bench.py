@@ -132,7 +132,7 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from
 # one ncu capture of the current kernel version on this workload (profiles/k_lay_apply_*.md):
 # reported as roofline.traffic when the bench runs the same kernel on the same workload
-NCU_TRAFFIC = {("precond", "manhattan_128x128x64", 2, True): 735.125504e6 + 45.432064e6}
+NCU_TRAFFIC = {("precond", "manhattan_128x128x64", 2, True): 732.06272e6 + 45.870336e6}
 
 
 def fp32_peak_tflops():
@@ -387,7 +387,7 @@ def run_ours(args, rank, world):
                "contrast": "k_rows/k_cols contrast passes (absorber planes)",
                "krylov": "Krylov vector kernels (k_vec, k_gdot, k_gupd, k_v64)",
                "transform": "lateral real<->HYBRID transforms (k_rows/k_cols)",
-               "precond": "k_lay_apply (per-column TE/TM inverse blocks x vector)",
+               "precond": "k_lay_apply_pipe (per-column TE/TM inverse blocks x vectors, tensor cores)",
                "lay_build": "k_lay_inv (per-column TE/TM assembly + Gauss-Jordan inversion, FP32)",
                "fno": "FNO forward kernels"}
     by_stage = {}
