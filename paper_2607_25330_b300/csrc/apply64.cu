@@ -1,15 +1,18 @@
-// FP64 operator apply for the outer residual of the mixed-precision solve.
+// Extended-precision operator apply for the outer residual of the mixed-precision solve.
 //
 // A complex64 field cannot represent the solution to much better than a
 // relative residual of ~1e-6 (rounding the exact FP64 solution to complex64
 // already leaves 5e-7..8e-7 on the 32x32x16 and 32x32x32 cases), so the solver
 // refines: complex64 inner Krylov solves of A M d = r, and an FP64 field
-// E <- E + M d whose residual r = b - A E is computed here in FP64.  Same
-// operator as apply.cu (A = curl_s curl_s - k0^2 - k0^2 deps (I + R), Sec. 2.2)
-// with every table (wavenumbers, PML, twiddles, reflection coefficients) in FP64.
+// E <- E + M d whose residual r = b - A E is computed here.  Same operator as
+// apply.cu (A = curl_s curl_s - k0^2 - k0^2 deps (I + R), Sec. 2.2).  Fields and
+// tables are FP64 in memory; the transforms and products run in double-float
+// arithmetic (ff.cuh, about 48 bits, on the FP32 units: B300's FP64 rate is a
+// small fraction of its FP32 rate), and the per-column reflection terms in FP64.
 #include <cmath>
 #include <vector>
 
+#include "ff.cuh"
 #include "fft.cuh"
 #include "internal.h"
 
@@ -21,8 +24,11 @@ struct Ax64 {
   zd* G;
   const double* kx;
   const double* ky;
+  const ff* kzf;      // [nz] wavenumbers, double-float, and FP64
   const double* kz;
+  const cff* sinvf;   // [nz] PML stretch 1/s
   const zd* sinv;
+  const cff* twf;     // [nz] twiddles
   const zd* tw;
   const double2* rs;
   const double2* rp;
@@ -34,11 +40,15 @@ struct Ax64 {
 };
 
 // Same job structure as k_axial (mode A): jobs 0, 1, 3 copy the input.
-template <int NZ, int T>
+template <int NZ, int T, class C>
 __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
   constexpr int P = 32 / T;
   constexpr int R = NZ / T;
-  using PZ = Pencil<NZ, T, P, zd>;
+  using PZ = Pencil<NZ, T, P, C>;
+  using RT = typename CTraits<C>::R;
+  const RT* kzt = pick_real<C>(a.kzf, a.kz);
+  const C* sinv = pick_tab<C>(a.sinvf, a.sinv);
+  const C* tw = pick_tab<C>(a.twf, a.tw);
   extern __shared__ zd smem64[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane / P, p = lane - t * P;
@@ -50,33 +60,33 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
   const zd* __restrict__ x = a.x + rhs * a.vstride;
   zd* __restrict__ y = a.y + rhs * a.vstride;
   const double kx = a.kx[cc % a.nx], ky = a.ky[cc / a.nx];
-  const double inv_n = 1.0 / (double)NZ;
-  const zd ikx = make_double2(0.0, kx), iky = make_double2(0.0, ky);
-  zd* st = smem64 + (size_t)warp * 4 * R * 32;
-  auto unst = [&](int sl, int m) -> zd { return st[(sl * R + m) * 32 + lane]; };
-  auto stash = [&](int sl, int m, zd v) { st[(sl * R + m) * 32 + lane] = v; };
+  const RT inv_n(1.0 / (double)NZ), k02(a.k02), zero(0.0);
+  const C ikx = CTraits<C>::make(zero, RT(kx)), iky = CTraits<C>::make(zero, RT(ky));
+  C* st = reinterpret_cast<C*>(smem64) + (size_t)warp * 4 * R * 32;
+  auto unst = [&](int sl, int m) -> C { return st[(sl * R + m) * 32 + lane]; };
+  auto stash = [&](int sl, int m, C v) { st[(sl * R + m) * 32 + lane] = v; };
 #pragma unroll 1
   for (int job = 0; job < 7; ++job) {
     const bool copy_only = (job == 0 || job == 1 || job == 3);
-    zd v[R];
+    C v[R];
     if (job < 5) {
       const int c = (job == 0) ? 2 : (job <= 2 ? 1 : 0);
       const zd* src = x + (long)(c * NZ + t) * nc + col;
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = act ? src[(long)(T * m) * nc] : make_double2(0.0, 0.0);
+      for (int m = 0; m < R; ++m) v[m] = act ? from_zd<C>(src[(long)(T * m) * nc]) : CTraits<C>::zero();
     } else {
       const int sl = (job == 5) ? 2 : 0;
 #pragma unroll
       for (int m = 0; m < R; ++m) v[m] = unst(sl, m);
     }
     if (!copy_only) {
-      PZ::template to_freq<false>(v, t, a.tw);
+      PZ::template to_freq<false>(v, t, tw);
 #pragma unroll
       for (int s = 0; s < R; ++s) {
-        const double kzv = a.kz[PZ::freq_index(t, s)] * inv_n;
-        v[s] = make_double2(-kzv * v[s].y, kzv * v[s].x);
+        const RT kzv = kzt[PZ::freq_index(t, s)] * inv_n;
+        v[s] = CTraits<C>::make(-(kzv * v[s].y), kzv * v[s].x);
       }
-      PZ::template to_time<true>(v, t, a.tw);
+      PZ::template to_time<true>(v, t, tw);
     }
     if (copy_only) {
       const int sl = (job == 0) ? 0 : (job == 1 ? 1 : 3);
@@ -84,14 +94,15 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
       for (int m = 0; m < R; ++m) stash(sl, m, v[m]);
     } else if (job == 2) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) stash(2, m, csub(cmul(iky, unst(0, m)), cmul(v[m], a.sinv[t + T * m])));
+      for (int m = 0; m < R; ++m) stash(2, m, csub(cmul(iky, unst(0, m)), cmul(v[m], sinv[t + T * m])));
     } else if (job == 4) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = csub(cmul(v[m], a.sinv[t + T * m]), cmul(ikx, unst(0, m)));
+      for (int m = 0; m < R; ++m) v[m] = csub(cmul(v[m], sinv[t + T * m]), cmul(ikx, unst(0, m)));
       __syncwarp();
+      // reflection of the field at z_ml (Sec. 2.2): per column, in FP64
       const int tml = a.z_ml % T, mml = a.z_ml / T;
-      const zd exm = st[(3 * R + mml) * 32 + tml * P + p];
-      const zd eym = st[(1 * R + mml) * 32 + tml * P + p];
+      const zd exm = to_zd(st[(3 * R + mml) * 32 + tml * P + p]);
+      const zd eym = to_zd(st[(1 * R + mml) * 32 + tml * P + p]);
       const zd rs = a.rs[cc], rp = a.rp[cc], kz0 = a.kz0[cc];
       const double kp = sqrt(kx * kx + ky * ky);
       double sx, sy, tx, ty;
@@ -105,14 +116,15 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
       const zd num = make_double2(-(kx * r0.x + ky * r1.x), -(kx * r0.y + ky * r1.y));
       const double kd = kz0.x * kz0.x + kz0.y * kz0.y;
       const zd r2 = make_double2((num.x * kz0.x + num.y * kz0.y) / kd, (num.y * kz0.x - num.x * kz0.y) / kd);
+      const C r0c = from_zd<C>(r0), r1c = from_zd<C>(r1), r2c = from_zd<C>(r2);
       const int nab = a.za1 - a.za0;
       zd* __restrict__ G = a.G + rhs * a.gstride;
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int z = t + T * m;
-        const zd qz = unst(0, m), cx = unst(2, m), cy = v[m];
-        const zd Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
-        if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
+        const C qz = unst(0, m), cx = unst(2, m), cy = v[m];
+        const C Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, k02));
+        if (act) y[(long)(2 * NZ + z) * nc + col] = to_zd(Wz);
         if (z >= a.za0 && z < a.za1 && act) {
           zd prof = make_double2(0.0, 0.0);
           if (z >= a.z_ml) {
@@ -122,10 +134,11 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
             const double mag = exp(-kz0.y * zr);
             prof = make_double2(mag * cs, mag * sn);
           }
+          const C pc = from_zd<C>(prof);
           const long o = (long)(z - a.za0) * nc + col;
-          G[o] = cfma(r0, prof, unst(3, m));
-          G[(long)nab * nc + o] = cfma(r1, prof, unst(1, m));
-          G[2L * nab * nc + o] = cfma(r2, prof, qz);
+          G[o] = to_zd(cfma(r0c, pc, unst(3, m)));
+          G[(long)nab * nc + o] = to_zd(cfma(r1c, pc, unst(1, m)));
+          G[2L * nab * nc + o] = to_zd(cfma(r2c, pc, qz));
         }
       }
 #pragma unroll
@@ -134,12 +147,12 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
       const int c = (job == 5) ? 1 : 0;
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const zd d = cmul(v[m], a.sinv[t + T * m]);
-        const zd qx = unst(3, m), qy = unst(1, m);
-        const zd cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        const zd W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
-                                : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
-        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = W;
+        const C d = cmul(v[m], sinv[t + T * m]);
+        const C qx = unst(3, m), qy = unst(1, m);
+        const C cz = csub(cmul(ikx, qy), cmul(iky, qx));
+        const C W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, k02))
+                                 : csub(csub(cmul(iky, cz), d), cscale(qx, k02));
+        if (act) y[(long)(c * NZ + t + T * m) * nc + col] = to_zd(W);
       }
     }
   }
@@ -151,36 +164,40 @@ struct Row64 {
   zd* buf;
   long nrows;
   double scale;
+  const cff* twf;   // twiddles, double-float and FP64
   const zd* tw;
   zd* y;
   int ny, nz, nab, za0;
 };
 
-template <int NX, int T, int OP>
+template <int NX, int T, int OP, class C>
 __global__ void __launch_bounds__(64) k_rows64(Row64 a) {
   constexpr int P = 32 / T, R = NX / T;
-  using PX = Pencil<NX, T, 1, zd>;
+  using PX = Pencil<NX, T, 1, C>;
+  using RT = typename CTraits<C>::R;
+  const C* tw = pick_tab<C>(a.twf, a.tw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane / T, t = lane - p * T;
   const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const bool act = row < a.nrows;
   zd* src = a.buf + (act ? row : 0) * NX;
-  zd v[R];
+  const RT scale(a.scale);
+  C v[R];
   if constexpr (OP == R64_INV) {
 #pragma unroll
-    for (int s = 0; s < R; ++s) v[s] = act ? src[PX::freq_index(t, s)] : make_double2(0.0, 0.0);
-    PX::template to_time<true>(v, t, a.tw);
+    for (int s = 0; s < R; ++s) v[s] = act ? from_zd<C>(src[PX::freq_index(t, s)]) : CTraits<C>::zero();
+    PX::template to_time<true>(v, t, tw);
 #pragma unroll
     for (int m = 0; m < R; ++m)
-      if (act) src[t + T * m] = cscale(v[m], a.scale);
+      if (act) src[t + T * m] = to_zd(cscale(v[m], scale));
   } else {
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : make_double2(0.0, 0.0);
-    PX::template to_freq<false>(v, t, a.tw);
+    for (int m = 0; m < R; ++m) v[m] = act ? from_zd<C>(src[t + T * m]) : CTraits<C>::zero();
+    PX::template to_freq<false>(v, t, tw);
     if constexpr (OP == R64_FWD) {
 #pragma unroll
       for (int s = 0; s < R; ++s)
-        if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
+        if (act) src[PX::freq_index(t, s)] = to_zd(cscale(v[s], scale));
     } else {
       const long per_c = (long)a.nab * a.ny;
       const long r = act ? row : 0;
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(64) k_rows64(Row64 a) {
       for (int s = 0; s < R; ++s)
         if (act) {
           const int k = PX::freq_index(t, s);
-          dst[k] = csub(dst[k], v[s]);
+          dst[k] = csub(dst[k], to_zd(v[s]));
         }
     }
   }
@@ -204,6 +221,7 @@ struct Col64 {
   long ncolumns;
   int nx;
   double scale;
+  const cff* twf;   // twiddles, double-float and FP64
   const zd* tw;
   const float* fill;
   const zd* pc;   // per-plane contrast; multiplier cs * c[z]
@@ -212,10 +230,12 @@ struct Col64 {
   long plane_elems;
 };
 
-template <int NY, int T, int OP>
+template <int NY, int T, int OP, class C>
 __global__ void __launch_bounds__(64) k_cols64(Col64 a) {
   constexpr int P = 32 / T, R = NY / T;
-  using PY = Pencil<NY, T, P, zd>;
+  using PY = Pencil<NY, T, P, C>;
+  using RT = typename CTraits<C>::R;
+  const C* tw = pick_tab<C>(a.twf, a.tw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane / P, p = lane - t * P;
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
@@ -225,38 +245,39 @@ __global__ void __launch_bounds__(64) k_cols64(Col64 a) {
   const int ix = (int)(cid - plane * a.nx);
   zd* base = a.buf + plane * a.plane_elems + ix;
   const long sx = a.nx;
-  zd v[R];
+  const RT scale(a.scale);
+  C v[R];
   if constexpr (OP == C64_FWD) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : make_double2(0.0, 0.0);
-    PY::template to_freq<false>(v, t, a.tw);
+    for (int m = 0; m < R; ++m) v[m] = act ? from_zd<C>(base[(long)(t + T * m) * sx]) : CTraits<C>::zero();
+    PY::template to_freq<false>(v, t, tw);
 #pragma unroll
     for (int s = 0; s < R; ++s)
-      if (act) base[(long)PY::freq_index(t, s) * sx] = cscale(v[s], a.scale);
+      if (act) base[(long)PY::freq_index(t, s) * sx] = to_zd(cscale(v[s], scale));
   } else if constexpr (OP == C64_INV) {
 #pragma unroll
-    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : make_double2(0.0, 0.0);
-    PY::template to_time<true>(v, t, a.tw);
+    for (int s = 0; s < R; ++s) v[s] = act ? from_zd<C>(base[(long)PY::freq_index(t, s) * sx]) : CTraits<C>::zero();
+    PY::template to_time<true>(v, t, tw);
 #pragma unroll
     for (int m = 0; m < R; ++m)
-      if (act) base[(long)(t + T * m) * sx] = cscale(v[m], a.scale);
+      if (act) base[(long)(t + T * m) * sx] = to_zd(cscale(v[m], scale));
   } else {
     const long zz = plane % a.nab;
     const float* f = a.fill + (a.za0 + zz) * a.plane_elems + ix;
     const zd c0 = a.pc[a.za0 + zz];
-    const double dre = a.cs * c0.x, dim = a.cs * c0.y;
+    const RT dre(a.cs * c0.x), dim(a.cs * c0.y);
 #pragma unroll
-    for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : make_double2(0.0, 0.0);
-    PY::template to_time<true>(v, t, a.tw);
+    for (int s = 0; s < R; ++s) v[s] = act ? from_zd<C>(base[(long)PY::freq_index(t, s) * sx]) : CTraits<C>::zero();
+    PY::template to_time<true>(v, t, tw);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      const double fv = act ? (double)f[(long)(t + T * m) * sx] : 0.0;
-      v[m] = cmul(v[m], make_double2(dre * fv, dim * fv));
+      const RT fv((double)(act ? f[(long)(t + T * m) * sx] : 0.f));   // the fill is a float: exact
+      v[m] = cmul(v[m], CTraits<C>::make(dre * fv, dim * fv));
     }
-    PY::template to_freq<false>(v, t, a.tw);
+    PY::template to_freq<false>(v, t, tw);
 #pragma unroll
     for (int s = 0; s < R; ++s)
-      if (act) base[(long)PY::freq_index(t, s) * sx] = v[s];
+      if (act) base[(long)PY::freq_index(t, s) * sx] = to_zd(v[s]);
   }
 }
 
@@ -266,9 +287,10 @@ int rows64_op(const Row64& a, int op, cudaStream_t s) {
   const long per = warps * (32 / T);
   dim3 g((unsigned)((a.nrows + per - 1) / per));
   if (!g.x) return PSFD_OK;
-  if (op == R64_FWD) k_rows64<NX, T, R64_FWD><<<g, warps * 32, 0, s>>>(a);
-  else if (op == R64_INV) k_rows64<NX, T, R64_INV><<<g, warps * 32, 0, s>>>(a);
-  else k_rows64<NX, T, R64_FWD_SUB><<<g, warps * 32, 0, s>>>(a);
+  using C = ExtC<NX, T>;
+  if (op == R64_FWD) k_rows64<NX, T, R64_FWD, C><<<g, warps * 32, 0, s>>>(a);
+  else if (op == R64_INV) k_rows64<NX, T, R64_INV, C><<<g, warps * 32, 0, s>>>(a);
+  else k_rows64<NX, T, R64_FWD_SUB, C><<<g, warps * 32, 0, s>>>(a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -291,9 +313,10 @@ int cols64_op(const Col64& a, int op, cudaStream_t s) {
   const long per = warps * (32 / T);
   dim3 g((unsigned)((a.ncolumns + per - 1) / per));
   if (!g.x) return PSFD_OK;
-  if (op == C64_FWD) k_cols64<NY, T, C64_FWD><<<g, warps * 32, 0, s>>>(a);
-  else if (op == C64_INV) k_cols64<NY, T, C64_INV><<<g, warps * 32, 0, s>>>(a);
-  else k_cols64<NY, T, C64_CONTRAST><<<g, warps * 32, 0, s>>>(a);
+  using C = ExtC<NY, T>;
+  if (op == C64_FWD) k_cols64<NY, T, C64_FWD, C><<<g, warps * 32, 0, s>>>(a);
+  else if (op == C64_INV) k_cols64<NY, T, C64_INV, C><<<g, warps * 32, 0, s>>>(a);
+  else k_cols64<NY, T, C64_CONTRAST, C><<<g, warps * 32, 0, s>>>(a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -316,7 +339,10 @@ int axial64_run(psfd_plan_s* P, const zd* x, zd* y) {
   constexpr int R = NZ / T;
   Ax64 a;
   a.x = x; a.y = y; a.G = P->F.G;
-  a.kx = P->F.kx; a.ky = P->F.ky; a.kz = P->F.kz; a.sinv = P->F.sinv; a.tw = P->F.twz;
+  a.kx = P->F.kx; a.ky = P->F.ky;
+  a.kz = P->F.kz; a.kzf = reinterpret_cast<const ff*>(P->F.kz_f);
+  a.sinv = P->F.sinv; a.sinvf = reinterpret_cast<const cff*>(P->F.sinv_f);
+  a.tw = P->F.twz; a.twf = reinterpret_cast<const cff*>(P->F.twz_f);
   a.rs = P->R.rs64; a.rp = P->R.rp64; a.kz0 = P->R.kz064;
   a.nx = P->nx; a.ncols = P->ncols; a.vstride = P->nvec;
   a.gstride = 3L * (P->za1 - P->za0) * P->ncols;
@@ -326,8 +352,9 @@ int axial64_run(psfd_plan_s* P, const zd* x, zd* y) {
   const long per = warps * (32 / T);
   dim3 g((unsigned)((P->ncols + per - 1) / per), (unsigned)P->nrhs);
   const size_t smem = (size_t)warps * 4 * R * 32 * sizeof(zd);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_axial64<NZ, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_axial64<NZ, T><<<g, warps * 32, smem, P->stream>>>(a);
+  using C = ExtC<NZ, T>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_axial64<NZ, T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_axial64<NZ, T, C><<<g, warps * 32, smem, P->stream>>>(a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -337,6 +364,16 @@ void host_tw64(int n, std::vector<zd>& out) {
   for (int m = 0; m < n; ++m) {
     const double ang = -2.0 * M_PI * (double)m / (double)n;
     out[m] = make_double2(cos(ang), sin(ang));
+  }
+}
+
+// FP64 values as double-float pairs (hi = nearest float, lo = nearest float to the remainder)
+void split_ff(const double* d, size_t n, std::vector<float>& out) {
+  out.resize(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    const float hi = (float)d[i];
+    out[2 * i] = hi;
+    out[2 * i + 1] = (float)(d[i] - (double)hi);
   }
 }
 
@@ -375,6 +412,19 @@ int fp64_prepare(psfd_plan_s* P) {
     PSFD_CUDA_TRY(cudaMemcpy(F.twx, twx.data(), P->nx * 16, cudaMemcpyHostToDevice));
     PSFD_CUDA_TRY(cudaMemcpy(F.twy, twy.data(), P->ny * 16, cudaMemcpyHostToDevice));
     PSFD_CUDA_TRY(cudaMemcpy(F.twz, twz.data(), P->nz * 16, cudaMemcpyHostToDevice));
+    // double-float copies for the transforms and products
+    std::vector<float> f;
+    struct T2 { const double* src; size_t n; float** dst; };
+    const T2 tabs[] = {{kz.data(), (size_t)P->nz, &F.kz_f},
+                       {reinterpret_cast<const double*>(sinv.data()), 2 * (size_t)P->nz, &F.sinv_f},
+                       {reinterpret_cast<const double*>(twx.data()), 2 * (size_t)P->nx, &F.twx_f},
+                       {reinterpret_cast<const double*>(twy.data()), 2 * (size_t)P->ny, &F.twy_f},
+                       {reinterpret_cast<const double*>(twz.data()), 2 * (size_t)P->nz, &F.twz_f}};
+    for (const T2& tb : tabs) {
+      split_ff(tb.src, tb.n, f);
+      PSFD_CUDA_TRY(cudaMalloc((void**)tb.dst, f.size() * sizeof(float)));
+      PSFD_CUDA_TRY(cudaMemcpy(*tb.dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
   }
   if (F.G_elems < gneed) {
     if (F.G) cudaFree(F.G);
@@ -388,7 +438,7 @@ int fp64_prepare(psfd_plan_s* P) {
 
 void fp64_free(psfd_plan_s* P) {
   Fp64Tables& F = P->F;
-  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.twx, F.twy, F.twz, F.G};
+  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.twx, F.twy, F.twz, F.G, F.kz_f, F.sinv_f, F.twx_f, F.twy_f, F.twz_f};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   F = Fp64Tables();
@@ -415,16 +465,17 @@ int apply64_hybrid(psfd_plan_s* P, const zd* x, zd* y) {
   StageScope sc(P->stream, ST_CONTRAST);
   const long nplanes = (long)P->nrhs * 3 * nab;
   Row64 r{};
-  r.buf = P->F.G; r.nrows = nplanes * P->ny; r.scale = 1.0; r.tw = P->F.twx;
+  r.buf = P->F.G; r.nrows = nplanes * P->ny; r.scale = 1.0; r.tw = P->F.twx; r.twf = reinterpret_cast<const cff*>(P->F.twx_f);
   if ((rc = rows64(P->nx, r, R64_INV, P->stream))) return rc;
   Col64 c{};
   const double scl = P->k0 * P->k0 / (double)P->ncols;
-  c.buf = P->F.G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.0; c.tw = P->F.twy;
+  c.buf = P->F.G; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.scale = 1.0;
+  c.tw = P->F.twy; c.twf = reinterpret_cast<const cff*>(P->F.twy_f);
   c.fill = P->fill; c.pc = P->pc64; c.cs = scl; c.nab = nab; c.za0 = P->za0;
   c.plane_elems = P->ncols;
   if ((rc = cols64(P->ny, c, C64_CONTRAST, P->stream))) return rc;
   Row64 w{};
-  w.buf = P->F.G; w.nrows = nplanes * P->ny; w.tw = P->F.twx; w.y = y;
+  w.buf = P->F.G; w.nrows = nplanes * P->ny; w.tw = P->F.twx; w.twf = reinterpret_cast<const cff*>(P->F.twx_f); w.y = y;
   w.ny = P->ny; w.nz = P->nz; w.nab = nab; w.za0 = P->za0;
   return rows64(P->nx, w, R64_FWD_SUB, P->stream);
 }
@@ -434,9 +485,10 @@ int transform64(psfd_plan_s* P, zd* buf, long nplanes, bool forward, double scal
   StageScope sc(P->stream, ST_TRANSFORM);
   int rc;
   Row64 r{};
-  r.buf = buf; r.nrows = nplanes * P->ny; r.tw = P->F.twx;
+  r.buf = buf; r.nrows = nplanes * P->ny; r.tw = P->F.twx; r.twf = reinterpret_cast<const cff*>(P->F.twx_f);
   Col64 c{};
-  c.buf = buf; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.tw = P->F.twy; c.plane_elems = P->ncols;
+  c.buf = buf; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.tw = P->F.twy; c.twf = reinterpret_cast<const cff*>(P->F.twy_f);
+  c.plane_elems = P->ncols;
   if (forward) {
     r.scale = 1.0;
     if ((rc = rows64(P->nx, r, R64_FWD, P->stream))) return rc;

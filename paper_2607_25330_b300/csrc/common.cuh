@@ -40,6 +40,12 @@ __device__ __forceinline__ zd cfma(zd a, zd b, zd c) {
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
+// warp shuffle and twiddle-table load by value type (overloaded for the double-float type)
+__device__ __forceinline__ float shfl_xor_r(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_xor_r(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ cf ld_tw(const cf* p) { return __ldg(p); }
+__device__ __forceinline__ zd ld_tw(const zd* p) { return __ldg(p); }
+
 template <class C> struct CTraits;
 template <> struct CTraits<cf> {
   using R = float;

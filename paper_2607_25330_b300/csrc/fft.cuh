@@ -113,8 +113,8 @@ struct Pencil {
               const int s0 = x0 * B + i, s1 = (x0 | b) * B + i;
               C send = tb ? v[s0] : v[s1];
               C got;
-              got.x = __shfl_xor_sync(0xffffffffu, send.x, b * LS);
-              got.y = __shfl_xor_sync(0xffffffffu, send.y, b * LS);
+              got.x = shfl_xor_r(send.x, b * LS);
+              got.y = shfl_xor_r(send.y, b * LS);
               if (tb) v[s0] = got; else v[s1] = got;
             }
           }
@@ -128,7 +128,7 @@ struct Pencil {
     if constexpr (T > 1) {
 #pragma unroll
       for (int k = 1; k < R; ++k) {
-        C w = __ldg(tw + t * k);   // t*k < T*R = N
+        C w = ld_tw(tw + t * k);   // t*k < T*R = N
         if (INV) w.y = -w.y;
         v[k] = cmul(v[k], w);
       }

@@ -25,6 +25,12 @@ struct Fp64Tables {
   double2* twz = nullptr;
   double2* G = nullptr;
   size_t G_elems = 0;
+  // double-float (hi, lo) copies used by the extended-precision transforms
+  float* kz_f = nullptr;
+  float* sinv_f = nullptr;
+  float* twx_f = nullptr;
+  float* twy_f = nullptr;
+  float* twz_f = nullptr;
 };
 
 struct psfd_plan_s {

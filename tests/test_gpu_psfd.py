@@ -286,3 +286,24 @@ def test_single_pass_plane_kernel_equals_three_pass_contrast(n, monkeypatch):
         y1 = plans[0][0].apply(x, flags=flags)
         y2 = plans[1][0].apply(x, flags=flags)
         assert rel_l2(y1.cpu(), y2.cpu()) < 2e-6
+
+
+def test_refinement_residual_matches_oracle_at_1e10():
+    """The outer residual b - A E of the refinement (FP64 field, transforms and products in
+    double-float arithmetic) against the oracle's complex128 residual of the returned FP64 field,
+    refined to 1e-10, with the same (float32) fill on both sides so that the two operators agree
+    to FP64 rounding: agreement to 2 % + 1e-12 puts the residual's absolute error near 1e-12 of
+    ||b||, far under the 1e-6 target."""
+    prob = I.preset("line_space_32x32x16")
+    a = I.mask_for(prob, 3)
+    g, fill_o = oracle_setup(prob, a)
+    from paper_2607_25330_b300 import psfd
+    plan = psfd.Plan(prob)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    res = plan.solve_ex(b, tol=1e-10, maxit=6000, method=psfd.PSFD_BICGSTAB, inner_tol=1e-2, out_c128=True)
+    info = res["info"][0]
+    assert info["status"] == 0 and info["r_rel_output"] <= 1e-10, info
+    bo = b[0].cpu().to(torch.complex128)
+    r_or = O.rel_residual(g, res["E"][0].cpu(), fill.cpu().to(torch.float64), bo)
+    assert abs(r_or - info["r_rel_output"]) <= 0.02 * r_or + 1e-12, (r_or, info["r_rel_output"])
