@@ -629,9 +629,11 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     xissued = k + 1;
   };
   if (leader && npc > 0 && !a.no_copy) load_boxes(0);
-  for (int i = wt; i < 2 * (VS - V) * R3S; i += P::WT) {   // slots past the vectors stay zero
-    const int c = i / ((VS - V) * R3S), e = i % ((VS - V) * R3S);
-    XS[(c * VS + V) * R3S + e] = make_uint4(0u, 0u, 0u, 0u);
+  if constexpr (VS > V) {   // slots past the vectors stay zero
+    for (int i = wt; i < 2 * (VS - V) * R3S; i += P::WT) {
+      const int c = i / ((VS - V) * R3S), e = i % ((VS - V) * R3S);
+      XS[(c * VS + V) * R3S + e] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   // this warp's column and slab
   const int col = ww / CW, cw = ww % CW;
@@ -645,6 +647,7 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     int ix0, h, iyB; bool two;
     pair_rows(k, ix0, h, iyB, two);
     const int b = (int)(k % P::NBUF);
+    const float bs = a.scales[(2 * (blockIdx.x + k * gridDim.x) + col) * 2 + (te ? 0 : 1)];   // used in step 4
     if (wt < 4) {   // rotation of (col, row) = (wt & 1, wt >> 1)
       const int c = wt & 1, p = wt >> 1;
       const float kx = a.kx[ix0 + c], ky = a.ky[p ? iyB : h];
@@ -660,11 +663,6 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     if (ok) ok = mbar_wait_cycles(smem_u32a(&xfull[b]), (unsigned)((k / P::NBUF) & 1), WAIT);
     if (!ok && !a.no_copy && !aborted()) give_up();
     group_sync(P::WT);
-    // the next pair's boxes go to the other buffer, once pair k - 1's store has read it
-    if (leader && k + 1 < npc && !aborted() && !a.no_copy) {
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      load_boxes(k + 1);
-    }
     // 1. per-vector power-of-two scale from the raw entries: a rotated entry is at most sqrt 2
     //    times the largest raw one (|sx| + |sy| <= sqrt 2), so s puts the rotated vector below
     //    2^14 and its largest entry at or above 2^12 (one bit of the split at most is lost)
@@ -766,10 +764,15 @@ __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32a(&empty[sl])) : "memory");
     }
+    // the next pair's boxes go to the other buffer, once pair k - 1's store (issued a whole
+    // multiplication ago) has read it
+    if (leader && k + 1 < npc && !aborted() && !a.no_copy) {
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      load_boxes(k + 1);
+    }
     // 4. products into O (rows of the stacked s, t, z vector): lane (g, t) holds vector 4 nt + t
     //    at slab rows 4g + 2m (c0, c1) and 4g + 2m + 1 (c2, c3)
     {
-      const float bs = a.scales[(2 * (blockIdx.x + k * gridDim.x) + col) * 2 + (te ? 0 : 1)];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int v = 4 * nt + t;
