@@ -175,6 +175,7 @@ TC_GRIDS = [  # nz a multiple of 32: the half-precision blocks are applied on th
     (16, 16, 32, 0.0, 0.0, 4),
     (16, 16, 64, 6.0, 0.0, 1),
     (32, 16, 32, 6.0, 0.0, 3),
+    (16, 16, 64, 8.0, 30.0, 2),   # nz = 64 without pairing
 ]
 
 
