@@ -241,7 +241,11 @@ PSFD_API size_t psfd_solve_workspace_size(psfd_plan plan, int method, int restar
  * each outer step solves A M d = r in complex64 (method, restart, preconditioner
  * as above) to the relative tolerance inner_tol (or only to 0.5 tol ||b|| / ||r||
  * when that is looser: the correction is not solved more accurately than the
- * final tolerance needs), then E += M d.  Convergence is
+ * final tolerance needs), then E += M d.  The first residual only feeds that
+ * first inner solve: it is b itself for a cold start and is formed with the
+ * complex64 operator for a warm start (so info.r_rel_initial of a refined warm
+ * solve carries complex64 rounding); every later residual, and the convergence
+ * test, use the extended-precision apply.  Convergence is
  * the FP64 relative residual <= tol (Eq. relative_residual); maxit bounds the
  * total number of inner iterations, max_outer (0 = 100) the outer steps.  The
  * returned field is the complex64 rounding of the FP64 field, or with out_c128
