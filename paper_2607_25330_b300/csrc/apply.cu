@@ -859,7 +859,7 @@ int apply_hybrid(psfd_plan_s* P, const cf* x, cf* y, int flags, const int* done)
   }
   if (flags & PSFD_LAYERED) {
     // A P x: the per-column inverses first, then the operator
-    if ((rc = layered_apply(P, x, P->tmpB))) return rc;
+    if ((rc = layered_apply(P, x, P->tmpB, done))) return rc;
     x = P->tmpB;
   }
   rc = launch_axial(P, x, y, (flags & PSFD_PRECOND) && !(flags & PSFD_LAYERED) ? AX_AM : AX_A, done, P->nrhs);

@@ -126,5 +126,6 @@ int layered_supported(const psfd_plan_s* P);
 bool layered_pairs(const psfd_plan_s* P);
 long layered_columns(const psfd_plan_s* P);
 size_t layered_bytes(const psfd_plan_s* P);
-int layered_apply(psfd_plan_s* P, const cf* x, cf* y);
+// done (nullable, device [nrhs]): when every right-hand side is done the apply returns at once
+int layered_apply(psfd_plan_s* P, const cf* x, cf* y, const int* done = nullptr);
 void layered_free(psfd_plan_s* P);

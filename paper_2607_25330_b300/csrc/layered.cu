@@ -61,7 +61,17 @@ struct LayArgs {
   int half;             // 1: half-precision storage
   int* err;             // [0] set to 1 if a pivot vanished, [1] if an apply gave up waiting for its blocks
   int no_copy;          // test of the bounded wait: the tensor-core apply requests no blocks
+  const int* done;      // nullable [nrhs]: the apply does nothing when every right-hand side is done
+  int nrhs;
 };
+
+// 1 when every right-hand side of the solve is done (the whole block returns, before any copy)
+__device__ __forceinline__ bool all_done(const LayArgs& a) {
+  if (!a.done) return false;
+  for (int r = 0; r < a.nrhs; ++r)
+    if (!a.done[r]) return false;
+  return true;
+}
 
 // Half-precision block layout: column-major, with the 16-byte chunks of four rows permuted
 // within each column by an XOR with 2 (j mod 4) when the block size is a multiple of 32, so
@@ -316,6 +326,7 @@ constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / apply_rpt<HALF>(); }
 template <int NZ, int NR, bool HALF>
 __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 2 ? 3 : 2)))
     k_lay_apply(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
+  if (all_done(a)) return;
   constexpr int nrhs = NR;
   constexpr int G = LAY_GROUP, NT = apply_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
   extern __shared__ cf xs[];       // [2G][3][NZ][nrhs]: (s, t, z) components after rotation
@@ -543,6 +554,7 @@ template <int NZ, int NR>
 __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     k_lay_apply_pipe(LayArgs a, const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ty,
                      long npairs) {
+  if (all_done(a)) return;
   using P = PipeCfg<NZ, NR>;
   using M = MmaCfg<NZ, NR>;
   constexpr int V = M::V, NT = M::NT, R3 = M::R3, VS = M::VS, R3S = M::R3S, R3O = M::R3O, CW = M::CW;
@@ -909,8 +921,10 @@ int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
 }
 
 template <int NZ>
-int apply_nz(psfd_plan_s* P, const cf* x, cf* y) {
+int apply_nz(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   LayArgs a = lay_args(P);
+  a.done = done;
+  a.nrhs = P->nrhs;
   switch (P->nrhs) {
     case 1: return apply_nr<NZ, 1>(P, a, x, y);
     case 2: return apply_nr<NZ, 2>(P, a, x, y);
@@ -938,14 +952,14 @@ size_t layered_bytes(const psfd_plan_s* P) {
   return (size_t)layered_columns(P) * per;
 }
 
-int layered_apply(psfd_plan_s* P, const cf* x, cf* y) {
+int layered_apply(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   if (!P->lay_built) { psfd_set_error("layered preconditioner: call psfd_layered_build first"); return PSFD_ERR_STATE; }
   StageScope scope(P->stream, ST_PRECOND, (double)layered_bytes(P) + 2.0 * P->nrhs * P->nvec * sizeof(cf));
   switch (P->nz) {
-    case 16: return apply_nz<16>(P, x, y);
-    case 32: return apply_nz<32>(P, x, y);
-    case 48: return apply_nz<48>(P, x, y);
-    case 64: return apply_nz<64>(P, x, y);
+    case 16: return apply_nz<16>(P, x, y, done);
+    case 32: return apply_nz<32>(P, x, y, done);
+    case 48: return apply_nz<48>(P, x, y, done);
+    case 64: return apply_nz<64>(P, x, y, done);
     default: psfd_set_error("layered preconditioner: unsupported nz %d", P->nz); return PSFD_ERR_ARG;
   }
 }
