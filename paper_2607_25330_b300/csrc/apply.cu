@@ -128,6 +128,20 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
     rh1 = cadd(cadd(cmulc(v0, T01), cmulc(v1, T11)), cmulc(v2, T21));
   }
 
+  // modes A and A^H read the components z, y, y, x, x in jobs 0-4: load each once, all three
+  // up front, so that their latencies overlap (where a thread holds at most 8 points of a pencil)
+  constexpr bool PRE = (MODE == AX_A || MODE == AX_AH) && R <= 8;
+  cf pre0[PRE ? R : 1], pre1[PRE ? R : 1], pre2[PRE ? R : 1];
+  if constexpr (PRE) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const long o = (long)(t + T * m) * nc + col;
+      pre2[m] = act ? __ldg(x + 2L * NZ * nc + o) : czero();
+      pre1[m] = act ? __ldg(x + (long)NZ * nc + o) : czero();
+      pre0[m] = act ? __ldg(x + o) : czero();
+    }
+  }
+
 #pragma unroll 1
   for (int job = 0; job < 7; ++job) {
     if (MODE == AX_M && (job == 2 || job >= 4)) continue;
@@ -135,10 +149,23 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
     cf v[R];
     // ---- source
     if (job < 5) {
-      const int c = (job == 0) ? 2 : (job <= 2 ? 1 : 0);
-      const cf* src = x + (long)(c * NZ + t) * nc + col;
+      if constexpr (PRE) {
+        if (job == 0) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = act ? __ldg(src + (long)(T * m) * nc) : czero();
+          for (int m = 0; m < R; ++m) v[m] = pre2[m];
+        } else if (job <= 2) {
+#pragma unroll
+          for (int m = 0; m < R; ++m) v[m] = pre1[m];
+        } else {
+#pragma unroll
+          for (int m = 0; m < R; ++m) v[m] = pre0[m];
+        }
+      } else {
+        const int c = (job == 0) ? 2 : (job <= 2 ? 1 : 0);
+        const cf* src = x + (long)(c * NZ + t) * nc + col;
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = act ? __ldg(src + (long)(T * m) * nc) : czero();
+      }
     } else {
       const int sl = (job == 5) ? 2 : 0;
 #pragma unroll

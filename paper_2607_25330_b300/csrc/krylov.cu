@@ -1102,7 +1102,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
   for (;; ++outer) {
     // r = b - A E with the extended-precision apply.  The first residual only feeds an inner solve
     // to inner_tol, so a cold start takes r = b (E = 0) and a warm start forms A E with the
-    // complex64 operator; convergence is only ever judged on an extended-precision residual.
+    // complex64 operator; convergence is only ever decided on an extended-precision residual.
     bool exact = !(outer == 0 && x0);
     if (outer == 0 && !x0) {
       PSFD_CUDA_TRY(cudaMemsetAsync(r64, 0, (size_t)nr * n * sizeof(zd), st));
@@ -1120,7 +1120,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
     PSFD_CUDA_TRY(cudaStreamSynchronize(st));
     if (!exact) {
-      // a warm start that may already meet the tolerance is judged on the exact residual
+      // a warm start that may already meet the tolerance is decided on the exact residual
       bool near = false;
       for (int r = 0; r < nr; ++r) near = near || hs[r].res1 <= 4.0 * o->tol * o->tol * bnorm2[r];
       if (near) {
