@@ -411,31 +411,31 @@ __global__ void __launch_bounds__(128) k_rows(RowArgs a) {
 #pragma unroll
     for (int m = 0; m < R; ++m)
       if (act) src[t + T * m] = cscale(v[m], a.scale);
-  } else {
+  } else if constexpr (OP == ROW_FWD) {
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : czero();
     PX::template to_freq<false>(v, t, a.tw);
-    if constexpr (OP == ROW_FWD) {
 #pragma unroll
-      for (int s = 0; s < R; ++s)
-        if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
-    } else {
-      // map the G row (rhs, c, zz, iy) to the y row (rhs, c, za0 + zz, iy)
-      const long per_c = (long)a.nab * a.ny;
-      const long r = act ? row : 0;
-      const long rhs = r / (3 * per_c), rem = r - rhs * 3 * per_c;
-      const long c = rem / per_c, rem2 = rem - c * per_c;
-      const long zz = rem2 / a.ny, iy = rem2 - zz * a.ny;
-      cf* __restrict__ dst = a.y + (((rhs * 3 + c) * a.nz + a.za0 + zz) * a.ny + iy) * NX;
+    for (int s = 0; s < R; ++s)
+      if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
+  } else {
+    // map the G row (rhs, c, zz, iy) to the y row (rhs, c, za0 + zz, iy); the y row is read with
+    // the G row, so that both latencies overlap
+    const long per_c = (long)a.nab * a.ny;
+    const long r = act ? row : 0;
+    const long rhs = r / (3 * per_c), rem = r - rhs * 3 * per_c;
+    const long c = rem / per_c, rem2 = rem - c * per_c;
+    const long zz = rem2 / a.ny, iy = rem2 - zz * a.ny;
+    cf* __restrict__ dst = a.y + (((rhs * 3 + c) * a.nz + a.za0 + zz) * a.ny + iy) * NX;
+    cf o[R];
 #pragma unroll
-      for (int s = 0; s < R; ++s) {
-        if (act) {
-          const int k = PX::freq_index(t, s);
-          const cf o = dst[k];
-          dst[k] = make_float2(fmaf(-a.scale, v[s].x, o.x), fmaf(-a.scale, v[s].y, o.y));
-        }
-      }
-    }
+    for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : czero();
+#pragma unroll
+    for (int s = 0; s < R; ++s) o[s] = act ? dst[PX::freq_index(t, s)] : czero();
+    PX::template to_freq<false>(v, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (act) dst[PX::freq_index(t, s)] = make_float2(fmaf(-a.scale, v[s].x, o[s].x), fmaf(-a.scale, v[s].y, o[s].y));
   }
 }
 
@@ -498,12 +498,12 @@ __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
     const float dre = a.cs * c0.x, dim = a.cs * (a.pc_conj ? -c0.y : c0.y);
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : czero();
+    float fv[R];   // the fill is loaded with the column, so that both latencies overlap
+#pragma unroll
+    for (int m = 0; m < R; ++m) fv[m] = act ? __ldg(f + (long)(t + T * m) * sx) : 0.f;
     PY::template to_time<true>(v, t, a.tw);
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      const float fv = act ? __ldg(f + (long)(t + T * m) * sx) : 0.f;
-      v[m] = cmul(v[m], make_float2(dre * fv, dim * fv));
-    }
+    for (int m = 0; m < R; ++m) v[m] = cmul(v[m], make_float2(dre * fv[m], dim * fv[m]));
     PY::template to_freq<false>(v, t, a.tw);
 #pragma unroll
     for (int s = 0; s < R; ++s)
