@@ -1084,11 +1084,13 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
   PSFD_CUDA_TRY(cudaStreamSynchronize(st));
   std::vector<double> bnorm2(nr), rr(nr, 0.0), rr0(nr, 0.0);
   for (int r = 0; r < nr; ++r) bnorm2[r] = hs[r].res0;
-  // E64 = x0 (HYBRID, FP64) or 0
+  // E64 = x0 (HYBRID, FP64) or 0.  The warm start only sets where the refinement begins, so its
+  // lateral transform runs in complex64 (kept in w.t, where the first residual reads it)
   if (x0) {
-    a64.a32 = (const cf*)x0; a64.o64 = E64;
+    PSFD_CUDA_TRY(cudaMemcpyAsync(w.t, x0, vbytes, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_lateral_transform(P, w.t, nplanes, true, (float)us))) return fail(rc);
+    a64.a32 = w.t; a64.o64 = E64;
     if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
-    if ((rc = transform64(P, E64, nplanes, true, us))) return fail(rc);
   } else {
     PSFD_CUDA_TRY(cudaMemsetAsync(E64, 0, (size_t)nr * n * sizeof(zd), st));
   }
@@ -1107,9 +1109,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     if (outer == 0 && !x0) {
       PSFD_CUDA_TRY(cudaMemsetAsync(r64, 0, (size_t)nr * n * sizeof(zd), st));
     } else if (outer == 0) {
-      a64.a64 = E64; a64.o32 = w.t; a64.skip = nullptr;
-      if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
-      if ((rc = apply_hybrid(P, w.t, w.v, 0, nullptr))) return fail(rc);
+      if ((rc = apply_hybrid(P, w.t, w.v, 0, nullptr))) return fail(rc);   // w.t = complex64 E (above)
       a64.a32 = w.v; a64.o64 = r64;
       if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
     } else {
