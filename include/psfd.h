@@ -19,9 +19,9 @@
  * - Every array pointer is caller-owned DEVICE memory unless the argument is
  *   documented as host memory.  Calls are asynchronous on the plan's stream
  *   unless stated otherwise; the library allocates only inside
- *   psfd_plan_create / psfd_background (plan-owned tables and scratch), inside
- *   psfd_solve when the caller passes no workspace (see
- *   psfd_solve_workspace_size) and, temporarily, inside psfd_spectral_upsample.
+ *   psfd_plan_create / psfd_background (plan-owned tables and scratch), on the
+ *   first psfd_apply64 of a plan (plan-owned FP64 tables), inside psfd_solve
+ *   when the caller passes no workspace (see psfd_solve_workspace_size) and, temporarily, inside psfd_spectral_upsample.
  * - Return codes: PSFD_OK (0) or one of the PSFD_ERR_* / PSFD_NOT_CONVERGED
  *   values; psfd_last_error() returns a message for the last failing call on
  *   the calling thread.  Argument errors are detected before any launch.
@@ -79,6 +79,12 @@ typedef struct {
   double theta_deg, phi_deg; /* incidence polar / azimuth angle; sets the Bloch shift       */
   int pml_planes;            /* PML thickness in planes at each z end (0 = periodic)        */
   double pml_R0;             /* nominal normal-incidence PML reflection (sets the strength) */
+  double pml_backing;        /* peak loss sigma_b of the PML's absorbing backing: eps_bg = 1 + i sigma
+                                on the outermost nb = max(1, pml_planes / 4) planes at each z end,
+                                where the two PMLs meet across the periodic wrap, with sigma =
+                                sigma_b ((nb - j) / nb)^2 on the j-th plane from the end (0 = none).
+                                A z-stretch leaves fields that are constant in z untouched, so
+                                without it a lateral mode near grazing keeps an undamped mode */
   int z_ml;                  /* plane index of the multilayer interface z_ml                */
   double eps_abs_re, eps_abs_im;  /* absorber permittivity; deps = fill * (eps_abs - 1)     */
   double m_min, k_ref, gamma, damp_eps_rel;  /* spectral damping (Eq. spectral_damping_mask);
@@ -101,7 +107,10 @@ typedef struct {
   int status;                /* PSFD_OK / PSFD_NOT_CONVERGED / PSFD_ERR_BREAKDOWN          */
   double r_rel;              /* true relative residual ||b - A E|| / ||b|| (FP64), Eq. relative_residual */
   double r_rel_recursive;    /* the solver's recursive estimate at exit                   */
-  double r_rel_initial;      /* ||b - A E_base|| / ||b|| before the first iteration       */
+  double r_rel_initial;      /* ||b - A E_base|| / ||b|| before the first iteration; for a
+                                refined warm start (psfd_solve_ex, refine = 1) it is formed
+                                with the complex64 operator unless that estimate is already
+                                at the tolerance, then with the extended-precision one     */
   int outer;                 /* outer FP64 refinement steps (psfd_solve_ex with refine)   */
   double r_rel_output;       /* FP64 relative residual of the returned complex64 field    */
 } psfd_info_t;
@@ -162,14 +171,27 @@ PSFD_API int psfd_reflection_tables(psfd_plan plan, double* rs, double* rp, doub
 
 /* ---------------------------------------------------------------- operator (Sec. 2.2)
  * y = A x with
- *   A E = curl_s curl_s E - k0^2 E - k0^2 deps (E + R E)    (Eqs. bg_source,
- *         vector_helmholtz_operator; derivatives pseudo-spectral, PML in z)
+ *   A E = curl_s curl_s E - k0^2 eps_bg E - k0^2 deps (E + R E)    (Eqs. bg_source,
+ *         vector_helmholtz_operator; derivatives pseudo-spectral, PML in z;
+ *         eps_bg = 1 except on the PML backing, see psfd_params_t.pml_backing)
  * flags: PSFD_PRECOND -> y = A M x (Eq. right_preconditioned);
  *        PSFD_ADJOINT -> y = A^H x (with PRECOND: M A^H x);
  *        PSFD_LAYERED -> y = A P x (P: layered-background preconditioner);
  *        PSFD_HYBRID  -> x, y in the HYBRID domain (no lateral transforms of x, y).
  * x, y: device [nrhs][3][nz][ny][nx]; x and y must not overlap. */
 PSFD_API int psfd_apply(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int flags);
+
+/* y = A x in FP64, the operator of Sec. 2.2 exactly as psfd_apply defines it
+ * (no preconditioner).  x, y: device complex128 arrays [nrhs][3][nz][ny][nx]
+ * of interleaved (re, im) doubles, real space, or HYBRID with PSFD_HYBRID (the
+ * only flag accepted; others give PSFD_ERR_ARG); x and y must not overlap.  The
+ * lateral and axial transforms and the products run in double-float arithmetic
+ * (about 48 significant bits) where a thread holds at most 16 points of a
+ * transform, in FP64 elsewhere; the multilayer tables are the FP64 ones.  This
+ * is the apply of the FP64 refinement residual of psfd_solve_ex.  The first call
+ * on a plan builds the FP64 tables (plan-owned, freed with the plan) and the
+ * first real-space call a plan-owned copy buffer of x. */
+PSFD_API int psfd_apply64(psfd_plan plan, const double* x, double* y, int flags);
 
 /* y = M x, spectral damping (Eq. spectral_damping_action): componentwise 3-D
  * Fourier multiplier m(k); with PSFD_LAYERED in flags, y = P x instead.
@@ -291,6 +313,24 @@ PSFD_API int psfd_solve_batched(const psfd_plan* plans, int nplans, const psfd_c
  * iteration k < capacity and right-hand side r to hist[r * capacity + k] (HOST). */
 PSFD_API int psfd_set_history(psfd_plan plan, double* hist, int capacity);
 
+/* ---------------------------------------------------------------- physics-informed loss (Sec. 3, Eq. loss)
+ * For every right-hand side a of the plan (the fill and b of the last psfd_background):
+ *   J[a] = (1/N) ||r_a||^2 + (lam_hf / N) ||w(nu) F3[r_a]||^2,   r_a = A E_a - b_a,
+ * N = nx ny nz, w(nu) = w0 + eta_hf |nu| with nu the 3-D DFT frequency in cycles per
+ * sample (|nu| <= sqrt(3)/2, the Nyquist index counted negative), F3 the unitary 3-D
+ * DFT (the paper fixes none of lam_hf, w0, eta_hf or the normalisation of F3).  grad
+ * (nullable) receives dJ[a]/dRe E_a + i dJ[a]/dIm E_a =
+ *   (2/N) A^H [ r_a + lam_hf F3^H (w^2 F3 r_a) ]
+ * (torch's convention for the gradient of a real function of a complex tensor).
+ * E, b, grad: device real-space [nrhs][3][nz][ny][nx]; grad must not overlap E or b.
+ * J: HOST double [nrhs].  workspace: device scratch of
+ * psfd_physics_loss_workspace_size() bytes (PSFD_ERR_ARG if smaller or NULL).  Operator
+ * applies and transforms in complex64, the two sums in FP64; synchronises the plan's
+ * stream.  PSFD_ERR_STATE before psfd_background. */
+PSFD_API size_t psfd_physics_loss_workspace_size(psfd_plan plan);
+PSFD_API int psfd_physics_loss(psfd_plan plan, const psfd_c64* E, const psfd_c64* b, double lam_hf, double w0,
+                               double eta_hf, double* J, psfd_c64* grad, void* workspace, size_t workspace_bytes);
+
 /* ---------------------------------------------------------------- factorised FNO (Sec. 2.1, Eqs. 1-5)
  * Device pointers to float32 parameters; complex kernels as psfd_c64.
  *   lift_w [dv][4], lift_b [dv]                         (inputs: a, x/Lx, y/Ly, z/Lz)
@@ -298,7 +338,10 @@ PSFD_API int psfd_set_history(psfd_plan plan, double* hist, int capacity);
  *   kz  [L][mz][dv][dv]
  *   w1 [L][dh][dv], b1 [L][dh], w2 [L][dv][dh], b2 [L][dv]
  *   q1 [dq][dv], qb1 [dq], q2 [6][dq], qb2 [6]           (6 = Re/Im of Ex, Ey, Ez)
- * Mode mixing rounds both operands to bfloat16 and accumulates in float32. */
+ * Mode mixing rounds both operands to bfloat16 and accumulates in float32.
+ * PSFD_MIX_FP32=1 in the environment keeps both operands in float32 instead (a
+ * verification mode: the network without the bfloat16 rounding, on the SIMT
+ * mixing kernel). */
 typedef struct {
   int dv, dh, layers, mx, my, mz, dq;
   const float* lift_w; const float* lift_b;

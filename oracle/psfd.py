@@ -15,6 +15,15 @@ PSFD paper; these are the readings used throughout):
 * the axial direction is a periodic FFT box that contains a PML at both ends:
   d/dz -> D_z = s(z)^-1 F_z^-1 (i k_z) F_z with s = 1 + i alpha (d/d_pml)^3
   and alpha = 4 ln(1/R0) / (2 k0 d_pml) (stretched-coordinate PML, Sec. 2.2).
+  The two PMLs meet across the periodic wrap.  A z-stretch cannot attenuate a
+  field that is constant in z (D_z annihilates it for any s), so a lateral
+  Bloch mode near grazing, |k_par| ~ k0, would keep an undamped standing mode
+  with the real eigenvalue |k_par|^2 - k0^2 ~ 0.  The PML is therefore backed
+  by an absorbing layer, as a PML is backed by a terminating wall: on the
+  outermost nb = max(1, npml / 4) planes at each end, eps_bg = 1 + i sigma with
+  sigma = sigma_b ((nb - j) / nb)^2 on the j-th plane from the end (sigma_b =
+  pml_backing), which the scattered field reaches only after the PML has
+  attenuated every wave that is not near grazing.
 * unknown: the scattered field E_s in the mask-only domain.  The multilayer
   enters through the reflection operator R (Sec. 2.2: up/down split, TE/TM
   split, transfer-matrix reflection, phase-matched propagation), applied to the
@@ -108,6 +117,16 @@ class Grid:
                 self.sigma[k] = alpha * (d / dpml) ** 3
         self.s = (1.0 + 1j * self.sigma).to(C128)
         self.s_inv = 1.0 / self.s
+        # absorbing backing of the PML: eps_bg = 1 + i sigma(z) on the outermost nb = max(1, npml / 4)
+        # planes at each end of the box (where the two PMLs meet across the periodic wrap), with
+        # sigma = sigma_b ((nb - j) / nb)^2 on the j-th plane from the end (j = 0 outermost)
+        self.backing = torch.zeros(self.nz, dtype=F64)
+        sb = float(p.get("pml_backing", 0.0))
+        if npml > 0 and sb > 0:
+            nb = max(1, npml // 4)
+            for j in range(nb):
+                self.backing[j] = self.backing[self.nz - 1 - j] = sb * ((nb - j) / nb) ** 2
+        self.eps_bg = (1.0 + 1j * self.backing).to(C128)
         # spectral damping (Eq. spectral_damping_mask)
         self.m_min = float(p["m_min"])
         self.k_ref = float(p["k_ref"]) if float(p["k_ref"]) > 0 else self.k0
@@ -286,17 +305,20 @@ def deps_field(g: Grid, fill: torch.Tensor) -> torch.Tensor:
 
 
 def apply_A(g: Grid, E: torch.Tensor, fill: torch.Tensor) -> torch.Tensor:
-    """A E = curl_s curl_s E - k0^2 E - k0^2 deps (E + R E)  (Eqs. bg_source, vector_helmholtz_operator)."""
+    """A E = curl_s curl_s E - k0^2 eps_bg E - k0^2 deps (E + R E)  (Eqs. bg_source,
+    vector_helmholtz_operator); eps_bg = 1 except on the PML's absorbing backing."""
     E = E.to(C128)
     de = deps_field(g, fill)[None]
-    return curlcurl(g, E) - g.k0 ** 2 * E - g.k0 ** 2 * de * (E + reflect(g, E))
+    ebg = g.eps_bg[None, :, None, None]
+    return curlcurl(g, E) - g.k0 ** 2 * ebg * E - g.k0 ** 2 * de * (E + reflect(g, E))
 
 
 def apply_AH(g: Grid, Y: torch.Tensor, fill: torch.Tensor) -> torch.Tensor:
-    """Adjoint A^H Y = (curl~ curl~) Y - k0^2 Y - k0^2 (I + R)^H (conj(deps) Y)."""
+    """Adjoint A^H Y = (curl~ curl~) Y - k0^2 conj(eps_bg) Y - k0^2 (I + R)^H (conj(deps) Y)."""
     Y = Y.to(C128)
     w = deps_field(g, fill).conj()[None] * Y
-    return curlcurl(g, Y, adjoint_form=True) - g.k0 ** 2 * Y - g.k0 ** 2 * (w + reflect_adjoint(g, w))
+    ebg = g.eps_bg.conj()[None, :, None, None]
+    return curlcurl(g, Y, adjoint_form=True) - g.k0 ** 2 * ebg * Y - g.k0 ** 2 * (w + reflect_adjoint(g, w))
 
 
 def damping_multiplier(g: Grid) -> torch.Tensor:
@@ -386,13 +408,21 @@ def layered_blocks(g: Grid, fill: torch.Tensor) -> torch.Tensor:
     return mats
 
 
-def apply_P_layered(g: Grid, fill: torch.Tensor, X: torch.Tensor, mats: torch.Tensor = None) -> torch.Tensor:
-    """y = A0^-1 x per lateral mode (real-space fields (3, nz, ny, nx))."""
-    if mats is None:
-        mats = layered_blocks(g, fill)
+def apply_P_layered(g: Grid, fill: torch.Tensor, X: torch.Tensor, mats: torch.Tensor = None,
+                    lu=None) -> torch.Tensor:
+    """y = A0^-1 x per lateral mode (real-space fields (3, nz, ny, nx)).
+
+    ``lu``: the (LU, pivots) of torch.linalg.lu_factor(mats), for repeated applications of the
+    same blocks (LU with partial pivoting, factored once); otherwise each call solves with ``mats``."""
     n = 3 * g.nz
     Xh = _fft2(X.to(C128)).permute(2, 3, 0, 1).reshape(g.ny, g.nx, n, 1)
-    Yh = torch.linalg.solve(mats, Xh).reshape(g.ny, g.nx, 3, g.nz).permute(2, 3, 0, 1)
+    if lu is not None:
+        Yh = torch.linalg.lu_solve(lu[0], lu[1], Xh)
+    else:
+        if mats is None:
+            mats = layered_blocks(g, fill)
+        Yh = torch.linalg.solve(mats, Xh)
+    Yh = Yh.reshape(g.ny, g.nx, 3, g.nz).permute(2, 3, 0, 1)
     return _ifft2(Yh)
 
 

@@ -1,12 +1,12 @@
 """torch.autograd bridge for the PSFD residual (differentiation through the operator).
 
-PSFDApply wraps y = A E (psfd_apply, real space) with the hand-written adjoint
-E_bar = A^H y_bar (psfd_apply with PSFD_ADJOINT) as its backward, so that the
-physics-informed loss of Eq. loss,
+PhysicsLoss wraps the library's psfd_physics_loss: the physics-informed loss of Eq. loss,
     J = (1/N) sum_a ||r_a||^2 + (lambda_hf / N) sum_a ||w(nu) F3[r_a]||^2,  r = A E - b,
-can be differentiated with respect to a predicted field E without precomputed
-solutions.  Both directions run in the library's kernels; torch only holds the
-tensors (the loss reductions and F3 of the penalty term are torch GPU ops).
+and its gradient (2/N) A^H [r + lambda_hf F3^H (w^2 F3 r)], both computed by the library's
+kernels (operator, hand-written adjoint, its own 3-D FFTs, FP64 sums); the backward only
+scales the stored gradient.  So J can be differentiated with respect to a predicted field E
+without precomputed solutions.  PSFDApply wraps y = A E (psfd_apply, real space) with the
+adjoint A^H (psfd_apply with PSFD_ADJOINT) as its backward, for other losses of the residual.
 
 FNOApply wraps the factorised FNO (Sec. 2.1) with its hand-written reverse pass
 (fno_forward_train / fno_backward), so that J can be minimised over the network
@@ -54,19 +54,23 @@ def fno_apply(trainer: "psfd.FnoTrainer", params, a: torch.Tensor) -> torch.Tens
     return FNOApply.apply(a, trainer, *[params[n] for n in psfd.FNO_PARAM_NAMES])
 
 
-def frequency_weight(nz: int, ny: int, nx: int, w0: float = 1.0, eta_hf: float = 1.0, device="cuda"):
-    f = lambda n: torch.fft.fftfreq(n, device=device, dtype=torch.float32)
-    nu = torch.sqrt(f(nz)[:, None, None] ** 2 + f(ny)[None, :, None] ** 2 + f(nx)[None, None, :] ** 2)
-    return w0 + eta_hf * nu
+class PhysicsLoss(torch.autograd.Function):
+    """J = mean over the plan's right-hand sides of Eq. loss (psfd_physics_loss)."""
+
+    @staticmethod
+    def forward(ctx, E: torch.Tensor, plan: "psfd.Plan", b: torch.Tensor, lam_hf: float, w0: float, eta_hf: float):
+        J, g = plan.physics_loss(E, b, lam_hf, w0, eta_hf, grad=bool(ctx.needs_input_grad[0]))
+        ctx.save_for_backward(g if g is not None else torch.empty(0, device=E.device))
+        ctx.nrhs = len(J)
+        return torch.tensor(float(J.mean()), dtype=torch.float32, device=E.device)
+
+    @staticmethod
+    def backward(ctx, gJ: torch.Tensor):
+        (g,) = ctx.saved_tensors
+        return g * (gJ.to(torch.float32) / ctx.nrhs), None, None, None, None, None
 
 
 def physics_loss(plan: "psfd.Plan", E: torch.Tensor, b: torch.Tensor, lam_hf: float = 0.1, w0: float = 1.0,
                  eta_hf: float = 1.0) -> torch.Tensor:
     """Eq. loss averaged over the right-hand sides: E, b [nrhs][3][nz][ny][nx] complex64."""
-    r = PSFDApply.apply(E, plan) - b
-    nz, ny, nx = r.shape[-3:]
-    N = nz * ny * nx
-    wgt = frequency_weight(nz, ny, nx, w0, eta_hf, device=r.device)
-    R3 = torch.fft.fftn(r, dim=(-3, -2, -1), norm="ortho")
-    per = (r.abs() ** 2).sum(dim=(-4, -3, -2, -1)) / N + lam_hf * ((wgt * R3.abs()) ** 2).sum(dim=(-4, -3, -2, -1)) / N
-    return per.mean()
+    return PhysicsLoss.apply(E, plan, b, lam_hf, w0, eta_hf)

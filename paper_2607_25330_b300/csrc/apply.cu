@@ -26,6 +26,7 @@ struct AxialArgs {
   const float* ky;
   const float* kz;
   const cf* sinv;
+  const cf* kbg;    // [nz] k0^2 eps_bg(z)
   const cf* tw;
   const float4* refl;
   const cf* kz0;
@@ -38,6 +39,14 @@ struct AxialArgs {
 };
 
 enum { AX_AM = 0, AX_A = 1, AX_M = 2, AX_AH = 3 };
+
+// k0^2 eps_bg(z) of the operator (its conjugate in the adjoint)
+template <int MODE>
+__device__ __forceinline__ cf kbg_at_(const AxialArgs& a, int z) {
+  const cf v = __ldg(a.kbg + z);
+  return MODE == AX_AH ? make_float2(v.x, -v.y) : v;
+}
+#define kbg_at(a, z) kbg_at_<MODE>(a, z)
 
 // The column work is a loop over "jobs"; each job is
 //   source (time layout) -> FFT_z -> one spectral factor -> IFFT_z -> post-op
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
       for (int m = 0; m < R; ++m) {
         const int z = t + T * m;
         const cf qz = unst(0, m), cx = unst(2, m), cy = v[m];
-        cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
+        cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cmul(qz, kbg_at(a, z)));
         if (z >= a.za0 && z < a.za1 && act) Wz = csub(Wz, G[(2L * nab + z - a.za0) * nc + col]);
         if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
       }
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
       for (int m = 0; m < R; ++m) {
         const int z = t + T * m;
         const cf qz = unst(0, m), cx = unst(2, m), cy = v[m];
-        const cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, a.k02));
+        const cf Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cmul(qz, kbg_at(a, z)));
         if (act) y[(long)(2 * NZ + z) * nc + col] = Wz;
         if (z >= a.za0 && z < a.za1 && act) {
           cf prof = czero();
@@ -292,8 +301,9 @@ __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
         const cf d = (MODE == AX_AH) ? v[m] : cmul(v[m], __ldg(a.sinv + z));
         const cf qx = unst(3, m), qy = unst(1, m);
         const cf cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        cf W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, a.k02))
-                          : csub(csub(cmul(iky, cz), d), cscale(qx, a.k02));
+        const cf kb = kbg_at(a, z);
+        cf W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cmul(qy, kb))
+                          : csub(csub(cmul(iky, cz), d), cmul(qx, kb));
         if (MODE == AX_AH) {
           if (z >= a.za0 && z < a.za1 && act) W = csub(W, G[((long)c * nab + z - a.za0) * nc + col]);
           if (z == a.z_ml) W = csub(W, c == 0 ? rh0 : rh1);
@@ -309,7 +319,7 @@ static int run_axial(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   constexpr int P_ = 32 / T, R = NZ / T;
   AxialArgs a;
   a.x = x; a.y = y; a.G = P->G;
-  a.kx = P->kx; a.ky = P->ky; a.kz = P->kz; a.sinv = P->sinv; a.tw = P->tw_z;
+  a.kx = P->kx; a.ky = P->ky; a.kz = P->kz; a.sinv = P->sinv; a.kbg = P->kbg; a.tw = P->tw_z;
   a.refl = P->R.refl; a.kz0 = P->R.kz0; a.done = done;
   a.nx = P->nx; a.ncols = P->ncols; a.vstride = P->nvec;
   a.gstride = 3L * (P->za1 - P->za0) * P->ncols;

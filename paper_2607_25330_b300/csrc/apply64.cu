@@ -28,6 +28,7 @@ struct Ax64 {
   const double* kz;
   const cff* sinvf;   // [nz] PML stretch 1/s
   const zd* sinv;
+  const double* sback;  // [nz] loss sigma_b(z) of the PML backing (eps_bg = 1 + i sigma_b)
   const cff* twf;     // [nz] twiddles
   const zd* tw;
   const double2* rs;
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
       for (int m = 0; m < R; ++m) {
         const int z = t + T * m;
         const C qz = unst(0, m), cx = unst(2, m), cy = v[m];
-        const C Wz = csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, k02));
+        const C Wz = csub(csub(csub(cmul(ikx, cy), cmul(iky, cx)), cscale(qz, k02)),
+                          ctimesi(cscale(qz, k02 * RT(a.sback[z]))));
         if (act) y[(long)(2 * NZ + z) * nc + col] = to_zd(Wz);
         if (z >= a.za0 && z < a.za1 && act) {
           zd prof = make_double2(0.0, 0.0);
@@ -150,8 +152,10 @@ __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
         const C d = cmul(v[m], sinv[t + T * m]);
         const C qx = unst(3, m), qy = unst(1, m);
         const C cz = csub(cmul(ikx, qy), cmul(iky, qx));
-        const C W = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, k02))
-                                 : csub(csub(cmul(iky, cz), d), cscale(qx, k02));
+        const C q = (job == 5) ? qy : qx;
+        const C W0 = (job == 5) ? csub(csub(d, cmul(ikx, cz)), cscale(qy, k02))
+                                : csub(csub(cmul(iky, cz), d), cscale(qx, k02));
+        const C W = csub(W0, ctimesi(cscale(q, k02 * RT(a.sback[t + T * m]))));
         if (act) y[(long)(c * NZ + t + T * m) * nc + col] = to_zd(W);
       }
     }
@@ -347,7 +351,7 @@ int axial64_run(psfd_plan_s* P, const zd* x, zd* y) {
   a.nx = P->nx; a.ncols = P->ncols; a.vstride = P->nvec;
   a.gstride = 3L * (P->za1 - P->za0) * P->ncols;
   a.z_ml = P->p.z_ml; a.za0 = P->za0; a.za1 = P->za1;
-  a.dz = P->p.dz; a.k02 = P->k0 * P->k0;
+  a.dz = P->p.dz; a.k02 = P->k0 * P->k0; a.sback = P->F.sback;
   const int warps = 2;
   const long per = warps * (32 / T);
   dim3 g((unsigned)((P->ncols + per - 1) / per), (unsigned)P->nrhs);
@@ -402,6 +406,8 @@ int fp64_prepare(psfd_plan_s* P) {
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.ky, P->ny * 8));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.kz, P->nz * 8));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.sinv, P->nz * 16));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.sback, P->nz * 8));
+    PSFD_CUDA_TRY(cudaMemcpy(F.sback, P->sback_host.data(), P->nz * 8, cudaMemcpyHostToDevice));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.twx, P->nx * 16));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.twy, P->ny * 16));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.twz, P->nz * 16));
@@ -438,7 +444,7 @@ int fp64_prepare(psfd_plan_s* P) {
 
 void fp64_free(psfd_plan_s* P) {
   Fp64Tables& F = P->F;
-  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.twx, F.twy, F.twz, F.G, F.kz_f, F.sinv_f, F.twx_f, F.twy_f, F.twz_f};
+  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.sback, F.twx, F.twy, F.twz, F.G, F.X, F.kz_f, F.sinv_f, F.twx_f, F.twy_f, F.twz_f};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   F = Fp64Tables();
@@ -499,4 +505,25 @@ int transform64(psfd_plan_s* P, zd* buf, long nplanes, bool forward, double scal
   if ((rc = cols64(P->ny, c, C64_INV, P->stream))) return rc;
   r.scale = scale;
   return rows64(P->nx, r, R64_INV, P->stream);
+}
+
+// y = A x in FP64 through the C ABI (the operator of the refinement residual).
+extern "C" int psfd_apply64(psfd_plan P, const double* x, double* y, int flags) {
+  if (!P || !x || !y) { psfd_set_error("psfd_apply64: null argument"); return PSFD_ERR_ARG; }
+  if (!P->have_background) { psfd_set_error("psfd_apply64: call psfd_background first"); return PSFD_ERR_STATE; }
+  if ((const void*)x == (void*)y) { psfd_set_error("psfd_apply64: x and y must not overlap"); return PSFD_ERR_ARG; }
+  if (flags & ~PSFD_HYBRID) { psfd_set_error("psfd_apply64: only PSFD_HYBRID is accepted"); return PSFD_ERR_ARG; }
+  int rc = fp64_prepare(P);
+  if (rc) return rc;
+  const zd* xi = reinterpret_cast<const zd*>(x);
+  zd* yo = reinterpret_cast<zd*>(y);
+  if (flags & PSFD_HYBRID) return apply64_hybrid(P, xi, yo);
+  const size_t n = (size_t)P->nrhs * P->nvec;
+  if (!P->F.X) PSFD_CUDA_TRY(cudaMalloc((void**)&P->F.X, n * sizeof(zd)));
+  PSFD_CUDA_TRY(cudaMemcpyAsync(P->F.X, xi, n * sizeof(zd), cudaMemcpyDeviceToDevice, P->stream));
+  const double us = 1.0 / sqrt((double)P->ncols);
+  const long nplanes = (long)P->nrhs * 3 * P->nz;
+  if ((rc = transform64(P, P->F.X, nplanes, true, us))) return rc;
+  if ((rc = apply64_hybrid(P, P->F.X, yo))) return rc;
+  return transform64(P, yo, nplanes, false, us);
 }

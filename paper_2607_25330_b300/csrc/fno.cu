@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <vector>
 
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(128) k_yfwd(const cf* __restrict__ T1, cf* __r
 constexpr int MIX_TN = 64;
 __global__ void __launch_bounds__(256) k_mix(const cf* __restrict__ V, cf* __restrict__ U, const cf* __restrict__ K,
                                              int C, long NB, int mx, int MX, int offy, int offx, bool conjT = false,
-                                             bool round_v = true) {
+                                             bool round_v = true, bool round_k = true) {
   extern __shared__ float sm[];
   float* Kr = sm;                       // [C][C]
   float* Ki = Kr + C * C;
@@ -117,8 +118,9 @@ __global__ void __launch_bounds__(256) k_mix(const cf* __restrict__ V, cf* __res
     // conjT: the adjoint mixing uses K^H, i.e. entry (o, i) = conj(K[i][o])
     const int o = e / C, i = e - o * C;
     cf k = conjT ? Km[i * C + o] : Km[e];
-    Kr[e] = bf16r(k.x);
-    Ki[e] = conjT ? -bf16r(k.y) : bf16r(k.y);
+    const float kr = round_k ? bf16r(k.x) : k.x, ki = round_k ? bf16r(k.y) : k.y;
+    Kr[e] = kr;
+    Ki[e] = conjT ? -ki : ki;
   }
   const long n0 = (long)blockIdx.x * MIX_TN;
   const cf* Vm = V + mode * C * NB;
@@ -801,25 +803,34 @@ static bool z_synthesis(const Dims& d, const FnoWs& ws, const cf* U, float* out,
 
 static size_t mix_smem_bytes(int C) { return (2 * C * C + 2 * C * MIX_TN) * sizeof(float); }
 
+// PSFD_MIX_FP32=1: the forward mixing keeps float32 operands (no bfloat16 rounding), on the SIMT kernel
+static bool mix_fp32() {
+  const char* e = getenv("PSFD_MIX_FP32");
+  return e && e[0] == '1';
+}
+
 // per-mode mixing of a branch; xy modes: grid (n-tiles, mx*my); z modes: grid (n-tiles, mz) with mx = MX = 1
 static void mix_xy(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, cudaStream_t s) {
   const long NB = (long)d.B * d.nz;
-  if (!adjoint && fno_mix_tc_enabled(d.C)) {
+  const bool exact = !adjoint && mix_fp32();
+  if (!adjoint && !exact && fno_mix_tc_enabled(d.C)) {
     fno_mix_tc(V, U, K, NB, d.mx * d.my, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2, s);
     return;
   }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)(d.mx * d.my));
   k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2,
-                                           adjoint, !adjoint);
+                                           adjoint, !adjoint && !exact, !exact);
 }
 static void mix_z(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, cudaStream_t s) {
   const long NB = (long)d.B * d.nx * d.ny;
-  if (!adjoint && fno_mix_tc_enabled(d.C)) {
+  const bool exact = !adjoint && mix_fp32();
+  if (!adjoint && !exact && fno_mix_tc_enabled(d.C)) {
     fno_mix_tc(V, U, K, NB, d.mz, 1, 1, (d.MZ - d.mz) / 2, 0, s);
     return;
   }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)d.mz);
-  k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, adjoint, !adjoint);
+  k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, adjoint, !adjoint && !exact,
+                                           !exact);
 }
 static void mixgrad_xy(const Dims& d, const cf* Ubar, const cf* V, cf* dK, float scale, cudaStream_t s) {
   const long NB = (long)d.B * d.nz;
@@ -1039,23 +1050,11 @@ __global__ void k_pad_spectrum(const cf* __restrict__ src, cf* __restrict__ dst,
   dst[o] = cscale(src[i], scale);
 }
 
-extern "C" int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0, psfd_c64* dst, int nx,
-                                      int ny, int nz, void* stream) {
-  if (!src || !dst || nb <= 0) { psfd_set_error("psfd_spectral_upsample: null argument"); return PSFD_ERR_ARG; }
-  if (nx < nx0 || ny < ny0 || nz < nz0 || !lateral_supported(nx0) || !lateral_supported(ny0) ||
-      !axial_supported(nz0) || !lateral_supported(nx) || !lateral_supported(ny) || !axial_supported(nz)) {
-    psfd_set_error("psfd_spectral_upsample: unsupported sizes");
-    return PSFD_ERR_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
+// the transforms of psfd_spectral_upsample on caller-provided scratch (tmp: nb * n0, tw: twiddles)
+static int upsample_run(const psfd_c64* src, int nb, int nx0, int ny0, int nz0, psfd_c64* dst, int nx, int ny, int nz,
+                        cf* tmp, cf* tw, const std::vector<cf>* t6, const int* sizes, const size_t* twoff,
+                        cudaStream_t s) {
   const long n0 = (long)nx0 * ny0 * nz0, n1 = (long)nx * ny * nz;
-  cf *tmp = nullptr, *tw = nullptr;
-  std::vector<cf> t6[6];
-  int sizes[6] = {nx0, ny0, nz0, nx, ny, nz};
-  size_t twoff[7] = {0};
-  for (int k = 0; k < 6; ++k) { host_tw(sizes[k], t6[k]); twoff[k + 1] = twoff[k] + sizes[k]; }
-  PSFD_CUDA_TRY(cudaMalloc((void**)&tmp, (size_t)nb * n0 * sizeof(cf)));
-  PSFD_CUDA_TRY(cudaMalloc((void**)&tw, twoff[6] * sizeof(cf)));
   for (int k = 0; k < 6; ++k)
     PSFD_CUDA_TRY(cudaMemcpy(tw + twoff[k], t6[k].data(), sizes[k] * sizeof(cf), cudaMemcpyHostToDevice));
   PSFD_CUDA_TRY(cudaMemcpyAsync(tmp, src, (size_t)nb * n0 * sizeof(cf), cudaMemcpyDeviceToDevice, s));
@@ -1072,7 +1071,36 @@ extern "C" int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int 
   if ((rc = launch_cols(ny, nx, (cf*)dst, (long)nb * nz * nx, false, 1.f, tw + twoff[4], s))) return rc;
   if ((rc = launch_rows(nx, (cf*)dst, (long)nb * nz * ny, false, 1.f, tw + twoff[3], s))) return rc;
   PSFD_CUDA_TRY(cudaStreamSynchronize(s));
-  cudaFree(tmp);
-  cudaFree(tw);
   return PSFD_OK;
+}
+
+extern "C" int psfd_spectral_upsample(const psfd_c64* src, int nb, int nx0, int ny0, int nz0, psfd_c64* dst, int nx,
+                                      int ny, int nz, void* stream) {
+  if (!src || !dst || nb <= 0) { psfd_set_error("psfd_spectral_upsample: null argument"); return PSFD_ERR_ARG; }
+  if (nx < nx0 || ny < ny0 || nz < nz0 || !lateral_supported(nx0) || !lateral_supported(ny0) ||
+      !axial_supported(nz0) || !lateral_supported(nx) || !lateral_supported(ny) || !axial_supported(nz)) {
+    psfd_set_error("psfd_spectral_upsample: unsupported sizes");
+    return PSFD_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long n0 = (long)nx0 * ny0 * nz0;
+  cf *tmp = nullptr, *tw = nullptr;
+  std::vector<cf> t6[6];
+  int sizes[6] = {nx0, ny0, nz0, nx, ny, nz};
+  size_t twoff[7] = {0};
+  for (int k = 0; k < 6; ++k) { host_tw(sizes[k], t6[k]); twoff[k + 1] = twoff[k] + sizes[k]; }
+  int rc = PSFD_OK;
+  cudaError_t e = cudaMalloc((void**)&tmp, (size_t)nb * n0 * sizeof(cf));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&tw, twoff[6] * sizeof(cf));
+  if (e != cudaSuccess) {
+    psfd_set_error("psfd_spectral_upsample: cudaMalloc: %s", cudaGetErrorString(e));
+    rc = PSFD_ERR_CUDA;
+  } else {
+    rc = upsample_run(src, nb, nx0, ny0, nz0, dst, nx, ny, nz, tmp, tw, t6, sizes, twoff, s);
+    if (rc != PSFD_OK) cudaStreamSynchronize(s);   // nothing queued may still read the scratch when it is freed
+  }
+  // the scratch is released on every path, failing ones included
+  if (tmp) cudaFree(tmp);
+  if (tw) cudaFree(tw);
+  return rc;
 }

@@ -20,11 +20,13 @@ struct Fp64Tables {
   double* ky = nullptr;
   double* kz = nullptr;
   double2* sinv = nullptr;
+  double* sback = nullptr;   // [nz] sigma_b(z) of the PML backing
   double2* twx = nullptr;
   double2* twy = nullptr;
   double2* twz = nullptr;
   double2* G = nullptr;
   size_t G_elems = 0;
+  double2* X = nullptr;      // [nrhs][3][nz][ny][nx] input copy of the real-space psfd_apply64
   // double-float (hi, lo) copies used by the extended-precision transforms
   float* kz_f = nullptr;
   float* sinv_f = nullptr;
@@ -50,6 +52,9 @@ struct psfd_plan_s {
   float* ky = nullptr;       // [ny]
   float* kz = nullptr;       // [nz] axial wavenumbers (FFT order)
   cf* sinv = nullptr;        // [nz] 1 / s(z)
+  cf* kbg = nullptr;         // [nz] k0^2 eps_bg(z) = k0^2 (1 + i sigma_b(z)) (the PML backing)
+  float* sback = nullptr;    // [nz] sigma_b(z)
+  std::vector<double> sback_host;
   cf* tw_x = nullptr;        // [nx] exp(-2 pi i m / nx)
   cf* tw_y = nullptr;
   cf* tw_z = nullptr;

@@ -51,6 +51,7 @@ struct LayArgs {
   const cf* D;          // [nz][nz] stretched axial derivative
   const cf* D2;         // [nz][nz] D * D
   const cf* deps;       // [nz] laterally averaged contrast
+  const float* sb;      // [nz] loss sigma_b(z) of the PML backing (eps_bg = 1 + i sigma_b)
   float k0sq, dz;
   int nx, ny, nz, zml;
   int pair;             // 1: blocks stored for rows 0 .. ny/2 only (ky and -ky share them)
@@ -121,7 +122,7 @@ __device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
   if (!TM) {
     cf v = cneg(a.D2[i * nz + j]);
     const cf de = a.deps[i];
-    if (i == j) v = cadd(v, make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * de.y));
+    if (i == j) v = cadd(v, make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[i])));
     if (j == a.zml && i >= a.zml) v = csub(v, cscale(cmul(cmul(de, m.rs), upgoing(a, m, i)), a.k0sq));
     return v;
   }
@@ -129,7 +130,7 @@ __device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
   const cf de = a.deps[ii];
   if (bi == 0 && bj == 0) {
     cf v = cneg(a.D2[ii * nz + jj]);
-    if (ii == jj) v = cadd(v, make_float2(-a.k0sq * (1.f + de.x), -a.k0sq * de.y));
+    if (ii == jj) v = cadd(v, make_float2(-a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[ii])));
     if (jj == a.zml && ii >= a.zml) v = csub(v, cscale(cmul(cmul(de, m.rp), upgoing(a, m, ii)), a.k0sq));
     return v;
   }
@@ -143,7 +144,7 @@ __device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
     }
     return v;
   }
-  if (ii == jj) return make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * de.y);
+  if (ii == jj) return make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[ii]));
   return czero();
 }
 
@@ -866,7 +867,7 @@ LayArgs lay_args(psfd_plan_s* P) {
   LayArgs a{};
   a.kx = P->kx; a.ky = P->ky; a.refl = P->R.refl; a.kz0 = P->R.kz0;
   a.D = P->lay_D; a.D2 = P->lay_D2; a.deps = P->lay_deps;
-  a.k0sq = (float)(P->k0 * P->k0); a.dz = (float)P->p.dz;
+  a.k0sq = (float)(P->k0 * P->k0); a.dz = (float)P->p.dz; a.sb = P->sback;
   a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.zml = P->p.z_ml;
   a.pair = layered_pairs(P) ? 1 : 0;
   a.mats = P->lay; a.err = P->lay_err;

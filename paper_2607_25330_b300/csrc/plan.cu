@@ -346,6 +346,19 @@ static double host_fftk(int i, int n, double d) {
 double fft_wavenumber(int i, int n, double d) { return host_fftk(i, n, d); }
 
 // 1/s(z) of the stretched-coordinate PML: s = 1 + i alpha (d/d_pml)^3, alpha = 4 ln(1/R0) / (2 k0 d_pml)
+// sigma(z) of the PML's absorbing backing: on the outermost nb = max(1, np / 4) planes of each end
+// of the box (where the two PMLs meet across the periodic wrap), pml_backing ((nb - j) / nb)^2 on
+// the j-th plane from the end; 0 elsewhere
+void pml_backing64(const psfd_params_t& p, std::vector<double>& sb) {
+  sb.assign(p.nz, 0.0);
+  if (p.pml_planes <= 0 || !(p.pml_backing > 0)) return;
+  const int nb = std::max(1, p.pml_planes / 4);
+  for (int j = 0; j < nb; ++j) {
+    const double w = (double)(nb - j) / nb;
+    sb[j] = sb[p.nz - 1 - j] = p.pml_backing * w * w;
+  }
+}
+
 void pml_sinv64(const psfd_plan_s* P, std::vector<zd>& sinv) {
   const psfd_params_t& p = P->p;
   sinv.resize(p.nz);
@@ -379,7 +392,7 @@ static int upload(void** dst, const void* src, size_t bytes) {
 static void plan_free(psfd_plan_s* P) {
   fp64_free(P);
   layered_free(P);
-  void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
+  void* ptrs[] = {P->kx, P->ky, P->kz, P->sinv, P->kbg, P->sback, P->tw_x, P->tw_y, P->tw_z, P->R.rs64, P->R.rp64,
                   P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err, P->pc, P->pc64};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -398,7 +411,8 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
     return PSFD_ERR_ARG;
   }
   if (p.pml_planes < 0 || 2 * p.pml_planes >= p.nz || p.z_ml < 0 || p.z_ml >= p.nz ||
-      (p.pml_planes > 0 && !(p.pml_R0 > 0 && p.pml_R0 < 1))) {
+      (p.pml_planes > 0 && !(p.pml_R0 > 0 && p.pml_R0 < 1)) || !(p.pml_backing >= 0) ||
+      !std::isfinite(p.pml_backing)) {
     psfd_set_error("psfd_plan_create: invalid PML / z_ml");
     return PSFD_ERR_ARG;
   }
@@ -434,6 +448,13 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
   pml_sinv64(P, sinv64);
   std::vector<cf> sinv(p.nz);
   for (int k = 0; k < p.nz; ++k) sinv[k] = make_float2((float)sinv64[k].x, (float)sinv64[k].y);
+  pml_backing64(p, P->sback_host);
+  std::vector<cf> kbg(p.nz);
+  std::vector<float> sback(p.nz);
+  for (int k = 0; k < p.nz; ++k) {
+    kbg[k] = make_float2((float)(P->k0 * P->k0), (float)(P->k0 * P->k0 * P->sback_host[k]));
+    sback[k] = (float)P->sback_host[k];
+  }
   std::vector<cf> twx, twy, twz;
   host_twiddles(p.nx, twx);
   host_twiddles(p.ny, twy);
@@ -443,6 +464,8 @@ extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
       (rc = upload((void**)&P->ky, ky.data(), ky.size() * 4)) ||
       (rc = upload((void**)&P->kz, kz.data(), kz.size() * 4)) ||
       (rc = upload((void**)&P->sinv, sinv.data(), sinv.size() * 8)) ||
+      (rc = upload((void**)&P->kbg, kbg.data(), kbg.size() * 8)) ||
+      (rc = upload((void**)&P->sback, sback.data(), sback.size() * 4)) ||
       (rc = upload((void**)&P->pc64, P->pc_host.data(), P->pc_host.size() * sizeof(zd))) ||
       (rc = upload((void**)&P->tw_x, twx.data(), twx.size() * 8)) ||
       (rc = upload((void**)&P->tw_y, twy.data(), twy.size() * 8)) ||

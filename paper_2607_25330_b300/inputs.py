@@ -81,6 +81,7 @@ class Problem:
     phi_deg: float = 0.0
     pml_planes: int = 2
     pml_R0: float = 1e-6
+    pml_backing: float = 0.5         # peak loss sigma_b of the PML's absorbing backing (0: none)
     z_ml: int = 2                    # plane index of the multilayer interface
     abs_intervals: float = 0.0       # absorber thickness in units of dz (starts at z_ml)
     n_abs: complex = N_ABSORBER

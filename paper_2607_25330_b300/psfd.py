@@ -36,7 +36,7 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nrhs", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("lam", C.c_double),
                 ("theta_deg", C.c_double), ("phi_deg", C.c_double),
-                ("pml_planes", C.c_int), ("pml_R0", C.c_double), ("z_ml", C.c_int),
+                ("pml_planes", C.c_int), ("pml_R0", C.c_double), ("pml_backing", C.c_double), ("z_ml", C.c_int),
                 ("eps_abs_re", C.c_double), ("eps_abs_im", C.c_double),
                 ("m_min", C.c_double), ("k_ref", C.c_double), ("gamma", C.c_double), ("damp_eps_rel", C.c_double),
                 ("sigma_px", C.c_double), ("stream", C.c_void_p)]
@@ -94,6 +94,9 @@ def lib() -> C.CDLL:
         "psfd_reflection_tables": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "psfd_apply": (i, [vp, vp, vp, i]),
         "psfd_precond": (i, [vp, vp, vp, i]),
+        "psfd_apply64": (i, [vp, vp, vp, i]),
+        "psfd_physics_loss_workspace_size": (sz, [vp]),
+        "psfd_physics_loss": (i, [vp, vp, vp, d, d, d, C.POINTER(C.c_double), vp, vp, sz]),
         "psfd_solve": (i, [vp, vp, vp, vp, d, i, i, i, i, C.POINTER(Info), vp, sz]),
         "psfd_solve_workspace_size": (sz, [vp, i, i]),
         "psfd_set_history": (i, [vp, C.POINTER(C.c_double), i]),
@@ -135,7 +138,8 @@ def lib() -> C.CDLL:
 def declared_symbols() -> List[str]:
     """Names of the functions the binding expects the library to export."""
     return ["psfd_plan_create", "psfd_plan_destroy", "psfd_supported", "psfd_mask_fill", "psfd_background",
-            "psfd_reflection_tables", "psfd_apply", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
+            "psfd_reflection_tables", "psfd_apply", "psfd_apply64", "psfd_physics_loss_workspace_size",
+            "psfd_physics_loss", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
             "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
             "psfd_layered_storage", "psfd_device_status",
@@ -197,7 +201,7 @@ class Plan:
         self.stream = stream
         eps = prob.eps_abs
         self.params = Params(prob.nx, prob.ny, prob.nz, self.nrhs, prob.dx, prob.dy, prob.dz, prob.lam,
-                             prob.theta_deg, prob.phi_deg, prob.pml_planes, prob.pml_R0, prob.z_ml,
+                             prob.theta_deg, prob.phi_deg, prob.pml_planes, prob.pml_R0, prob.pml_backing, prob.z_ml,
                              eps.real, eps.imag, prob.m_min, prob.k_ref, prob.gamma, prob.damp_eps_rel,
                              prob.sigma_px, _stream_handle(stream))
         h = C.c_void_p()
@@ -248,6 +252,28 @@ class Plan:
         y = self.empty() if out is None else out
         _check(lib().psfd_apply(self.h, _ptr(x), _ptr(y), flags), "psfd_apply")
         return y
+
+    def apply64(self, x: torch.Tensor, flags: int = 0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """y = A x in FP64 (complex128 device tensors); flags 0 or PSFD_HYBRID."""
+        if x.dtype != torch.complex128:
+            raise ValueError("complex128 x expected")
+        y = torch.empty(self.shape, dtype=torch.complex128, device="cuda") if out is None else out
+        _check(lib().psfd_apply64(self.h, _ptr(x), _ptr(y), flags), "psfd_apply64")
+        return y
+
+    def physics_loss(self, E: torch.Tensor, b: torch.Tensor, lam_hf: float = 0.1, w0: float = 1.0,
+                     eta_hf: float = 1.0, grad: bool = True):
+        """Eq. loss per right-hand side (host float64 array [nrhs]) and, with grad, its gradient
+        dJ/dRe E + i dJ/dIm E (device complex64, same shape as E); both from the library."""
+        n = int(lib().psfd_physics_loss_workspace_size(self.h))
+        if getattr(self, "_loss_ws", None) is None or self._loss_ws.numel() < n:
+            self._loss_ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+        J = np.zeros(self.nrhs, dtype=np.float64)
+        g = torch.empty(self.shape, dtype=torch.complex64, device="cuda") if grad else None
+        _check(lib().psfd_physics_loss(self.h, _ptr(E.contiguous()), _ptr(b.contiguous()), lam_hf, w0, eta_hf,
+                                       J.ctypes.data_as(C.POINTER(C.c_double)), _ptr(g), _ptr(self._loss_ws),
+                                       self._loss_ws.numel()), "psfd_physics_loss")
+        return J, g
 
     def precond(self, x: torch.Tensor, flags: int = 0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         y = self.empty() if out is None else out

@@ -30,14 +30,17 @@ def _weights(seed: int) -> Dict[str, torch.Tensor]:
             for k, v in I.fno_weights(S, seed, spectral_scale=1.0).items()}
 
 
-def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, log_every: int = 10):
-    """Adam on the physics loss over `pool` seeded masks (a random batch of them per step)."""
+def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, log_every: int = 10,
+          pol: int = None, mask_seed: int = 1000):
+    """Adam on the physics loss over `pool` seeded masks (a random batch of them per step); `pol`
+    selects the illumination (one model per polarisation), default the preset's first."""
     prob = I.preset(preset)
+    prob.pols = [prob.pols[0] if pol is None else int(pol)]
     S = I.FNOShape()
     w = _weights(seed)
     trainer = psfd.FnoTrainer(psfd.fno_struct(w, S), batch, prob.nz, prob.ny, prob.nx, checkpoint=True)
     plans = [psfd.Plan(prob, nrhs=1) for _ in range(batch)]
-    masks = [torch.from_numpy(I.mask_for(prob, 1000 + i)) for i in range(pool)]
+    masks = [torch.from_numpy(I.mask_for(prob, mask_seed + i)) for i in range(pool)]
     stack, zprof = prob.stack(), prob.zprofile()
     opt = torch.optim.Adam(list(w.values()), lr=lr)
     rng = np.random.default_rng(seed)

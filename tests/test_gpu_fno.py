@@ -3,7 +3,8 @@
 The oracle rounds both operands of the per-mode mixing to bfloat16 exactly as
 the workload prescribes, then accumulates in float64; the GPU accumulates in
 float32 from float32 FFTs, so the only differences are float32 rounding and the
-rare bfloat16 rounding decision flipped by it.  Tolerance: relative L2 2e-3.
+rare bfloat16 rounding decision flipped by it (measured: about 2.3e-7 relative
+L2).  Tolerance: relative L2 1e-4, the complex64 bar.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ from paper_2607_25330_b300 import inputs as I
 from tests.helpers import rel_l2
 
 pytestmark = pytest.mark.gpu
-TOL_FNO = 2e-3
+TOL_FNO = 1e-4
 
 
 def device_weights(w):

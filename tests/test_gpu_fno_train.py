@@ -48,12 +48,14 @@ def test_fno_backward_matches_oracle_autograd(dims, ckpt):
     tr.backward(ad, c.to(torch.complex64).cuda(), grads)
     torch.cuda.synchronize()
     E_ref, g_ref = _oracle_grads(w, a, c)
-    assert rel_l2(E.cpu(), E_ref) < TOL_GRAD
+    print(f"FNO forward (train) rel L2 {rel_l2(E.cpu(), E_ref):.2e}")
+    assert rel_l2(E.cpu(), E_ref) < 1e-4
     # the training forward is the inference forward
     E2 = psfd.fno_forward(psfd.fno_struct(dw, S), ad)
     assert torch.equal(E.cpu(), E2.cpu())
     for k in psfd.FNO_PARAM_NAMES:
         err = rel_l2(grads[k].cpu(), g_ref[k])
+        print(f"FNO gradient {k}: rel L2 {err:.2e}")
         assert err < TOL_GRAD, (k, err)
 
 

@@ -234,3 +234,40 @@ def test_tensor_core_apply_wait_gives_up_and_reports(monkeypatch):
     assert rel_l2(y, y_ref) == 0.0
     res = plan.solve_ex(b, tol=1e-6, maxit=400, precond=psfd.PC_LAYERED)
     assert res["code"] == 0
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_layered_solve_with_converged_right_hand_sides(half):
+    """Right-hand sides that have converged are skipped by the layered apply and the operator kernels
+    of every later iteration.  One rhs starts converged (its x0 is a solution), the other from zero:
+    the active one must still reach the same field; with every rhs converged, nothing iterates and
+    the field is x0 itself."""
+    from paper_2607_25330_b300 import psfd
+    prob = problem(64, 64, 64, theta=6.0, pols=[0, 1])
+    a = I.mask_for(prob, 5, "manhattan")
+    plan = psfd.Plan(prob, nrhs=2)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    plan.layered_storage(half)
+    plan.layered_build()
+    ref = plan.solve_ex(b, tol=1e-9, maxit=400, method=psfd.PSFD_BICGSTAB, precond=psfd.PC_LAYERED,
+                        inner_tol=1e-3, out_c128=True)
+    assert all(i["status"] == 0 for i in ref["info"]), ref["info"]
+    E_ref = ref["E"]
+    # rhs 1 starts at (the complex64 rounding of) its solution: residual ~1e-6 < 1e-5
+    x0 = torch.zeros(plan.shape, dtype=torch.complex64, device="cuda")
+    x0[1] = E_ref[1].to(torch.complex64)
+    res = plan.solve_ex(b, x0=x0, tol=1e-5, maxit=400, method=psfd.PSFD_BICGSTAB, precond=psfd.PC_LAYERED,
+                        inner_tol=1e-3, out_c128=True)
+    i0, i1 = res["info"]
+    assert i0["status"] == 0 and i1["status"] == 0, res["info"]
+    assert i1["iters"] == 0 and i0["iters"] > 0
+    assert i0["r_rel"] <= 1e-5 and i1["r_rel"] <= 1e-5
+    assert rel_l2(res["E"][1], x0[1]) < 1e-5     # x0 enters through a complex64 lateral transform
+    assert rel_l2(res["E"][0], E_ref[0]) < 1e-3
+    # every rhs converged from the start
+    x0[0] = E_ref[0].to(torch.complex64)
+    res2 = plan.solve_ex(b, x0=x0, tol=1e-5, maxit=400, method=psfd.PSFD_BICGSTAB, precond=psfd.PC_LAYERED,
+                         inner_tol=1e-3, out_c128=True)
+    assert all(i["status"] == 0 and i["iters"] == 0 for i in res2["info"]), res2["info"]
+    assert rel_l2(res2["E"], x0) < 1e-5

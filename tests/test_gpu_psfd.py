@@ -250,21 +250,30 @@ def test_adjoint_matches_oracle(grid, flags):
     assert abs(complex(lhs - rhs)) < 1e-5 * abs(complex(lhs))
 
 
-def test_physics_loss_gradient_matches_oracle():
-    """Eq. loss and its gradient w.r.t. the field through the hand-written adjoint (autograd.Function)."""
+@pytest.mark.parametrize("grid", [(32, 32, 16, 6.0, 0.0, 1), (64, 32, 48, 4.0, 0.0, 2), (16, 16, 96, 8.0, 20.0, 1)])
+def test_physics_loss_gradient_matches_oracle(grid):
+    """Eq. loss and its gradient w.r.t. the field, both from the library (psfd_physics_loss: operator,
+    hand-written adjoint, the library's 3-D FFTs), through the autograd bridge, against the oracle's
+    loss and torch autograd of it (mean over the right-hand sides)."""
     from oracle import fno as OF
     from paper_2607_25330_b300 import autograd as AG
-    prob, a, g, fill_o, plan, fill, b = setup(32, 32, 16, 6.0, 0.0, 1)
+    prob, a, g, fill_o, plan, fill, b = setup(*grid)
     E0 = torch.from_numpy(I.random_field(plan.shape, 13) * 0.2).to(torch.complex64)
     E = E0.cuda().requires_grad_(True)
     J = AG.physics_loss(plan, E, b)
     J.backward()
-    Eo = E0[0].to(torch.complex128).requires_grad_(True)
-    bo = b[0].cpu().to(torch.complex128)
-    Jo = OF.loss(lambda X: O.apply_A(g, X, fill_o), Eo, bo)
-    Jo.backward()
-    assert abs(float(J) - float(Jo)) < 1e-4 * abs(float(Jo))
-    assert rel_l2(E.grad[0].cpu(), Eo.grad) < 1e-4
+    Jo_tot = 0.0
+    for r in range(plan.nrhs):
+        Eo = E0[r].to(torch.complex128).requires_grad_(True)
+        bo = b[r].cpu().to(torch.complex128)
+        Jo = OF.loss(lambda X: O.apply_A(g, X, fill_o), Eo, bo) / plan.nrhs
+        Jo.backward()
+        Jo_tot += float(Jo)
+        assert rel_l2(E.grad[r].cpu(), Eo.grad) < 1e-4, r
+    assert abs(float(J) - Jo_tot) < 1e-4 * abs(Jo_tot)
+    # the loss alone (no gradient buffer) gives the same values
+    Jr, gr = plan.physics_loss(E.detach(), b, grad=False)
+    assert gr is None and abs(float(Jr.mean()) - Jo_tot) < 1e-4 * abs(Jo_tot)
 
 
 @pytest.mark.parametrize("n", [16, 32, 64, 96, 128])

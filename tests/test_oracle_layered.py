@@ -40,6 +40,10 @@ def test_uniform_fill_makes_P_the_exact_inverse_of_A():
     # and the other order
     z = O.apply_A(g, O.apply_P_layered(g, fill, x), fill)
     assert float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)) < 1e-10
+    # the same blocks factored once (LU with partial pivoting) and applied by triangular solves
+    lu = torch.linalg.lu_factor(O.layered_blocks(g, fill))
+    w = O.apply_P_layered(g, fill, O.apply_A(g, x, fill), lu=lu)
+    assert float(torch.linalg.vector_norm(w - x) / torch.linalg.vector_norm(x)) < 1e-10
 
 
 def test_blocks_decouple_te_from_tm():

@@ -104,14 +104,49 @@ def test_divergence_of_curlcurl_vanishes_with_pml():
 
 
 def test_curlcurl_annihilates_gradients_with_pml():
-    """curl_s grad_s phi = 0, so A (grad phi) = -k0^2 grad phi where deps = 0."""
+    """curl_s grad_s phi = 0, so A (grad phi) = -k0^2 eps_bg grad phi where deps = 0."""
     p = small_problem()
     g = O.Grid(p.to_dict(), I.empty_stack())
     phi = rand_c((g.nz, g.ny, g.nx), 2)
     G = _grad(g, phi)
     fill = torch.zeros(g.nz, g.ny, g.nx, dtype=torch.float64)
     out = O.apply_A(g, G, fill)
-    assert float((out + g.k0 ** 2 * G).abs().max()) < 1e-11 * float(G.abs().max())
+    assert float((out + g.k0 ** 2 * g.eps_bg[None, :, None, None] * G).abs().max()) < 1e-11 * float(G.abs().max())
+
+
+@pytest.mark.parametrize("npml,backing", [(4, 0.5), (8, 1.0), (2, 0.5), (4, 0.0)])
+def test_pml_backing_damps_the_z_constant_lateral_mode(npml, backing):
+    """A field constant in z is annihilated by D_z for any stretch s, so for a lateral mode with
+    E perpendicular to k_par the vacuum operator reduces to the closed form
+    A E = (|k_par|^2 - k0^2 eps_bg(z)) E: with no backing its Rayleigh quotient is real (an
+    undamped mode whose eigenvalue |k_par|^2 - k0^2 vanishes at grazing); the backing adds
+    -i k0^2 sigma_b ((nb - j) / nb)^2 on the j-th of the outermost nb = max(1, npml / 4) planes of
+    each end, and nothing elsewhere."""
+    nz = 4 * npml + 8
+    p = I.Problem(nx=6, ny=4, nz=nz, dx=2.0, dy=2.5, dz=2.0, theta_deg=7.0, pml_planes=npml, z_ml=npml,
+                  abs_intervals=2.0, pml_backing=backing)
+    g = O.Grid(p.to_dict(), I.empty_stack())
+    mx, my = 2, 1
+    kx, ky = float(g.kx[mx]), float(g.ky[my])
+    kk = (kx - g.kx_inc, ky - g.ky_inc)
+    x = np.arange(g.nx) * g.dx
+    y = np.arange(g.ny) * g.dy
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    phase = np.exp(1j * (kk[0] * X + kk[1] * Y))
+    s_hat = np.array([-ky, kx, 0.0]) / math.hypot(kx, ky)
+    E = torch.from_numpy(s_hat[:, None, None, None] * np.broadcast_to(phase, (g.nz, g.ny, g.nx))[None])
+    fill = torch.zeros(g.nz, g.ny, g.nx, dtype=torch.float64)
+    out = O.apply_A(g, E, fill)
+    nb = max(1, npml // 4) if backing > 0 else 0
+    sig = np.zeros(nz)
+    for j in range(nb):
+        sig[j] = sig[nz - 1 - j] = backing * ((nb - j) / nb) ** 2
+    lam = (kx ** 2 + ky ** 2) - g.k0 ** 2 * (1.0 + 1j * sig)
+    ref = torch.from_numpy(lam)[None, :, None, None] * E
+    assert float((out - ref).abs().max()) < 1e-11 * g.k0 ** 2
+    rq = complex(torch.vdot(E.flatten(), out.flatten()) / torch.vdot(E.flatten(), E.flatten()))
+    assert abs(rq.imag + g.k0 ** 2 * sig.sum() / nz) < 1e-12 * g.k0 ** 2
+    assert (sig.sum() > 0) == (backing > 0)
 
 
 def test_pml_profile_vanishes_in_the_physical_region():
