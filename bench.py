@@ -73,7 +73,13 @@ def parse():
     ap.add_argument("--train-step", action="store_true",
                     help="time the physics-informed FNO training step (16 masks 128x128x48) and exit")
     ap.add_argument("--train-batch", type=int, default=16)
-    ap.add_argument("--train-warm-steps", type=int, default=200,
+    ap.add_argument("--skip-batch", action="store_true",
+                    help="leave out the 384-rhs batching arm of the default run")
+    ap.add_argument("--skip-fine", action="store_true",
+                    help="leave out the 512x512x128 fine-discretisation arm of the default run")
+    ap.add_argument("--skip-train-step", action="store_true",
+                    help="leave out the timed physics-informed training step (16 masks 128x128x48) of the default run")
+    ap.add_argument("--train-warm-steps", type=int, default=400,
                     help="Adam steps of the physics-informed training of the warm-start FNO (one model per "
                          "polarisation, on seeded masks disjoint from the timed ones) before the timed steps; "
                          "0 keeps the seed-initialised weights")
@@ -199,11 +205,13 @@ def run_ours(args, rank, world):
         # one model per polarisation, on 32 seeded masks that the timed steps never see
         from paper_2607_25330_b300 import train as TR
         t_tr = time.perf_counter()
-        train_info = {"steps": args.train_warm_steps, "batch": args.train_warm_batch, "pool": 32, "lr": 1e-3,
+        train_info = {"steps": args.train_warm_steps, "batch": args.train_warm_batch, "pool": 32, "lr": 3e-3,
+                      "output_layer": "zero-initialised (the untrained network predicts the cold start E = 0)",
                       "loss_first_last": []}
         for pol in prob.pols:
-            w, log = TR.train(args.train_warm_steps, args.train_warm_batch, 1e-3, 32, 91 + pol, args.workload,
-                              log_every=max(1, args.train_warm_steps // 4), pol=pol, mask_seed=50000 + 1000 * rank)
+            w, log = TR.train(args.train_warm_steps, args.train_warm_batch, 3e-3, 32, 91 + pol, args.workload,
+                              log_every=max(1, args.train_warm_steps // 4), pol=pol, mask_seed=50000 + 1000 * rank,
+                              zero_output=True)
             wd = {k: v.detach().contiguous() for k, v in w.items()}
             models.append(psfd.fno_struct(wd, shape))
             train_info["loss_first_last"].append([log[0]["loss"], log[-1]["loss"]])
@@ -610,6 +618,160 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_fine(args):
+    """The fine-discretisation workload at full size: 512x512x128 (0.5 nm lateral pixels), TE + TM at
+    6 deg, a dense Manhattan layout; warm start from the FNO evaluated on the 128x128x32 grid of the
+    same box and spectrally upsampled (the network trained on that coarse grid by the physics loss),
+    against the cold start; GMRES(30) in complex64 with FP64 orthogonalisation inside the FP64
+    refinement, layered-background P (Schur form at nz = 128), to 1e-6.  Also the A apply's roofline
+    at this size, where the vectors (0.8 GB per rhs) are far larger than L2."""
+    import torch
+    from paper_2607_25330_b300 import inputs as I
+    from paper_2607_25330_b300 import psfd
+    prob = I.preset("fine_512x512x128")
+    coarse = I.preset("fno_coarse_128x128x32")
+    shape = I.FNOShape()
+    out = {"workload": "fine_512x512x128", "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
+           "coarse_grid": [coarse.nx, coarse.ny, coarse.nz], "solver": "gmres(30), FP64 refinement (inner 1e-3)",
+           "preconditioner": "layered-background P, Schur form, half-precision blocks", "tol": TOL}
+    models = []
+    t0 = time.perf_counter()
+    if args.train_warm_steps > 0:
+        from paper_2607_25330_b300 import train as TR
+        for pol in prob.pols:
+            w, log = TR.train(max(1, args.train_warm_steps // 2), args.train_warm_batch, 3e-3, 32, 191 + pol,
+                              "fno_coarse_128x128x32", log_every=max(1, args.train_warm_steps // 4), pol=pol,
+                              mask_seed=70000, zero_output=True)
+            models.append(psfd.fno_struct({k: v.detach().contiguous() for k, v in w.items()}, shape))
+        out["coarse_training"] = {"steps": max(1, args.train_warm_steps // 2), "seconds": time.perf_counter() - t0}
+    else:
+        for pol in prob.pols:
+            w = I.fno_weights(shape, 77 + pol)
+            models.append(psfd.fno_struct({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in w.items()},
+                                          shape))
+    plan = psfd.Plan(prob)
+    plan.layered_storage(True)
+    cplan = psfd.Plan(coarse, nrhs=1)
+    ws = torch.empty(plan.workspace_size_ex(psfd.PSFD_GMRES, 30, True), dtype=torch.uint8, device="cuda")
+    E = torch.empty(plan.shape, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for warm in (True, False):
+        infos, ms = [], 0.0
+        for k in range(2):
+            a = I.mask_for(prob, 400 + k, "manhattan_dense")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fill = plan.mask_fill(torch.from_numpy(a).cuda(), prob.zprofile())
+            b = plan.background(prob.stack(), fill, prob.pols)
+            plan.layered_build()
+            x0 = None
+            if warm:
+                cfill = cplan.mask_fill(torch.from_numpy(np.ascontiguousarray(a[::4, ::4])).cuda(), coarse.zprofile())
+                Ec = torch.cat([psfd.fno_forward(m, cfill[None].contiguous()) for m in models])
+                x0 = psfd.spectral_upsample(Ec, prob.nz, prob.ny, prob.nx).contiguous()
+            r = plan.solve_ex(b, x0=x0, tol=TOL, maxit=2000, method=psfd.PSFD_GMRES, restart=30,
+                              precond=psfd.PC_LAYERED, inner_tol=1e-3, out=E, workspace=ws, out_c128=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            infos.append(r["info"])
+        conv = sum(1 for inf in infos for i in inf if i["status"] == 0)
+        res["warm" if warm else "cold"] = {
+            "value": conv / (ms / 1e3), "unit": "solves/s", "ms_per_mask": ms / len(infos),
+            "converged": f"{conv} of {sum(len(x) for x in infos)}",
+            "iters": [i["iters"] for inf in infos for i in inf], "r_rel_fp64": [i["r_rel"] for inf in infos for i in inf],
+            "r_rel_initial": [i["r_rel_initial"] for inf in infos for i in inf],
+            "step": "mask -> fill -> TMM + source -> P build -> (coarse FNO + upsample) -> solve, all timed"}
+    out.update(res)
+    # the A apply at this size (HBM-bound), CUDA events on the launching stream
+    x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    nap = 5
+    plan.apply(x, flags=psfd.PSFD_HYBRID, out=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psfd.timing_enable(True)
+    e0.record(stream)
+    for _ in range(nap):
+        plan.apply(x, flags=psfd.PSFD_HYBRID, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = psfd.timing_read()
+    psfd.timing_enable(False)
+    ms_A = e0.elapsed_time(e1) / nap
+    npts = prob.nx * prob.ny * prob.nz * len(prob.pols)
+    peak, peak_kind = measured_peaks()
+    gbs = BYTES_PER_POINT * npts / (ms_A / 1e3) / 1e9
+    out["roofline_matvec"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                              "frac_of_8TBps_spec": gbs / 8000.0, "ms_per_apply": ms_A,
+                              "algorithmic_bytes_per_apply": BYTES_PER_POINT * npts,
+                              "stages_ms_per_apply": {k: v["ms"] / nap for k, v in st.items() if v["calls"]},
+                              "stage_GBps_own_bytes": {k: v["bytes"] / (v["ms"] / 1e3) / 1e9 for k, v in st.items()
+                                                       if v["calls"] and v["bytes"] > 0},
+                              "peak_kind": peak_kind}
+    out["layered_bytes"] = plan.layered_bytes()
+    plan.close()
+    cplan.close()
+    return out
+
+
+def run_batch(args, chunk=16):
+    """The batching workload at its size: 64 Manhattan masks of uneven lateral size (64^2, 96^2,
+    128^2, 256^2) and depth (nz 32, 48, 64, 96), each at 3 angles (4, 6, 8 deg) x TE + TM = 384
+    right-hand sides, 192 operators.  Per chunk of operators: plans on their own streams, fill,
+    TMM + source, layered P (half precision; Schur form at nz 96), then psfd_solve_batched
+    (BiCGSTAB in FP64 refinement to 1e-6) over the chunk on concurrent streams; plans freed per
+    chunk.  Everything from the mask to the FP64 residual is timed (host clock around the whole
+    set; one device synchronisation per chunk)."""
+    import torch
+    from paper_2607_25330_b300 import inputs as I
+    from paper_2607_25330_b300 import psfd
+    probs = I.batch_presets()
+    t0 = time.perf_counter()
+    infos_all, by_size = [], {}
+    for c0 in range(0, len(probs), chunk):
+        group = probs[c0:c0 + chunk]
+        streams = [torch.cuda.Stream() for _ in group]
+        plans, bs = [], []
+        for k, (pr, st) in enumerate(zip(group, streams)):
+            idx = c0 + k
+            a = I.mask_for(pr, 600 + idx // 3)          # one mask per 3 angles
+            pl = psfd.Plan(pr, stream=st)
+            pl.layered_storage(True)
+            with torch.cuda.stream(st):
+                fill = pl.mask_fill(torch.from_numpy(a).cuda(non_blocking=True), pr.zprofile())
+                b = pl.background(pr.stack(), fill, pr.pols)
+            pl.layered_build()
+            plans.append(pl)
+            bs.append(b)
+        torch.cuda.synchronize()
+        Es, infos = psfd.solve_batched(plans, bs, tol=TOL, maxit=600, method=psfd.PSFD_BICGSTAB, precond=2,
+                                       refine=True, inner_tol=1e-3, nworkers=8)
+        for pr, inf in zip(group, infos):
+            key = f"{pr.nx}x{pr.ny}x{pr.nz}"
+            d = by_size.setdefault(key, {"rhs": 0, "converged": 0, "iters": []})
+            d["rhs"] += len(inf)
+            d["converged"] += sum(1 for i in inf if i["status"] == 0)
+            d["iters"] += [i["iters"] for i in inf]
+        infos_all += infos
+        del Es, bs
+        for pl in plans:
+            pl.close()
+        torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    conv = sum(1 for inf in infos_all for i in inf if i["status"] == 0)
+    total = sum(len(inf) for inf in infos_all)
+    for d in by_size.values():
+        d["mean_iters"] = float(np.mean(d["iters"])) if d["iters"] else None
+        del d["iters"]
+    return {"workload": "batch_64_masks_x_3_angles_x_2_pols", "operators": len(probs), "rhs": total,
+            "converged": f"{conv} of {total}", "seconds": sec, "value": conv / sec, "unit": "solves/s",
+            "points_all_rhs": int(sum(p.nx * p.ny * p.nz * len(p.pols) for p in probs)),
+            "by_grid": by_size, "max_r_rel_fp64": max(i["r_rel"] for inf in infos_all for i in inf),
+            "execution": f"chunks of {chunk} operators on their own streams, psfd_solve_batched with 8 host "
+                         "workers (concurrent streams; not one persistent launch)"}
+
+
 def run_profile_apply(args):
     """N applies of A P (layered) or A M (damping) in the HYBRID domain on one mask (kernel captures)."""
     import torch
@@ -638,7 +800,7 @@ def run_profile_apply(args):
             "ms_per_apply": e0.elapsed_time(e1) / max(1, args.profile_apply)}
 
 
-def run_train_step(args):
+def run_train_step(args, steps=None, warmup=None):
     """Physics-informed training step of the factorised FNO (config 4): 16 masks 128x128x48,
     E = G_theta(a) for the batch, J = mean over masks of Eq. loss through the PSFD operator
     (hand-written adjoint), reverse pass of the FNO (checkpointed), Adam update."""
@@ -670,23 +832,25 @@ def run_train_step(args):
         opt.step()
         return J
 
-    for _ in range(args.warmup):
+    n_steps = args.steps if steps is None else steps
+    n_warm = args.warmup if warmup is None else warmup
+    for _ in range(n_warm):
         train_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     psfd.timing_enable(True)
     e0.record()
-    losses = [train_step() for _ in range(args.steps)]
+    losses = [train_step() for _ in range(n_steps)]
     e1.record()
     torch.cuda.synchronize()
     st = psfd.timing_read()
     psfd.timing_enable(False)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / n_steps
     mem = torch.cuda.max_memory_allocated() / 2 ** 30
-    return {"mode": "train_step", "workload": "fno_train_128x128x48", "batch": B, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "masks_per_s": B / (ms / 1e3),
-            "loss": [float(l) for l in losses], "fno_ms_per_step": st["fno"]["ms"] / args.steps,
-            "psfd_ms_per_step": (st["axial"]["ms"] + st["contrast"]["ms"]) / args.steps,
+    return {"mode": "train_step", "workload": "fno_train_128x128x48", "batch": B, "steps": n_steps,
+            "warmup": n_warm, "ms_per_step": ms, "masks_per_s": B / (ms / 1e3),
+            "loss": [float(l) for l in losses], "fno_ms_per_step": st["fno"]["ms"] / n_steps,
+            "psfd_ms_per_step": (st["axial"]["ms"] + st["contrast"]["ms"]) / n_steps,
             "workspace_GiB": trainer.n / 2 ** 30, "max_allocated_GiB": mem,
             "note": "forward + physics loss (PSFD apply and adjoint per mask) + checkpointed FNO reverse pass + "
                     "Adam; Eq. loss and its gradient by psfd_physics_loss (library FFTs, FP64 sums)"}
@@ -802,6 +966,19 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
+    if rank == 0 and not args.skip_batch:
+        import torch
+        torch.cuda.empty_cache()
+        out["batch"] = run_batch(args)
+    if rank == 0 and not args.skip_fine:
+        import torch
+        torch.cuda.empty_cache()
+        out["fine_grid"] = run_fine(args)
+    if rank == 0 and not args.skip_train_step:
+        # the differentiation workload: one physics-informed FNO training step (3 timed after 2)
+        import torch
+        torch.cuda.empty_cache()
+        out["train_step"] = run_train_step(args, steps=3, warmup=2)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args)

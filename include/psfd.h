@@ -205,7 +205,8 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * Bloch modes; per mode it splits into a TE block (nz x nz, E along s) and a TM
  * block (2nz x 2nz, (E_t, E_z)), which psfd_layered_build assembles and inverts
  * (FP32, partial pivoting) on the device and stores in the plan:
- * psfd_layered_bytes() bytes = columns * 5 nz^2 entries, where columns = nx*ny, or
+ * psfd_layered_bytes() bytes = columns * 5 nz^2 entries (2 nz^2 in the Schur form
+ * below), where columns = nx*ny, or
  * nx*(ny/2+1) without a Bloch shift along y (the blocks depend on |k_par| only,
  * so ky and -ky share them): 1.36 GB at 128x128x64 at 6 deg in complex64.
  * psfd_layered_build makes the blocks exact for the fill registered by the last
@@ -220,8 +221,15 @@ PSFD_API int psfd_precond(psfd_plan plan, const psfd_c64* x, psfd_c64* y, int fl
  * entering as a two-term f16 split with a power-of-two scale per column (about
  * 22 bits), so P stays linear to FP32 level.  PSFD_LAY_TC=0 in the environment
  * selects the FP32 SIMT kernel.
- * Supported for nz in {16, 32, 48, 64}, nx a multiple of 4 and nrhs <= 4 (else
- * PSFD_ERR_ARG / psfd_layered_bytes() = 0); PSFD_ERR_STATE before
+ * For nz = 96 and 128 (and any nz in {32, 64} with PSFD_LAY_SCHUR=1) the blocks
+ * are stored in the Schur form: the E_z-E_z part of the TM block is diagonal in z,
+ * so E_z is eliminated and only TE^-1 and S^-1 (S the nz x nz Schur complement on
+ * E_t) are stored, 2 nz^2 entries per column, always in complex64 (a half-precision
+ * request applies to the full-block form only: S^-1 carries the large
+ * kappa^2 D Dg^-1 D part of near-grazing columns); the apply forms the E_z part with
+ * the shared stretched derivative matrix (SIMT kernel).
+ * Supported for nz in {16, 32, 48, 64, 96, 128}, nx a multiple of 4 and nrhs <= 4
+ * (else PSFD_ERR_ARG / psfd_layered_bytes() = 0); PSFD_ERR_STATE before
  * psfd_background; PSFD_ERR_BREAKDOWN if a block is singular.  Both synchronise
  * the plan's stream. */
 PSFD_API int psfd_layered_build(psfd_plan plan);
@@ -341,7 +349,9 @@ PSFD_API int psfd_physics_loss(psfd_plan plan, const psfd_c64* E, const psfd_c64
  * Mode mixing rounds both operands to bfloat16 and accumulates in float32.
  * PSFD_MIX_FP32=1 in the environment keeps both operands in float32 instead (a
  * verification mode: the network without the bfloat16 rounding, on the SIMT
- * mixing kernel). */
+ * mixing kernel).  The pointwise layers (the MLP of Eq. 4 and the projection)
+ * run on the CUDA cores in FP32; PSFD_MLP_TC=1 runs them on the tensor cores at
+ * FP32 accuracy (TF32 products of split operands) for dv = 32, dh = 64, dq = 128. */
 typedef struct {
   int dv, dh, layers, mx, my, mz, dq;
   const float* lift_w; const float* lift_b;

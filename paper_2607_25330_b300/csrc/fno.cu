@@ -160,8 +160,9 @@ __global__ void __launch_bounds__(256) k_mixgrad(const cf* __restrict__ Ubar, co
   const long krow = (long)(jy + offy) * MX + (jx + offx);
   const cf* Um = Ubar + mode * C * NB;
   const cf* Vm = V + mode * C * NB;
-  // each thread owns 4 (o, i) entries: e = threadIdx.x + 256 q
-  float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  // each thread owns 4 (o, i) entries: e = threadIdx.x + 256 q; each tile's fp32 partial sum is
+  // added to an FP64 total (a chunk is up to GRAD_CHUNK terms of mixed sign)
+  double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
   const long n_begin = (long)blockIdx.x * GRAD_CHUNK;
   const long n_end = min(NB, n_begin + GRAD_CHUNK);
   for (long n0 = n_begin; n0 < n_end; n0 += MIX_TN) {
@@ -179,20 +180,23 @@ __global__ void __launch_bounds__(256) k_mixgrad(const cf* __restrict__ Ubar, co
     for (int q = 0; q < 4; ++q) {
       const int e = threadIdx.x + 256 * q;
       const int o = e / 32, i = e - o * 32;
+      float tr = 0.f, ti = 0.f;
 #pragma unroll 8
       for (int j = 0; j < MIX_TN; ++j) {
         // u * conj(v)
-        ar[q] = fmaf(Ur[o][j], Vr[i][j], fmaf(Ui[o][j], Vi[i][j], ar[q]));
-        ai[q] = fmaf(Ui[o][j], Vr[i][j], fmaf(-Ur[o][j], Vi[i][j], ai[q]));
+        tr = fmaf(Ur[o][j], Vr[i][j], fmaf(Ui[o][j], Vi[i][j], tr));
+        ti = fmaf(Ui[o][j], Vr[i][j], fmaf(-Ur[o][j], Vi[i][j], ti));
       }
+      ar[q] += tr;
+      ai[q] += ti;
     }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int e = threadIdx.x + 256 * q;
     float* dst = dK + 2 * (krow * C * C + e);
-    atomicAdd(dst, ar[q] * scale);
-    atomicAdd(dst + 1, ai[q] * scale);
+    atomicAdd(dst, (float)(ar[q] * scale));
+    atomicAdd(dst + 1, (float)(ai[q] * scale));
   }
 }
 
@@ -892,6 +896,7 @@ static int fno_run(const fno_weights_t* w, const float* a, int B, int nx, int ny
   const int L = w->layers;
   // layer inputs: in checkpoint mode v_l lives in vL[l] (kept), else the layers update ws.v in place
   auto vin = [&](int l) -> float* { return mode == FNO_CHECKPOINT ? ws.vL + l * ws.act : ws.v; };
+  const bool tc = fno_mlp_tc_enabled(C, w->dh, w->dq);
   k_lift<<<blocks_for((long)B * N, 256), 256, 0, s>>>(a, vin(0), w->lift_w, w->lift_b, B, C, nx, ny, nz);
   PSFD_CHECK_LAUNCH();
   for (int l = 0; l < L; ++l) {
@@ -904,12 +909,19 @@ static int fno_run(const fno_weights_t* w, const float* a, int B, int nx, int ny
     PSFD_CHECK_LAUNCH();
     // MLP + residual (Eq. 4)
     float* vout = (mode == FNO_CHECKPOINT && l + 1 < L) ? vin(l + 1) : ws.v;
-    k_mlp<32, 64><<<blocks_for((long)B * N, 128), 128, 0, s>>>(
-        vin(l), vout, uxy, uz, w->w1 + (size_t)l * 64 * 32, w->b1 + (size_t)l * 64, w->w2 + (size_t)l * 32 * 64,
-        w->b2 + (size_t)l * 32, N, B, l < L - 1);
-    PSFD_CHECK_LAUNCH();
+    if (tc) {
+      rc = fno_mlp_tc(vin(l), vout, uxy, uz, w->w1 + (size_t)l * 64 * 32, w->b1 + (size_t)l * 64,
+                      w->w2 + (size_t)l * 32 * 64, w->b2 + (size_t)l * 32, N, B, l < L - 1, s);
+      if (rc) return rc;
+    } else {
+      k_mlp<32, 64><<<blocks_for((long)B * N, 128), 128, 0, s>>>(
+          vin(l), vout, uxy, uz, w->w1 + (size_t)l * 64 * 32, w->b1 + (size_t)l * 64, w->w2 + (size_t)l * 32 * 64,
+          w->b2 + (size_t)l * 32, N, B, l < L - 1);
+      PSFD_CHECK_LAUNCH();
+    }
   }
   if (!ok) { psfd_set_error("fno: unsupported size"); return PSFD_ERR_ARG; }
+  if (tc) return fno_proj_tc(ws.v, (cf*)E_out, w->q1, w->qb1, w->q2, w->qb2, N, B, s);
   k_proj<32, 128><<<blocks_for((long)B * N, 128), 128, 0, s>>>(ws.v, (cf*)E_out, w->q1, w->qb1, w->q2, w->qb2, N, B);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;

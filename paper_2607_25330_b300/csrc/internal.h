@@ -91,6 +91,7 @@ struct psfd_plan_s {
   void* lay16 = nullptr;                // half-precision blocks (storage PSFD_LAY_HALF)
   float* lay_scale = nullptr;           // their per-block power-of-two scales
   bool lay_half = false;
+  bool lay_schur = false;               // blocks in the Schur form (TE^-1 and S^-1, 2 nz^2 per column)
   std::vector<double> lay_mean;         // plane means of the fill the blocks were built for
   bool lay_built = false;
 };
@@ -124,12 +125,21 @@ bool fno_mix_tc_enabled(int C);
 int fno_mix_tc(const cf* V, cf* U, const cf* K, long NB, int modes, int mx, int MX, int offy, int offx,
                cudaStream_t s);
 int fno_mix_tc_error(int* host_flag);   // reads and clears the flag
+// fno_mlp_tc.cu: the pointwise MLP (C = 32, H = 64) and projection (Q = 128) on the tensor cores
+bool fno_mlp_tc_enabled(int C, int H, int Q);
+int fno_mlp_tc(const float* vin, float* vout, const float* uxy, const float* uz, const float* W1, const float* b1,
+               const float* W2, const float* b2, long N, int B, bool outer_gelu, cudaStream_t s);
+int fno_proj_tc(const float* v, cf* E, const float* Q1, const float* qb1, const float* Q2, const float* qb2, long N,
+                int B, cudaStream_t s);
+int fno_mlp_tc_error(int* host_flag);   // reads and clears the flag
 int plan_wait_status(psfd_plan_s* P);   // PSFD_ERR_TIMEOUT if a bounded device wait gave up
 
 // layered.cu
 int layered_supported(const psfd_plan_s* P);
 bool layered_pairs(const psfd_plan_s* P);
 long layered_columns(const psfd_plan_s* P);
+bool layered_schur_for(const psfd_plan_s* P);   // the block form a build of this plan uses
+bool layered_half(const psfd_plan_s* P);        // half-precision blocks in effect
 size_t layered_bytes(const psfd_plan_s* P);
 // done (nullable, device [nrhs]): when every right-hand side is done the apply returns at once
 int layered_apply(psfd_plan_s* P, const cf* x, cf* y, const int* done = nullptr);

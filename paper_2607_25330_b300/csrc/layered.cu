@@ -15,7 +15,16 @@
 //          [ iκ D + k0² Δε̄ (κ r_p / k_z) e e_mlᵀ          κ² − k0² (1 + Δε̄)   ]
 // Both are assembled per column on the device and inverted in FP32 by Gauss-Jordan exchange
 // steps with partial pivoting (one CTA per matrix, the matrix held in registers), then applied as
-// dense per-column matrix-vector products in the HYBRID (kx, ky, z) domain.  Used as the right
+// dense per-column matrix-vector products in the HYBRID (kx, ky, z) domain.
+//
+// Schur form (nz = 96, 128, where a 2nz x 2nz block no longer fits one CTA's registers; any nz
+// with PSFD_LAY_SCHUR=1): the E_z-E_z block of TM is diagonal, Dg = κ² − k0² ε̄(z) with
+// ε̄ = 1 + Δε̄ + i σ_b (the PML backing), so E_z is eliminated.  With B = iκ D and
+// C = iκ D + c e_mlᵀ, c(z) = k0² Δε̄ κ r_p e(z) / k_z, the complement on E_t is
+//     S = TM_tt − B Dg⁻¹ C = TM_tt + κ² D Dg⁻¹ D − iκ (D Dg⁻¹ c) e_mlᵀ
+// and the TM solve of (u_t, u_z) is  y_t = S⁻¹ (u_t − iκ D Dg⁻¹ u_z),
+// y_z = Dg⁻¹ (u_z − iκ D y_t − c y_t(z_ml)).  Only TE⁻¹ and S⁻¹ are stored (2 nz² entries per
+// column); D is shared by every column and Dg, c are formed on the fly.  Used as the right
 // preconditioner P in A P y = b − A E_base, E = E_base + P y, in place of the spectral damping
 // M of Eq. spectral_damping_action (an addition to the paper's method: the damping alone leaves
 // restarted Krylov stalling near 1e-5 at oblique incidence, where near-grazing diffraction orders
@@ -64,7 +73,14 @@ struct LayArgs {
   int no_copy;          // test of the bounded wait: the tensor-core apply requests no blocks
   const int* done;      // nullable [nrhs]: the apply does nothing when every right-hand side is done
   int nrhs;
+  int schur;            // 1: per column TE^-1 then S^-1 (2 nz^2 entries, the TM block reduced to its
+                        // Schur complement on E_t); 0: TE^-1 then the TM inverse (5 nz^2 entries)
 };
+
+// entries stored per block column
+__host__ __device__ __forceinline__ long block_stride(const LayArgs& a) {
+  return (a.schur ? 2L : 5L) * a.nz * a.nz;
+}
 
 // 1 when every right-hand side of the solve is done (the whole block returns, before any copy)
 __device__ __forceinline__ bool all_done(const LayArgs& a) {
@@ -154,7 +170,7 @@ __device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
 //     T[p][k] <- 1/π,  T[p][j] <- −T[p][j]/π,  T[i][k] <- T[i][k]/π,  T[i][j] <- T[i][j] − T[i][k] T[p][j]/π
 // with π = T[p][k].  After N steps, row p_k holds x_k and column k' holds y_{p_k'}:
 // Minv[k][p_k'] = T[p_k][k'].
-template <int N, bool TM>
+template <int N, bool TM, bool SCHUR = false>
 __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_off) {
   constexpr int TT = N / 16;
   __shared__ cf colv[2][N], rowv[2][N];
@@ -164,10 +180,72 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
   const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15, lane = tid & 31;
   const Mode m = mode_of(a, col);
   cf T[TT][TT];
+  if constexpr (SCHUR) {
+    // S = TM_tt + κ² D Dg⁻¹ D − iκ (D Dg⁻¹ c) e_mlᵀ (N = nz); Dg⁻¹ and Dg⁻¹ c in shared memory
+    cf* gs = colv[0];
+    cf* gc = rowv[0];
+    for (int z = tid; z < N; z += LAY_THREADS) {
+      const cf de = a.deps[z];
+      const cf dg = make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[z]));
+      const cf g = cdiv1(dg);
+      gs[z] = g;
+      cf c = czero();
+      if (z >= a.zml) c = cscale(cmul(cmul(de, m.rp), cmul(upgoing(a, m, z), cdiv1(m.kz))), a.k0sq * m.kap);
+      gc[z] = cmul(g, c);
+    }
+    __syncthreads();
 #pragma unroll
-  for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TT; ++u)
 #pragma unroll
-    for (int v = 0; v < TT; ++v) T[u][v] = entry<TM>(a, m, rg + 16 * u, cg + 16 * v);
+      for (int v = 0; v < TT; ++v) T[u][v] = entry<false>(a, m, rg + 16 * u, cg + 16 * v);
+    // the TE entry carries κ² on the diagonal, TM_tt does not
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+      for (int v = 0; v < TT; ++v)
+        if (rg + 16 * u == cg + 16 * v) T[u][v].x -= m.kap2;
+    // TE uses r_s in its reflection column where TM_tt uses r_p
+    {
+      const int jm = a.zml;
+#pragma unroll
+      for (int v = 0; v < TT; ++v) {
+        if (cg + 16 * v != jm) continue;
+#pragma unroll
+        for (int u = 0; u < TT; ++u) {
+          const int i = rg + 16 * u;
+          if (i < a.zml) continue;
+          const cf e = cscale(cmul(a.deps[i], upgoing(a, m, i)), a.k0sq);
+          T[u][v] = cadd(T[u][v], csub(cmul(e, m.rs), cmul(e, m.rp)));
+        }
+      }
+    }
+    const cf ik = make_float2(0.f, -m.kap);   // −iκ
+    for (int k = 0; k < N; ++k) {
+      const cf g = gs[k];
+      cf dik[TT], dkj[TT];
+#pragma unroll
+      for (int u = 0; u < TT; ++u) dik[u] = __ldg(a.D + (long)(rg + 16 * u) * N + k);
+#pragma unroll
+      for (int v = 0; v < TT; ++v) dkj[v] = cscale(cmul(g, __ldg(a.D + (long)k * N + cg + 16 * v)), m.kap2);
+#pragma unroll
+      for (int u = 0; u < TT; ++u)
+#pragma unroll
+        for (int v = 0; v < TT; ++v) T[u][v] = cfma(dik[u], dkj[v], T[u][v]);
+      const cf gck = cmul(ik, gc[k]);
+#pragma unroll
+      for (int v = 0; v < TT; ++v) {
+        if (cg + 16 * v != a.zml) continue;
+#pragma unroll
+        for (int u = 0; u < TT; ++u) T[u][v] = cfma(dik[u], gck, T[u][v]);
+      }
+    }
+    __syncthreads();   // colv / rowv are reused by the elimination below
+  } else {
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+      for (int v = 0; v < TT; ++v) T[u][v] = entry<TM>(a, m, rg + 16 * u, cg + 16 * v);
+  }
   unsigned used = 0;   // bit u: owned row rg + 16 u has been a pivot row
   for (int k = 0; k < N; ++k) {
     const int buf = k & 1;
@@ -255,7 +333,7 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
   __syncthreads();
   // column-major output: element (r, c) of the inverse at c * N + r
   if (!a.half) {
-    cf* out = a.mats + col * (5L * a.nz * a.nz) + block_off;
+    cf* out = a.mats + col * block_stride(a) + block_off;
 #pragma unroll
     for (int u = 0; u < TT; ++u)
 #pragma unroll
@@ -282,8 +360,8 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
   int e = 0;
   if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &e);   // mx = f 2^e with f in [0.5, 1)
   const float scale = ldexpf(1.f, e), inv = ldexpf(1.f, -e);
-  if (tid == 0) a.scales[col * 2 + (TM ? 1 : 0)] = scale;
-  __half2* out = a.mats16 + col * (5L * a.nz * a.nz) + block_off;
+  if (tid == 0) a.scales[col * 2 + ((TM || SCHUR) ? 1 : 0)] = scale;
+  __half2* out = a.mats16 + col * block_stride(a) + block_off;
 #pragma unroll
   for (int u = 0; u < TT; ++u)
 #pragma unroll
@@ -363,7 +441,7 @@ __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 
     xs[((v * 3 + 2) * NZ + z) * nrhs + r] = ez;
   }
   __syncthreads();
-  constexpr long MS = 5L * NZ * NZ;
+  const long MS = block_stride(a);
   // thread -> (block column g, rows rr .. rr + RPT - 1) of the 3 NZ stacked rows (TE, then TM)
   constexpr int TPC = 3 * NZ / RPT;                         // threads per block column
   const int g = tid / TPC, rr = RPT * (tid - g * TPC);
@@ -450,6 +528,213 @@ __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 
     y[base] = cadd(cscale(es, sx), cscale(et, tx));
     y[base + (long)NZ * ncols] = cadd(cscale(es, sy), cscale(et, ty));
     y[base + 2L * NZ * ncols] = xs[((v * 3 + 2) * NZ + z) * nrhs + r];
+  }
+}
+
+// Schur-form apply (blocks TE^-1 and S^-1 per column, see the top of this file):
+//   y_s = TE^-1 u_s,  w = u_t - i kappa D (Dg^-1 u_z),  y_t = S^-1 w,
+//   y_z = Dg^-1 (u_z - i kappa D y_t - c y_t(z_ml)).
+// Same CTA layout as k_lay_apply (LAY_GROUP kx columns of row h and of its partner row, every
+// right-hand side); the products with the shared derivative matrix D run one output row per
+// thread over every vector of the CTA, the block products as in k_lay_apply on 2 NZ stacked rows.
+template <int NZ, bool HALF>
+constexpr int schur_threads() { return LAY_GROUP * 2 * NZ / apply_rpt<HALF>(); }
+
+template <int NZ, int NR, bool HALF>
+__global__ void __launch_bounds__(schur_threads<NZ, HALF>())
+    k_lay_apply_schur(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
+  if (all_done(a)) return;
+  constexpr int G = LAY_GROUP, NT = schur_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
+  static_assert(NT >= NZ, "one thread per row in the D products");
+  extern __shared__ cf sh[];
+  cf* xs = sh;                                   // [2G][3][NZ][NR] (s, t, z) after rotation
+  cf* ws = xs + 2 * G * 3 * NZ * NR;             // [2G][NZ][NR]   w
+  cf* gs = ws + 2 * G * NZ * NR;                 // [G][NZ]        Dg^-1
+  cf* cs = gs + G * NZ;                          // [G][NZ]        c
+  __shared__ float rot[2 * G][4];
+  __shared__ float kapv[G];
+  const long hc0 = (long)blockIdx.x * G;
+  const int ix0 = (int)(hc0 % a.nx), h = (int)(hc0 / a.nx);
+  const int ny = a.ny;
+  const int iyB = a.pair ? (ny - h) % ny : h;
+  const bool two = a.pair && iyB != h;
+  const int nv = two ? 2 * G : G;
+  const int tid = threadIdx.x;
+  if (tid < nv) {
+    const int iy = tid < G ? h : iyB;
+    const float kx = a.kx[ix0 + (tid % G)], ky = a.ky[iy];
+    const float kap = sqrtf(kx * kx + ky * ky);
+    const bool small = !(kap > 0.f);
+    rot[tid][0] = small ? 0.f : -ky / kap;
+    rot[tid][1] = small ? 1.f : kx / kap;
+    rot[tid][2] = small ? 1.f : kx / kap;
+    rot[tid][3] = small ? 0.f : ky / kap;
+  }
+  // Dg^-1 and c of each block column (both rows of a pair share kappa, r_p and k_z)
+  for (int it = tid; it < G * NZ; it += NT) {
+    const int g = it / NZ, z = it - g * NZ;
+    const Mode m = mode_of(a, hc0 + g);
+    if (z == 0) kapv[g] = m.kap;
+    const cf de = a.deps[z];
+    const cf gz = cdiv1(make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[z])));
+    gs[it] = gz;
+    cs[it] = (z >= a.zml) ? cscale(cmul(cmul(de, m.rp), cmul(upgoing(a, m, z), cdiv1(m.kz))), a.k0sq * m.kap)
+                          : czero();
+  }
+  __syncthreads();
+  const long n = 3L * NZ * ncols;
+  auto colof = [&](int v) -> long { return (long)(v < G ? h : iyB) * a.nx + ix0 + (v % G); };
+  for (int it = tid; it < NR * NZ * nv; it += NT) {
+    const int v = it % nv, z = (it / nv) % NZ, r = it / (nv * NZ);
+    const long base = (long)r * n + (long)z * ncols + colof(v);
+    const cf ex = x[base], ey = x[base + (long)NZ * ncols], ez = x[base + 2L * NZ * ncols];
+    const float sx = rot[v][0], sy = rot[v][1], tx = rot[v][2], ty = rot[v][3];
+    xs[((v * 3 + 0) * NZ + z) * NR + r] = cadd(cscale(ex, sx), cscale(ey, sy));
+    xs[((v * 3 + 1) * NZ + z) * NR + r] = cadd(cscale(ex, tx), cscale(ey, ty));
+    xs[((v * 3 + 2) * NZ + z) * NR + r] = ez;
+  }
+  __syncthreads();
+  // w = u_t - i kappa D (Dg^-1 u_z): thread i < NZ owns output row i of every vector
+  if (tid < NZ) {
+    const int i = tid;
+    cf acc[2 * G][NR];
+#pragma unroll
+    for (int v = 0; v < 2 * G; ++v)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[v][r] = czero();
+    for (int k = 0; k < NZ; ++k) {
+      const cf d = __ldg(a.D + (long)i * NZ + k);
+#pragma unroll
+      for (int v = 0; v < 2 * G; ++v) {
+        if (v >= nv) continue;
+        const cf dg = cmul(d, gs[(v % G) * NZ + k]);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[v][r] = cfma(dg, xs[((v * 3 + 2) * NZ + k) * NR + r], acc[v][r]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * G; ++v) {
+      if (v >= nv) continue;
+      const cf mik = make_float2(0.f, -kapv[v % G]);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        ws[(v * NZ + i) * NR + r] = cfma(mik, acc[v][r], xs[((v * 3 + 1) * NZ + i) * NR + r]);
+    }
+  }
+  __syncthreads();
+  // block products: thread -> (block column g, rows rr .. rr + RPT - 1 of [TE; S])
+  {
+    constexpr long NN = (long)NZ * NZ;
+    constexpr int TPC = 2 * NZ / RPT;
+    const int g = tid / TPC, rr = RPT * (tid - g * TPC);
+    const bool te = rr < NZ;
+    const int i = te ? rr : rr - NZ;
+    const long MS = block_stride(a);
+    const cf* Mb = a.mats + (hc0 + g) * MS + (te ? 0 : NN);
+    const __half2* Mh = a.mats16 + (hc0 + g) * MS + (te ? 0 : NN);
+    const cf* xa = te ? xs + (g * 3) * NZ * NR : ws + g * NZ * NR;
+    const cf* xb = te ? xs + ((g + G) * 3) * NZ * NR : ws + (g + G) * NZ * NR;
+    cf A[RPT][NR], Bv[RPT][NR];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) { A[q][r] = czero(); Bv[q][r] = czero(); }
+    auto load = [&](int j, cf (&m)[RPT]) {
+      if constexpr (HALF) {
+        const uint4 hv = __ldg(reinterpret_cast<const uint4*>(Mh + half_pos(i, j, NZ)));
+        m[0] = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+        m[1] = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+        m[2] = __half22float2(*reinterpret_cast<const __half2*>(&hv.z));
+        m[3] = __half22float2(*reinterpret_cast<const __half2*>(&hv.w));
+      } else {
+        const float4 mv = __ldg(reinterpret_cast<const float4*>(Mb + (long)j * NZ + i));
+        m[0] = make_float2(mv.x, mv.y);
+        m[1] = make_float2(mv.z, mv.w);
+      }
+    };
+#pragma unroll 4
+    for (int j = 0; j < NZ; ++j) {
+      cf mm[RPT];
+      load(j, mm);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const cf xv = xa[j * NR + r];
+        const cf xw = two ? xb[j * NR + r] : czero();
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          A[q][r] = cfma(mm[q], xv, A[q][r]);
+          Bv[q][r] = cfma(mm[q], xw, Bv[q][r]);
+        }
+      }
+    }
+    if constexpr (HALF) {
+      const float sc = a.scales[(hc0 + g) * 2 + (te ? 0 : 1)];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { A[q][r] = cscale(A[q][r], sc); Bv[q][r] = cscale(Bv[q][r], sc); }
+    }
+    __syncthreads();   // every thread has read u_s and w: y_s, y_t overwrite components 0 and 1
+    const int comp = te ? 0 : 1;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        xs[((g * 3 + comp) * NZ + i + q) * NR + r] = A[q][r];
+        if (two) xs[(((g + G) * 3 + comp) * NZ + i + q) * NR + r] = Bv[q][r];
+      }
+  }
+  __syncthreads();
+  // y_z = Dg^-1 (u_z - i kappa D y_t - c y_t(z_ml)): thread i < NZ owns row i
+  cf acc[2 * G][NR];
+#pragma unroll
+  for (int v = 0; v < 2 * G; ++v)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[v][r] = czero();
+  if (tid < NZ) {
+    const int i = tid;
+    for (int k = 0; k < NZ; ++k) {
+      const cf d = __ldg(a.D + (long)i * NZ + k);
+#pragma unroll
+      for (int v = 0; v < 2 * G; ++v) {
+        if (v >= nv) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[v][r] = cfma(d, xs[((v * 3 + 1) * NZ + k) * NR + r], acc[v][r]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * G; ++v) {
+      if (v >= nv) continue;
+      const int g = v % G;
+      const cf mik = make_float2(0.f, -kapv[g]);
+      const cf gi = gs[g * NZ + i], ci = cs[g * NZ + i];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const cf ytm = xs[((v * 3 + 1) * NZ + a.zml) * NR + r];
+        cf t = cfma(mik, acc[v][r], xs[((v * 3 + 2) * NZ + i) * NR + r]);
+        t = csub(t, cmul(ci, ytm));
+        acc[v][r] = cmul(gi, t);
+      }
+    }
+  }
+  __syncthreads();   // every row's reads of u_z and y_t are done
+  if (tid < NZ) {
+#pragma unroll
+    for (int v = 0; v < 2 * G; ++v) {
+      if (v >= nv) continue;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xs[((v * 3 + 2) * NZ + tid) * NR + r] = acc[v][r];
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < NR * NZ * nv; it += NT) {
+    const int v = it % nv, z = (it / nv) % NZ, r = it / (nv * NZ);
+    const long base = (long)r * n + (long)z * ncols + colof(v);
+    const cf es = xs[((v * 3 + 0) * NZ + z) * NR + r], et = xs[((v * 3 + 1) * NZ + z) * NR + r];
+    const float sx = rot[v][0], sy = rot[v][1], tx = rot[v][2], ty = rot[v][3];
+    y[base] = cadd(cscale(es, sx), cscale(et, tx));
+    y[base + (long)NZ * ncols] = cadd(cscale(es, sy), cscale(et, ty));
+    y[base + 2L * NZ * ncols] = xs[((v * 3 + 2) * NZ + z) * NR + r];
   }
 }
 
@@ -871,7 +1156,8 @@ LayArgs lay_args(psfd_plan_s* P) {
   a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.zml = P->p.z_ml;
   a.pair = layered_pairs(P) ? 1 : 0;
   a.mats = P->lay; a.err = P->lay_err;
-  a.mats16 = (__half2*)P->lay16; a.scales = P->lay_scale; a.half = P->lay_half ? 1 : 0;
+  a.mats16 = (__half2*)P->lay16; a.scales = P->lay_scale; a.half = layered_half(P) ? 1 : 0;
+  a.schur = P->lay_schur ? 1 : 0;
   const char* e = getenv("PSFD_TEST_LAY_NO_COPY");
   a.no_copy = (e && e[0] == '1') ? 1 : 0;
   return a;
@@ -883,7 +1169,38 @@ int build_nz(psfd_plan_s* P) {
   const unsigned nblk = (unsigned)layered_columns(P);
   k_lay_inv<NZ, false><<<nblk, LAY_THREADS, 0, P->stream>>>(a, 0);
   PSFD_CHECK_LAUNCH();
-  k_lay_inv<2 * NZ, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+  if (a.schur) {
+    if constexpr (NZ % 32 == 0) {
+      k_lay_inv<NZ, false, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+    } else {
+      psfd_set_error("layered preconditioner: the Schur form is built for nz in {32, 64, 96, 128}");
+      return PSFD_ERR_ARG;
+    }
+  } else {
+    if constexpr (2 * NZ <= 128) {
+      k_lay_inv<2 * NZ, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+    } else {
+      psfd_set_error("layered preconditioner: nz %d needs the Schur form", NZ);
+      return PSFD_ERR_ARG;
+    }
+  }
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <int NZ, int NR>
+int apply_schur_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
+  const size_t smem = (size_t)(2 * LAY_GROUP * 3 * NZ * NR + 2 * LAY_GROUP * NZ * NR + 2 * LAY_GROUP * NZ) * sizeof(cf);
+  const unsigned grid = (unsigned)(layered_columns(P) / LAY_GROUP);
+  if (a.half) {
+    PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_schur<NZ, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_lay_apply_schur<NZ, NR, true><<<grid, schur_threads<NZ, true>(), smem, P->stream>>>(a, x, y, P->ncols);
+  } else {
+    PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_schur<NZ, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_lay_apply_schur<NZ, NR, false><<<grid, schur_threads<NZ, false>(), smem, P->stream>>>(a, x, y, P->ncols);
+  }
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -926,18 +1243,47 @@ int apply_nz(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   LayArgs a = lay_args(P);
   a.done = done;
   a.nrhs = P->nrhs;
-  switch (P->nrhs) {
-    case 1: return apply_nr<NZ, 1>(P, a, x, y);
-    case 2: return apply_nr<NZ, 2>(P, a, x, y);
-    case 3: return apply_nr<NZ, 3>(P, a, x, y);
-    default: return apply_nr<NZ, 4>(P, a, x, y);
+  if (a.schur) {
+    if constexpr (NZ % 32 == 0) {
+      switch (P->nrhs) {
+        case 1: return apply_schur_nr<NZ, 1>(P, a, x, y);
+        case 2: return apply_schur_nr<NZ, 2>(P, a, x, y);
+        case 3: return apply_schur_nr<NZ, 3>(P, a, x, y);
+        default: return apply_schur_nr<NZ, 4>(P, a, x, y);
+      }
+    }
+    psfd_set_error("layered preconditioner: the Schur form is built for nz in {32, 64, 96, 128}");
+    return PSFD_ERR_ARG;
   }
+  if constexpr (NZ <= 64) {
+    switch (P->nrhs) {
+      case 1: return apply_nr<NZ, 1>(P, a, x, y);
+      case 2: return apply_nr<NZ, 2>(P, a, x, y);
+      case 3: return apply_nr<NZ, 3>(P, a, x, y);
+      default: return apply_nr<NZ, 4>(P, a, x, y);
+    }
+  }
+  psfd_set_error("layered preconditioner: nz %d needs the Schur form", NZ);
+  return PSFD_ERR_ARG;
 }
 
 }  // namespace
 
 int layered_supported(const psfd_plan_s* P) {
-  return (P->nz == 16 || P->nz == 32 || P->nz == 48 || P->nz == 64) && P->nx % LAY_GROUP == 0 && P->nrhs <= 4;
+  return (P->nz == 16 || P->nz == 32 || P->nz == 48 || P->nz == 64 || P->nz == 96 || P->nz == 128) &&
+         P->nx % LAY_GROUP == 0 && P->nrhs <= 4;
+}
+
+// half-precision storage in effect: requested, and not the Schur form (S^-1 carries the large
+// kappa^2 D Dg^-1 D part near grazing, and an 11-bit mantissa measured 3e-2 off the complex64
+// apply, with some 256^2 x 96 solves diverging; its blocks stay complex64)
+bool layered_half(const psfd_plan_s* P) { return P->lay_half && !P->lay_schur; }
+
+// the Schur form for nz above 64 (a 2 nz x 2 nz TM block no longer fits one CTA's registers), and
+// for any nz with PSFD_LAY_SCHUR=1
+bool layered_schur_for(const psfd_plan_s* P) {
+  const char* e = getenv("PSFD_LAY_SCHUR");
+  return P->nz > 64 || (e && e[0] == '1' && P->nz % 32 == 0);
 }
 
 // ky and -ky share their blocks when there is no Bloch shift along y (the blocks depend on kappa)
@@ -949,7 +1295,7 @@ long layered_columns(const psfd_plan_s* P) {
 }
 
 size_t layered_bytes(const psfd_plan_s* P) {
-  const size_t per = (size_t)5 * P->nz * P->nz * (P->lay_half ? sizeof(__half2) : sizeof(cf));
+  const size_t per = (size_t)(P->lay_schur ? 2 : 5) * P->nz * P->nz * (layered_half(P) ? sizeof(__half2) : sizeof(cf));
   return (size_t)layered_columns(P) * per;
 }
 
@@ -961,6 +1307,8 @@ int layered_apply(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
     case 32: return apply_nz<32>(P, x, y, done);
     case 48: return apply_nz<48>(P, x, y, done);
     case 64: return apply_nz<64>(P, x, y, done);
+    case 96: return apply_nz<96>(P, x, y, done);
+    case 128: return apply_nz<128>(P, x, y, done);
     default: psfd_set_error("layered preconditioner: unsupported nz %d", P->nz); return PSFD_ERR_ARG;
   }
 }
@@ -1003,21 +1351,32 @@ extern "C" int psfd_layered_storage(psfd_plan P, int storage) {
 
 extern "C" size_t psfd_layered_bytes(psfd_plan P) {
   if (!P || !layered_supported(P)) return 0;
-  return layered_bytes(P);
+  const bool built_form = P->lay_schur;
+  P->lay_schur = (P->lay || P->lay16) ? built_form : layered_schur_for(P);
+  const size_t b = layered_bytes(P);
+  P->lay_schur = built_form;
+  return b;
 }
 
 extern "C" int psfd_layered_build(psfd_plan P) {
   if (!P) { psfd_set_error("psfd_layered_build: null plan"); return PSFD_ERR_ARG; }
   if (!P->have_background) { psfd_set_error("psfd_layered_build: call psfd_background first"); return PSFD_ERR_STATE; }
   if (!layered_supported(P)) {
-    psfd_set_error("psfd_layered_build: supported for nz in {16, 32, 48, 64}, nx a multiple of 4, nrhs <= 4");
+    psfd_set_error("psfd_layered_build: supported for nz in {16, 32, 48, 64, 96, 128}, nx a multiple of 4, "
+                   "nrhs <= 4");
     return PSFD_ERR_ARG;
   }
   const int nz = P->nz;
   cudaStream_t s = P->stream;
   StageScope scope(s, ST_LAYBUILD);
-  if (P->lay_half ? !P->lay16 : !P->lay) {
-    if (P->lay_half) {
+  if (layered_schur_for(P) != P->lay_schur) {
+    // the block form changes the storage: release the blocks, keep the storage precision
+    PSFD_CUDA_TRY(cudaStreamSynchronize(s));
+    layered_free(P);
+    P->lay_schur = layered_schur_for(P);
+  }
+  if (layered_half(P) ? !P->lay16 : !P->lay) {
+    if (layered_half(P)) {
       PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay16, layered_bytes(P)));
       PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_scale, (size_t)layered_columns(P) * 2 * sizeof(float)));
     } else {
@@ -1071,7 +1430,9 @@ extern "C" int psfd_layered_build(psfd_plan P) {
     case 16: rc = build_nz<16>(P); break;
     case 32: rc = build_nz<32>(P); break;
     case 48: rc = build_nz<48>(P); break;
-    default: rc = build_nz<64>(P); break;
+    case 64: rc = build_nz<64>(P); break;
+    case 96: rc = build_nz<96>(P); break;
+    default: rc = build_nz<128>(P); break;
   }
   if (rc) return rc;
   int herr = 0;

@@ -124,12 +124,16 @@ int plan_wait_status(psfd_plan_s* P) {
   PSFD_CUDA_TRY(cudaStreamSynchronize(s));
   int rc = fno_mix_tc_error(&tc);
   if (rc) return rc;
+  int tm = 0;
+  if ((rc = fno_mlp_tc_error(&tm))) return rc;
+  tc = tc || tm;
   if (!h[0] && !h[1] && !tc) return PSFD_OK;
   if (h[0]) PSFD_CUDA_TRY(cudaMemsetAsync(P->err, 0, sizeof(int), s));
   if (h[1]) PSFD_CUDA_TRY(cudaMemsetAsync(P->lay_err + 1, 0, sizeof(int), s));
   PSFD_CUDA_TRY(cudaStreamSynchronize(s));
   psfd_set_error("a bounded device-side wait gave up (%s)",
-                 h[0] ? "operator plane kernel" : h[1] ? "layered preconditioner apply" : "FNO mode mixing");
+                 h[0] ? "operator plane kernel" : h[1] ? "layered preconditioner apply"
+                                                : (tm ? "FNO pointwise layers" : "FNO mode mixing"));
   return PSFD_ERR_TIMEOUT;
 }
 

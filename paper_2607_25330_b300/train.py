@@ -24,20 +24,27 @@ from . import psfd
 from .autograd import fno_apply, physics_loss
 
 
-def _weights(seed: int) -> Dict[str, torch.Tensor]:
+def _weights(seed: int, zero_output: bool = False) -> Dict[str, torch.Tensor]:
+    """Seed-initialised parameters; zero_output starts the last projection layer at zero, so that
+    the untrained network predicts E = 0 (the cold start) and training only improves on it."""
     S = I.FNOShape()
-    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda().requires_grad_(True)
-            for k, v in I.fno_weights(S, seed, spectral_scale=1.0).items()}
+    w = I.fno_weights(S, seed, spectral_scale=1.0)
+    if zero_output:
+        w["q2"] = np.zeros_like(w["q2"])
+        w["qb2"] = np.zeros_like(w["qb2"])
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda().requires_grad_(True) for k, v in w.items()}
 
 
 def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, log_every: int = 10,
-          pol: int = None, mask_seed: int = 1000):
+          pol: int = None, mask_seed: int = 1000, zero_output: bool = False, w: Dict = None):
     """Adam on the physics loss over `pool` seeded masks (a random batch of them per step); `pol`
-    selects the illumination (one model per polarisation), default the preset's first."""
+    selects the illumination (one model per polarisation), default the preset's first; `w`
+    continues from given parameters."""
     prob = I.preset(preset)
     prob.pols = [prob.pols[0] if pol is None else int(pol)]
     S = I.FNOShape()
-    w = _weights(seed)
+    if w is None:
+        w = _weights(seed, zero_output)
     trainer = psfd.FnoTrainer(psfd.fno_struct(w, S), batch, prob.nz, prob.ny, prob.nx, checkpoint=True)
     plans = [psfd.Plan(prob, nrhs=1) for _ in range(batch)]
     masks = [torch.from_numpy(I.mask_for(prob, mask_seed + i)) for i in range(pool)]
@@ -64,10 +71,11 @@ def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, 
     return w, log
 
 
-def evaluate(w: Dict[str, torch.Tensor], preset: str, masks: int, tol: float = 1e-6) -> Dict:
+def evaluate(w: Dict[str, torch.Tensor], preset: str, masks: int, tol: float = 1e-6, pol: int = None) -> Dict:
     """Warm start from the network on held-out masks: initial relative residual and BiCGSTAB
     iterations to `tol` with the layered preconditioner (mean over masks)."""
     prob = I.preset(preset)
+    prob.pols = [prob.pols[0] if pol is None else int(pol)]
     S = I.FNOShape()
     ws = psfd.fno_struct({k: v.detach() for k, v in w.items()}, S)
     plan = psfd.Plan(prob, nrhs=1)

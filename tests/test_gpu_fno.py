@@ -82,3 +82,23 @@ def test_tensor_core_mixing_equals_simt_mixing(dims, monkeypatch):
     E_simt = psfd.fno_forward(ws, a)
     torch.cuda.synchronize()
     assert rel_l2(E_tc.cpu(), E_simt.cpu()) < 1e-5
+
+
+@pytest.mark.parametrize("dims", [(2, 32, 32, 16), (1, 64, 32, 48), (1, 128, 128, 64)])
+def test_tensor_core_pointwise_layers_equal_simt(dims, monkeypatch):
+    """The MLP and projection on the tensor cores (kind::tf32, operands split into TF32 high and low
+    parts, FP32 accumulation) give the CUDA-core result to FP32 level; both match the oracle above."""
+    from paper_2607_25330_b300 import psfd
+    B, nx, ny, nz = dims
+    S = I.FNOShape()
+    w = I.fno_weights(S, 23, spectral_scale=4.0)
+    ws = psfd.fno_struct(device_weights(w), S)
+    a = torch.from_numpy(np.random.default_rng(6).random((B, nz, ny, nx)).astype(np.float32)).cuda()
+    monkeypatch.setenv("PSFD_MLP_TC", "1")
+    E_tc = psfd.fno_forward(ws, a).clone()
+    monkeypatch.setenv("PSFD_MLP_TC", "0")
+    E_simt = psfd.fno_forward(ws, a)
+    torch.cuda.synchronize()
+    e = rel_l2(E_tc.cpu(), E_simt.cpu())
+    print(f"FNO {dims}: tensor-core vs CUDA-core pointwise layers rel L2 {e:.2e}")
+    assert e < 1e-5
