@@ -58,6 +58,10 @@ def parse():
                     help="iteration cap per solve (lower it only for profiling runs)")
     ap.add_argument("--profile-apply", type=int, default=0,
                     help="run N HYBRID A M applies on one mask and exit (small ncu captures)")
+    ap.add_argument("--profile-op", default="default", choices=["default", "A", "AM", "AP"],
+                    help="operator of --profile-apply: A, A M, A P (default: A P with the layered P, else A M)")
+    ap.add_argument("--profile-fno", type=int, default=0,
+                    help="run N FNO forwards (B = 1) on the workload's grid and exit (small ncu captures)")
     ap.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
     ap.add_argument("--precond", default="layered", choices=["layered", "damping"],
                     help="headline preconditioner: layered-background P (default) or the paper's damping M")
@@ -783,11 +787,13 @@ def run_profile_apply(args):
     fill = plan.mask_fill(torch.from_numpy(I.mask_for(prob, 0)).cuda(), prob.zprofile())
     plan.background(prob.stack(), fill, prob.pols[:nrhs] if nrhs <= len(prob.pols) else [0] * nrhs)
     flags = psfd.PSFD_HYBRID | psfd.PSFD_PRECOND
-    if args.precond == "layered" and plan.layered_bytes() > 0:
+    if args.profile_op in ("default", "AP") and args.precond == "layered" and plan.layered_bytes() > 0:
         if args.lay_half:
             plan.layered_storage(True)
         plan.layered_build()
         flags = psfd.PSFD_HYBRID | psfd.PSFD_LAYERED
+    elif args.profile_op == "A":
+        flags = psfd.PSFD_HYBRID
     x = torch.randn(plan.shape, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -798,6 +804,30 @@ def run_profile_apply(args):
     torch.cuda.synchronize()
     return {"profile_apply": args.profile_apply, "workload": args.workload, "nrhs": nrhs, "flags": flags,
             "ms_per_apply": e0.elapsed_time(e1) / max(1, args.profile_apply)}
+
+
+def run_profile_fno(args):
+    """N forwards of the seed-initialised FNO (B = 1) on the workload's grid (kernel captures)."""
+    import torch
+    from paper_2607_25330_b300 import inputs as I
+    from paper_2607_25330_b300 import psfd
+    prob = I.preset(args.workload)
+    S = I.FNOShape()
+    w = I.fno_weights(S, 77)
+    ws = psfd.fno_struct({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in w.items()}, S)
+    a = torch.rand((1, prob.nz, prob.ny, prob.nx), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    out = torch.empty((1, 3, prob.nz, prob.ny, prob.nx), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        psfd.fno_forward(ws, a, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.profile_fno):
+        psfd.fno_forward(ws, a, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"profile_fno": args.profile_fno, "workload": args.workload,
+            "ms_per_forward": e0.elapsed_time(e1) / max(1, args.profile_fno)}
 
 
 def run_train_step(args, steps=None, warmup=None):
@@ -958,6 +988,9 @@ def main():
         return
     if args.profile_apply:
         print(json.dumps(run_profile_apply(args)), flush=True)
+        return
+    if args.profile_fno:
+        print(json.dumps(run_profile_fno(args)), flush=True)
         return
     if args.train_step:
         print(json.dumps(run_train_step(args)), flush=True)

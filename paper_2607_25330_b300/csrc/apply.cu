@@ -351,7 +351,7 @@ static int run_axial_mode(psfd_plan_s* P, const cf* x, cf* y, int mode, const in
 
 int axial_supported(int nz) {
   switch (nz) {
-    case 16: case 32: case 48: case 64: case 96: case 128: return 1;
+    case 16: case 32: case 48: case 64: case 96: case 128: case 256: case 512: case 1024: return 1;
     default: return 0;
   }
 }
@@ -369,6 +369,10 @@ int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, 
     case 64: return (T == 4) ? run_axial_mode<64, 4>(P, x, y, mode, done) : run_axial_mode<64, 8>(P, x, y, mode, done);
     case 96: return run_axial_mode<96, 4>(P, x, y, mode, done);
     case 128: return (T == 4) ? run_axial_mode<128, 4>(P, x, y, mode, done) : run_axial_mode<128, 8>(P, x, y, mode, done);
+    // long columns (layer stacks meshed in the domain): one warp per column above 256 planes
+    case 256: return run_axial_mode<256, 16>(P, x, y, mode, done);
+    case 512: return run_axial_mode<512, 16>(P, x, y, mode, done);
+    case 1024: return run_axial_mode<1024, 32>(P, x, y, mode, done);
   }
   psfd_set_error("axial: unsupported nz %d", P->nz);
   return PSFD_ERR_ARG;
@@ -383,6 +387,9 @@ int axial_candidates(int nz, int* out) {
     case 64: out[0] = 8; out[1] = 4; return 2;
     case 96: out[0] = 4; return 1;
     case 128: out[0] = 8; out[1] = 4; return 2;
+    case 256: out[0] = 16; return 1;
+    case 512: out[0] = 16; return 1;
+    case 1024: out[0] = 32; return 1;
   }
   return 0;
 }

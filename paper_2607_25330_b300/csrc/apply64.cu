@@ -462,6 +462,9 @@ int apply64_hybrid(psfd_plan_s* P, const zd* x, zd* y) {
       case 64: rc = axial64_run<64, 8>(P, x, y); break;
       case 96: rc = axial64_run<96, 4>(P, x, y); break;
       case 128: rc = axial64_run<128, 8>(P, x, y); break;
+      case 256: rc = axial64_run<256, 16>(P, x, y); break;
+      case 512: rc = axial64_run<512, 16>(P, x, y); break;
+      case 1024: rc = axial64_run<1024, 32>(P, x, y); break;
       default: psfd_set_error("apply64: nz %d", P->nz); return PSFD_ERR_ARG;
     }
     if (rc) return rc;

@@ -16,6 +16,7 @@
 // 16-byte core matrices, K-adjacent core matrices 128 B apart, 8-row groups (K bytes / 16) x 128 B
 // apart.  Every wait on the tensor core is bounded; on a timeout the kernel records it in the same
 // device flag as the mode mixing, waits once more, frees its tensor memory and returns.
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 
@@ -150,6 +151,21 @@ constexpr int MLP_B1 = MLP_H * MLP_C * 4;    // 8 KB per part
 constexpr int MLP_B2 = MLP_C * MLP_H * 4;    // 8 KB per part
 constexpr int MLP_SMEM = 2 * MLP_A + 2 * MLP_B1 + 2 * MLP_B2;
 
+// split x into TF32 high and low parts and store four consecutive K entries of one row (16 bytes)
+template <int K>
+__device__ __forceinline__ void stage4(unsigned char* hi, unsigned char* lo, int row, int k, const float* x) {
+  float4 h, l;
+  split(x[0], h.x, l.x);
+  split(x[1], h.y, l.y);
+  split(x[2], h.z, l.z);
+  split(x[3], h.w, l.w);
+  *reinterpret_cast<float4*>(hi + koff<K>(row, k)) = h;
+  *reinterpret_cast<float4*>(lo + koff<K>(row, k)) = l;
+}
+
+// Persistent: each CTA stages the weights once, keeps its tensor memory, and walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's inputs are requested from global memory
+// while the current tile's products run.
 // v_out = v_in + s(W2 gelu(W1 (uxy + uz) + b1) + b2), s = GELU when outer_gelu; v_out may alias v_in
 __global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, const float* __restrict__ uxy,
                                                const float* __restrict__ uz, const float* __restrict__ W1,
@@ -169,78 +185,80 @@ __global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, co
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t mb = saddr(&mbar);
   alloc_tmem(&tmem_base, mb);
-  const long i = (long)blockIdx.x * MT + tid;
-  const bool in = i < (long)B * N;
-  const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
-  const long base = b * MLP_C * N + pt;
-  // A1 = uxy + uz (row = point, K = C), split
-#pragma unroll 8
-  for (int c = 0; c < MLP_C; ++c) {
-    const float h = in ? uxy[base + c * N] + uz[base + c * N] : 0.f;
-    float hi, lo;
-    split(h, hi, lo);
-    *reinterpret_cast<float*>(Ahi + koff<MLP_C>(tid, c)) = hi;
-    *reinterpret_cast<float*>(Alo + koff<MLP_C>(tid, c)) = lo;
-  }
-  for (int e = tid; e < MLP_H * MLP_C; e += MT) {
+  for (int e = 4 * tid; e < MLP_H * MLP_C; e += 4 * MT) {
     const int j = e / MLP_C, c = e - j * MLP_C;      // W1 [H][C]: row j of B1 (N = H, K = C)
-    float hi, lo;
-    split(W1[e], hi, lo);
-    *reinterpret_cast<float*>(B1hi + koff<MLP_C>(j, c)) = hi;
-    *reinterpret_cast<float*>(B1lo + koff<MLP_C>(j, c)) = lo;
+    stage4<MLP_C>(B1hi, B1lo, j, c, W1 + e);
     const int o = e / MLP_H, k = e - o * MLP_H;      // W2 [C][H]: row o of B2 (N = C, K = H)
-    split(W2[e], hi, lo);
-    *reinterpret_cast<float*>(B2hi + koff<MLP_H>(o, k)) = hi;
-    *reinterpret_cast<float*>(B2lo + koff<MLP_H>(o, k)) = lo;
+    stage4<MLP_H>(B2hi, B2lo, o, k, W2 + e);
   }
   if (tid < MLP_H) sb1[tid] = b1[tid];
   if (tid < MLP_C) sb2[tid] = b2[tid];
-  to_tensor_core();
-  const uint32_t taddr = tmem_base;
-  if (tid == 0) {
-    mma3<MLP_C, MLP_H>(taddr, saddr(Ahi), saddr(Alo), saddr(B1hi), saddr(B1lo));
-    commit(mb);
-  }
-  if (!wait_products(mb, 0, taddr, err)) return;
-  const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
-  // GELU(W1 h + b1) -> A2 (row = point, K = H), split
+  const long total = (long)B * N;
+  const long ntiles = (total + MT - 1) / MT;
+  auto load_h = [&](long tile, float* h) {
+    const long i = tile * MT + tid;
+    const bool in = tile < ntiles && i < total;
+    const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
+    const long base = b * MLP_C * N + pt;
 #pragma unroll
-  for (int q = 0; q < MLP_H / 16; ++q) {
-    float d[16];
-    tmem_ld16(trow + q * 16, d);
+    for (int c = 0; c < MLP_C; ++c) h[c] = in ? uxy[base + c * N] + uz[base + c * N] : 0.f;
+  };
+  float h[MLP_C];
+  load_h(blockIdx.x, h);
+  uint32_t ph = 0;
+  uint32_t taddr = 0;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int j = q * 16 + u;
-      float hi, lo;
-      split(gelu_f(d[u] + sb1[j]), hi, lo);
-      *reinterpret_cast<float*>(Ahi + koff<MLP_H>(tid, j)) = hi;
-      *reinterpret_cast<float*>(Alo + koff<MLP_H>(tid, j)) = lo;
+    for (int c = 0; c < MLP_C; c += 4) stage4<MLP_C>(Ahi, Alo, tid, c, h + c);
+    to_tensor_core();
+    taddr = tmem_base;
+    if (tid == 0) {
+      mma3<MLP_C, MLP_H>(taddr, saddr(Ahi), saddr(Alo), saddr(B1hi), saddr(B1lo));
+      commit(mb);
+    }
+    load_h(tile + gridDim.x, h);                     // next tile, while the products run
+    if (!wait_products(mb, ph, taddr, err)) return;
+    ph ^= 1u;
+    const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
+    // GELU(W1 h + b1) -> A2 (row = point, K = H)
+#pragma unroll
+    for (int q = 0; q < MLP_H / 16; ++q) {
+      float d[16];
+      tmem_ld16(trow + q * 16, d);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) d[u] = gelu_f(d[u] + sb1[q * 16 + u]);
+#pragma unroll
+      for (int u = 0; u < 16; u += 4) stage4<MLP_H>(Ahi, Alo, tid, q * 16 + u, d + u);
+    }
+    to_tensor_core();
+    if (tid == 0) {
+      mma3<MLP_H, MLP_C>(taddr + MLP_H, saddr(Ahi), saddr(Alo), saddr(B2hi), saddr(B2lo));
+      commit(mb);
+    }
+    if (!wait_products(mb, ph, taddr, err)) return;
+    ph ^= 1u;
+    float o[MLP_C];
+    tmem_ld16(trow + MLP_H, o);
+    tmem_ld16(trow + MLP_H + 16, o + 16);
+    const long i = tile * MT + tid;
+    if (i < total) {
+      const long b = i / N, pt = i - b * N;
+      const long base = b * MLP_C * N + pt;
+#pragma unroll
+      for (int c = 0; c < MLP_C; ++c) {
+        const float t = o[c] + sb2[c];
+        vout[base + c * N] = vin[base + c * N] + (outer_gelu ? gelu_f(t) : t);
+      }
     }
   }
-  to_tensor_core();
-  if (tid == 0) {
-    mma3<MLP_H, MLP_C>(taddr + MLP_H, saddr(Ahi), saddr(Alo), saddr(B2hi), saddr(B2lo));
-    commit(mb);
-  }
-  if (!wait_products(mb, 1, taddr, err)) return;
-  float o[MLP_C];
-  tmem_ld16(trow + MLP_H, o);
-  tmem_ld16(trow + MLP_H + 16, o + 16);
-  if (in) {
-#pragma unroll
-    for (int c = 0; c < MLP_C; ++c) {
-      const float t = o[c] + sb2[c];
-      vout[base + c * N] = vin[base + c * N] + (outer_gelu ? gelu_f(t) : t);
-    }
-  }
-  free_tmem(taddr);
+  free_tmem(tmem_base);
 }
 
 constexpr int PROJ_A = MT * MLP_C * 4;       // 16 KB per part
 constexpr int PROJ_B = PROJ_Q * MLP_C * 4;   // 16 KB per part
 constexpr int PROJ_SMEM = 2 * PROJ_A + 2 * PROJ_B;
 
-// E = (Q2 gelu(Q1 v + qb1) + qb2) as (Re, Im) of (Ex, Ey, Ez)
+// E = (Q2 gelu(Q1 v + qb1) + qb2) as (Re, Im) of (Ex, Ey, Ez); persistent as k_mlp_tc
 __global__ void __launch_bounds__(MT) k_proj_tc(const float* __restrict__ v, cf* __restrict__ E,
                                                 const float* __restrict__ Q1, const float* __restrict__ qb1,
                                                 const float* __restrict__ Q2, const float* __restrict__ qb2, long N,
@@ -256,55 +274,61 @@ __global__ void __launch_bounds__(MT) k_proj_tc(const float* __restrict__ v, cf*
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t mb = saddr(&mbar);
   alloc_tmem(&tmem_base, mb);
-  const long i = (long)blockIdx.x * MT + tid;
-  const bool in = i < (long)B * N;
-  const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
-#pragma unroll 8
-  for (int c = 0; c < MLP_C; ++c) {
-    const float x = in ? v[(b * MLP_C + c) * N + pt] : 0.f;
-    float hi, lo;
-    split(x, hi, lo);
-    *reinterpret_cast<float*>(Ahi + koff<MLP_C>(tid, c)) = hi;
-    *reinterpret_cast<float*>(Alo + koff<MLP_C>(tid, c)) = lo;
-  }
-  for (int e = tid; e < PROJ_Q * MLP_C; e += MT) {
+  for (int e = 4 * tid; e < PROJ_Q * MLP_C; e += 4 * MT) {
     const int j = e / MLP_C, c = e - j * MLP_C;      // Q1 [Q][C]
-    float hi, lo;
-    split(Q1[e], hi, lo);
-    *reinterpret_cast<float*>(Bhi + koff<MLP_C>(j, c)) = hi;
-    *reinterpret_cast<float*>(Blo + koff<MLP_C>(j, c)) = lo;
+    stage4<MLP_C>(Bhi, Blo, j, c, Q1 + e);
   }
   for (int e = tid; e < 6 * PROJ_Q; e += MT) sq2[e] = Q2[e];
   sq1[tid] = qb1[tid];
   if (tid < 6) sqb2[tid] = qb2[tid];
-  to_tensor_core();
-  const uint32_t taddr = tmem_base;
-  if (tid == 0) {
-    mma3<MLP_C, PROJ_Q>(taddr, saddr(Ahi), saddr(Alo), saddr(Bhi), saddr(Blo));
-    commit(mb);
-  }
-  if (!wait_products(mb, 0, taddr, err)) return;
-  const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
-  float o[6];
+  const long total = (long)B * N;
+  const long ntiles = (total + MT - 1) / MT;
+  auto load_v = [&](long tile, float* x) {
+    const long i = tile * MT + tid;
+    const bool in = tile < ntiles && i < total;
+    const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) o[k] = sqb2[k];
+    for (int c = 0; c < MLP_C; ++c) x[c] = in ? v[(b * MLP_C + c) * N + pt] : 0.f;
+  };
+  float x[MLP_C];
+  load_v(blockIdx.x, x);
+  uint32_t ph = 0;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#pragma unroll
+    for (int c = 0; c < MLP_C; c += 4) stage4<MLP_C>(Ahi, Alo, tid, c, x + c);
+    to_tensor_core();
+    const uint32_t taddr = tmem_base;
+    if (tid == 0) {
+      mma3<MLP_C, PROJ_Q>(taddr, saddr(Ahi), saddr(Alo), saddr(Bhi), saddr(Blo));
+      commit(mb);
+    }
+    load_v(tile + gridDim.x, x);
+    if (!wait_products(mb, ph, taddr, err)) return;
+    ph ^= 1u;
+    const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
+    float o[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[k] = sqb2[k];
 #pragma unroll 1
-  for (int q = 0; q < PROJ_Q / 16; ++q) {
-    float d[16];
-    tmem_ld16(trow + q * 16, d);
+    for (int q = 0; q < PROJ_Q / 16; ++q) {
+      float d[16];
+      tmem_ld16(trow + q * 16, d);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int j = q * 16 + u;
-      const float g = gelu_f(d[u] + sq1[j]);
+      for (int u = 0; u < 16; ++u) {
+        const int j = q * 16 + u;
+        const float g = gelu_f(d[u] + sq1[j]);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) o[k] = fmaf(sq2[k * PROJ_Q + j], g, o[k]);
+        for (int k = 0; k < 6; ++k) o[k] = fmaf(sq2[k * PROJ_Q + j], g, o[k]);
+      }
+    }
+    const long i = tile * MT + tid;
+    if (i < total) {
+      const long b = i / N, pt = i - b * N;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) E[(b * 3 + c) * N + pt] = make_float2(o[2 * c], o[2 * c + 1]);
     }
   }
-  if (in) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) E[(b * 3 + c) * N + pt] = make_float2(o[2 * c], o[2 * c + 1]);
-  }
-  free_tmem(taddr);
+  free_tmem(tmem_base);
 }
 
 int* g_mlp_err = nullptr;
@@ -328,11 +352,23 @@ static int mlp_err_ptr() {
   return PSFD_OK;
 }
 
+// persistent grid: CTAs per SM (shared memory bound) x SMs, at most one CTA per tile
+static unsigned persistent_grid(long ntiles, int per_sm) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  return (unsigned)std::min<long>(ntiles, (long)nsm * per_sm);
+}
+
 int fno_mlp_tc(const float* vin, float* vout, const float* uxy, const float* uz, const float* W1, const float* b1,
                const float* W2, const float* b2, long N, int B, bool outer_gelu, cudaStream_t s) {
   int rc = mlp_err_ptr();
   if (rc) return rc;
-  const unsigned grid = (unsigned)(((long)B * N + MT - 1) / MT);
+  const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 2);
   k_mlp_tc<<<grid, MT, MLP_SMEM, s>>>(vin, vout, uxy, uz, W1, b1, W2, b2, N, B, outer_gelu ? 1 : 0, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -342,7 +378,7 @@ int fno_proj_tc(const float* v, cf* E, const float* Q1, const float* qb1, const 
                 int B, cudaStream_t s) {
   int rc = mlp_err_ptr();
   if (rc) return rc;
-  const unsigned grid = (unsigned)(((long)B * N + MT - 1) / MT);
+  const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 3);
   k_proj_tc<<<grid, MT, PROJ_SMEM, s>>>(v, E, Q1, qb1, Q2, qb2, N, B, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
