@@ -350,8 +350,8 @@ PSFD_API int psfd_physics_loss(psfd_plan plan, const psfd_c64* E, const psfd_c64
  * PSFD_MIX_FP32=1 in the environment keeps both operands in float32 instead (a
  * verification mode: the network without the bfloat16 rounding, on the SIMT
  * mixing kernel).  The pointwise layers (the MLP of Eq. 4 and the projection)
- * run on the CUDA cores in FP32; PSFD_MLP_TC=1 runs them on the tensor cores at
- * FP32 accuracy (TF32 products of split operands) for dv = 32, dh = 64, dq = 128. */
+ * run on the tensor cores at FP32 accuracy (TF32 products of split operands) for
+ * dv = 32, dh = 64, dq = 128; PSFD_MLP_TC=0 selects the CUDA-core kernels. */
 typedef struct {
   int dv, dh, layers, mx, my, mz, dq;
   const float* lift_w; const float* lift_b;

@@ -163,15 +163,20 @@ __device__ __forceinline__ void stage4(unsigned char* hi, unsigned char* lo, int
   *reinterpret_cast<float4*>(lo + koff<K>(row, k)) = l;
 }
 
-// Persistent: each CTA stages the weights once, keeps its tensor memory, and walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's inputs are requested from global memory
+// Persistent, 8 warps: each CTA stages the weights once, keeps its tensor memory, and walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Two threads serve a point: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (its quarter of the tile's points) and owns half hh = w / 4 of every
+// accumulator row and of the point's channels.  The next tile's inputs are loaded into registers
 // while the current tile's products run.
+constexpr int NT2 = 2 * MT;   // threads per CTA
+
 // v_out = v_in + s(W2 gelu(W1 (uxy + uz) + b1) + b2), s = GELU when outer_gelu; v_out may alias v_in
-__global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, const float* __restrict__ uxy,
-                                               const float* __restrict__ uz, const float* __restrict__ W1,
-                                               const float* __restrict__ b1, const float* __restrict__ W2,
-                                               const float* __restrict__ b2, long N, int B, int outer_gelu,
-                                               int* err) {
+__global__ void __launch_bounds__(NT2) k_mlp_tc(const float* vin, float* vout, const float* __restrict__ uxy,
+                                                const float* __restrict__ uz, const float* __restrict__ W1,
+                                                const float* __restrict__ b1, const float* __restrict__ W2,
+                                                const float* __restrict__ b2, long N, int B, int outer_gelu,
+                                                int* err) {
+  constexpr int HC = MLP_C / 2, HH = MLP_H / 2;   // channels and hidden units per thread
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* Ahi = sm;
   unsigned char* Alo = sm + MLP_A;
@@ -182,10 +187,11 @@ __global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, co
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sb1[MLP_H], sb2[MLP_C];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = 32 * (warp & 3) + lane, hh = warp >> 2;
   const uint32_t mb = saddr(&mbar);
   alloc_tmem(&tmem_base, mb);
-  for (int e = 4 * tid; e < MLP_H * MLP_C; e += 4 * MT) {
+  for (int e = 4 * tid; e < MLP_H * MLP_C; e += 4 * NT2) {
     const int j = e / MLP_C, c = e - j * MLP_C;      // W1 [H][C]: row j of B1 (N = H, K = C)
     stage4<MLP_C>(B1hi, B1lo, j, c, W1 + e);
     const int o = e / MLP_H, k = e - o * MLP_H;      // W2 [C][H]: row o of B2 (N = C, K = H)
@@ -195,40 +201,47 @@ __global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, co
   if (tid < MLP_C) sb2[tid] = b2[tid];
   const long total = (long)B * N;
   const long ntiles = (total + MT - 1) / MT;
-  auto load_h = [&](long tile, float* h) {
-    const long i = tile * MT + tid;
+  // point `row` of a tile; channels HC hh .. HC hh + HC - 1 of uxy + uz and of v_in
+  auto load = [&](long tile, float* h, float* r) {
+    const long i = tile * MT + row;
     const bool in = tile < ntiles && i < total;
     const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
-    const long base = b * MLP_C * N + pt;
+    const long base = (b * MLP_C + HC * hh) * N + pt;
 #pragma unroll
-    for (int c = 0; c < MLP_C; ++c) h[c] = in ? uxy[base + c * N] + uz[base + c * N] : 0.f;
+    for (int c = 0; c < HC; ++c) {
+      h[c] = in ? uxy[base + c * N] + uz[base + c * N] : 0.f;
+      r[c] = in ? vin[base + c * N] : 0.f;
+    }
   };
-  float h[MLP_C];
-  load_h(blockIdx.x, h);
+  float h[HC], r[HC];
+  load(blockIdx.x, h, r);
   uint32_t ph = 0;
-  uint32_t taddr = 0;
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
 #pragma unroll
-    for (int c = 0; c < MLP_C; c += 4) stage4<MLP_C>(Ahi, Alo, tid, c, h + c);
+    for (int c = 0; c < HC; c += 4) stage4<MLP_C>(Ahi, Alo, row, HC * hh + c, h + c);
+    float rin[HC];
+#pragma unroll
+    for (int c = 0; c < HC; ++c) rin[c] = r[c];
     to_tensor_core();
-    taddr = tmem_base;
+    const uint32_t taddr = tmem_base;
     if (tid == 0) {
       mma3<MLP_C, MLP_H>(taddr, saddr(Ahi), saddr(Alo), saddr(B1hi), saddr(B1lo));
       commit(mb);
     }
-    load_h(tile + gridDim.x, h);                     // next tile, while the products run
+    load(tile + gridDim.x, h, r);                    // next tile, while the products run
     if (!wait_products(mb, ph, taddr, err)) return;
     ph ^= 1u;
-    const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
-    // GELU(W1 h + b1) -> A2 (row = point, K = H)
+    const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    // GELU(W1 h + b1) -> A2 (row = point, K = H): this thread's half of the hidden units
 #pragma unroll
-    for (int q = 0; q < MLP_H / 16; ++q) {
+    for (int q = 0; q < HH / 16; ++q) {
       float d[16];
-      tmem_ld16(trow + q * 16, d);
+      const int j0 = HH * hh + 16 * q;
+      tmem_ld16(trow + j0, d);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) d[u] = gelu_f(d[u] + sb1[q * 16 + u]);
+      for (int u = 0; u < 16; ++u) d[u] = gelu_f(d[u] + sb1[j0 + u]);
 #pragma unroll
-      for (int u = 0; u < 16; u += 4) stage4<MLP_H>(Ahi, Alo, tid, q * 16 + u, d + u);
+      for (int u = 0; u < 16; u += 4) stage4<MLP_H>(Ahi, Alo, row, j0 + u, d + u);
     }
     to_tensor_core();
     if (tid == 0) {
@@ -237,17 +250,16 @@ __global__ void __launch_bounds__(MT) k_mlp_tc(const float* vin, float* vout, co
     }
     if (!wait_products(mb, ph, taddr, err)) return;
     ph ^= 1u;
-    float o[MLP_C];
-    tmem_ld16(trow + MLP_H, o);
-    tmem_ld16(trow + MLP_H + 16, o + 16);
-    const long i = tile * MT + tid;
+    float o[HC];
+    tmem_ld16(trow + MLP_H + HC * hh, o);
+    const long i = tile * MT + row;
     if (i < total) {
       const long b = i / N, pt = i - b * N;
-      const long base = b * MLP_C * N + pt;
+      const long base = (b * MLP_C + HC * hh) * N + pt;
 #pragma unroll
-      for (int c = 0; c < MLP_C; ++c) {
-        const float t = o[c] + sb2[c];
-        vout[base + c * N] = vin[base + c * N] + (outer_gelu ? gelu_f(t) : t);
+      for (int c = 0; c < HC; ++c) {
+        const float t = o[c] + sb2[HC * hh + c];
+        vout[base + c * N] = rin[c] + (outer_gelu ? gelu_f(t) : t);
       }
     }
   }
@@ -258,11 +270,14 @@ constexpr int PROJ_A = MT * MLP_C * 4;       // 16 KB per part
 constexpr int PROJ_B = PROJ_Q * MLP_C * 4;   // 16 KB per part
 constexpr int PROJ_SMEM = 2 * PROJ_A + 2 * PROJ_B;
 
-// E = (Q2 gelu(Q1 v + qb1) + qb2) as (Re, Im) of (Ex, Ey, Ez); persistent as k_mlp_tc
-__global__ void __launch_bounds__(MT) k_proj_tc(const float* __restrict__ v, cf* __restrict__ E,
-                                                const float* __restrict__ Q1, const float* __restrict__ qb1,
-                                                const float* __restrict__ Q2, const float* __restrict__ qb2, long N,
-                                                int B, int* err) {
+// E = (Q2 gelu(Q1 v + qb1) + qb2) as (Re, Im) of (Ex, Ey, Ez); persistent, 8 warps as k_mlp_tc
+// (each half of the hidden units gives partial sums of the six outputs; the halves meet in
+// shared memory)
+__global__ void __launch_bounds__(NT2) k_proj_tc(const float* __restrict__ v, cf* __restrict__ E,
+                                                 const float* __restrict__ Q1, const float* __restrict__ qb1,
+                                                 const float* __restrict__ Q2, const float* __restrict__ qb2, long N,
+                                                 int B, int* err) {
+  constexpr int HC = MLP_C / 2, HQ = PROJ_Q / 2;
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* Ahi = sm;
   unsigned char* Alo = sm + PROJ_A;
@@ -271,61 +286,71 @@ __global__ void __launch_bounds__(MT) k_proj_tc(const float* __restrict__ v, cf*
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sq1[PROJ_Q], sq2[6 * PROJ_Q], sqb2[6];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ float part[MT][7];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = 32 * (warp & 3) + lane, hh = warp >> 2;
   const uint32_t mb = saddr(&mbar);
   alloc_tmem(&tmem_base, mb);
-  for (int e = 4 * tid; e < PROJ_Q * MLP_C; e += 4 * MT) {
+  for (int e = 4 * tid; e < PROJ_Q * MLP_C; e += 4 * NT2) {
     const int j = e / MLP_C, c = e - j * MLP_C;      // Q1 [Q][C]
     stage4<MLP_C>(Bhi, Blo, j, c, Q1 + e);
   }
-  for (int e = tid; e < 6 * PROJ_Q; e += MT) sq2[e] = Q2[e];
-  sq1[tid] = qb1[tid];
+  for (int e = tid; e < 6 * PROJ_Q; e += NT2) sq2[e] = Q2[e];
+  if (tid < PROJ_Q) sq1[tid] = qb1[tid];
   if (tid < 6) sqb2[tid] = qb2[tid];
   const long total = (long)B * N;
   const long ntiles = (total + MT - 1) / MT;
-  auto load_v = [&](long tile, float* x) {
-    const long i = tile * MT + tid;
+  auto load = [&](long tile, float* x) {
+    const long i = tile * MT + row;
     const bool in = tile < ntiles && i < total;
     const long b = in ? i / N : 0, pt = in ? i - b * N : 0;
+    const long base = (b * MLP_C + HC * hh) * N + pt;
 #pragma unroll
-    for (int c = 0; c < MLP_C; ++c) x[c] = in ? v[(b * MLP_C + c) * N + pt] : 0.f;
+    for (int c = 0; c < HC; ++c) x[c] = in ? v[base + c * N] : 0.f;
   };
-  float x[MLP_C];
-  load_v(blockIdx.x, x);
+  float x[HC];
+  load(blockIdx.x, x);
   uint32_t ph = 0;
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
 #pragma unroll
-    for (int c = 0; c < MLP_C; c += 4) stage4<MLP_C>(Ahi, Alo, tid, c, x + c);
+    for (int c = 0; c < HC; c += 4) stage4<MLP_C>(Ahi, Alo, row, HC * hh + c, x + c);
     to_tensor_core();
     const uint32_t taddr = tmem_base;
     if (tid == 0) {
       mma3<MLP_C, PROJ_Q>(taddr, saddr(Ahi), saddr(Alo), saddr(Bhi), saddr(Blo));
       commit(mb);
     }
-    load_v(tile + gridDim.x, x);
+    load(tile + gridDim.x, x);
     if (!wait_products(mb, ph, taddr, err)) return;
     ph ^= 1u;
-    const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
+    const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
     float o[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) o[k] = sqb2[k];
+    for (int k = 0; k < 6; ++k) o[k] = hh == 0 ? sqb2[k] : 0.f;
 #pragma unroll 1
-    for (int q = 0; q < PROJ_Q / 16; ++q) {
+    for (int q = 0; q < HQ / 16; ++q) {
       float d[16];
-      tmem_ld16(trow + q * 16, d);
+      const int j0 = HQ * hh + 16 * q;
+      tmem_ld16(trow + j0, d);
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const int j = q * 16 + u;
+        const int j = j0 + u;
         const float g = gelu_f(d[u] + sq1[j]);
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = fmaf(sq2[k * PROJ_Q + j], g, o[k]);
       }
     }
-    const long i = tile * MT + tid;
-    if (i < total) {
+    if (hh == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) part[row][k] = o[k];
+    }
+    __syncthreads();
+    const long i = tile * MT + row;
+    if (hh == 0 && i < total) {
       const long b = i / N, pt = i - b * N;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) E[(b * 3 + c) * N + pt] = make_float2(o[2 * c], o[2 * c + 1]);
+      for (int c = 0; c < 3; ++c)
+        E[(b * 3 + c) * N + pt] = make_float2(o[2 * c] + part[row][2 * c], o[2 * c + 1] + part[row][2 * c + 1]);
     }
   }
   free_tmem(tmem_base);
@@ -335,11 +360,11 @@ int* g_mlp_err = nullptr;
 
 }  // namespace
 
-// 1 when the pointwise layers run on the tensor cores (C = 32, H = 64, Q = 128): with
-// PSFD_MLP_TC=1 in the environment; the CUDA-core kernels are the default
+// 1 when the pointwise layers run on the tensor cores (C = 32, H = 64, Q = 128; PSFD_MLP_TC=0
+// selects the CUDA-core kernels)
 bool fno_mlp_tc_enabled(int C, int H, int Q) {
   const char* e = getenv("PSFD_MLP_TC");
-  return C == MLP_C && H == MLP_H && Q == PROJ_Q && (e && e[0] == '1');
+  return C == MLP_C && H == MLP_H && Q == PROJ_Q && !(e && e[0] == '0');
 }
 
 static int mlp_err_ptr() {
@@ -369,7 +394,7 @@ int fno_mlp_tc(const float* vin, float* vout, const float* uxy, const float* uz,
   int rc = mlp_err_ptr();
   if (rc) return rc;
   const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 2);
-  k_mlp_tc<<<grid, MT, MLP_SMEM, s>>>(vin, vout, uxy, uz, W1, b1, W2, b2, N, B, outer_gelu ? 1 : 0, g_mlp_err);
+  k_mlp_tc<<<grid, NT2, MLP_SMEM, s>>>(vin, vout, uxy, uz, W1, b1, W2, b2, N, B, outer_gelu ? 1 : 0, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -378,8 +403,8 @@ int fno_proj_tc(const float* v, cf* E, const float* Q1, const float* qb1, const 
                 int B, cudaStream_t s) {
   int rc = mlp_err_ptr();
   if (rc) return rc;
-  const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 3);
-  k_proj_tc<<<grid, MT, PROJ_SMEM, s>>>(v, E, Q1, qb1, Q2, qb2, N, B, g_mlp_err);
+  const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 2);
+  k_proj_tc<<<grid, NT2, PROJ_SMEM, s>>>(v, E, Q1, qb1, Q2, qb2, N, B, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }

@@ -84,6 +84,7 @@ struct psfd_plan_s {
   // layered-background preconditioner (per-column TE/TM inverses, built by psfd_layered_build)
   cf* lay = nullptr;         // [ncols][5 nz^2]
   cf* lay_D = nullptr;       // [nz][nz] stretched axial derivative
+  cf* lay_DT = nullptr;      // [nz][nz] its transpose
   cf* lay_D2 = nullptr;      // [nz][nz]
   cf* lay_deps = nullptr;    // [nz] laterally averaged contrast
   int* lay_err = nullptr;

@@ -58,6 +58,7 @@ struct LayArgs {
   const float4* refl;   // (r_s, r_p) per mode
   const cf* kz0;        // upgoing k_z per mode
   const cf* D;          // [nz][nz] stretched axial derivative
+  const cf* DT;         // [nz][nz] its transpose (row k holds column k of D: coalesced over rows i)
   const cf* D2;         // [nz][nz] D * D
   const cf* deps;       // [nz] laterally averaged contrast
   const float* sb;      // [nz] loss sigma_b(z) of the PML backing (eps_bg = 1 + i sigma_b)
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
     k_lay_apply_schur(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
   if (all_done(a)) return;
   constexpr int G = LAY_GROUP, NT = schur_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
-  static_assert(NT >= NZ, "one thread per row in the D products");
+  static_assert(NT >= NZ && NT % NZ == 0, "whole groups of NZ threads in the D products");
   extern __shared__ cf sh[];
   cf* xs = sh;                                   // [2G][3][NZ][NR] (s, t, z) after rotation
   cf* ws = xs + 2 * G * 3 * NZ * NR;             // [2G][NZ][NR]   w
@@ -594,31 +595,35 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
     xs[((v * 3 + 2) * NZ + z) * NR + r] = ez;
   }
   __syncthreads();
-  // w = u_t - i kappa D (Dg^-1 u_z): thread i < NZ owns output row i of every vector
-  if (tid < NZ) {
-    const int i = tid;
-    cf acc[2 * G][NR];
+  // w = u_t - i kappa D (Dg^-1 u_z): thread (group q, row i) owns output row i of the vectors
+  // v = q, q + NG, ... (NG = NT / NZ groups share the virtual columns)
+  constexpr int NG = NT / NZ, VPG = (2 * G + NG - 1) / NG;
+  const int grp = tid / NZ, irow = tid - (tid / NZ) * NZ;
+  if (grp < NG) {
+    cf acc[VPG][NR];
 #pragma unroll
-    for (int v = 0; v < 2 * G; ++v)
+    for (int u = 0; u < VPG; ++u)
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc[v][r] = czero();
+      for (int r = 0; r < NR; ++r) acc[u][r] = czero();
     for (int k = 0; k < NZ; ++k) {
-      const cf d = __ldg(a.D + (long)i * NZ + k);
+      const cf d = __ldg(a.DT + (long)k * NZ + irow);
 #pragma unroll
-      for (int v = 0; v < 2 * G; ++v) {
+      for (int u = 0; u < VPG; ++u) {
+        const int v = grp + NG * u;
         if (v >= nv) continue;
         const cf dg = cmul(d, gs[(v % G) * NZ + k]);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[v][r] = cfma(dg, xs[((v * 3 + 2) * NZ + k) * NR + r], acc[v][r]);
+        for (int r = 0; r < NR; ++r) acc[u][r] = cfma(dg, xs[((v * 3 + 2) * NZ + k) * NR + r], acc[u][r]);
       }
     }
 #pragma unroll
-    for (int v = 0; v < 2 * G; ++v) {
+    for (int u = 0; u < VPG; ++u) {
+      const int v = grp + NG * u;
       if (v >= nv) continue;
       const cf mik = make_float2(0.f, -kapv[v % G]);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
-        ws[(v * NZ + i) * NR + r] = cfma(mik, acc[v][r], xs[((v * 3 + 1) * NZ + i) * NR + r]);
+        ws[(v * NZ + irow) * NR + r] = cfma(mik, acc[u][r], xs[((v * 3 + 1) * NZ + irow) * NR + r]);
     }
   }
   __syncthreads();
@@ -685,45 +690,47 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
       }
   }
   __syncthreads();
-  // y_z = Dg^-1 (u_z - i kappa D y_t - c y_t(z_ml)): thread i < NZ owns row i
-  cf acc[2 * G][NR];
+  // y_z = Dg^-1 (u_z - i kappa D y_t - c y_t(z_ml)): thread (group q, row i) as above
+  cf acc[VPG][NR];
 #pragma unroll
-  for (int v = 0; v < 2 * G; ++v)
+  for (int u = 0; u < VPG; ++u)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[v][r] = czero();
-  if (tid < NZ) {
-    const int i = tid;
+    for (int r = 0; r < NR; ++r) acc[u][r] = czero();
+  if (grp < NG) {
     for (int k = 0; k < NZ; ++k) {
-      const cf d = __ldg(a.D + (long)i * NZ + k);
+      const cf d = __ldg(a.DT + (long)k * NZ + irow);
 #pragma unroll
-      for (int v = 0; v < 2 * G; ++v) {
+      for (int u = 0; u < VPG; ++u) {
+        const int v = grp + NG * u;
         if (v >= nv) continue;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[v][r] = cfma(d, xs[((v * 3 + 1) * NZ + k) * NR + r], acc[v][r]);
+        for (int r = 0; r < NR; ++r) acc[u][r] = cfma(d, xs[((v * 3 + 1) * NZ + k) * NR + r], acc[u][r]);
       }
     }
 #pragma unroll
-    for (int v = 0; v < 2 * G; ++v) {
+    for (int u = 0; u < VPG; ++u) {
+      const int v = grp + NG * u;
       if (v >= nv) continue;
       const int g = v % G;
       const cf mik = make_float2(0.f, -kapv[g]);
-      const cf gi = gs[g * NZ + i], ci = cs[g * NZ + i];
+      const cf gi = gs[g * NZ + irow], ci = cs[g * NZ + irow];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const cf ytm = xs[((v * 3 + 1) * NZ + a.zml) * NR + r];
-        cf t = cfma(mik, acc[v][r], xs[((v * 3 + 2) * NZ + i) * NR + r]);
+        cf t = cfma(mik, acc[u][r], xs[((v * 3 + 2) * NZ + irow) * NR + r]);
         t = csub(t, cmul(ci, ytm));
-        acc[v][r] = cmul(gi, t);
+        acc[u][r] = cmul(gi, t);
       }
     }
   }
   __syncthreads();   // every row's reads of u_z and y_t are done
-  if (tid < NZ) {
+  if (grp < NG) {
 #pragma unroll
-    for (int v = 0; v < 2 * G; ++v) {
+    for (int u = 0; u < VPG; ++u) {
+      const int v = grp + NG * u;
       if (v >= nv) continue;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) xs[((v * 3 + 2) * NZ + tid) * NR + r] = acc[v][r];
+      for (int r = 0; r < NR; ++r) xs[((v * 3 + 2) * NZ + irow) * NR + r] = acc[u][r];
     }
   }
   __syncthreads();
@@ -1151,7 +1158,7 @@ bool vector_box_map(const psfd_plan_s* P, int nz, int nrhs, const void* base, CU
 LayArgs lay_args(psfd_plan_s* P) {
   LayArgs a{};
   a.kx = P->kx; a.ky = P->ky; a.refl = P->R.refl; a.kz0 = P->R.kz0;
-  a.D = P->lay_D; a.D2 = P->lay_D2; a.deps = P->lay_deps;
+  a.D = P->lay_D; a.DT = P->lay_DT; a.D2 = P->lay_D2; a.deps = P->lay_deps;
   a.k0sq = (float)(P->k0 * P->k0); a.dz = (float)P->p.dz; a.sb = P->sback;
   a.nx = P->nx; a.ny = P->ny; a.nz = P->nz; a.zml = P->p.z_ml;
   a.pair = layered_pairs(P) ? 1 : 0;
@@ -1314,10 +1321,12 @@ int layered_apply(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
 }
 
 void layered_free(psfd_plan_s* P) {
-  void* ptrs[] = {P->lay, P->lay_D, P->lay_D2, P->lay_deps, P->lay_err, P->lay_fmean, P->lay16, P->lay_scale};
+  void* ptrs[] = {P->lay, P->lay_D, P->lay_DT, P->lay_D2, P->lay_deps, P->lay_err, P->lay_fmean, P->lay16,
+                  P->lay_scale};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  P->lay = nullptr; P->lay_D = nullptr; P->lay_D2 = nullptr; P->lay_deps = nullptr; P->lay_err = nullptr;
+  P->lay = nullptr; P->lay_D = nullptr; P->lay_DT = nullptr; P->lay_D2 = nullptr; P->lay_deps = nullptr;
+  P->lay_err = nullptr;
   P->lay_fmean = nullptr; P->lay16 = nullptr; P->lay_scale = nullptr;
   P->lay_built = false;
   P->lay_mean.clear();
@@ -1385,6 +1394,7 @@ extern "C" int psfd_layered_build(psfd_plan P) {
   }
   if (!P->lay_D) {
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D, (size_t)nz * nz * sizeof(cf)));
+    PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_DT, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_D2, (size_t)nz * nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_deps, (size_t)nz * sizeof(cf)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&P->lay_err, 2 * sizeof(int)));   // [0] singular pivot, [1] apply wait
@@ -1410,12 +1420,15 @@ extern "C" int psfd_layered_build(psfd_plan P) {
         const zc dik = D[(size_t)i * nz + k];
         for (int j = 0; j < nz; ++j) D2[(size_t)i * nz + j] += dik * D[(size_t)k * nz + j];
       }
-    std::vector<cf> hD((size_t)nz * nz), hD2((size_t)nz * nz);
+    std::vector<cf> hD((size_t)nz * nz), hDT((size_t)nz * nz), hD2((size_t)nz * nz);
     for (size_t e = 0; e < hD.size(); ++e) {
       hD[e] = make_float2((float)D[e].real(), (float)D[e].imag());
       hD2[e] = make_float2((float)D2[e].real(), (float)D2[e].imag());
     }
+    for (int i = 0; i < nz; ++i)
+      for (int k = 0; k < nz; ++k) hDT[(size_t)k * nz + i] = hD[(size_t)i * nz + k];
     PSFD_CUDA_TRY(cudaMemcpy(P->lay_D, hD.data(), hD.size() * sizeof(cf), cudaMemcpyHostToDevice));
+    PSFD_CUDA_TRY(cudaMemcpy(P->lay_DT, hDT.data(), hDT.size() * sizeof(cf), cudaMemcpyHostToDevice));
     PSFD_CUDA_TRY(cudaMemcpy(P->lay_D2, hD2.data(), hD2.size() * sizeof(cf), cudaMemcpyHostToDevice));
   }
   std::vector<double> mean;
