@@ -395,7 +395,9 @@ int axial_candidates(int nz, int* out) {
 }
 
 // ======================================================================= lateral passes
-// Rows (x axis, contiguous): lane = p*T + t, P = 32/T rows per warp.
+// Rows (x axis, contiguous): lane = p*T + t, P = 32/T rows per warp.  The lateral passes
+// exchange through shared-memory tiles (measured faster than shuffles here; the axial kernel
+// keeps shuffles, whose shared memory already limits its occupancy).
 enum { ROW_FWD = 0, ROW_INV = 1, ROW_FWD_SUB = 2 };
 
 struct RowArgs {
@@ -414,9 +416,11 @@ template <int NX, int T, int OP>
 __global__ void __launch_bounds__(128) k_rows(RowArgs a) {
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
+  __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane / T, t = lane - p * T;
   const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
+  cf* const xt = xch[warp];
   bool act = row < a.nrows;
   if (act && a.done && a.done[row / a.rows_per_rhs]) act = false;
   cf* __restrict__ src = a.buf + (act ? row : 0) * NX;
@@ -424,14 +428,14 @@ __global__ void __launch_bounds__(128) k_rows(RowArgs a) {
   if constexpr (OP == ROW_INV) {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = act ? src[PX::freq_index(t, s)] : czero();
-    PX::template to_time<true>(v, t, a.tw);
+    PX::template to_time<true>(v, t, a.tw, xt);
 #pragma unroll
     for (int m = 0; m < R; ++m)
       if (act) src[t + T * m] = cscale(v[m], a.scale);
   } else if constexpr (OP == ROW_FWD) {
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : czero();
-    PX::template to_freq<false>(v, t, a.tw);
+    PX::template to_freq<false>(v, t, a.tw, xt);
 #pragma unroll
     for (int s = 0; s < R; ++s)
       if (act) src[PX::freq_index(t, s)] = cscale(v[s], a.scale);
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(128) k_rows(RowArgs a) {
     for (int m = 0; m < R; ++m) v[m] = act ? src[t + T * m] : czero();
 #pragma unroll
     for (int s = 0; s < R; ++s) o[s] = act ? dst[PX::freq_index(t, s)] : czero();
-    PX::template to_freq<false>(v, t, a.tw);
+    PX::template to_freq<false>(v, t, a.tw, xt);
 #pragma unroll
     for (int s = 0; s < R; ++s)
       if (act) dst[PX::freq_index(t, s)] = make_float2(fmaf(-a.scale, v[s].x, o[s].x), fmaf(-a.scale, v[s].y, o[s].y));
@@ -482,8 +486,10 @@ template <int NY, int T, int OP>
 __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
+  __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane / P, p = lane - t * P;
+  cf* const xt = xch[warp];
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   bool act = colid < a.ncolumns;
   const long cid = act ? colid : 0;
@@ -496,14 +502,14 @@ __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
   if constexpr (OP == COL_FWD) {
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : czero();
-    PY::template to_freq<false>(v, t, a.tw);
+    PY::template to_freq<false>(v, t, a.tw, xt);
 #pragma unroll
     for (int s = 0; s < R; ++s)
       if (act) base[(long)PY::freq_index(t, s) * sx] = cscale(v[s], a.scale);
   } else if constexpr (OP == COL_INV) {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = act ? base[(long)PY::freq_index(t, s) * sx] : czero();
-    PY::template to_time<true>(v, t, a.tw);
+    PY::template to_time<true>(v, t, a.tw, xt);
 #pragma unroll
     for (int m = 0; m < R; ++m)
       if (act) base[(long)(t + T * m) * sx] = cscale(v[m], a.scale);
@@ -518,10 +524,10 @@ __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
     float fv[R];   // the fill is loaded with the column, so that both latencies overlap
 #pragma unroll
     for (int m = 0; m < R; ++m) fv[m] = act ? __ldg(f + (long)(t + T * m) * sx) : 0.f;
-    PY::template to_time<true>(v, t, a.tw);
+    PY::template to_time<true>(v, t, a.tw, xt);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = cmul(v[m], make_float2(dre * fv[m], dim * fv[m]));
-    PY::template to_freq<false>(v, t, a.tw);
+    PY::template to_freq<false>(v, t, a.tw, xt);
 #pragma unroll
     for (int s = 0; s < R; ++s)
       if (act) base[(long)PY::freq_index(t, s) * sx] = v[s];
@@ -530,14 +536,14 @@ __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
     const float kxp = 6.283185307179586f * (float)fft_signed(ix, a.nx) / (float)a.nx;
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = act ? base[(long)(t + T * m) * sx] : czero();
-    PY::template to_freq<false>(v, t, a.tw);
+    PY::template to_freq<false>(v, t, a.tw, xt);
 #pragma unroll
     for (int s = 0; s < R; ++s) {
       const float kyp = 6.283185307179586f * (float)fft_signed(PY::freq_index(t, s), NY) / (float)NY;
       const float g = expf(-0.5f * a.sigma * a.sigma * (kxp * kxp + kyp * kyp));
       v[s] = cscale(v[s], g);
     }
-    PY::template to_time<true>(v, t, a.tw);
+    PY::template to_time<true>(v, t, a.tw, xt);
 #pragma unroll
     for (int m = 0; m < R; ++m)
       if (act) base[(long)(t + T * m) * sx] = v[m];

@@ -5,7 +5,8 @@
 //   time layout:  lane t, slot m      holds x[t + T*m]            (m < R)
 //   freq layout:  lane t, slot k2*B+i holds X[t*B + i + R*k2]      (B = R/T)
 // to_freq() maps time -> freq layout (four-step: R-point DFT in registers,
-// twiddle w_N^(t*k1), all-to-all through warp shuffles, T-point DFTs);
+// twiddle w_N^(t*k1), all-to-all through warp shuffles or a shared-memory tile,
+// T-point DFTs);
 // to_time() is the mirror image.  Either may use the forward (e^-) or the
 // inverse (e^+) sign; transforms are unnormalised.
 #pragma once
@@ -123,6 +124,32 @@ struct Pencil {
     });
   }
 
+  // The same all-to-all through a per-warp shared-memory tile of TILE elements (kernels that
+  // can spare the shared memory use it: 2R stores and 2R loads per lane instead of
+  // B T/2 log2(T) shuffle pairs with their selects).  Lane (t, p) stores its slot (x, i) at
+  // tile[(i T + x) XS + lane] and loads slot (s, i) from the entry that lane (s, p) stored for
+  // it, tile[(i T + t) XS + lane + (s - t) LS].  With XS = 32 + 1 (LS = 1) or 32 + LS both
+  // phases touch 16 distinct 8-byte bank pairs per half warp (and 8 distinct 16-byte ones per
+  // quarter warp).
+  static constexpr int XS = 32 + (LS == 1 ? 1 : LS);
+  static constexpr int TILE = (T > 1) ? R * XS : 1;
+  static __device__ __forceinline__ void all2all_smem(C* v, int t, C* tile) {
+    static_assert(LS == 1 || LS * T == 32, "pencil lanes are consecutive or 32/T apart");
+    const int lane = threadIdx.x & 31;
+    __syncwarp();   // the previous exchange through this tile has been read by every lane
+    C* w = tile + lane;
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+      for (int x = 0; x < T; ++x) w[(i * T + x) * XS] = v[x * B + i];
+    __syncwarp();
+    const C* r = tile + t * XS + lane - t * LS;
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+      for (int s = 0; s < T; ++s) v[s * B + i] = r[i * T * XS + s * LS];
+  }
+
   template <bool INV>
   static __device__ __forceinline__ void twiddle(C* v, int t, const C* __restrict__ tw) {
     if constexpr (T > 1) {
@@ -135,13 +162,14 @@ struct Pencil {
     }
   }
 
-  // time layout -> freq layout
-  template <bool INV>
-  static __device__ __forceinline__ void to_freq(C* v, int t, const C* __restrict__ tw) {
+  // time layout -> freq layout; SM: exchange through this warp's tile (all2all_smem), else shuffles
+  template <bool INV, bool SM>
+  static __device__ __forceinline__ void to_freq_impl(C* v, int t, const C* __restrict__ tw, C* tile) {
     DFT<R, INV, C>::run(v);
     if constexpr (T > 1) {
       twiddle<INV>(v, t, tw);
-      all2all(v, t);
+      if constexpr (SM) all2all_smem(v, t, tile);
+      else all2all(v, t);
 #pragma unroll
       for (int i = 0; i < B; ++i) {
         C u[T];
@@ -155,8 +183,8 @@ struct Pencil {
   }
 
   // freq layout -> time layout
-  template <bool INV>
-  static __device__ __forceinline__ void to_time(C* v, int t, const C* __restrict__ tw) {
+  template <bool INV, bool SM>
+  static __device__ __forceinline__ void to_time_impl(C* v, int t, const C* __restrict__ tw, C* tile) {
     if constexpr (T > 1) {
 #pragma unroll
       for (int i = 0; i < B; ++i) {
@@ -167,10 +195,28 @@ struct Pencil {
 #pragma unroll
         for (int x = 0; x < T; ++x) v[x * B + i] = u[x];
       }
-      all2all(v, t);
+      if constexpr (SM) all2all_smem(v, t, tile);
+      else all2all(v, t);
       twiddle<INV>(v, t, tw);
     }
     DFT<R, INV, C>::run(v);
+  }
+
+  template <bool INV>
+  static __device__ __forceinline__ void to_freq(C* v, int t, const C* __restrict__ tw) {
+    to_freq_impl<INV, false>(v, t, tw, nullptr);
+  }
+  template <bool INV>
+  static __device__ __forceinline__ void to_freq(C* v, int t, const C* __restrict__ tw, C* tile) {
+    to_freq_impl<INV, true>(v, t, tw, tile);
+  }
+  template <bool INV>
+  static __device__ __forceinline__ void to_time(C* v, int t, const C* __restrict__ tw) {
+    to_time_impl<INV, false>(v, t, tw, nullptr);
+  }
+  template <bool INV>
+  static __device__ __forceinline__ void to_time(C* v, int t, const C* __restrict__ tw, C* tile) {
+    to_time_impl<INV, true>(v, t, tw, tile);
   }
 
   // index helpers

@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(128) k_xfwd(const float* __restrict__ v, cf* _
                                               const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
+  __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int p = lane / T, t = lane - p * T;
   const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const bool act = row < nrows;
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(128) k_xfwd(const float* __restrict__ v, cf* _
   cf w[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) w[m] = make_float2(act ? src[t + T * m] : 0.f, 0.f);
-  PX::template to_freq<false>(w, t, tw);
+  PX::template to_freq<false>(w, t, tw, xt);
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     const int j = fft_to_kept(PX::freq_index(t, s), mx, NX);
@@ -70,7 +72,9 @@ __global__ void __launch_bounds__(128) k_yfwd(const cf* __restrict__ T1, cf* __r
                                               const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
+  __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int t = lane / P, p = lane - t * P;
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const long ncol = (long)d.B * d.C * d.nz * d.mx;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(128) k_yfwd(const cf* __restrict__ T1, cf* __r
   cf w[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) w[m] = act ? base[(long)(t + T * m) * d.mx] : czero();
-  PY::template to_freq<false>(w, t, tw);
+  PY::template to_freq<false>(w, t, tw, xt);
   const int z = (int)(plane % d.nz);
   const long bc = plane / d.nz;
   const int c = (int)(bc % d.C);
@@ -206,7 +210,9 @@ __global__ void __launch_bounds__(128) k_yinv(const cf* __restrict__ U, cf* __re
                                               const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
+  __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int t = lane / P, p = lane - t * P;
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const long ncol = (long)d.B * d.C * d.nz * d.mx;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(128) k_yinv(const cf* __restrict__ U, cf* __re
     const int jy = fft_to_kept(PY::freq_index(t, s), d.my, NY);
     w[s] = (act && jy >= 0) ? U[(((long)jy * d.mx + kx) * d.C + c) * NB + n] : czero();
   }
-  PY::template to_time<true>(w, t, tw);
+  PY::template to_time<true>(w, t, tw, xt);
   cf* base = T2 + plane * (long)NY * d.mx + kx;
 #pragma unroll
   for (int m = 0; m < R; ++m)
@@ -238,7 +244,9 @@ __global__ void __launch_bounds__(128) k_xinv(const cf* __restrict__ T2, float* 
                                               float scale, const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
+  __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int p = lane / T, t = lane - p * T;
   const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const bool act = row < nrows;
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(128) k_xinv(const cf* __restrict__ T2, float* 
     const int j = fft_to_kept(PX::freq_index(t, s), mx, NX);
     w[s] = (act && j >= 0) ? T2[r * mx + j] : czero();
   }
-  PX::template to_time<true>(w, t, tw);
+  PX::template to_time<true>(w, t, tw, xt);
 #pragma unroll
   for (int m = 0; m < R; ++m)
     if (act) out[r * NX + t + T * m] = w[m].x * scale;
@@ -262,7 +270,9 @@ __global__ void __launch_bounds__(128) k_zfwd(const float* __restrict__ u, cf* _
                                               const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NZ / T;
   using PZ = Pencil<NZ, T, P>;
+  __shared__ cf xch[4][PZ::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int t = lane / P, p = lane - t * P;
   const long nxy = (long)d.nx * d.ny;
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(128) k_zfwd(const float* __restrict__ u, cf* _
   cf w[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) w[m] = make_float2(act ? base[(long)(t + T * m) * nxy] : 0.f, 0.f);
-  PZ::template to_freq<false>(w, t, tw);
+  PZ::template to_freq<false>(w, t, tw, xt);
   const long NB = (long)d.B * nxy, n = b * nxy + yx;
 #pragma unroll
   for (int s = 0; s < R; ++s) {
@@ -290,7 +300,9 @@ __global__ void __launch_bounds__(128) k_zinv(const cf* __restrict__ U, float* _
                                               const cf* __restrict__ tw) {
   constexpr int P = 32 / T, R = NZ / T;
   using PZ = Pencil<NZ, T, P>;
+  __shared__ cf xch[4][PZ::TILE];   // per-warp exchange tiles (4 warps per block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cf* const xt = xch[warp];
   const int t = lane / P, p = lane - t * P;
   const long nxy = (long)d.nx * d.ny;
   const long colid = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(128) k_zinv(const cf* __restrict__ U, float* _
     const int jz = fft_to_kept(PZ::freq_index(t, s), d.mz, NZ);
     w[s] = (act && jz >= 0) ? U[((long)jz * d.C + c) * NB + n] : czero();
   }
-  PZ::template to_time<true>(w, t, tw);
+  PZ::template to_time<true>(w, t, tw, xt);
   float* base = out + bc * NZ * nxy + yx;
 #pragma unroll
   for (int m = 0; m < R; ++m)
