@@ -183,15 +183,32 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   if constexpr (OP == OK_S || OP == OK_XR) alp = zf(S->alpha);
   if constexpr (OP == OK_XR) omg = zf(S->omega);
 
-  // two independent elements per iteration (separate accumulators) for memory-level parallelism
+  // Batches of kU elements per thread: every load of a batch is issued before the first use,
+  // so that kU x (vectors read) float4 loads are in flight; even and odd batch slots feed two
+  // accumulator sets (shorter dependence chains in the compensated sums).
   Acc2 accB[kMaxQ];
 #pragma unroll
   for (int q = 0; q < kMaxQ; ++q) accB[q] = {0.f, 0.f, 0.f};
-  auto body = [&](long i, Acc2* A) {
-    const long e = off / 2 + i;
+  constexpr int NIN = (OP == OK_XR) ? 5 : (OP == OK_P) ? 3 : (OP == OK_INIT || OP == OK_NORM) ? 1 : 2;
+  constexpr int kU = (NIN >= 3) ? 2 : 4;
+  auto ld4 = [&](const cf* v, long e) { return __ldg(reinterpret_cast<const float4*>(v) + e); };
+  auto load = [&](long e, float4 (&L)[5]) {
+    if constexpr (OP == OK_INIT || OP == OK_NORM) {
+      L[0] = ld4(a.v0, e);
+    } else if constexpr (OP == OK_P) {          // p, r, v
+      L[0] = ld4(a.v0, e); L[1] = ld4(a.v1, e); L[2] = ld4(a.v2, e);
+    } else if constexpr (OP == OK_S) {          // r, v
+      L[1] = ld4(a.v1, e); L[2] = ld4(a.v2, e);
+    } else if constexpr (OP == OK_XR) {         // y, p, s, t, rhat
+      L[0] = ld4(a.v0, e); L[1] = ld4(a.v2, e); L[2] = ld4(a.v3, e); L[3] = ld4(a.v4, e); L[4] = ld4(a.v5, e);
+    } else {                                    // RV, TS, SUB, AXPY: v0, v1
+      L[0] = ld4(a.v0, e); L[1] = ld4(a.v1, e);
+    }
+  };
+  auto body = [&](long e, const float4 (&L)[5], Acc2* A) {
     if constexpr (OP == OK_INIT) {
       // v0 = r, v1 = rhat, v2 = p, v3 = v, v4 = y
-      const float4 r = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 r = L[0];
       reinterpret_cast<float4*>(a.v1)[e] = r;
       const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
       reinterpret_cast<float4*>(a.v2)[e] = z;
@@ -201,9 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       acc_cdot(A[0], A[1], make_float2(r.z, r.w), make_float2(r.z, r.w));
     } else if constexpr (OP == OK_P) {
       // v0 = p (in/out), v1 = r, v2 = v
-      const float4 pp = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 rr = reinterpret_cast<const float4*>(a.v1)[e];
-      const float4 vv = reinterpret_cast<const float4*>(a.v2)[e];
+      const float4 pp = L[0], rr = L[1], vv = L[2];
       cf p0 = make_float2(pp.x, pp.y), p1 = make_float2(pp.z, pp.w);
       cf t0 = csub(p0, cmul(omg, make_float2(vv.x, vv.y)));
       cf t1 = csub(p1, cmul(omg, make_float2(vv.z, vv.w)));
@@ -212,21 +227,18 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       reinterpret_cast<float4*>(a.v0)[e] = make_float4(o0.x, o0.y, o1.x, o1.y);
     } else if constexpr (OP == OK_RV) {
       // v0 = rhat, v1 = v
-      const float4 h = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 v = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 h = L[0], v = L[1];
       acc_cdot(A[0], A[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
       acc_cdot(A[0], A[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
     } else if constexpr (OP == OK_S) {
       // v0 = s (out), v1 = r, v2 = v
-      const float4 rr = reinterpret_cast<const float4*>(a.v1)[e];
-      const float4 vv = reinterpret_cast<const float4*>(a.v2)[e];
+      const float4 rr = L[1], vv = L[2];
       cf s0 = csub(make_float2(rr.x, rr.y), cmul(alp, make_float2(vv.x, vv.y)));
       cf s1 = csub(make_float2(rr.z, rr.w), cmul(alp, make_float2(vv.z, vv.w)));
       reinterpret_cast<float4*>(a.v0)[e] = make_float4(s0.x, s0.y, s1.x, s1.y);
     } else if constexpr (OP == OK_TS) {
       // v0 = t, v1 = s
-      const float4 tt = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 ss = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 tt = L[0], ss = L[1];
       cf t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
       acc_cdot(A[0], A[1], t0, make_float2(ss.x, ss.y));
       acc_cdot(A[0], A[1], t1, make_float2(ss.z, ss.w));
@@ -234,11 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       acc_cdot(A[2], A[3], t1, t1);
     } else if constexpr (OP == OK_XR) {
       // v0 = y, v1 = r (out), v2 = p, v3 = s, v4 = t, v5 = rhat
-      const float4 yy = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 pp = reinterpret_cast<const float4*>(a.v2)[e];
-      const float4 ss = reinterpret_cast<const float4*>(a.v3)[e];
-      const float4 tt = reinterpret_cast<const float4*>(a.v4)[e];
-      const float4 hh = reinterpret_cast<const float4*>(a.v5)[e];
+      const float4 yy = L[0], pp = L[1], ss = L[2], tt = L[3], hh = L[4];
       cf s0 = make_float2(ss.x, ss.y), s1 = make_float2(ss.z, ss.w);
       cf y0 = cfma(alp, make_float2(pp.x, pp.y), make_float2(yy.x, yy.y));
       cf y1 = cfma(alp, make_float2(pp.z, pp.w), make_float2(yy.z, yy.w));
@@ -253,26 +261,29 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       acc_cdot(A[2], A[3], r0, r0);
       acc_cdot(A[2], A[3], r1, r1);
     } else if constexpr (OP == OK_NORM) {
-      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
+      const float4 x = L[0];
       acc_cdot(A[0], A[1], make_float2(x.x, x.y), make_float2(x.x, x.y));
       acc_cdot(A[0], A[1], make_float2(x.z, x.w), make_float2(x.z, x.w));
     } else if constexpr (OP == OK_SUB) {
       // v2 = v0 - v1
-      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 x = L[0], y = L[1];
       const float4 c = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
       reinterpret_cast<float4*>(a.v2)[e] = c;
       acc_cdot(A[0], A[1], make_float2(c.x, c.y), make_float2(c.x, c.y));
       acc_cdot(A[0], A[1], make_float2(c.z, c.w), make_float2(c.z, c.w));
     } else if constexpr (OP == OK_AXPY) {
-      const float4 x = reinterpret_cast<const float4*>(a.v0)[e];
-      const float4 y = reinterpret_cast<const float4*>(a.v1)[e];
+      const float4 x = L[0], y = L[1];
       reinterpret_cast<float4*>(a.v2)[e] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
     }
-    };
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
-    body(i, acc);
-    if (i + stride < n2) body(i + stride, accB);
+  };
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += kU * stride) {
+    float4 L[kU][5];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + u * stride < n2) load(off / 2 + i0 + u * stride, L[u]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + u * stride < n2) body(off / 2 + i0 + u * stride, L[u], (u & 1) ? accB : acc);
   }
 
   constexpr int NQ = (OP == OK_TS || OP == OK_XR) ? 4 : ((OP == OK_INIT || OP == OK_RV || OP == OK_NORM || OP == OK_SUB) ? 2 : 0);
@@ -418,16 +429,34 @@ __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
   const bool want_ww = a.save_norm && chunk == 0;
   const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
   const float4* w4 = reinterpret_cast<const float4*>(a.w);
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
-    const float4 wv = w4[off2 + i];
-    if (want_ww) ww = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, fmaf(wv.z, wv.z, fmaf(wv.w, wv.w, ww))));
+  // two elements per thread and pass, all (nq + 1) x 2 loads issued before the arithmetic
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    const bool two = i + stride < n2;
+    const float4 wv0 = __ldg(w4 + off2 + i);
+    const float4 wv1 = two ? __ldg(w4 + off2 + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v0[GCH], v1[GCH];
 #pragma unroll
     for (int q = 0; q < GCH; ++q) {
       if (q < nq) {
-        const float4 vv = reinterpret_cast<const float4*>(a.V + (i0 + q) * a.vs)[off2 + i];
-        // conj(v) * w for the two complex entries
-        sr[q] = fmaf(vv.x, wv.x, fmaf(vv.y, wv.y, fmaf(vv.z, wv.z, fmaf(vv.w, wv.w, sr[q]))));
-        si[q] = fmaf(vv.x, wv.y, fmaf(-vv.y, wv.x, fmaf(vv.z, wv.w, fmaf(-vv.w, wv.z, si[q]))));
+        const float4* vq = reinterpret_cast<const float4*>(a.V + (i0 + q) * a.vs) + off2;
+        v0[q] = __ldg(vq + i);
+        v1[q] = two ? __ldg(vq + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (want_ww) {
+      ww = fmaf(wv0.x, wv0.x, fmaf(wv0.y, wv0.y, fmaf(wv0.z, wv0.z, fmaf(wv0.w, wv0.w, ww))));
+      ww = fmaf(wv1.x, wv1.x, fmaf(wv1.y, wv1.y, fmaf(wv1.z, wv1.z, fmaf(wv1.w, wv1.w, ww))));
+    }
+#pragma unroll
+    for (int q = 0; q < GCH; ++q) {
+      if (q < nq) {
+        // conj(v) * w for the four complex entries
+        const float4 a0 = v0[q], b0 = v1[q];
+        sr[q] = fmaf(a0.x, wv0.x, fmaf(a0.y, wv0.y, fmaf(a0.z, wv0.z, fmaf(a0.w, wv0.w, sr[q]))));
+        si[q] = fmaf(a0.x, wv0.y, fmaf(-a0.y, wv0.x, fmaf(a0.z, wv0.w, fmaf(-a0.w, wv0.z, si[q]))));
+        sr[q] = fmaf(b0.x, wv1.x, fmaf(b0.y, wv1.y, fmaf(b0.z, wv1.z, fmaf(b0.w, wv1.w, sr[q]))));
+        si[q] = fmaf(b0.x, wv1.y, fmaf(-b0.y, wv1.x, fmaf(b0.z, wv1.w, fmaf(-b0.w, wv1.z, si[q]))));
       }
     }
   }
@@ -475,16 +504,47 @@ __global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
   const long n2 = a.n / 2, off2 = (long)rhs * a.n / 2;
   float4* t4 = reinterpret_cast<float4*>(ADD ? a.y : a.w);
   float ww = 0.f;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
-    float4 acc = t4[off2 + i];
-    cf a0 = make_float2(acc.x, acc.y), a1 = make_float2(acc.z, acc.w);
-    for (int q = 0; q < nv; ++q) {
-      const float4 vv = reinterpret_cast<const float4*>(a.V + q * a.vs)[off2 + i];
-      a0 = cfma(coef[q], make_float2(vv.x, vv.y), a0);
-      a1 = cfma(coef[q], make_float2(vv.z, vv.w), a1);
+  // two elements per thread and pass; the basis vectors in groups of four, loads first
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    const bool two = i + stride < n2;
+    const float4 acc0 = t4[off2 + i];
+    const float4 acc1 = two ? t4[off2 + i + stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+    cf a0 = make_float2(acc0.x, acc0.y), a1 = make_float2(acc0.z, acc0.w);
+    cf b0 = make_float2(acc1.x, acc1.y), b1 = make_float2(acc1.z, acc1.w);
+    int q = 0;
+    for (; q + 4 <= nv; q += 4) {
+      float4 u[4], v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4* vq = reinterpret_cast<const float4*>(a.V + (q + k) * a.vs) + off2;
+        u[k] = __ldg(vq + i);
+        v[k] = two ? __ldg(vq + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const cf c = coef[q + k];
+        a0 = cfma(c, make_float2(u[k].x, u[k].y), a0);
+        a1 = cfma(c, make_float2(u[k].z, u[k].w), a1);
+        b0 = cfma(c, make_float2(v[k].x, v[k].y), b0);
+        b1 = cfma(c, make_float2(v[k].z, v[k].w), b1);
+      }
+    }
+    for (; q < nv; ++q) {
+      const float4* vq = reinterpret_cast<const float4*>(a.V + q * a.vs) + off2;
+      const float4 u = __ldg(vq + i);
+      const float4 v = two ? __ldg(vq + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+      a0 = cfma(coef[q], make_float2(u.x, u.y), a0);
+      a1 = cfma(coef[q], make_float2(u.z, u.w), a1);
+      b0 = cfma(coef[q], make_float2(v.x, v.y), b0);
+      b1 = cfma(coef[q], make_float2(v.z, v.w), b1);
     }
     t4[off2 + i] = make_float4(a0.x, a0.y, a1.x, a1.y);
-    if (!ADD) ww = fmaf(a0.x, a0.x, fmaf(a0.y, a0.y, fmaf(a1.x, a1.x, fmaf(a1.y, a1.y, ww))));
+    if (two) t4[off2 + i + stride] = make_float4(b0.x, b0.y, b1.x, b1.y);
+    if (!ADD) {
+      ww = fmaf(a0.x, a0.x, fmaf(a0.y, a0.y, fmaf(a1.x, a1.x, fmaf(a1.y, a1.y, ww))));
+      ww = fmaf(b0.x, b0.x, fmaf(b0.y, b0.y, fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, ww))));
+    }
   }
   if constexpr (!ADD) {
     // ||w||^2 after the update (per-thread float partials, FP64 across threads)
