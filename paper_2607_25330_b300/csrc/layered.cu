@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
     const float sx = rot[v][0], sy = rot[v][1], tx = rot[v][2], ty = rot[v][3];
     xs[((v * 3 + 0) * NZ + z) * NR + r] = cadd(cscale(ex, sx), cscale(ey, sy));
     xs[((v * 3 + 1) * NZ + z) * NR + r] = cadd(cscale(ex, tx), cscale(ey, ty));
-    xs[((v * 3 + 2) * NZ + z) * NR + r] = ez;
+    xs[((v * 3 + 2) * NZ + z) * NR + r] = cmul(gs[(v % G) * NZ + z], ez);   // Dg^-1 u_z
   }
   __syncthreads();
   // w = u_t - i kappa D (Dg^-1 u_z): thread (group q, row i) owns output row i of the vectors
@@ -605,15 +605,15 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
     for (int u = 0; u < VPG; ++u)
 #pragma unroll
       for (int r = 0; r < NR; ++r) acc[u][r] = czero();
+#pragma unroll 8
     for (int k = 0; k < NZ; ++k) {
       const cf d = __ldg(a.DT + (long)k * NZ + irow);
 #pragma unroll
       for (int u = 0; u < VPG; ++u) {
         const int v = grp + NG * u;
         if (v >= nv) continue;
-        const cf dg = cmul(d, gs[(v % G) * NZ + k]);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[u][r] = cfma(dg, xs[((v * 3 + 2) * NZ + k) * NR + r], acc[u][r]);
+        for (int r = 0; r < NR; ++r) acc[u][r] = cfma(d, xs[((v * 3 + 2) * NZ + k) * NR + r], acc[u][r]);
       }
     }
 #pragma unroll
@@ -697,6 +697,7 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[u][r] = czero();
   if (grp < NG) {
+#pragma unroll 8
     for (int k = 0; k < NZ; ++k) {
       const cf d = __ldg(a.DT + (long)k * NZ + irow);
 #pragma unroll
@@ -716,10 +717,10 @@ __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
       const cf gi = gs[g * NZ + irow], ci = cs[g * NZ + irow];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
+        // y_z = Dg^-1 u_z + Dg^-1 (-i kappa D y_t - c y_t(z_ml)), the first term stored by the gather
         const cf ytm = xs[((v * 3 + 1) * NZ + a.zml) * NR + r];
-        cf t = cfma(mik, acc[u][r], xs[((v * 3 + 2) * NZ + irow) * NR + r]);
-        t = csub(t, cmul(ci, ytm));
-        acc[u][r] = cmul(gi, t);
+        const cf t = csub(cmul(mik, acc[u][r]), cmul(ci, ytm));
+        acc[u][r] = cfma(gi, t, xs[((v * 3 + 2) * NZ + irow) * NR + r]);
       }
     }
   }
