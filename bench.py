@@ -568,6 +568,11 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
                    "rhs_per_step": nrhs, "pols": ["TE", "TM"][:nrhs], "theta_deg": prob.theta_deg, "tol": TOL,
                    "preconditioner": pc_name,
+                   "preconditioner_setup": (f"per-mask refresh: blocks rebuilt only when a plane's mean fill moved by "
+                                            f"> {args.lay_shift} since the last build; {rebuilds_warm} rebuilds in the "
+                                            "timed warm steps (rebuilding for every mask: "
+                                            "layered_blocks.warm_with_rebuild_every_mask)")
+                                           if pc_main == psfd.PC_LAYERED else "none (M is a fixed multiplier)",
                    "solver": (f"{args.method}({args.restart})" if args.method == "gmres" else args.method) +
                              " in complex64 inside FP64 iterative refinement "
                              f"(FP64 residual and field, inner tol {args.inner_tol:g}), right preconditioning, "
@@ -637,7 +642,7 @@ def run_fine(args):
     shape = I.FNOShape()
     out = {"workload": "fine_512x512x128", "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
            "coarse_grid": [coarse.nx, coarse.ny, coarse.nz], "solver": "gmres(30), FP64 refinement (inner 1e-3)",
-           "preconditioner": "layered-background P, Schur form, half-precision blocks", "tol": TOL}
+           "preconditioner": "layered-background P, Schur form, complex64 blocks", "tol": TOL}
     models = []
     t0 = time.perf_counter()
     if args.train_warm_steps > 0:
