@@ -1004,19 +1004,26 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
+
+    def side_arm(key, fn):
+        """Run one of the other workloads after the headline; a failure is recorded in its key (with
+        the library's message) instead of losing the headline line."""
+        import torch
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        try:
+            out[key] = fn()
+        except Exception as e:   # noqa: BLE001 -- reported in the JSON line
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+            print(f"bench: {key} failed: {e}", file=sys.stderr, flush=True)
+
     if rank == 0 and not args.skip_batch:
-        import torch
-        torch.cuda.empty_cache()
-        out["batch"] = run_batch(args)
+        side_arm("batch", lambda: run_batch(args))
     if rank == 0 and not args.skip_fine:
-        import torch
-        torch.cuda.empty_cache()
-        out["fine_grid"] = run_fine(args)
+        side_arm("fine_grid", lambda: run_fine(args))
     if rank == 0 and not args.skip_train_step:
         # the differentiation workload: one physics-informed FNO training step (3 timed after 2)
-        import torch
-        torch.cuda.empty_cache()
-        out["train_step"] = run_train_step(args, steps=3, warmup=2)
+        side_arm("train_step", lambda: run_train_step(args, steps=3, warmup=2))
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args)

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -85,12 +86,14 @@ extern "C" int psfd_solve_batched(const psfd_plan* plans, int nplans, const psfd
   const int nw = std::max(1, std::min(nworkers > 0 ? nworkers : 8, nplans));
   std::atomic<int> next{0};
   std::vector<int> rcs(nplans, PSFD_OK);
+  std::vector<std::string> msgs(nplans);   // a worker's error text (the error string is per thread)
   auto worker = [&]() {
     cudaSetDevice(dev);
     for (;;) {
       const int i = next.fetch_add(1);
       if (i >= nplans) break;
       rcs[i] = psfd_solve_ex(plans[i], b[i], x0 ? x0[i] : nullptr, E[i], opts, info + off[i], nullptr, 0);
+      if (rcs[i] != PSFD_OK) msgs[i] = psfd_last_error();
     }
   };
   std::vector<std::thread> pool;
@@ -98,7 +101,10 @@ extern "C" int psfd_solve_batched(const psfd_plan* plans, int nplans, const psfd
   for (auto& t : pool) t.join();
   int worst = PSFD_OK;
   for (int i = 0; i < nplans; ++i) {
-    if (rcs[i] == PSFD_ERR_ARG || rcs[i] == PSFD_ERR_CUDA || rcs[i] == PSFD_ERR_STATE) return rcs[i];
+    if (rcs[i] == PSFD_ERR_ARG || rcs[i] == PSFD_ERR_CUDA || rcs[i] == PSFD_ERR_STATE) {
+      psfd_set_error("psfd_solve_batched: plan %d: %s", i, msgs[i].c_str());
+      return rcs[i];
+    }
     if (rcs[i] != PSFD_OK && worst == PSFD_OK) worst = rcs[i];
   }
   return worst;
