@@ -629,8 +629,9 @@ def run_ours(args, rank, world):
 
 def run_fine(args):
     """The fine-discretisation workload at full size: 512x512x128 (0.5 nm lateral pixels), TE + TM at
-    6 deg, a dense Manhattan layout; warm start from the FNO evaluated on the 128x128x32 grid of the
-    same box and spectrally upsampled (the network trained on that coarse grid by the physics loss),
+    6 deg, a dense Manhattan layout; warm start from the FNO evaluated on the 128x128x128 grid of the
+    same box and axial planes (2 nm lateral pixels) and spectrally upsampled in x and y (the network
+    trained on that coarse grid by the physics loss, on dense layouts of the same recipe),
     against the cold start; GMRES(30) in complex64 with FP64 orthogonalisation inside the FP64
     refinement, layered-background P (Schur form at nz = 128), to 1e-6.  Also the A apply's roofline
     at this size, where the vectors (0.8 GB per rhs) are far larger than L2."""
@@ -638,7 +639,7 @@ def run_fine(args):
     from paper_2607_25330_b300 import inputs as I
     from paper_2607_25330_b300 import psfd
     prob = I.preset("fine_512x512x128")
-    coarse = I.preset("fno_coarse_128x128x32")
+    coarse = I.preset("fno_coarse_128x128x128")
     shape = I.FNOShape()
     out = {"workload": "fine_512x512x128", "grid": [prob.nx, prob.ny, prob.nz], "pixels_nm": [prob.dx, prob.dy, prob.dz],
            "coarse_grid": [coarse.nx, coarse.ny, coarse.nz], "solver": "gmres(30), FP64 refinement (inner 1e-3)",
@@ -649,8 +650,8 @@ def run_fine(args):
         from paper_2607_25330_b300 import train as TR
         for pol in prob.pols:
             w, log = TR.train(max(1, args.train_warm_steps // 2), args.train_warm_batch, 3e-3, 32, 191 + pol,
-                              "fno_coarse_128x128x32", log_every=max(1, args.train_warm_steps // 4), pol=pol,
-                              mask_seed=70000, zero_output=True)
+                              "fno_coarse_128x128x128", log_every=max(1, args.train_warm_steps // 4), pol=pol,
+                              mask_seed=70000, zero_output=True, mask_kind="manhattan_dense")
             models.append(psfd.fno_struct({k: v.detach().contiguous() for k, v in w.items()}, shape))
         out["coarse_training"] = {"steps": max(1, args.train_warm_steps // 2), "seconds": time.perf_counter() - t0}
     else:

@@ -158,6 +158,11 @@ def preset(name: str) -> Problem:
         # one of the batched workload's (lateral size, depth) pairs: 60 nm absorber, 12 PML planes
         return Problem(nx=128, ny=128, nz=96, dx=2.0, dy=2.0, dz=2.0, theta_deg=6.0,
                        pml_planes=12, z_ml=12, abs_intervals=30.0, cap=True, pols=[TE, TM])
+    if name == "fno_coarse_128x128x128":
+        # coarse grid of the fine-discretisation warm start: the 512 case's box and axial planes
+        # (2 nm, a third of the 13.5 nm wavelength) with 4x coarser lateral pixels
+        return Problem(nx=128, ny=128, nz=128, dx=2.0, dy=2.0, dz=2.0, theta_deg=6.0,
+                       pml_planes=16, z_ml=16, abs_intervals=30.0, cap=True, pols=[TE, TM])
     if name == "fno_coarse_128x128x32":
         # coarse grid of the fine-discretisation warm start (same physical box as the 512 case)
         return Problem(nx=128, ny=128, nz=32, dx=2.0, dy=2.0, dz=8.0, theta_deg=6.0,

@@ -36,7 +36,8 @@ def _weights(seed: int, zero_output: bool = False) -> Dict[str, torch.Tensor]:
 
 
 def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, log_every: int = 10,
-          pol: int = None, mask_seed: int = 1000, zero_output: bool = False, w: Dict = None):
+          pol: int = None, mask_seed: int = 1000, zero_output: bool = False, w: Dict = None,
+          mask_kind: str = None):
     """Adam on the physics loss over `pool` seeded masks (a random batch of them per step); `pol`
     selects the illumination (one model per polarisation), default the preset's first; `w`
     continues from given parameters."""
@@ -47,7 +48,7 @@ def train(steps: int, batch: int, lr: float, pool: int, seed: int, preset: str, 
         w = _weights(seed, zero_output)
     trainer = psfd.FnoTrainer(psfd.fno_struct(w, S), batch, prob.nz, prob.ny, prob.nx, checkpoint=True)
     plans = [psfd.Plan(prob, nrhs=1) for _ in range(batch)]
-    masks = [torch.from_numpy(I.mask_for(prob, mask_seed + i)) for i in range(pool)]
+    masks = [torch.from_numpy(I.mask_for(prob, mask_seed + i, mask_kind)) for i in range(pool)]
     stack, zprof = prob.stack(), prob.zprofile()
     opt = torch.optim.Adam(list(w.values()), lr=lr)
     rng = np.random.default_rng(seed)
