@@ -49,6 +49,11 @@ __device__ __forceinline__ void acc_prod(Acc2& A, float a, float b) {
 __device__ __forceinline__ double acc_value(const Acc2& A) {
   return (double)A.s - (double)A.c + (double)A.e;
 }
+// |a|^2 into the running sum, uncompensated: a sum of positive terms has no cancellation, so the
+// per-thread FP32 partial (a few tens of terms) keeps about 1e-6 relative accuracy, ample for
+// omega's denominator and the convergence tests; the partials are summed in FP64
+__device__ __forceinline__ void acc_norm(Acc2& A, cf a) { A.s = fmaf(a.x, a.x, fmaf(a.y, a.y, A.s)); }
+
 // re/im of conj(a) * b
 __device__ __forceinline__ void acc_cdot(Acc2& re, Acc2& im, cf a, cf b) {
   acc_prod(re, a.x, b.x);
@@ -214,8 +219,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       reinterpret_cast<float4*>(a.v2)[e] = z;
       reinterpret_cast<float4*>(a.v3)[e] = z;
       reinterpret_cast<float4*>(a.v4)[e] = z;
-      acc_cdot(A[0], A[1], make_float2(r.x, r.y), make_float2(r.x, r.y));
-      acc_cdot(A[0], A[1], make_float2(r.z, r.w), make_float2(r.z, r.w));
+      acc_norm(A[0], make_float2(r.x, r.y));
+      acc_norm(A[0], make_float2(r.z, r.w));
     } else if constexpr (OP == OK_P) {
       // v0 = p (in/out), v1 = r, v2 = v
       const float4 pp = L[0], rr = L[1], vv = L[2];
@@ -242,8 +247,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       cf t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
       acc_cdot(A[0], A[1], t0, make_float2(ss.x, ss.y));
       acc_cdot(A[0], A[1], t1, make_float2(ss.z, ss.w));
-      acc_cdot(A[2], A[3], t0, t0);
-      acc_cdot(A[2], A[3], t1, t1);
+      acc_norm(A[2], t0);
+      acc_norm(A[2], t1);
     } else if constexpr (OP == OK_XR) {
       // v0 = y, v1 = r (out), v2 = p, v3 = s, v4 = t, v5 = rhat
       const float4 yy = L[0], pp = L[1], ss = L[2], tt = L[3], hh = L[4];
@@ -258,19 +263,19 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       reinterpret_cast<float4*>(a.v1)[e] = make_float4(r0.x, r0.y, r1.x, r1.y);
       acc_cdot(A[0], A[1], make_float2(hh.x, hh.y), r0);
       acc_cdot(A[0], A[1], make_float2(hh.z, hh.w), r1);
-      acc_cdot(A[2], A[3], r0, r0);
-      acc_cdot(A[2], A[3], r1, r1);
+      acc_norm(A[2], r0);
+      acc_norm(A[2], r1);
     } else if constexpr (OP == OK_NORM) {
       const float4 x = L[0];
-      acc_cdot(A[0], A[1], make_float2(x.x, x.y), make_float2(x.x, x.y));
-      acc_cdot(A[0], A[1], make_float2(x.z, x.w), make_float2(x.z, x.w));
+      acc_norm(A[0], make_float2(x.x, x.y));
+      acc_norm(A[0], make_float2(x.z, x.w));
     } else if constexpr (OP == OK_SUB) {
       // v2 = v0 - v1
       const float4 x = L[0], y = L[1];
       const float4 c = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
       reinterpret_cast<float4*>(a.v2)[e] = c;
-      acc_cdot(A[0], A[1], make_float2(c.x, c.y), make_float2(c.x, c.y));
-      acc_cdot(A[0], A[1], make_float2(c.z, c.w), make_float2(c.z, c.w));
+      acc_norm(A[0], make_float2(c.x, c.y));
+      acc_norm(A[0], make_float2(c.z, c.w));
     } else if constexpr (OP == OK_AXPY) {
       const float4 x = L[0], y = L[1];
       reinterpret_cast<float4*>(a.v2)[e] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
