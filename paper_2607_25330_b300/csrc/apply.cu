@@ -12,6 +12,7 @@
 // with q = M x (or x).  The contrast term is then added on the absorber planes
 // only by three lateral passes: IFFT_x (rows), IFFT_y * k0^2 deps / N * FFT_y
 // (columns), FFT_x with y -= result (rows).
+#include <mutex>
 #include <cstdio>
 
 #include "fft.cuh"
@@ -799,10 +800,14 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(PlaneArgs a) {
 template <int N, int TR, int TC>
 static int run_plane(psfd_plan_s* P, const PlaneArgs& a, long nplanes) {
   const size_t smem = sizeof(cf) * N * (N + kRowPad) + sizeof(float) * N * N + 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_plane<N, TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
+  static std::once_flag once;   // complete before any host thread launches
+  static cudaError_t init = cudaSuccess;
+  std::call_once(once, [smem] {
+    init = cudaFuncSetAttribute(k_plane<N, TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (init != cudaSuccess) {
+    psfd_set_error("plane contrast: %s", cudaGetErrorString(init));
+    return PSFD_ERR_CUDA;
   }
   k_plane<N, TR, TC><<<(unsigned)nplanes, kPlaneThreads, smem, P->stream>>>(a);
   PSFD_CHECK_LAUNCH();

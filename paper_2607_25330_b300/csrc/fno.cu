@@ -12,6 +12,7 @@
 //   pointwise MLP with residual (Eq. 4), GELU (erf form) inside and, except in
 //     the last layer, outside.
 // Lift: (a, x/nx, y/ny, z/nz) -> dv.  Projection: dv -> dq -> 6 (Re/Im of E).
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -870,13 +871,19 @@ static int upload_twiddles(const FnoWs& ws, int nx, int ny, int nz, cudaStream_t
 }
 
 static int set_smem_attrs() {
-  static bool done = false;
-  if (done) return PSFD_OK;
-  PSFD_CUDA_TRY(cudaFuncSetAttribute(k_mlp_bwd<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)mlp_bwd_smem<32, 64>()));
-  PSFD_CUDA_TRY(cudaFuncSetAttribute(k_proj_bwd<32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)proj_bwd_smem<32, 128>()));
-  done = true;
+  static std::once_flag once;   // complete before any host thread launches
+  static cudaError_t init = cudaSuccess;
+  std::call_once(once, [] {
+    init = cudaFuncSetAttribute(k_mlp_bwd<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mlp_bwd_smem<32, 64>());
+    if (init == cudaSuccess)
+      init = cudaFuncSetAttribute(k_proj_bwd<32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)proj_bwd_smem<32, 128>());
+  });
+  if (init != cudaSuccess) {
+    psfd_set_error("fno: shared-memory attributes: %s", cudaGetErrorString(init));
+    return PSFD_ERR_CUDA;
+  }
   return PSFD_OK;
 }
 

@@ -16,6 +16,7 @@
 // 16-byte core matrices, K-adjacent core matrices 128 B apart, 8-row groups (K bytes / 16) x 128 B
 // apart.  Every wait on the tensor core is bounded; on a timeout the kernel records it in the same
 // device flag as the mode mixing, waits once more, frees its tensor memory and returns.
+#include <mutex>
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -368,24 +369,33 @@ bool fno_mlp_tc_enabled(int C, int H, int Q) {
 }
 
 static int mlp_err_ptr() {
-  if (!g_mlp_err) {
-    PSFD_CUDA_TRY(cudaMalloc((void**)&g_mlp_err, sizeof(int)));
-    PSFD_CUDA_TRY(cudaMemset(g_mlp_err, 0, sizeof(int)));
-    PSFD_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM));
-    PSFD_CUDA_TRY(cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM));
+  // once per process, complete before any host thread launches
+  static std::once_flag once;
+  static cudaError_t init = cudaSuccess;
+  std::call_once(once, [] {
+    int* p = nullptr;
+    init = cudaMalloc((void**)&p, sizeof(int));
+    if (init == cudaSuccess) init = cudaMemset(p, 0, sizeof(int));
+    if (init == cudaSuccess) init = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
+    if (init == cudaSuccess) init = cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+    if (init == cudaSuccess) g_mlp_err = p;
+  });
+  if (init != cudaSuccess || !g_mlp_err) {
+    psfd_set_error("fno tensor-core layers: set-up: %s", cudaGetErrorString(init));
+    return PSFD_ERR_CUDA;
   }
   return PSFD_OK;
 }
 
 // persistent grid: CTAs per SM (shared memory bound) x SMs, at most one CTA per tile
 static unsigned persistent_grid(long ntiles, int per_sm) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 148;
-  }
+  static const int nsm = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+      n = 148;
+    return n;
+  }();
   return (unsigned)std::min<long>(ntiles, (long)nsm * per_sm);
 }
 

@@ -9,6 +9,7 @@
 // in tensor memory: tcgen05.mma kind::f16, M = 128, N = 2C = 64, four K = 16 steps, issued by
 // one thread; operands staged in shared memory in the canonical K-major layout without swizzle
 // (8-row x 16-byte core matrices: K-adjacent core matrices 128 B apart, 8-row groups 1024 B apart).
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -188,9 +189,17 @@ bool fno_mix_tc_enabled(int C) {
 
 int fno_mix_tc(const cf* V, cf* U, const cf* K, long NB, int modes, int mx, int MX, int offy, int offx,
                cudaStream_t s) {
-  if (!g_tc_err) {
-    PSFD_CUDA_TRY(cudaMalloc((void**)&g_tc_err, sizeof(int)));
-    PSFD_CUDA_TRY(cudaMemset(g_tc_err, 0, sizeof(int)));
+  static std::once_flag once;   // once per process, complete before any host thread launches
+  static cudaError_t init = cudaSuccess;
+  std::call_once(once, [] {
+    int* p = nullptr;
+    init = cudaMalloc((void**)&p, sizeof(int));
+    if (init == cudaSuccess) init = cudaMemset(p, 0, sizeof(int));
+    if (init == cudaSuccess) g_tc_err = p;
+  });
+  if (init != cudaSuccess || !g_tc_err) {
+    psfd_set_error("fno mixing: set-up: %s", cudaGetErrorString(init));
+    return PSFD_ERR_CUDA;
   }
   dim3 g((unsigned)((NB + TC_M - 1) / TC_M), (unsigned)modes);
   k_mix_tc<<<g, TC_THREADS, A_BYTES + B_BYTES, s>>>(V, U, K, NB, mx, MX, offy, offx, g_tc_err);

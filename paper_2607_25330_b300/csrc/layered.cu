@@ -29,6 +29,7 @@
 // M of Eq. spectral_damping_action (an addition to the paper's method: the damping alone leaves
 // restarted Krylov stalling near 1e-5 at oblique incidence, where near-grazing diffraction orders
 // are barely absorbed by the axial PML; the averaged operator resolves those modes exactly).
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -1136,15 +1137,14 @@ bool vector_box_map(const psfd_plan_s* P, int nz, int nrhs, const void* base, CU
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   static Encode enc = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;   // the batched solve calls this from several host threads
+  std::call_once(once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       enc = reinterpret_cast<Encode>(fn);
-  }
+  });
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const cuuint64_t e = sizeof(cf);
   const cuuint64_t dims[5] = {(cuuint64_t)P->nx, (cuuint64_t)P->ny, (cuuint64_t)nz, 3, (cuuint64_t)nrhs};
@@ -1220,13 +1220,22 @@ int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
       using C = PipeCfg<NZ, NR>;
       CUtensorMap tx, ty;
       if (vector_box_map(P, NZ, NR, x, &tx) && vector_box_map(P, NZ, NR, y, &ty)) {
+        // once per instantiation and process, complete before any thread launches (the batched
+        // solve applies P from several host threads)
+        static std::once_flag once;
         static int nsm = 0;
-        if (!nsm) {
+        static cudaError_t init = cudaSuccess;
+        std::call_once(once, [] {
           int dev = 0;
-          PSFD_CUDA_TRY(cudaGetDevice(&dev));
-          PSFD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-          PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_pipe<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM));
+          init = cudaGetDevice(&dev);
+          if (init == cudaSuccess) init = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+          if (init == cudaSuccess)
+            init = cudaFuncSetAttribute(k_lay_apply_pipe<NZ, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)C::SMEM);
+        });
+        if (init != cudaSuccess || nsm <= 0) {
+          psfd_set_error("layered apply: set-up of the tensor-core pipeline: %s", cudaGetErrorString(init));
+          return PSFD_ERR_CUDA;
         }
         const long npairs = layered_columns(P) / 2;
         const unsigned grid = (unsigned)std::min<long>(npairs, nsm);

@@ -86,3 +86,40 @@ def test_batched_layered_solves_reach_1e6():
     for r, pol in enumerate(prob.pols):
         bo = O.source_b(g, fill_o, pol)
         assert O.rel_residual(g, Es[4][r].cpu().to(torch.complex128), fill_o, bo) < 3e-6
+
+
+_FIRST_USE = r"""
+import sys, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2607_25330_b300 import inputs as I
+from paper_2607_25330_b300 import psfd
+from tests.helpers import problem
+plans, bs = [], []
+for k in range(8):
+    prob = problem(64, 64, 32, theta=4.0 + k % 3, pols=[0, 1])
+    pl = psfd.Plan(prob, stream=torch.cuda.Stream())
+    pl.layered_storage(True)
+    with torch.cuda.stream(pl.stream):
+        fill = pl.mask_fill(torch.from_numpy(I.mask_for(prob, 50 + k)).cuda(), prob.zprofile())
+        bs.append(pl.background(prob.stack(), fill, prob.pols))
+    pl.layered_build()
+    plans.append(pl)
+torch.cuda.synchronize()
+Es, infos = psfd.solve_batched(plans, bs, tol=1e-6, maxit=400, method=psfd.PSFD_BICGSTAB, precond=2,
+                               refine=True, inner_tol=1e-3, nworkers=8)
+assert all(i["status"] == 0 for inf in infos for i in inf), infos
+print("ok")
+"""
+
+
+def test_first_use_from_several_host_threads():
+    """A fresh process whose first applies of the layered P (the tensor-core pipeline, which needs a
+    shared-memory attribute set once) come from eight host threads at once: the one-time set-up
+    completes before any thread launches."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_USE, root], capture_output=True, text=True, timeout=600,
+                       cwd=root)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]

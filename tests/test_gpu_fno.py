@@ -26,7 +26,8 @@ def device_weights(w):
     return out
 
 
-@pytest.mark.parametrize("dims", [(2, 32, 32, 16), (1, 64, 32, 32), (2, 16, 16, 48), (1, 96, 64, 16)])
+@pytest.mark.parametrize("dims", [(2, 32, 32, 16), (1, 64, 32, 32), (2, 16, 16, 48), (1, 96, 64, 16),
+                                  (1, 32, 16, 64), (1, 16, 16, 96), (1, 32, 32, 128)])
 def test_fno_forward_matches_oracle(dims):
     from paper_2607_25330_b300 import psfd
     B, nx, ny, nz = dims
@@ -56,7 +57,8 @@ def test_fno_forward_128x128x48_training_shape():
     assert rel_l2(E.cpu(), ref) < TOL_FNO
 
 
-@pytest.mark.parametrize("shapes", [((16, 16, 16), (32, 64, 32)), ((32, 32, 16), (128, 128, 64))])
+@pytest.mark.parametrize("shapes", [((16, 16, 16), (32, 64, 32)), ((32, 32, 16), (128, 128, 64)),
+                                    ((128, 32, 32), (128, 128, 128))])
 def test_spectral_upsample_matches_oracle(shapes):
     from paper_2607_25330_b300 import psfd
     (nz0, ny0, nx0), (nz, ny, nx) = shapes
