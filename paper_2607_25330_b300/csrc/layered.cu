@@ -166,27 +166,30 @@ __device__ cf entry(const LayArgs& a, const Mode& m, int i, int j) {
   return czero();
 }
 
-// Assemble and invert one N x N block per CTA.  Thread (rg, cg) of the 16 x 16 grid owns rows
-// rg + 16 u and columns cg + 16 v (u, v < N/16).  Step k exchanges the roles of x_k and y_p for
+// Assemble and invert one N x N block per CTA.  Thread (rg, cg) of the RG x 16 grid owns rows
+// rg + RG u and columns cg + 16 v (u < N/RG, v < N/16).  Step k exchanges the roles of x_k and y_p for
 // the pivot row p (largest |T[p][k]| among rows not yet used):
 //     T[p][k] <- 1/π,  T[p][j] <- −T[p][j]/π,  T[i][k] <- T[i][k]/π,  T[i][j] <- T[i][j] − T[i][k] T[p][j]/π
 // with π = T[p][k].  After N steps, row p_k holds x_k and column k' holds y_{p_k'}:
 // Minv[k][p_k'] = T[p_k][k'].
-template <int N, bool TM, bool SCHUR = false>
-__global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_off) {
-  constexpr int TT = N / 16;
+template <int N, bool TM, bool SCHUR = false, int RG = 16>
+__global__ void __launch_bounds__(RG * 16) k_lay_inv(LayArgs a, int block_off) {
+  // thread grid RG x 16 over the N x N matrix: thread (rg, cg) owns rows rg + RG u and columns
+  // cg + 16 v, a TU x TV complex tile in registers
+  constexpr int NTH = RG * 16, TU = N / RG, TV = N / 16;
+  static_assert(TU * RG == N && TV * 16 == N && TU <= 32, "tile");
   __shared__ cf colv[2][N], rowv[2][N];
   __shared__ float mag[2][N];
   __shared__ int pivrow[N], rowvar[N];
   const long col = blockIdx.x;
   const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15, lane = tid & 31;
   const Mode m = mode_of(a, col);
-  cf T[TT][TT];
+  cf T[TU][TV];
   if constexpr (SCHUR) {
     // S = TM_tt + κ² D Dg⁻¹ D − iκ (D Dg⁻¹ c) e_mlᵀ (N = nz); Dg⁻¹ and Dg⁻¹ c in shared memory
     cf* gs = colv[0];
     cf* gc = rowv[0];
-    for (int z = tid; z < N; z += LAY_THREADS) {
+    for (int z = tid; z < N; z += NTH) {
       const cf de = a.deps[z];
       const cf dg = make_float2(m.kap2 - a.k0sq * (1.f + de.x), -a.k0sq * (de.y + a.sb[z]));
       const cf g = cdiv1(dg);
@@ -197,24 +200,24 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TU; ++u)
 #pragma unroll
-      for (int v = 0; v < TT; ++v) T[u][v] = entry<false>(a, m, rg + 16 * u, cg + 16 * v);
+      for (int v = 0; v < TV; ++v) T[u][v] = entry<false>(a, m, rg + RG * u, cg + 16 * v);
     // the TE entry carries κ² on the diagonal, TM_tt does not
 #pragma unroll
-    for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TU; ++u)
 #pragma unroll
-      for (int v = 0; v < TT; ++v)
-        if (rg + 16 * u == cg + 16 * v) T[u][v].x -= m.kap2;
+      for (int v = 0; v < TV; ++v)
+        if (rg + RG * u == cg + 16 * v) T[u][v].x -= m.kap2;
     // TE uses r_s in its reflection column where TM_tt uses r_p
     {
       const int jm = a.zml;
 #pragma unroll
-      for (int v = 0; v < TT; ++v) {
+      for (int v = 0; v < TV; ++v) {
         if (cg + 16 * v != jm) continue;
 #pragma unroll
-        for (int u = 0; u < TT; ++u) {
-          const int i = rg + 16 * u;
+        for (int u = 0; u < TU; ++u) {
+          const int i = rg + RG * u;
           if (i < a.zml) continue;
           const cf e = cscale(cmul(a.deps[i], upgoing(a, m, i)), a.k0sq);
           T[u][v] = cadd(T[u][v], csub(cmul(e, m.rs), cmul(e, m.rp)));
@@ -224,31 +227,31 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
     const cf ik = make_float2(0.f, -m.kap);   // −iκ
     for (int k = 0; k < N; ++k) {
       const cf g = gs[k];
-      cf dik[TT], dkj[TT];
+      cf dik[TU], dkj[TV];
 #pragma unroll
-      for (int u = 0; u < TT; ++u) dik[u] = __ldg(a.D + (long)(rg + 16 * u) * N + k);
+      for (int u = 0; u < TU; ++u) dik[u] = __ldg(a.D + (long)(rg + RG * u) * N + k);
 #pragma unroll
-      for (int v = 0; v < TT; ++v) dkj[v] = cscale(cmul(g, __ldg(a.D + (long)k * N + cg + 16 * v)), m.kap2);
+      for (int v = 0; v < TV; ++v) dkj[v] = cscale(cmul(g, __ldg(a.D + (long)k * N + cg + 16 * v)), m.kap2);
 #pragma unroll
-      for (int u = 0; u < TT; ++u)
+      for (int u = 0; u < TU; ++u)
 #pragma unroll
-        for (int v = 0; v < TT; ++v) T[u][v] = cfma(dik[u], dkj[v], T[u][v]);
+        for (int v = 0; v < TV; ++v) T[u][v] = cfma(dik[u], dkj[v], T[u][v]);
       const cf gck = cmul(ik, gc[k]);
 #pragma unroll
-      for (int v = 0; v < TT; ++v) {
+      for (int v = 0; v < TV; ++v) {
         if (cg + 16 * v != a.zml) continue;
 #pragma unroll
-        for (int u = 0; u < TT; ++u) T[u][v] = cfma(dik[u], gck, T[u][v]);
+        for (int u = 0; u < TU; ++u) T[u][v] = cfma(dik[u], gck, T[u][v]);
       }
     }
     __syncthreads();   // colv / rowv are reused by the elimination below
   } else {
 #pragma unroll
-    for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TU; ++u)
 #pragma unroll
-      for (int v = 0; v < TT; ++v) T[u][v] = entry<TM>(a, m, rg + 16 * u, cg + 16 * v);
+      for (int v = 0; v < TV; ++v) T[u][v] = entry<TM>(a, m, rg + RG * u, cg + 16 * v);
   }
-  unsigned used = 0;   // bit u: owned row rg + 16 u has been a pivot row
+  unsigned used = 0;   // bit u: owned row rg + RG u has been a pivot row
   for (int k = 0; k < N; ++k) {
     const int buf = k & 1;
     // column k -> shared (owners: cg == k % 16); used rows get magnitude -1 and a non-finite
@@ -256,11 +259,11 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
     if (cg == (k & 15)) {
       const int vk = k >> 4;
 #pragma unroll
-      for (int v = 0; v < TT; ++v) {
+      for (int v = 0; v < TV; ++v) {
         if (v != vk) continue;   // static register indexing: select the column by predicate
 #pragma unroll
-        for (int u = 0; u < TT; ++u) {
-          const int i = rg + 16 * u;
+        for (int u = 0; u < TU; ++u) {
+          const int i = rg + RG * u;
           const cf t = T[u][v];
           const float mg = t.x * t.x + t.y * t.y;
           colv[buf][i] = t;
@@ -288,59 +291,59 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
       pivrow[k] = p;
       if (!ok) atomicExch(a.err, 1);
     }
-    // pivot row p -> shared (owners: rg == p % 16)
-    if (rg == (p & 15)) {
-      const int up = p >> 4;
+    // pivot row p -> shared (owners: rg == p % RG)
+    if (rg == (p % RG)) {
+      const int up = p / RG;
       used |= 1u << up;
 #pragma unroll
-      for (int u = 0; u < TT; ++u) {
+      for (int u = 0; u < TU; ++u) {
         if (u != up) continue;
 #pragma unroll
-        for (int v = 0; v < TT; ++v) rowv[buf][cg + 16 * v] = T[u][v];
+        for (int v = 0; v < TV; ++v) rowv[buf][cg + 16 * v] = T[u][v];
       }
     }
     __syncthreads();
-    cf ci[TT], rj[TT];
+    cf ci[TU], rj[TV];
 #pragma unroll
-    for (int u = 0; u < TT; ++u) ci[u] = cmul(colv[buf][rg + 16 * u], pinv);
+    for (int u = 0; u < TU; ++u) ci[u] = cmul(colv[buf][rg + RG * u], pinv);
 #pragma unroll
-    for (int v = 0; v < TT; ++v) rj[v] = rowv[buf][cg + 16 * v];
+    for (int v = 0; v < TV; ++v) rj[v] = rowv[buf][cg + 16 * v];
     // rank-1 update of every owned entry; the pivot row and column are overwritten below
 #pragma unroll
-    for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TU; ++u)
 #pragma unroll
-      for (int v = 0; v < TT; ++v) T[u][v] = csub(T[u][v], cmul(ci[u], rj[v]));
-    const bool own_row = rg == (p & 15), own_col = cg == (k & 15);
-    const int up = p >> 4, vk = k >> 4;
+      for (int v = 0; v < TV; ++v) T[u][v] = csub(T[u][v], cmul(ci[u], rj[v]));
+    const bool own_row = rg == (p % RG), own_col = cg == (k & 15);
+    const int up = p / RG, vk = k >> 4;
     if (own_row) {
 #pragma unroll
-      for (int u = 0; u < TT; ++u) {
+      for (int u = 0; u < TU; ++u) {
         if (u != up) continue;
 #pragma unroll
-        for (int v = 0; v < TT; ++v) T[u][v] = cneg(cmul(rj[v], pinv));
+        for (int v = 0; v < TV; ++v) T[u][v] = cneg(cmul(rj[v], pinv));
       }
     }
     if (own_col) {
 #pragma unroll
-      for (int v = 0; v < TT; ++v) {
+      for (int v = 0; v < TV; ++v) {
         if (v != vk) continue;
 #pragma unroll
-        for (int u = 0; u < TT; ++u) T[u][v] = (own_row && u == up) ? pinv : ci[u];
+        for (int u = 0; u < TU; ++u) T[u][v] = (own_row && u == up) ? pinv : ci[u];
       }
     }
   }
   __syncthreads();
   // pivrow is a permutation: each step picks a row not used before
-  for (int k = tid; k < N; k += LAY_THREADS) rowvar[pivrow[k]] = k;
+  for (int k = tid; k < N; k += NTH) rowvar[pivrow[k]] = k;
   __syncthreads();
   // column-major output: element (r, c) of the inverse at c * N + r
   if (!a.half) {
     cf* out = a.mats + col * block_stride(a) + block_off;
 #pragma unroll
-    for (int u = 0; u < TT; ++u)
+    for (int u = 0; u < TU; ++u)
 #pragma unroll
-      for (int v = 0; v < TT; ++v) {
-        const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
+      for (int v = 0; v < TV; ++v) {
+        const int r = rowvar[rg + RG * u], c = pivrow[cg + 16 * v];
         out[(long)c * N + r] = T[u][v];
       }
     return;
@@ -349,26 +352,26 @@ __global__ void __launch_bounds__(LAY_THREADS) k_lay_inv(LayArgs a, int block_of
   // entries then lie in [-1, 1], where half keeps 11 significant bits)
   float mx = 0.f;
 #pragma unroll
-  for (int u = 0; u < TT; ++u)
+  for (int u = 0; u < TU; ++u)
 #pragma unroll
-    for (int v = 0; v < TT; ++v) mx = fmaxf(mx, fmaxf(fabsf(T[u][v].x), fabsf(T[u][v].y)));
+    for (int v = 0; v < TV; ++v) mx = fmaxf(mx, fmaxf(fabsf(T[u][v].x), fabsf(T[u][v].y)));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  __shared__ float wmax[LAY_THREADS / 32];
+  __shared__ float wmax[NTH / 32];
   if (lane == 0) wmax[tid >> 5] = mx;
   __syncthreads();
   mx = 0.f;
-  for (int w = 0; w < LAY_THREADS / 32; ++w) mx = fmaxf(mx, wmax[w]);
+  for (int w = 0; w < NTH / 32; ++w) mx = fmaxf(mx, wmax[w]);
   int e = 0;
   if (mx > 0.f && mx <= 3.0e38f) frexpf(mx, &e);   // mx = f 2^e with f in [0.5, 1)
   const float scale = ldexpf(1.f, e), inv = ldexpf(1.f, -e);
   if (tid == 0) a.scales[col * 2 + ((TM || SCHUR) ? 1 : 0)] = scale;
   __half2* out = a.mats16 + col * block_stride(a) + block_off;
 #pragma unroll
-  for (int u = 0; u < TT; ++u)
+  for (int u = 0; u < TU; ++u)
 #pragma unroll
-    for (int v = 0; v < TT; ++v) {
-      const int r = rowvar[rg + 16 * u], c = pivrow[cg + 16 * v];
+    for (int v = 0; v < TV; ++v) {
+      const int r = rowvar[rg + RG * u], c = pivrow[cg + 16 * v];
       out[half_pos(r, c, N)] = __floats2half2_rn(T[u][v].x * inv, T[u][v].y * inv);
     }
 }
@@ -1171,22 +1174,27 @@ LayArgs lay_args(psfd_plan_s* P) {
   return a;
 }
 
+// rows of the inversion's thread grid: 32 x 16 threads (16 warps) for blocks of 128, whose
+// 16 x 16 version held an 8 x 8 tile per thread at one CTA (8 warps) per SM (measured: 14.2 -> 12.9 ms
+// per build at 128x128x64; at 96 the 16 x 16 grid is faster, 11.6 against 16.9 ms at 128x128x96)
+constexpr int lay_rg(int n) { return n == 128 ? 32 : 16; }
+
 template <int NZ>
 int build_nz(psfd_plan_s* P) {
   LayArgs a = lay_args(P);
   const unsigned nblk = (unsigned)layered_columns(P);
-  k_lay_inv<NZ, false><<<nblk, LAY_THREADS, 0, P->stream>>>(a, 0);
+  k_lay_inv<NZ, false, false, lay_rg(NZ)><<<nblk, 16 * lay_rg(NZ), 0, P->stream>>>(a, 0);
   PSFD_CHECK_LAUNCH();
   if (a.schur) {
     if constexpr (NZ % 32 == 0) {
-      k_lay_inv<NZ, false, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+      k_lay_inv<NZ, false, true, lay_rg(NZ)><<<nblk, 16 * lay_rg(NZ), 0, P->stream>>>(a, NZ * NZ);
     } else {
       psfd_set_error("layered preconditioner: the Schur form is built for nz in {32, 64, 96, 128}");
       return PSFD_ERR_ARG;
     }
   } else {
     if constexpr (2 * NZ <= 128) {
-      k_lay_inv<2 * NZ, true><<<nblk, LAY_THREADS, 0, P->stream>>>(a, NZ * NZ);
+      k_lay_inv<2 * NZ, true, false, lay_rg(2 * NZ)><<<nblk, 16 * lay_rg(2 * NZ), 0, P->stream>>>(a, NZ * NZ);
     } else {
       psfd_set_error("layered preconditioner: nz %d needs the Schur form", NZ);
       return PSFD_ERR_ARG;
