@@ -29,23 +29,21 @@ struct KScal {
   double tol2;
 };
 
-// Per-thread compensated accumulator: Kahan summation of the rounded products
-// p = fl(a b) plus a separate sum of their exact rounding errors fma(a, b, -p).
-// Error of a partial: about 2u * sum|p| (u = 2^-24), far below float rounding of
-// a plain sum; partials are then summed in FP64.
+// Per-thread compensated accumulator (Kahan): the BiCGSTAB kernels add the plain FP32 partial of
+// one batch of elements (at most 16 products, exact inside each FMA, error about 16 u sum|p| with
+// u = 2^-24) into it once per batch, so the compensated chain runs once per batch instead of once
+// per product; partials of threads and blocks are then summed in FP64.
 struct Acc2 {
   float s, c, e;
 };
 
-__device__ __forceinline__ void acc_prod(Acc2& A, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float ep = fmaf(a, b, -p);
-  const float y = __fsub_rn(p, A.c);
+__device__ __forceinline__ void acc_add(Acc2& A, float v) {
+  const float y = __fsub_rn(v, A.c);
   const float t = __fadd_rn(A.s, y);
   A.c = __fsub_rn(__fsub_rn(t, A.s), y);
   A.s = t;
-  A.e = __fadd_rn(A.e, ep);
 }
+
 __device__ __forceinline__ double acc_value(const Acc2& A) {
   return (double)A.s - (double)A.c + (double)A.e;
 }
@@ -54,12 +52,10 @@ __device__ __forceinline__ double acc_value(const Acc2& A) {
 // omega's denominator and the convergence tests; the partials are summed in FP64
 __device__ __forceinline__ void acc_norm(Acc2& A, cf a) { A.s = fmaf(a.x, a.x, fmaf(a.y, a.y, A.s)); }
 
-// re/im of conj(a) * b
-__device__ __forceinline__ void acc_cdot(Acc2& re, Acc2& im, cf a, cf b) {
-  acc_prod(re, a.x, b.x);
-  acc_prod(re, a.y, b.y);
-  acc_prod(im, a.x, b.y);
-  acc_prod(im, -a.y, b.x);
+// re/im of conj(a) * b into a batch partial (plain FMA chains)
+__device__ __forceinline__ void acc_cdot_plain(Acc2& re, Acc2& im, cf a, cf b) {
+  re.s = fmaf(a.x, b.x, fmaf(a.y, b.y, re.s));
+  im.s = fmaf(a.x, b.y, fmaf(-a.y, b.x, im.s));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -189,11 +185,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   if constexpr (OP == OK_XR) omg = zf(S->omega);
 
   // Batches of kU elements per thread: every load of a batch is issued before the first use,
-  // so that kU x (vectors read) float4 loads are in flight; even and odd batch slots feed two
-  // accumulator sets (shorter dependence chains in the compensated sums).
-  Acc2 accB[kMaxQ];
-#pragma unroll
-  for (int q = 0; q < kMaxQ; ++q) accB[q] = {0.f, 0.f, 0.f};
+  // so that kU x (vectors read) float4 loads are in flight; the batch's products are summed in
+  // plain FMA chains and enter the compensated sums once per batch.
   constexpr int NIN = (OP == OK_XR) ? 5 : (OP == OK_P) ? 3 : (OP == OK_INIT || OP == OK_NORM) ? 1 : 2;
   constexpr int kU = (NIN >= 3) ? 2 : 4;
   auto ld4 = [&](const cf* v, long e) { return __ldg(reinterpret_cast<const float4*>(v) + e); };
@@ -233,8 +226,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
     } else if constexpr (OP == OK_RV) {
       // v0 = rhat, v1 = v
       const float4 h = L[0], v = L[1];
-      acc_cdot(A[0], A[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
-      acc_cdot(A[0], A[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
+      acc_cdot_plain(A[0], A[1], make_float2(h.x, h.y), make_float2(v.x, v.y));
+      acc_cdot_plain(A[0], A[1], make_float2(h.z, h.w), make_float2(v.z, v.w));
     } else if constexpr (OP == OK_S) {
       // v0 = s (out), v1 = r, v2 = v
       const float4 rr = L[1], vv = L[2];
@@ -245,8 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       // v0 = t, v1 = s
       const float4 tt = L[0], ss = L[1];
       cf t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
-      acc_cdot(A[0], A[1], t0, make_float2(ss.x, ss.y));
-      acc_cdot(A[0], A[1], t1, make_float2(ss.z, ss.w));
+      acc_cdot_plain(A[0], A[1], t0, make_float2(ss.x, ss.y));
+      acc_cdot_plain(A[0], A[1], t1, make_float2(ss.z, ss.w));
       acc_norm(A[2], t0);
       acc_norm(A[2], t1);
     } else if constexpr (OP == OK_XR) {
@@ -261,8 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       cf r1 = csub(s1, cmul(omg, make_float2(tt.z, tt.w)));
       reinterpret_cast<float4*>(a.v0)[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
       reinterpret_cast<float4*>(a.v1)[e] = make_float4(r0.x, r0.y, r1.x, r1.y);
-      acc_cdot(A[0], A[1], make_float2(hh.x, hh.y), r0);
-      acc_cdot(A[0], A[1], make_float2(hh.z, hh.w), r1);
+      acc_cdot_plain(A[0], A[1], make_float2(hh.x, hh.y), r0);
+      acc_cdot_plain(A[0], A[1], make_float2(hh.z, hh.w), r1);
       acc_norm(A[2], r0);
       acc_norm(A[2], r1);
     } else if constexpr (OP == OK_NORM) {
@@ -286,16 +279,21 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
 #pragma unroll
     for (int u = 0; u < kU; ++u)
       if (i0 + u * stride < n2) load(off / 2 + i0 + u * stride, L[u]);
+    Acc2 Bt[kMaxQ];   // this batch's plain partials
+#pragma unroll
+    for (int q = 0; q < kMaxQ; ++q) Bt[q] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < kU; ++u)
-      if (i0 + u * stride < n2) body(off / 2 + i0 + u * stride, L[u], (u & 1) ? accB : acc);
+      if (i0 + u * stride < n2) body(off / 2 + i0 + u * stride, L[u], Bt);
+#pragma unroll
+    for (int q = 0; q < kMaxQ; ++q) acc_add(acc[q], Bt[q].s);
   }
 
   constexpr int NQ = (OP == OK_TS || OP == OK_XR) ? 4 : ((OP == OK_INIT || OP == OK_RV || OP == OK_NORM || OP == OK_SUB) ? 2 : 0);
   if constexpr (NQ > 0) {
     double val[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) val[q] = acc_value(acc[q]) + acc_value(accB[q]);
+    for (int q = 0; q < NQ; ++q) val[q] = acc_value(acc[q]);
     double tot[NQ];
     if (!reduce_finish<NQ>(val, a.partials, a.counters, tot)) return;
     if (threadIdx.x != 0) return;
