@@ -264,36 +264,42 @@ struct SourceArgs {
 };
 
 // grid: (ceil(ncols / blockDim), nz); the z-only factors are computed once per block
-__global__ void k_source(SourceArgs a) {
+// per plane z: (re, im) of E_inc + R E_inc for the three components (one thread per plane; the
+// FP64 trigonometry runs once per plane instead of once per block)
+__global__ void k_source_z(SourceArgs a, double* ftab) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= a.nz) return;
+  double st = sin(a.theta), ctt = cos(a.theta), sp = sin(a.phi), cp = cos(a.phi);
+  double e[3];
+  if (a.pol == 0) { e[0] = -sp; e[1] = cp; e[2] = 0.0; }
+  else { e[0] = ctt * cp; e[1] = ctt * sp; e[2] = st; }
+  double kx = a.k0 * st * cp, ky = a.k0 * st * sp;
+  double kpar = sqrt(kx * kx + ky * ky);
+  double sx, sy, tx, ty;
+  if (kpar < 1e-12 * a.k0) { sx = 0; sy = 1; tx = 1; ty = 0; }
+  else { sx = -ky / kpar; sy = kx / kpar; tx = kx / kpar; ty = ky / kpar; }
+  cd rs = {a.rs64[0].x, a.rs64[0].y}, rp = {a.rp64[0].x, a.rp64[0].y};
+  cd kz0 = {a.kz064[0].x, a.kz064[0].y};
+  double as = sx * e[0] + sy * e[1], at = tx * e[0] + ty * e[1];
+  cd r0 = as * sx * rs + at * tx * rp;
+  cd r1 = as * sy * rs + at * ty * rp;
+  cd r2 = cdiv(cd_(-1, 0) * (kx * r0 + ky * r1), kz0);
+  double zr = (z - a.z_ml) * a.dz;
+  double kzi = a.k0 * ctt;
+  cd einc = {cos(kzi * zr), -sin(kzi * zr)};
+  cd prof = {0, 0};
+  if (zr >= 0) {
+    double mag = exp(-kz0.im * zr);
+    prof = {mag * cos(kz0.re * zr), mag * sin(kz0.re * zr)};
+  }
+  cd tot[3] = {e[0] * einc + r0 * prof, e[1] * einc + r1 * prof, e[2] * einc + r2 * prof};
+  for (int c = 0; c < 3; ++c) { ftab[z * 6 + 2 * c] = tot[c].re; ftab[z * 6 + 2 * c + 1] = tot[c].im; }
+}
+
+__global__ void k_source(SourceArgs a, const double* __restrict__ ftab) {
   __shared__ double f_tot[6];   // (re, im) of E_inc + R E_inc for the three components at this z
   const int z = blockIdx.y;
-  if (threadIdx.x == 0) {
-    double st = sin(a.theta), ctt = cos(a.theta), sp = sin(a.phi), cp = cos(a.phi);
-    double e[3];
-    if (a.pol == 0) { e[0] = -sp; e[1] = cp; e[2] = 0.0; }
-    else { e[0] = ctt * cp; e[1] = ctt * sp; e[2] = st; }
-    double kx = a.k0 * st * cp, ky = a.k0 * st * sp;
-    double kpar = sqrt(kx * kx + ky * ky);
-    double sx, sy, tx, ty;
-    if (kpar < 1e-12 * a.k0) { sx = 0; sy = 1; tx = 1; ty = 0; }
-    else { sx = -ky / kpar; sy = kx / kpar; tx = kx / kpar; ty = ky / kpar; }
-    cd rs = {a.rs64[0].x, a.rs64[0].y}, rp = {a.rp64[0].x, a.rp64[0].y};
-    cd kz0 = {a.kz064[0].x, a.kz064[0].y};
-    double as = sx * e[0] + sy * e[1], at = tx * e[0] + ty * e[1];
-    cd r0 = as * sx * rs + at * tx * rp;
-    cd r1 = as * sy * rs + at * ty * rp;
-    cd r2 = cdiv(cd_(-1, 0) * (kx * r0 + ky * r1), kz0);
-    double zr = (z - a.z_ml) * a.dz;
-    double kzi = a.k0 * ctt;
-    cd einc = {cos(kzi * zr), -sin(kzi * zr)};
-    cd prof = {0, 0};
-    if (zr >= 0) {
-      double mag = exp(-kz0.im * zr);
-      prof = {mag * cos(kz0.re * zr), mag * sin(kz0.re * zr)};
-    }
-    cd tot[3] = {e[0] * einc + r0 * prof, e[1] * einc + r1 * prof, e[2] * einc + r2 * prof};
-    for (int c = 0; c < 3; ++c) { f_tot[2 * c] = tot[c].re; f_tot[2 * c + 1] = tot[c].im; }
-  }
+  if (threadIdx.x < 6) f_tot[threadIdx.x] = ftab[z * 6 + threadIdx.x];
   __syncthreads();
   const long xy = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (xy >= a.ncols) return;
@@ -605,6 +611,8 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
   }
   P->fill = fill;
   // sources
+  double* ftab = nullptr;
+  PSFD_CUDA_TRY(cudaMallocAsync((void**)&ftab, (size_t)P->nz * 6 * sizeof(double), s));
   for (int r = 0; r < P->nrhs; ++r) {
     SourceArgs a;
     a.fill = fill; a.b = (cf*)b + (long)r * P->nvec;
@@ -614,10 +622,13 @@ extern "C" int psfd_background(psfd_plan P, const psfd_stack_t* stack, const flo
     a.pc64 = P->pc64;
     a.rs64 = P->R.rs64; a.rp64 = P->R.rp64; a.kz064 = P->R.kz064;
     a.pol = pol[r];
+    k_source_z<<<(unsigned)((P->nz + 127) / 128), 128, 0, s>>>(a, ftab);
+    PSFD_CHECK_LAUNCH();
     dim3 grid((unsigned)((nm + 255) / 256), (unsigned)P->nz);
-    k_source<<<grid, 256, 0, s>>>(a);
+    k_source<<<grid, 256, 0, s>>>(a, ftab);
     PSFD_CHECK_LAUNCH();
   }
+  PSFD_CUDA_TRY(cudaFreeAsync(ftab, s));
   P->have_background = true;
   return PSFD_OK;
 }
