@@ -25,6 +25,9 @@
  * - Return codes: PSFD_OK (0) or one of the PSFD_ERR_* / PSFD_NOT_CONVERGED
  *   values; psfd_last_error() returns a message for the last failing call on
  *   the calling thread.  Argument errors are detected before any launch.
+ * - Threads: different plans may be used from different host threads at once
+ *   (a plan from one thread at a time); the library's one-time kernel set-up
+ *   completes before any thread launches.
  */
 #ifndef PSFD_H
 #define PSFD_H
@@ -312,7 +315,8 @@ PSFD_API int psfd_autotune(psfd_plan plan, int* chosen_T);
  * output E[i]; every plan must have its own stream for the solves to overlap.
  * info: HOST array of sum(plans[i].nrhs) entries, in plan order.  nworkers host
  * threads (<= 0: 8) take plans in order and run psfd_solve_ex on each.  Blocks
- * until all solves finish; returns the worst status. */
+ * until all solves finish; returns the worst status (an argument, state or CUDA
+ * error of any plan is returned with that plan's index and message). */
 PSFD_API int psfd_solve_batched(const psfd_plan* plans, int nplans, const psfd_c64* const* b,
                                 const psfd_c64* const* x0, psfd_c64* const* E,
                                 const psfd_solve_opts_t* opts, psfd_info_t* info, int nworkers);
