@@ -346,6 +346,38 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
   }
 }
 
+// SMs of the current device (thread-safe one-time query; 148 when it fails)
+int device_sms() {
+  static const int n = [] {
+    int dev = 0, m = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        m <= 0)
+      m = 148;
+    return m;
+  }();
+  return n;
+}
+
+// CTAs of KERNEL resident per SM at kThreads threads (one-time query per kernel; 1 when it fails)
+template <auto KERNEL>
+int per_sm_of() {
+  static const int b = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KERNEL, kThreads, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+  }();
+  return b;
+}
+
+// Grid-stride streaming kernels run as one wave of resident CTAs shared by `groups` grid slices
+// (right-hand sides, basis chunks), at most `cap` CTAs per slice (what the reduction partials were
+// sized for): a fraction of a second wave would leave SMs idle at the end of every pass.
+template <auto KERNEL>
+int one_wave(int cap, int groups) {
+  const long w = (long)per_sm_of<KERNEL>() * device_sms() / std::max(1, groups);
+  return (int)std::max(1L, std::min<long>(cap, w));
+}
+
 // compulsory complex64 vector passes (reads + writes) of each vector kernel
 constexpr int vec_passes(int op) {
   return op == OK_INIT ? 5 : op == OK_P ? 4 : op == OK_RV ? 2 : op == OK_S ? 3 : op == OK_TS ? 2
@@ -355,7 +387,7 @@ constexpr int vec_passes(int op) {
 template <int OP>
 int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
   StageScope sc(s, ST_KRYLOV, (double)vec_passes(OP) * nrhs * a.n * sizeof(cf));
-  dim3 grid((unsigned)nblocks, (unsigned)nrhs);
+  dim3 grid((unsigned)one_wave<k_vec<OP>>(nblocks, nrhs), (unsigned)nrhs);
   k_vec<OP><<<grid, kThreads, 0, s>>>(a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -765,10 +797,9 @@ static int bicgstab_loop(psfd_plan_s* P, SolveWs& w, VArgs va, int maxit, int af
 }
 
 static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxit, int m, int aflags, int nb) {
-  // the multi-dot and update kernels stream (j + 2) vectors per launch: about two CTAs per SM over
-  // all right-hand sides measured best (fewer end-of-block reductions, one wave)
-  const int nbg = std::max(1, std::min(nb, 2 * 148 / std::max(1, P->nrhs)));
+  // the multi-dot and update kernels stream (j + 2) vectors per launch, one wave of CTAs each
   const int nr = P->nrhs;
+  const int nbu = one_wave<k_gupd<false>>(nb, nr), nby = one_wave<k_gupd<true>>(nb, nr);
   cudaStream_t st = P->stream;
   const long n = P->nvec;
   const size_t vbytes = (size_t)nr * n * sizeof(cf);
@@ -824,10 +855,10 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         StageScope sc(st, ST_KRYLOV, (2.0 * (j + 1) + 3.0) * nr * n * sizeof(cf));
         g.hout = w.h1;
         g.save_norm = true;
-        k_gdot<<<dim3(nbg, nr, nch), kThreads, 0, st>>>(g);
+        k_gdot<<<dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
         g.save_norm = false;
-        k_gupd<false><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
+        k_gupd<false><<<dim3(nbu, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
       }
       k_greorth<<<1, tpb, 0, st>>>(w.sc, w.active, w.skip2, nr);
@@ -837,9 +868,9 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         const int* keep = g.mask;
         g.mask = w.skip2;
         g.hout = w.h2;
-        k_gdot<<<dim3(nbg, nr, nch), kThreads, 0, st>>>(g);
+        k_gdot<<<dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
-        k_gupd<false><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
+        k_gupd<false><<<dim3(nbu, nr), kThreads, 0, st>>>(g);
         PSFD_CHECK_LAUNCH();
         g.mask = keep;
       }
@@ -859,7 +890,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
     k_gtri<<<1, tpb, 0, st>>>(w.gs, nr);
     PSFD_CHECK_LAUNCH();
     g.mask = nullptr;  // every rhs with jd > 0 updates y
-    k_gupd<true><<<dim3(nbg, nr), kThreads, 0, st>>>(g);
+    k_gupd<true><<<dim3(nby, nr), kThreads, 0, st>>>(g);
     PSFD_CHECK_LAUNCH();
   }
   k_gfinish<<<1, tpb, 0, st>>>(w.gs, w.sc, nr);
