@@ -74,6 +74,10 @@ struct psfd_plan_s {
   // history (host)
   double* hist = nullptr;
   int hist_cap = 0;
+  // BiCGSTAB progress that the host reads without synchronising the stream: pinned, device-mapped
+  // [2][nrhs] ints (iterations completed, done flag), written by the vector kernels
+  int* prog_h = nullptr;
+  int* prog_d = nullptr;
   // launch choices (set by the tuner)
   int axial_T = 0;
   // FP64 residual path (built on first refined solve)

@@ -10,7 +10,9 @@
 // summed in FP64 in a fixed order (warp tree, block tree, blocks in index
 // order by the last block to finish), so results are reproducible run to run.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <vector>
 
@@ -160,7 +162,17 @@ struct VArgs {
   double* hist;
   int hist_cap;
   bool use_done;
+  int* prog;   // nullable, host-mapped [2][nrhs]: iterations completed and done flag per rhs
 };
+
+// the progress word of a rhs for the host (a hint: the kernels decide on a.done alone)
+__device__ __forceinline__ void post_progress(int* prog, int rhs, int iters, int done) {
+  if (!prog) return;
+  volatile int* q = prog;
+  q[rhs] = iters;
+  q[gridDim.y + rhs] = done;
+  __threadfence_system();
+}
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
@@ -311,6 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       if (tot[0] <= S->tol2 * S->bnorm2) { d = 1; S->status = PSFD_OK; }
       if (S->maxit <= 0) d = 1;
       a.done[rhs] = d;
+      post_progress(a.prog, rhs, 0, d);
     } else if constexpr (OP == OK_RV) {
       S->rv = make_double2(tot[0], tot[1]);
       const double arv = zabs(S->rv);
@@ -318,6 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
         S->status = PSFD_ERR_BREAKDOWN;
         S->alpha = make_double2(0.0, 0.0);
         a.done[rhs] = 1;
+        post_progress(a.prog, rhs, S->iters, 1);
       } else {
         S->alpha = zdiv(S->rho, S->rv);
       }
@@ -338,6 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
       else if (!(zabs(S->rho) > 1e-300) || !(zabs(S->omega) > 0.0)) { S->status = PSFD_ERR_BREAKDOWN; d = 1; }
       else if (it >= S->maxit) { S->status = PSFD_NOT_CONVERGED; d = 1; }
       a.done[rhs] = d;
+      post_progress(a.prog, rhs, it, d);
     } else if constexpr (OP == OK_NORM) {
       S->res0 = tot[0];
     } else if constexpr (OP == OK_SUB) {
@@ -406,6 +421,16 @@ __global__ void k_set_scalars(KScal* sc, int nrhs, double tol2, int maxit) {
 __global__ void k_copy_bnorm(KScal* sc, int nrhs) {
   int r = threadIdx.x;
   if (r < nrhs) sc[r].bnorm2 = sc[r].res0;
+}
+
+// per-rhs flags from the host, passed as a kernel argument (one bit per rhs) instead of a copy
+struct RhsBits {
+  static constexpr int kMax = 1024;
+  unsigned long long w[kMax / 64];
+};
+__global__ void k_set_flags(int* f, int nrhs, RhsBits b) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs) f[r] = (int)((b.w[r >> 6] >> (r & 63)) & 1ull);
 }
 
 }  // namespace
@@ -763,35 +788,88 @@ extern "C" size_t psfd_solve_workspace_size(psfd_plan P, int method, int restart
   return ws_layout(P, method, restart, &w, nullptr);
 }
 
+// Pinned, device-mapped progress words of the plan (allocated on first use); nullptr when the
+// allocation fails, and the loop then checks convergence by synchronising every 8 iterations.
+static int* plan_progress(psfd_plan_s* P) {
+  if (!P->prog_h) {
+    int* h = nullptr;
+    if (cudaHostAlloc((void**)&h, sizeof(int) * 2 * P->nrhs, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    int* d = nullptr;
+    if (cudaHostGetDevicePointer((void**)&d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(h);
+      return nullptr;
+    }
+    P->prog_h = h;
+    P->prog_d = d;
+  }
+  return P->prog_d;
+}
+
 static int bicgstab_loop(psfd_plan_s* P, SolveWs& w, VArgs va, int maxit, int aflags, int nb) {
   const int nr = P->nrhs;
   cudaStream_t st = P->stream;
   int rc;
+  // The host enqueues one iteration at a time and, before the next, waits (without a stream
+  // synchronisation) until the one before has completed on every rhs that is still running, as
+  // the vector kernels post it to host-mapped memory: the GPU always has the next iteration queued,
+  // and at most one iteration of early-returning launches follows convergence.
+  va.prog = plan_progress(P);
+  volatile int* prog = P->prog_h;
+  if (va.prog)
+    for (int r = 0; r < 2 * nr; ++r) prog[r] = 0;
   va.v0 = w.r; va.v1 = w.rhat; va.v2 = w.p; va.v3 = w.v; va.v4 = w.y;
   if ((rc = launch_vec<OK_INIT>(va, nr, st, nb))) return rc;
   va.use_done = true;
   std::vector<int> hdone(nr);
   const int check_every = 8;
-  for (int it = 0; it < maxit; it += check_every) {
-    for (int k = 0; k < check_every && it + k < maxit; ++k) {
-      va.v0 = w.p; va.v1 = w.r; va.v2 = w.v;
-      if ((rc = launch_vec<OK_P>(va, nr, st, nb))) return rc;
-      if ((rc = apply_hybrid(P, w.p, w.v, aflags, w.done))) return rc;
-      va.v0 = w.rhat; va.v1 = w.v;
-      if ((rc = launch_vec<OK_RV>(va, nr, st, nb))) return rc;
-      va.v0 = w.s; va.v1 = w.r; va.v2 = w.v;
-      if ((rc = launch_vec<OK_S>(va, nr, st, nb))) return rc;
-      if ((rc = apply_hybrid(P, w.s, w.t, aflags, w.done))) return rc;
-      va.v0 = w.t; va.v1 = w.s;
-      if ((rc = launch_vec<OK_TS>(va, nr, st, nb))) return rc;
-      va.v0 = w.y; va.v1 = w.r; va.v2 = w.p; va.v3 = w.s; va.v4 = w.t; va.v5 = w.rhat;
-      if ((rc = launch_vec<OK_XR>(va, nr, st, nb))) return rc;
+  for (int it = 0; it < maxit; ++it) {
+    va.v0 = w.p; va.v1 = w.r; va.v2 = w.v;
+    if ((rc = launch_vec<OK_P>(va, nr, st, nb))) return rc;
+    if ((rc = apply_hybrid(P, w.p, w.v, aflags, w.done))) return rc;
+    va.v0 = w.rhat; va.v1 = w.v;
+    if ((rc = launch_vec<OK_RV>(va, nr, st, nb))) return rc;
+    va.v0 = w.s; va.v1 = w.r; va.v2 = w.v;
+    if ((rc = launch_vec<OK_S>(va, nr, st, nb))) return rc;
+    if ((rc = apply_hybrid(P, w.s, w.t, aflags, w.done))) return rc;
+    va.v0 = w.t; va.v1 = w.s;
+    if ((rc = launch_vec<OK_TS>(va, nr, st, nb))) return rc;
+    va.v0 = w.y; va.v1 = w.r; va.v2 = w.p; va.v3 = w.s; va.v4 = w.t; va.v5 = w.rhat;
+    if ((rc = launch_vec<OK_XR>(va, nr, st, nb))) return rc;
+    if (va.prog) {
+      // iteration it - 1 complete (it iterations) on every running rhs, or every rhs done
+      auto state = [&](bool& all_done) {
+        all_done = true;
+        bool ready = true;
+        for (int r = 0; r < nr; ++r) {
+          if (prog[nr + r]) continue;
+          all_done = false;
+          ready = ready && prog[r] >= it;
+        }
+        return ready || all_done;
+      };
+      bool all_done = false;
+      const auto t0 = std::chrono::steady_clock::now();
+      while (!state(all_done)) {
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
+          // a long iteration: wait for the queue instead of spinning
+          PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+          state(all_done);
+          break;
+        }
+        std::this_thread::yield();
+      }
+      if (all_done) break;
+    } else if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+      PSFD_CUDA_TRY(cudaMemcpyAsync(hdone.data(), w.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+      PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+      bool all = true;
+      for (int r = 0; r < nr; ++r) all = all && hdone[r];
+      if (all) break;
     }
-    PSFD_CUDA_TRY(cudaMemcpyAsync(hdone.data(), w.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
-    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
-    bool all = true;
-    for (int r = 0; r < nr; ++r) all = all && hdone[r];
-    if (all) break;
   }
   return PSFD_OK;
 }
@@ -1173,11 +1251,9 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
   if ((rc = transform64(P, b64, nplanes, true, us))) return fail(rc);
   a64.a64 = b64;
   if ((rc = launch_v64<V64_NORM>(a64, nr, st, nb))) return fail(rc);
+  // ||b||^2 stays in res0 until the first inner solve: it is read with the first residual
   std::vector<KScal> hs(nr);
-  PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
-  PSFD_CUDA_TRY(cudaStreamSynchronize(st));
   std::vector<double> bnorm2(nr), rr(nr, 0.0), rr0(nr, 0.0);
-  for (int r = 0; r < nr; ++r) bnorm2[r] = hs[r].res0;
   // E64 = x0 (HYBRID, FP64) or 0.  The warm start only sets where the refinement begins, so its
   // lateral transform runs in complex64 (kept in w.t, where the first residual reads it)
   if (x0) {
@@ -1213,6 +1289,13 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     if ((rc = launch_v64<V64_RES>(a64, nr, st, nb))) return fail(rc);
     PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
     PSFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (outer == 0) {
+      for (int r = 0; r < nr; ++r) bnorm2[r] = hs[r].res0;
+    } else {
+      // the last inner solve's iteration counts are still in the scalar block
+      for (int r = 0; r < nr; ++r)
+        if (!conv[r]) inner_its[r] += hs[r].iters;
+    }
     if (!exact) {
       // a warm start that may already meet the tolerance is decided on the exact residual
       bool near = false;
@@ -1238,7 +1321,15 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
       total_max = std::max(total_max, inner_its[r]);
     }
     if (all) break;
-    PSFD_CUDA_TRY(cudaMemcpyAsync(dskip, conv.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    if (nr <= RhsBits::kMax) {
+      RhsBits bits{};
+      for (int r = 0; r < nr; ++r)
+        if (conv[r]) bits.w[r >> 6] |= 1ull << (r & 63);
+      k_set_flags<<<(nr + 255) / 256, 256, 0, st>>>(dskip, nr, bits);
+      PSFD_CHECK_LAUNCH();
+    } else {
+      PSFD_CUDA_TRY(cudaMemcpyAsync(dskip, conv.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    }
     a64.a64 = r64; a64.o32 = w.r; a64.skip = dskip;
     if ((rc = launch_v64<V64_CAST>(a64, nr, st, nb))) return fail(rc);
     // inner complex64 solve of A M y = r to inner_tol (relative to ||r||), or only as far as the
@@ -1258,10 +1349,6 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     if (o->method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, inner_max, aflags, nb);
     else rc = gmres_loop(P, w, va, itol, inner_max, o->restart, aflags, nb);
     if (rc) return fail(rc);
-    PSFD_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.sc, sizeof(KScal) * nr, cudaMemcpyDeviceToHost, st));
-    PSFD_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int r = 0; r < nr; ++r)
-      if (!conv[r]) inner_its[r] += hs[r].iters;
     // E += M y
     cf* My = w.t;
     if (o->use_precond == 2) {

@@ -406,6 +406,7 @@ static void plan_free(psfd_plan_s* P) {
                   P->R.kz064, P->R.refl, P->R.kz0, P->G, P->tmpA, P->tmpB, P->err, P->pc, P->pc64};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (P->prog_h) cudaFreeHost(P->prog_h);
 }
 
 extern "C" int psfd_plan_create(psfd_plan* out, const psfd_params_t* prm) {
