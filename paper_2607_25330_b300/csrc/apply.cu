@@ -17,6 +17,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 // ======================================================================= axial kernel
 struct AxialArgs {
@@ -69,6 +70,7 @@ __device__ __forceinline__ cf kbg_at_(const AxialArgs& a, int z) {
 // over the column and is subtracted at z_ml.
 template <int NZ, int T, int MODE>
 __global__ void __launch_bounds__(128) k_axial(AxialArgs a) {
+  pdl_enter();
   constexpr int P = 32 / T;
   constexpr int R = NZ / T;
   using PZ = Pencil<NZ, T, P>;
@@ -335,7 +337,7 @@ static int run_axial(psfd_plan_s* P, const cf* x, cf* y, const int* done) {
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_axial<NZ, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
-  k_axial<NZ, T, MODE><<<grid, warps * 32, smem, P->stream>>>(a);
+  (void)launch_pdl(k_axial<NZ, T, MODE>, grid, dim3(warps * 32), smem, P->stream, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -415,6 +417,7 @@ struct RowArgs {
 
 template <int NX, int T, int OP>
 __global__ void __launch_bounds__(128) k_rows(RowArgs a) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
   __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -485,6 +488,7 @@ struct ColArgs {
 
 template <int NY, int T, int OP>
 __global__ void __launch_bounds__(128) k_cols(ColArgs a) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
   __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -566,9 +570,9 @@ static int rows_op(const RowArgs& a, int op, cudaStream_t s) {
   dim3 grid((unsigned)((a.nrows + per_block - 1) / per_block));
   if (grid.x == 0) return PSFD_OK;
   switch (op) {
-    case ROW_FWD: k_rows<NX, T, ROW_FWD><<<grid, warps * 32, 0, s>>>(a); break;
-    case ROW_INV: k_rows<NX, T, ROW_INV><<<grid, warps * 32, 0, s>>>(a); break;
-    default: k_rows<NX, T, ROW_FWD_SUB><<<grid, warps * 32, 0, s>>>(a); break;
+    case ROW_FWD: (void)launch_pdl(k_rows<NX, T, ROW_FWD>, grid, dim3(warps * 32), 0, s, a); break;
+    case ROW_INV: (void)launch_pdl(k_rows<NX, T, ROW_INV>, grid, dim3(warps * 32), 0, s, a); break;
+    default: (void)launch_pdl(k_rows<NX, T, ROW_FWD_SUB>, grid, dim3(warps * 32), 0, s, a); break;
   }
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -600,10 +604,10 @@ static int cols_op(const ColArgs& a, int op, cudaStream_t s) {
   dim3 grid((unsigned)((a.ncolumns + per_block - 1) / per_block));
   if (grid.x == 0) return PSFD_OK;
   switch (op) {
-    case COL_FWD: k_cols<NY, T, COL_FWD><<<grid, warps * 32, 0, s>>>(a); break;
-    case COL_INV: k_cols<NY, T, COL_INV><<<grid, warps * 32, 0, s>>>(a); break;
-    case COL_CONTRAST: k_cols<NY, T, COL_CONTRAST><<<grid, warps * 32, 0, s>>>(a); break;
-    default: k_cols<NY, T, COL_GAUSS><<<grid, warps * 32, 0, s>>>(a); break;
+    case COL_FWD: (void)launch_pdl(k_cols<NY, T, COL_FWD>, grid, dim3(warps * 32), 0, s, a); break;
+    case COL_INV: (void)launch_pdl(k_cols<NY, T, COL_INV>, grid, dim3(warps * 32), 0, s, a); break;
+    case COL_CONTRAST: (void)launch_pdl(k_cols<NY, T, COL_CONTRAST>, grid, dim3(warps * 32), 0, s, a); break;
+    default: (void)launch_pdl(k_cols<NY, T, COL_GAUSS>, grid, dim3(warps * 32), 0, s, a); break;
   }
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;

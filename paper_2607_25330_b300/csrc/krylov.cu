@@ -18,6 +18,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -176,6 +177,7 @@ __device__ __forceinline__ void post_progress(int* prog, int rhs, int iters, int
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_vec(VArgs a) {
+  pdl_enter();
   const int rhs = blockIdx.y;
   KScal* S = a.sc + rhs;
   if (a.use_done && a.done[rhs]) return;
@@ -403,7 +405,7 @@ template <int OP>
 int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
   StageScope sc(s, ST_KRYLOV, (double)vec_passes(OP) * nrhs * a.n * sizeof(cf));
   dim3 grid((unsigned)one_wave<k_vec<OP>>(nblocks, nrhs), (unsigned)nrhs);
-  k_vec<OP><<<grid, kThreads, 0, s>>>(a);
+  (void)launch_pdl(k_vec<OP>, grid, dim3(kThreads), 0, s, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }

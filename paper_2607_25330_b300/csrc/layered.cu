@@ -39,6 +39,7 @@
 #include <cuda_fp16.h>
 
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -410,6 +411,7 @@ constexpr int apply_threads() { return LAY_GROUP * 3 * NZ / apply_rpt<HALF>(); }
 template <int NZ, int NR, bool HALF>
 __global__ void __launch_bounds__(apply_threads<NZ, HALF>(), (HALF ? 4 : (NR <= 2 ? 3 : 2)))
     k_lay_apply(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
+  pdl_enter();
   if (all_done(a)) return;
   constexpr int nrhs = NR;
   constexpr int G = LAY_GROUP, NT = apply_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
@@ -548,6 +550,7 @@ constexpr int schur_threads() { return LAY_GROUP * 2 * NZ / apply_rpt<HALF>(); }
 template <int NZ, int NR, bool HALF>
 __global__ void __launch_bounds__(schur_threads<NZ, HALF>())
     k_lay_apply_schur(LayArgs a, const cf* __restrict__ x, cf* __restrict__ y, long ncols) {
+  pdl_enter();
   if (all_done(a)) return;
   constexpr int G = LAY_GROUP, NT = schur_threads<NZ, HALF>(), RPT = apply_rpt<HALF>();
   static_assert(NT >= NZ && NT % NZ == 0, "whole groups of NZ threads in the D products");
@@ -852,6 +855,7 @@ template <int NZ, int NR>
 __global__ void __launch_bounds__(PipeCfg<NZ, NR>::THREADS, 1)
     k_lay_apply_pipe(LayArgs a, const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ty,
                      long npairs) {
+  pdl_enter();
   if (all_done(a)) return;
   using P = PipeCfg<NZ, NR>;
   using M = MmaCfg<NZ, NR>;
@@ -1211,11 +1215,13 @@ int apply_schur_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
   if (a.half) {
     PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_schur<NZ, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_lay_apply_schur<NZ, NR, true><<<grid, schur_threads<NZ, true>(), smem, P->stream>>>(a, x, y, P->ncols);
+    (void)launch_pdl(k_lay_apply_schur<NZ, NR, true>, dim3(grid), dim3(schur_threads<NZ, true>()), smem, P->stream, a, x,
+                     y, P->ncols);
   } else {
     PSFD_CUDA_TRY(cudaFuncSetAttribute(k_lay_apply_schur<NZ, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_lay_apply_schur<NZ, NR, false><<<grid, schur_threads<NZ, false>(), smem, P->stream>>>(a, x, y, P->ncols);
+    (void)launch_pdl(k_lay_apply_schur<NZ, NR, false>, dim3(grid), dim3(schur_threads<NZ, false>()), smem, P->stream, a,
+                     x, y, P->ncols);
   }
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -1247,7 +1253,8 @@ int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
         }
         const long npairs = layered_columns(P) / 2;
         const unsigned grid = (unsigned)std::min<long>(npairs, nsm);
-        k_lay_apply_pipe<NZ, NR><<<grid, C::THREADS, C::SMEM, P->stream>>>(a, tx, ty, npairs);
+        (void)launch_pdl(k_lay_apply_pipe<NZ, NR>, dim3(grid), dim3(C::THREADS), (size_t)C::SMEM, P->stream, a, tx, ty,
+                         npairs);
         PSFD_CHECK_LAUNCH();
         return PSFD_OK;
       }
@@ -1256,9 +1263,11 @@ int apply_nr(psfd_plan_s* P, const LayArgs& a, const cf* x, cf* y) {
   const size_t smem = (size_t)2 * LAY_GROUP * 3 * NZ * NR * sizeof(cf);
   const unsigned grid = (unsigned)(layered_columns(P) / LAY_GROUP);
   if (a.half)
-    k_lay_apply<NZ, NR, true><<<grid, apply_threads<NZ, true>(), smem, P->stream>>>(a, x, y, P->ncols);
+    (void)launch_pdl(k_lay_apply<NZ, NR, true>, dim3(grid), dim3(apply_threads<NZ, true>()), smem, P->stream, a, x, y,
+                     P->ncols);
   else
-    k_lay_apply<NZ, NR, false><<<grid, apply_threads<NZ, false>(), smem, P->stream>>>(a, x, y, P->ncols);
+    (void)launch_pdl(k_lay_apply<NZ, NR, false>, dim3(grid), dim3(apply_threads<NZ, false>()), smem, P->stream, a, x, y,
+                     P->ncols);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
