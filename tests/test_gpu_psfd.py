@@ -320,3 +320,37 @@ def test_refinement_residual_matches_oracle_at_1e10():
     bo = b[0].cpu().to(torch.complex128)
     r_or = O.rel_residual(g, res["E"][0].cpu(), fill.cpu().to(torch.float64), bo)
     assert abs(r_or - info["r_rel_output"]) <= 0.02 * r_or + 1e-12, (r_or, info["r_rel_output"])
+
+
+def test_bicgstab_iteration_cap_and_reuse_under_host_polling():
+    """BiCGSTAB enqueues one iteration at a time and stops on progress posted to host-mapped memory:
+    a cap below convergence stops at exactly maxit on every rhs, the history holds one entry per
+    iteration, and the next solve on the same plan (fresh progress words) converges; a rhs that
+    converges early (blank second rhs, b = 0) does not hold back the other."""
+    from paper_2607_25330_b300 import psfd
+    prob = problem(32, 32, 16, theta=6.0, pols=[0, 1])
+    a = I.mask_for(prob, 3)
+    plan = psfd.Plan(prob, nrhs=2)
+    fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+    b = plan.background(prob.stack(), fill, prob.pols)
+    for cap in (1, 5, 9):
+        res = plan.solve(b, tol=1e-12, maxit=cap, history=64)
+        for r in range(2):
+            assert res["info"][r]["status"] == psfd.PSFD_NOT_CONVERGED
+            assert res["info"][r]["iters"] == cap
+            h = res["history"][r]
+            assert np.all(h[:cap] > 0) and np.all(h[cap:] == 0)
+    full = plan.solve(b, tol=1e-6, maxit=2000)
+    assert all(i["status"] == 0 for i in full["info"]), full["info"]
+    # the refined solve counts inner iterations across outer steps against the same cap
+    res = plan.solve_ex(b, tol=1e-12, maxit=7, method=psfd.PSFD_BICGSTAB, inner_tol=1e-2)
+    for r in range(2):
+        assert res["info"][r]["status"] == psfd.PSFD_NOT_CONVERGED
+        assert res["info"][r]["iters"] <= 7
+    # one blank rhs: done at entry; the other still converges to the same field
+    b2 = b.clone()
+    b2[1] = 0
+    res2 = plan.solve(b2, tol=1e-6, maxit=2000)
+    assert res2["info"][1]["iters"] == 0 and float(res2["E"][1].abs().max()) == 0.0
+    assert res2["info"][0]["status"] == 0
+    assert rel_l2(res2["E"][0].cpu(), full["E"][0].cpu()) < 1e-4
