@@ -729,7 +729,8 @@ def run_batch(args, chunk=16):
     """The batching workload at its size: 64 Manhattan masks of uneven lateral size (64^2, 96^2,
     128^2, 256^2) and depth (nz 32, 48, 64, 96), each at 3 angles (4, 6, 8 deg) x TE + TM = 384
     right-hand sides, 192 operators.  Per chunk of operators: plans on their own streams, fill,
-    TMM + source, layered P (half precision; Schur form at nz 96), then psfd_solve_batched
+    TMM + source, layered P (Schur form for nz 32, 64 and 96: each operator's blocks serve one solve
+    and the Schur build is about 3x cheaper; half-precision full blocks at nz 48), then psfd_solve_batched
     (BiCGSTAB in FP64 refinement to 1e-6) over the chunk on concurrent streams; plans freed per
     chunk.  Everything from the device-resident mask to the FP64 residual is timed (host clock
     around the whole set; one device synchronisation per chunk)."""
@@ -751,6 +752,7 @@ def run_batch(args, chunk=16):
             idx = c0 + k                                 # one mask per 3 angles
             pl = psfd.Plan(pr, stream=st)
             pl.layered_storage(True)
+            pl.layered_form(True)      # blocks built for one solve: the cheaper Schur build
             with torch.cuda.stream(st):
                 fill = pl.mask_fill(dmasks[idx], pr.zprofile())
                 b = pl.background(pr.stack(), fill, pr.pols)

@@ -245,6 +245,18 @@ PSFD_API int psfd_layered_build(psfd_plan plan);
  * match complex64 storage.  PSFD_ERR_ARG for an unknown storage. */
 enum { PSFD_LAY_C64 = 0, PSFD_LAY_HALF = 1 };
 PSFD_API int psfd_layered_storage(psfd_plan plan, int storage);
+/* Form of the blocks, taking effect at the next psfd_layered_build (blocks of the
+ * other form are released then): PSFD_LAY_FORM_AUTO (default) full TE / TM
+ * inverses for nz <= 64 and the Schur form above; PSFD_LAY_FORM_SCHUR the Schur
+ * form for every nz that is a multiple of 32 (nz 16 and 48 keep the full blocks).
+ * The Schur build inverts two nz x nz blocks per column instead of an nz x nz and a
+ * 2 nz x 2 nz one (about 3x faster at nz = 64), while its apply is FP32-arithmetic
+ * bound (about 1.4x slower at nz = 64 than the half-precision tensor-core apply):
+ * the better choice when the blocks are built for a single solve.  The environment
+ * variable PSFD_LAY_SCHUR=1 requests the Schur form for every plan.  PSFD_ERR_ARG
+ * for a null plan or an unknown form. */
+enum { PSFD_LAY_FORM_AUTO = 0, PSFD_LAY_FORM_SCHUR = 1 };
+PSFD_API int psfd_layered_form(psfd_plan plan, int form);
 PSFD_API int psfd_layered_refresh(psfd_plan plan, double max_shift, int* rebuilt);
 PSFD_API size_t psfd_layered_bytes(psfd_plan plan);
 

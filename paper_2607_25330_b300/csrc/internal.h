@@ -97,6 +97,7 @@ struct psfd_plan_s {
   float* lay_scale = nullptr;           // their per-block power-of-two scales
   bool lay_half = false;
   bool lay_schur = false;               // blocks in the Schur form (TE^-1 and S^-1, 2 nz^2 per column)
+  int lay_form = 0;                     // requested form: PSFD_LAY_FORM_AUTO or PSFD_LAY_FORM_SCHUR
   std::vector<double> lay_mean;         // plane means of the fill the blocks were built for
   bool lay_built = false;
 };

@@ -1314,10 +1314,11 @@ int layered_supported(const psfd_plan_s* P) {
 bool layered_half(const psfd_plan_s* P) { return P->lay_half && !P->lay_schur; }
 
 // the Schur form for nz above 64 (a 2 nz x 2 nz TM block no longer fits one CTA's registers), and
-// for any nz with PSFD_LAY_SCHUR=1
+// for nz a multiple of 32 when the plan asks for it (psfd_layered_form) or PSFD_LAY_SCHUR=1
 bool layered_schur_for(const psfd_plan_s* P) {
   const char* e = getenv("PSFD_LAY_SCHUR");
-  return P->nz > 64 || (e && e[0] == '1' && P->nz % 32 == 0);
+  const bool asked = P->lay_form == PSFD_LAY_FORM_SCHUR || (e && e[0] == '1');
+  return P->nz > 64 || (asked && P->nz % 32 == 0);
 }
 
 // ky and -ky share their blocks when there is no Bloch shift along y (the blocks depend on kappa)
@@ -1382,6 +1383,15 @@ extern "C" int psfd_layered_storage(psfd_plan P, int storage) {
     layered_free(P);   // blocks are rebuilt in the new storage by the next psfd_layered_build
     P->lay_half = half;
   }
+  return PSFD_OK;
+}
+
+extern "C" int psfd_layered_form(psfd_plan P, int form) {
+  if (!P || (form != PSFD_LAY_FORM_AUTO && form != PSFD_LAY_FORM_SCHUR)) {
+    psfd_set_error("psfd_layered_form: null plan or unknown form");
+    return PSFD_ERR_ARG;
+  }
+  P->lay_form = form;   // the next psfd_layered_build releases blocks of the other form
   return PSFD_OK;
 }
 

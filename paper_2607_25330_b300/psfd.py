@@ -21,6 +21,7 @@ PSFD_OK, PSFD_ERR_ARG, PSFD_ERR_CUDA, PSFD_NOT_CONVERGED, PSFD_ERR_BREAKDOWN, PS
 PSFD_TE, PSFD_TM = 0, 1
 PSFD_PRECOND, PSFD_HYBRID, PSFD_ADJOINT, PSFD_LAYERED = 1, 2, 4, 8
 LAY_C64, LAY_HALF = 0, 1
+LAY_FORM_AUTO, LAY_FORM_SCHUR = 0, 1
 # use_precond values of the solves: identity, spectral damping M, layered-background P
 PC_NONE, PC_DAMPING, PC_LAYERED = 0, 1, 2
 PSFD_BICGSTAB, PSFD_GMRES = 0, 1
@@ -105,6 +106,7 @@ def lib() -> C.CDLL:
         "psfd_autotune": (i, [vp, C.POINTER(C.c_int)]),
         "psfd_layered_build": (i, [vp]),
         "psfd_layered_storage": (i, [vp, i]),
+        "psfd_layered_form": (i, [vp, i]),
         "psfd_width_metric": (i, [vp, vp, vp, i, i, i, C.c_float, i, d, C.POINTER(C.c_double)]),
         "psfd_set_plane_contrast": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "psfd_set_layer_stack_contrast": (i, [vp, C.POINTER(Stack), d, C.POINTER(C.c_float)]),
@@ -142,7 +144,7 @@ def declared_symbols() -> List[str]:
             "psfd_physics_loss", "psfd_precond", "psfd_solve", "psfd_solve_workspace_size",
             "psfd_set_history", "psfd_solve_ex", "psfd_solve_ex_workspace_size", "psfd_autotune", "psfd_solve_batched",
             "psfd_layered_build", "psfd_layered_refresh", "psfd_layered_bytes", "psfd_width_metric",
-            "psfd_layered_storage", "psfd_device_status",
+            "psfd_layered_storage", "psfd_layered_form", "psfd_device_status",
             "psfd_set_plane_contrast", "psfd_set_layer_stack_contrast",
             "fno_workspace_size", "fno_forward", "fno_train_workspace_size", "fno_forward_train", "fno_backward",
             "psfd_spectral_upsample",
@@ -349,6 +351,11 @@ class Plan:
     def layered_storage(self, half: bool) -> None:
         """Store the layered blocks in half precision (True) or complex64 (False) from the next build."""
         _check(lib().psfd_layered_storage(self.h, LAY_HALF if half else LAY_C64), "psfd_layered_storage")
+
+    def layered_form(self, schur: bool) -> None:
+        """Schur form of the blocks for nz a multiple of 32 (True), or the default rule (False), from the
+        next build."""
+        _check(lib().psfd_layered_form(self.h, LAY_FORM_SCHUR if schur else LAY_FORM_AUTO), "psfd_layered_form")
 
     def layered_bytes(self) -> int:
         return int(lib().psfd_layered_bytes(self.h))

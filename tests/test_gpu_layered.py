@@ -343,3 +343,37 @@ def test_schur_layered_solve_converges_fast(nz):
                         inner_tol=1e-3, out_c128=True)
     assert all(i["status"] == 0 and i["r_rel"] <= 1e-10 for i in ref["info"]), ref["info"]
     assert rel_l2(res["E"], ref["E"]) < 1e-4
+
+
+def test_layered_form_selects_the_schur_form_per_plan():
+    """psfd_layered_form: the Schur form on request for nz a multiple of 32 (the same operator as the
+    full blocks, two FP32 computations of one exact inverse), the full blocks at nz 48, and back to
+    the default rule at the next build."""
+    from paper_2607_25330_b300 import psfd
+    cols = 32 * 17
+    for nz in (64, 48):
+        prob = problem(32, 32, nz, theta=6.0, pols=[0, 1])
+        a = I.mask_for(prob, 7, "manhattan")
+        x = torch.from_numpy(I.random_field((2, 3, nz, 32, 32), 8)).to(torch.complex64).cuda()
+        plan = psfd.Plan(prob, nrhs=2)
+        plan.layered_storage(True)
+        fill = plan.mask_fill(torch.from_numpy(a), prob.zprofile())
+        plan.background(prob.stack(), fill, prob.pols)
+        plan.layered_build()
+        assert plan.layered_bytes() == cols * 5 * nz * nz * 4
+        full = plan.precond(x, flags=psfd.PSFD_LAYERED).cpu()
+        plan.layered_form(True)
+        plan.layered_build()
+        schur = nz % 32 == 0
+        assert plan.layered_bytes() == cols * (2 * nz * nz * 8 if schur else 5 * nz * nz * 4)
+        y = plan.precond(x, flags=psfd.PSFD_LAYERED).cpu()
+        if schur:
+            assert rel_l2(y, full) < 2e-3
+        else:
+            assert torch.equal(y, full)
+        plan.layered_form(False)
+        plan.layered_build()
+        assert plan.layered_bytes() == cols * 5 * nz * nz * 4
+        assert torch.equal(plan.precond(x, flags=psfd.PSFD_LAYERED).cpu(), full)
+    assert psfd.lib().psfd_layered_form(None, 0) == psfd.PSFD_ERR_ARG
+    assert psfd.lib().psfd_layered_form(plan.h, 7) == psfd.PSFD_ERR_ARG
