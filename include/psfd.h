@@ -19,9 +19,18 @@
  * - Every array pointer is caller-owned DEVICE memory unless the argument is
  *   documented as host memory.  Calls are asynchronous on the plan's stream
  *   unless stated otherwise; the library allocates only inside
- *   psfd_plan_create / psfd_background (plan-owned tables and scratch), on the
- *   first psfd_apply64 of a plan (plan-owned FP64 tables), inside psfd_solve
- *   when the caller passes no workspace (see psfd_solve_workspace_size) and, temporarily, inside psfd_spectral_upsample.
+ *   psfd_plan_create, psfd_mask_fill and psfd_background (plan-owned tables and
+ *   scratch; stream-ordered temporaries freed within the call),
+ *   psfd_layered_build (the blocks), on the first psfd_apply64 or refined solve
+ *   of a plan (plan-owned FP64 tables), on the first BiCGSTAB solve of a plan
+ *   (2 nrhs pinned, device-mapped host ints through which the kernels report
+ *   their progress to the host loop), inside psfd_solve / psfd_solve_ex when the
+ *   caller passes no workspace (see psfd_solve_workspace_size) and, temporarily,
+ *   inside psfd_spectral_upsample.
+ * - The kernels of a Krylov iteration are launched with programmatic dependent
+ *   launch; each one's first instruction waits for the completion of the work
+ *   before it on the stream, so stream order holds for anything the caller
+ *   interleaves.
  * - Return codes: PSFD_OK (0) or one of the PSFD_ERR_* / PSFD_NOT_CONVERGED
  *   values; psfd_last_error() returns a message for the last failing call on
  *   the calling thread.  Argument errors are detected before any launch.
