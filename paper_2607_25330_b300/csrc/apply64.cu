@@ -15,6 +15,7 @@
 #include "ff.cuh"
 #include "fft.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -43,6 +44,7 @@ struct Ax64 {
 // Same job structure as k_axial (mode A): jobs 0, 1, 3 copy the input.
 template <int NZ, int T, class C>
 __global__ void __launch_bounds__(64) k_axial64(Ax64 a) {
+  pdl_enter();
   constexpr int P = 32 / T;
   constexpr int R = NZ / T;
   using PZ = Pencil<NZ, T, P, C>;
@@ -176,6 +178,7 @@ struct Row64 {
 
 template <int NX, int T, int OP, class C>
 __global__ void __launch_bounds__(64) k_rows64(Row64 a) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1, C>;
   using RT = typename CTraits<C>::R;
@@ -236,6 +239,7 @@ struct Col64 {
 
 template <int NY, int T, int OP, class C>
 __global__ void __launch_bounds__(64) k_cols64(Col64 a) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P, C>;
   using RT = typename CTraits<C>::R;
@@ -292,9 +296,9 @@ int rows64_op(const Row64& a, int op, cudaStream_t s) {
   dim3 g((unsigned)((a.nrows + per - 1) / per));
   if (!g.x) return PSFD_OK;
   using C = ExtC<NX, T>;
-  if (op == R64_FWD) k_rows64<NX, T, R64_FWD, C><<<g, warps * 32, 0, s>>>(a);
-  else if (op == R64_INV) k_rows64<NX, T, R64_INV, C><<<g, warps * 32, 0, s>>>(a);
-  else k_rows64<NX, T, R64_FWD_SUB, C><<<g, warps * 32, 0, s>>>(a);
+  if (op == R64_FWD) (void)launch_pdl(k_rows64<NX, T, R64_FWD, C>, dim3(g), dim3(warps * 32), 0, s, a);
+  else if (op == R64_INV) (void)launch_pdl(k_rows64<NX, T, R64_INV, C>, dim3(g), dim3(warps * 32), 0, s, a);
+  else (void)launch_pdl(k_rows64<NX, T, R64_FWD_SUB, C>, dim3(g), dim3(warps * 32), 0, s, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -318,9 +322,9 @@ int cols64_op(const Col64& a, int op, cudaStream_t s) {
   dim3 g((unsigned)((a.ncolumns + per - 1) / per));
   if (!g.x) return PSFD_OK;
   using C = ExtC<NY, T>;
-  if (op == C64_FWD) k_cols64<NY, T, C64_FWD, C><<<g, warps * 32, 0, s>>>(a);
-  else if (op == C64_INV) k_cols64<NY, T, C64_INV, C><<<g, warps * 32, 0, s>>>(a);
-  else k_cols64<NY, T, C64_CONTRAST, C><<<g, warps * 32, 0, s>>>(a);
+  if (op == C64_FWD) (void)launch_pdl(k_cols64<NY, T, C64_FWD, C>, dim3(g), dim3(warps * 32), 0, s, a);
+  else if (op == C64_INV) (void)launch_pdl(k_cols64<NY, T, C64_INV, C>, dim3(g), dim3(warps * 32), 0, s, a);
+  else (void)launch_pdl(k_cols64<NY, T, C64_CONTRAST, C>, dim3(g), dim3(warps * 32), 0, s, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -358,7 +362,7 @@ int axial64_run(psfd_plan_s* P, const zd* x, zd* y) {
   const size_t smem = (size_t)warps * 4 * R * 32 * sizeof(zd);
   using C = ExtC<NZ, T>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_axial64<NZ, T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_axial64<NZ, T, C><<<g, warps * 32, smem, P->stream>>>(a);
+  (void)launch_pdl(k_axial64<NZ, T, C>, dim3(g), dim3(warps * 32), smem, P->stream, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }

@@ -411,6 +411,7 @@ int launch_vec(const VArgs& a, int nrhs, cudaStream_t s, int nblocks) {
 }
 
 __global__ void k_set_scalars(KScal* sc, int nrhs, double tol2, int maxit) {
+  pdl_enter();
   int r = threadIdx.x;
   if (r < nrhs) {
     KScal z{};
@@ -421,6 +422,7 @@ __global__ void k_set_scalars(KScal* sc, int nrhs, double tol2, int maxit) {
   }
 }
 __global__ void k_copy_bnorm(KScal* sc, int nrhs) {
+  pdl_enter();
   int r = threadIdx.x;
   if (r < nrhs) sc[r].bnorm2 = sc[r].res0;
 }
@@ -431,6 +433,7 @@ struct RhsBits {
   unsigned long long w[kMax / 64];
 };
 __global__ void k_set_flags(int* f, int nrhs, RhsBits b) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < nrhs) f[r] = (int)((b.w[r >> 6] >> (r & 63)) & 1ull);
 }
@@ -479,6 +482,7 @@ __device__ __forceinline__ bool skip_rhs(const GArgs& a, int rhs) { return a.mas
 // threads and blocks; a second Gram-Schmidt pass is taken whenever the first one
 // cancels more than half of ||w||^2, which also absorbs the rounding of these partials.
 __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
+  pdl_enter();
   const int rhs = blockIdx.y, chunk = blockIdx.z;
   if (skip_rhs(a, rhs)) return;
   const int i0 = chunk * GCH;
@@ -539,11 +543,13 @@ __global__ void __launch_bounds__(kThreads) k_gdot(GArgs a) {
 // per rhs: keep the norm of w before orthogonalisation (res0 -> tt), zero the second-pass
 // coefficients, and after the first pass decide whether a second one is needed
 __global__ void k_gsave(double2* h2, int nrhs, int nv) {
+  pdl_enter();
   const int r = blockIdx.x;
   if (r >= nrhs) return;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) h2[r * GMAX + i] = make_double2(0.0, 0.0);
 }
 __global__ void k_greorth(const KScal* sc, const int* skip, int* skip2, int nrhs) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs) return;
   // second pass when ||w_after||^2 < ||w_before||^2 / 2 (Daniel-Gragg-Kaufman-Stewart, eta = 1/sqrt(2))
@@ -553,6 +559,7 @@ __global__ void k_greorth(const KScal* sc, const int* skip, int* skip2, int nrhs
 // w -= sum_i h[i] V_i  (h from hout)   or   y += sum_i z[i] V_i (ADD, count jd per rhs)
 template <bool ADD>
 __global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
+  pdl_enter();
   const int rhs = blockIdx.y;
   if (skip_rhs(a, rhs)) return;
   const int nv = ADD ? a.gs[rhs].jd : a.nv;
@@ -619,6 +626,7 @@ __global__ void __launch_bounds__(kThreads) k_gupd(GArgs a) {
 
 // V_0 = r / beta, or V_{j+1} = w / H[j+1][j]
 __global__ void k_gscale(GArgs a, bool first) {
+  pdl_enter();
   const int rhs = blockIdx.y;
   if (skip_rhs(a, rhs)) return;
   const GState& G = a.gs[rhs];
@@ -633,6 +641,7 @@ __global__ void k_gscale(GArgs a, bool first) {
 }
 
 __global__ void k_ginit(GState* gs, const KScal* sc, int nrhs, int m, double tol2, int maxit) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs) return;
   GState& G = gs[r];
@@ -643,6 +652,7 @@ __global__ void k_ginit(GState* gs, const KScal* sc, int nrhs, int m, double tol
 // start of a cycle: beta = ||r|| (from res1 of the scalar block); skip[r] = 1 for
 // right-hand sides that are finished
 __global__ void k_gstart(GState* gs, KScal* sc, int* skip, int* done, int nrhs) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs) return;
   GState& G = gs[r];
@@ -665,6 +675,7 @@ __global__ void k_gstart(GState* gs, KScal* sc, int* skip, int* done, int nrhs) 
 // Hessenberg column j: h = h1 + h2 (two CGS passes), H[j+1][j] = ||w||, Givens update
 __global__ void k_givens(GState* gs, const double2* h1, const double2* h2, const KScal* sc, int* skip,
                          double* hist, int hist_cap, int nrhs, int j) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs || skip[r]) return;
   GState& G = gs[r];
@@ -705,6 +716,7 @@ __global__ void k_givens(GState* gs, const double2* h1, const double2* h2, const
 
 // z = H^-1 g on the leading jd x jd triangle (FP64 back substitution)
 __global__ void k_gtri(GState* gs, int nrhs) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs) return;
   GState& G = gs[r];
@@ -724,6 +736,7 @@ __global__ void k_gtri(GState* gs, int nrhs) {
 }
 
 __global__ void k_gfinish(GState* gs, KScal* sc, int nrhs) {
+  pdl_enter();
   const int r = threadIdx.x;
   if (r >= nrhs) return;
   sc[r].iters = gs[r].iters;
@@ -890,7 +903,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
   PSFD_CUDA_TRY(cudaMemsetAsync(w.done, 0, sizeof(int) * nr, st));
   PSFD_CUDA_TRY(cudaMemsetAsync(w.y, 0, vbytes, st));
   PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr * nch_max, st));
-  k_ginit<<<1, tpb, 0, st>>>(w.gs, w.sc, nr, m, tol * tol, maxit);
+  (void)launch_pdl(k_ginit, dim3(1), dim3(tpb), 0, st, w.gs, w.sc, nr, m, tol * tol, maxit);
   PSFD_CHECK_LAUNCH();
   GArgs g{};
   g.V = w.V; g.vs = vs; g.n = n; g.gs = w.gs; g.partials = w.partials; g.counters = w.counters; g.y = w.y;
@@ -911,7 +924,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
     va.v2 = w.V;
     if ((rc = launch_vec<OK_SUB>(va, nr, st, nb))) return rc;
     first = false;
-    k_gstart<<<1, tpb, 0, st>>>(w.gs, w.sc, w.active, w.done, nr);
+    (void)launch_pdl(k_gstart, dim3(1), dim3(tpb), 0, st, w.gs, w.sc, w.active, w.done, nr);
     PSFD_CHECK_LAUNCH();
     PSFD_CUDA_TRY(cudaMemcpyAsync(hv.data(), w.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
     PSFD_CUDA_TRY(cudaStreamSynchronize(st));
@@ -919,7 +932,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
     for (int r = 0; r < nr; ++r) any = any || !hv[r];
     if (!any) break;
     g.mask = w.active; g.w = w.V; g.j = 0;
-    k_gscale<<<dim3(nb, nr), kThreads, 0, st>>>(g, true);
+    (void)launch_pdl(k_gscale, dim3(nb, nr), dim3(kThreads), 0, st, g, true);
     PSFD_CHECK_LAUNCH();
     for (int j = 0; j < m; ++j) {
       cf* Vj = w.V + (long)j * vs;
@@ -927,7 +940,7 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
       if ((rc = apply_hybrid(P, Vj, Wn, aflags, w.active))) return rc;
       g.w = Wn; g.nv = j + 1; g.j = j;
       const int nch = (j + 1 + GCH - 1) / GCH;
-      k_gsave<<<nr, 64, 0, st>>>(w.h2, nr, j + 1);
+      (void)launch_pdl(k_gsave, dim3(nr), dim3(64), 0, st, w.h2, nr, j + 1);
       PSFD_CHECK_LAUNCH();
       {
         // dot (+ ||w||^2 before): read w + (j+1) basis vectors; update (+ ||w||^2 after):
@@ -935,28 +948,28 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
         StageScope sc(st, ST_KRYLOV, (2.0 * (j + 1) + 3.0) * nr * n * sizeof(cf));
         g.hout = w.h1;
         g.save_norm = true;
-        k_gdot<<<dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), kThreads, 0, st>>>(g);
+        (void)launch_pdl(k_gdot, dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), dim3(kThreads), 0, st, g);
         PSFD_CHECK_LAUNCH();
         g.save_norm = false;
-        k_gupd<false><<<dim3(nbu, nr), kThreads, 0, st>>>(g);
+        (void)launch_pdl(k_gupd<false>, dim3(nbu, nr), dim3(kThreads), 0, st, g);
         PSFD_CHECK_LAUNCH();
       }
-      k_greorth<<<1, tpb, 0, st>>>(w.sc, w.active, w.skip2, nr);
+      (void)launch_pdl(k_greorth, dim3(1), dim3(tpb), 0, st, w.sc, w.active, w.skip2, nr);
       PSFD_CHECK_LAUNCH();
       {
         StageScope sc(st, ST_KRYLOV, 0.0);   // second pass: data-dependent, not counted as algorithmic
         const int* keep = g.mask;
         g.mask = w.skip2;
         g.hout = w.h2;
-        k_gdot<<<dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), kThreads, 0, st>>>(g);
+        (void)launch_pdl(k_gdot, dim3(one_wave<k_gdot>(nb, nr * nch), nr, nch), dim3(kThreads), 0, st, g);
         PSFD_CHECK_LAUNCH();
-        k_gupd<false><<<dim3(nbu, nr), kThreads, 0, st>>>(g);
+        (void)launch_pdl(k_gupd<false>, dim3(nbu, nr), dim3(kThreads), 0, st, g);
         PSFD_CHECK_LAUNCH();
         g.mask = keep;
       }
-      k_givens<<<1, tpb, 0, st>>>(w.gs, w.h1, w.h2, w.sc, w.active, va.hist, va.hist_cap, nr, j);
+      (void)launch_pdl(k_givens, dim3(1), dim3(tpb), 0, st, w.gs, w.h1, w.h2, w.sc, w.active, va.hist, va.hist_cap, nr, j);
       PSFD_CHECK_LAUNCH();
-      k_gscale<<<dim3(nb, nr), kThreads, 0, st>>>(g, false);
+      (void)launch_pdl(k_gscale, dim3(nb, nr), dim3(kThreads), 0, st, g, false);
       PSFD_CHECK_LAUNCH();
       if ((j & 3) == 3 || j == m - 1) {
         PSFD_CUDA_TRY(cudaMemcpyAsync(hv.data(), w.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
@@ -967,13 +980,13 @@ static int gmres_loop(psfd_plan_s* P, SolveWs& w, VArgs va, double tol, int maxi
       }
     }
     // y += V z for every rhs that ran this cycle
-    k_gtri<<<1, tpb, 0, st>>>(w.gs, nr);
+    (void)launch_pdl(k_gtri, dim3(1), dim3(tpb), 0, st, w.gs, nr);
     PSFD_CHECK_LAUNCH();
     g.mask = nullptr;  // every rhs with jd > 0 updates y
-    k_gupd<true><<<dim3(nby, nr), kThreads, 0, st>>>(g);
+    (void)launch_pdl(k_gupd<true>, dim3(nby, nr), dim3(kThreads), 0, st, g);
     PSFD_CHECK_LAUNCH();
   }
-  k_gfinish<<<1, tpb, 0, st>>>(w.gs, w.sc, nr);
+  (void)launch_pdl(k_gfinish, dim3(1), dim3(tpb), 0, st, w.gs, w.sc, nr);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -1020,7 +1033,7 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
   };
 
   PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr, st));
-  k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, tol * tol, maxit);
+  (void)launch_pdl(k_set_scalars, dim3(1), dim3(tpb), 0, st, w.sc, nr, tol * tol, maxit);
   PSFD_CHECK_LAUNCH();
   VArgs va{};
   va.n = n; va.sc = w.sc; va.done = w.done; va.partials = w.partials; va.counters = w.counters;
@@ -1035,7 +1048,7 @@ extern "C" int psfd_solve(psfd_plan P, const psfd_c64* b, const psfd_c64* x0, ps
   if ((rc = launch_lateral_transform(P, w.bH, nplanes, true, us))) return fail(rc);
   va.v0 = w.bH;
   if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return fail(rc);
-  k_copy_bnorm<<<1, tpb, 0, st>>>(w.sc, nr);
+  (void)launch_pdl(k_copy_bnorm, dim3(1), dim3(tpb), 0, st, w.sc, nr);
   PSFD_CHECK_LAUNCH();
   // c = b - A E_base (the right-hand side of A M y = c)
   if (x0) {
@@ -1119,6 +1132,7 @@ struct V64Args {
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_v64(V64Args a) {
+  pdl_enter();
   const int rhs = blockIdx.y;
   const long off = (long)rhs * a.n;
   const long stride = (long)gridDim.x * blockDim.x;
@@ -1162,7 +1176,7 @@ __global__ void __launch_bounds__(kThreads) k_v64(V64Args a) {
 template <int OP>
 int launch_v64(const V64Args& a, int nrhs, cudaStream_t s, int nb) {
   StageScope sc(s, ST_KRYLOV);
-  k_v64<OP><<<dim3(nb, nrhs), kThreads, 0, s>>>(a);
+  (void)launch_pdl(k_v64<OP>, dim3(nb, nrhs), dim3(kThreads), 0, s, a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -1243,7 +1257,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
 
   const int nch_max = (GMAX + GCH - 1) / GCH;
   PSFD_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nr * (o->method == PSFD_GMRES ? nch_max : 1), st));
-  k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, 0.0, 0);
+  (void)launch_pdl(k_set_scalars, dim3(1), dim3(tpb), 0, st, w.sc, nr, 0.0, 0);
   PSFD_CHECK_LAUNCH();
   V64Args a64{};
   a64.n = n; a64.sc = w.sc; a64.partials = w.partials; a64.counters = w.counters;
@@ -1327,7 +1341,7 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
       RhsBits bits{};
       for (int r = 0; r < nr; ++r)
         if (conv[r]) bits.w[r >> 6] |= 1ull << (r & 63);
-      k_set_flags<<<(nr + 255) / 256, 256, 0, st>>>(dskip, nr, bits);
+      (void)launch_pdl(k_set_flags, dim3((nr + 255) / 256), dim3(256), 0, st, dskip, nr, bits);
       PSFD_CHECK_LAUNCH();
     } else {
       PSFD_CUDA_TRY(cudaMemcpyAsync(dskip, conv.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
@@ -1341,12 +1355,12 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
     for (int r = 0; r < nr; ++r)
       if (!conv[r] && rr[r] > 0) itol = std::min(itol, 0.5 * o->tol * sqrt(bnorm2[r] / rr[r]));
     itol = std::max(itol, o->inner_tol);
-    k_set_scalars<<<1, tpb, 0, st>>>(w.sc, nr, itol * itol, inner_max);
+    (void)launch_pdl(k_set_scalars, dim3(1), dim3(tpb), 0, st, w.sc, nr, itol * itol, inner_max);
     PSFD_CHECK_LAUNCH();
     va.use_done = false;
     va.v0 = w.r;
     if ((rc = launch_vec<OK_NORM>(va, nr, st, nb))) return fail(rc);
-    k_copy_bnorm<<<1, tpb, 0, st>>>(w.sc, nr);
+    (void)launch_pdl(k_copy_bnorm, dim3(1), dim3(tpb), 0, st, w.sc, nr);
     PSFD_CHECK_LAUNCH();
     if (o->method == PSFD_BICGSTAB) rc = bicgstab_loop(P, w, va, inner_max, aflags, nb);
     else rc = gmres_loop(P, w, va, itol, inner_max, o->restart, aflags, nb);
