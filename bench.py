@@ -151,7 +151,7 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from
 # one ncu capture of the current kernel version on this workload (profiles/k_lay_apply_*.md):
 # reported as roofline.traffic when the bench runs the same kernel on the same workload
-NCU_TRAFFIC = {("precond", "manhattan_128x128x64", 2, True): 732.030464e6 + 46.136576e6}
+NCU_TRAFFIC = {("precond", "manhattan_128x128x64", 2, True): 732.049664e6 + 46.290944e6}
 
 
 def fp32_peak_tflops():
