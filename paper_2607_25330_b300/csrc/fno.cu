@@ -22,6 +22,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -46,6 +47,7 @@ __device__ __forceinline__ int fft_to_kept(int idx, int m, int n) {
 template <int NX, int T>
 __global__ void __launch_bounds__(128) k_xfwd(const float* __restrict__ v, cf* __restrict__ T1, long nrows, int mx,
                                               const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
   __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(128) k_xfwd(const float* __restrict__ v, cf* _
 template <int NY, int T>
 __global__ void __launch_bounds__(128) k_yfwd(const cf* __restrict__ T1, cf* __restrict__ V, Dims d,
                                               const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
   __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -110,6 +113,7 @@ constexpr int MIX_TN = 64;
 __global__ void __launch_bounds__(256) k_mix(const cf* __restrict__ V, cf* __restrict__ U, const cf* __restrict__ K,
                                              int C, long NB, int mx, int MX, int offy, int offx, bool conjT = false,
                                              bool round_v = true, bool round_k = true) {
+  pdl_enter();
   extern __shared__ float sm[];
   float* Kr = sm;                       // [C][C]
   float* Ki = Kr + C * C;
@@ -159,6 +163,7 @@ constexpr int GRAD_CHUNK = 2048;
 __global__ void __launch_bounds__(256) k_mixgrad(const cf* __restrict__ Ubar, const cf* __restrict__ V,
                                                  float* __restrict__ dK, int C, long NB, int mx, int MX, int offy,
                                                  int offx, float scale) {
+  pdl_enter();
   __shared__ float Ur[32][MIX_TN + 1], Ui[32][MIX_TN + 1], Vr[32][MIX_TN + 1], Vi[32][MIX_TN + 1];
   const long mode = blockIdx.y;
   const int jy = (int)(mode / mx), jx = (int)(mode - (long)jy * mx);
@@ -209,6 +214,7 @@ __global__ void __launch_bounds__(256) k_mixgrad(const cf* __restrict__ Ubar, co
 template <int NY, int T>
 __global__ void __launch_bounds__(128) k_yinv(const cf* __restrict__ U, cf* __restrict__ T2, Dims d,
                                               const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NY / T;
   using PY = Pencil<NY, T, P>;
   __shared__ cf xch[4][PY::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(128) k_yinv(const cf* __restrict__ U, cf* __re
 template <int NX, int T>
 __global__ void __launch_bounds__(128) k_xinv(const cf* __restrict__ T2, float* __restrict__ out, long nrows, int mx,
                                               float scale, const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NX / T;
   using PX = Pencil<NX, T, 1>;
   __shared__ cf xch[4][PX::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -269,6 +276,7 @@ __global__ void __launch_bounds__(128) k_xinv(const cf* __restrict__ T2, float* 
 template <int NZ, int T>
 __global__ void __launch_bounds__(128) k_zfwd(const float* __restrict__ u, cf* __restrict__ W, Dims d,
                                               const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NZ / T;
   using PZ = Pencil<NZ, T, P>;
   __shared__ cf xch[4][PZ::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -299,6 +307,7 @@ __global__ void __launch_bounds__(128) k_zfwd(const float* __restrict__ u, cf* _
 template <int NZ, int T>
 __global__ void __launch_bounds__(128) k_zinv(const cf* __restrict__ U, float* __restrict__ out, Dims d, float scale,
                                               const cf* __restrict__ tw) {
+  pdl_enter();
   constexpr int P = 32 / T, R = NZ / T;
   using PZ = Pencil<NZ, T, P>;
   __shared__ cf xch[4][PZ::TILE];   // per-warp exchange tiles (4 warps per block)
@@ -330,6 +339,7 @@ __global__ void __launch_bounds__(128) k_zinv(const cf* __restrict__ U, float* _
 // ---------------------------------------------------------------- pointwise layers
 __global__ void k_lift(const float* __restrict__ a, float* __restrict__ v, const float* __restrict__ W,
                        const float* __restrict__ bias, int B, int C, int nx, int ny, int nz) {
+  pdl_enter();
   const long N = (long)nx * ny * nz;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)B * N) return;
@@ -348,6 +358,7 @@ __global__ void __launch_bounds__(128) k_mlp(const float* vin, float* vout, cons
                                              const float* __restrict__ uz, const float* __restrict__ W1,
                                              const float* __restrict__ b1, const float* __restrict__ W2,
                                              const float* __restrict__ b2, long N, int B, bool outer_gelu) {
+  pdl_enter();
   __shared__ float w1[H * C], w2[C * H], sb1[H], sb2[C];
   for (int e = threadIdx.x; e < H * C; e += blockDim.x) { w1[e] = W1[e]; w2[e] = W2[e]; }
   for (int e = threadIdx.x; e < H; e += blockDim.x) sb1[e] = b1[e];
@@ -377,6 +388,7 @@ template <int C, int Q>
 __global__ void __launch_bounds__(128) k_proj(const float* __restrict__ v, cf* __restrict__ E, const float* __restrict__ Q1,
                                               const float* __restrict__ qb1, const float* __restrict__ Q2,
                                               const float* __restrict__ qb2, long N, int B) {
+  pdl_enter();
   __shared__ float q1[Q * C], q2[6 * Q], sb1[Q], sb2[6];
   for (int e = threadIdx.x; e < Q * C; e += blockDim.x) q1[e] = Q1[e];
   for (int e = threadIdx.x; e < 6 * Q; e += blockDim.x) q2[e] = Q2[e];
@@ -448,6 +460,7 @@ __global__ void __launch_bounds__(BW_TILE) k_mlp_bwd(const float* __restrict__ u
                                                    float* __restrict__ dW1, float* __restrict__ db1,
                                                    float* __restrict__ dW2, float* __restrict__ db2, long N, int B,
                                                    bool outer_gelu) {
+  pdl_enter();
   extern __shared__ float sm[];
   float* w1 = sm;                  // [H][C]
   float* w2 = w1 + H * C;          // [C][H]
@@ -541,6 +554,7 @@ __global__ void __launch_bounds__(BW_TILE) k_proj_bwd(const float* __restrict__ 
                                                     const float* __restrict__ qb1, const float* __restrict__ Q2,
                                                     float* __restrict__ dQ1, float* __restrict__ dqb1,
                                                     float* __restrict__ dQ2, float* __restrict__ dqb2, long N, int B) {
+  pdl_enter();
   static_assert(Q == 128 && BW_TILE == 128, "thread-to-block mapping assumes Q = 128 = BW_TILE");
   extern __shared__ float sm[];
   float* q1 = sm;                  // [Q][C]
@@ -630,6 +644,7 @@ __global__ void __launch_bounds__(BW_TILE) k_proj_bwd(const float* __restrict__ 
 __global__ void __launch_bounds__(256) k_lift_bwd(const float* __restrict__ a, const float* __restrict__ dv0,
                                                 float* __restrict__ dW, float* __restrict__ db, int B, int C, int nx,
                                                 int ny, int nz) {
+  pdl_enter();
   __shared__ float acc[32 * 5];
   for (int e = threadIdx.x; e < 32 * 5; e += blockDim.x) acc[e] = 0.f;
   __syncthreads();
@@ -663,6 +678,7 @@ __global__ void __launch_bounds__(256) k_lift_bwd(const float* __restrict__ a, c
 }
 
 __global__ void k_axpy_f(float* __restrict__ y, const float* __restrict__ x, long n) {
+  pdl_enter();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
 }
@@ -781,10 +797,10 @@ static Dims make_dims(const fno_weights_t* w, int B, int nx, int ny, int nz) {
 static bool xy_analysis(const Dims& d, const FnoWs& ws, const float* in, cf* V, cudaStream_t s) {
   bool bad = false;
   const long rows = (long)d.B * d.C * d.nz * d.ny, ycols = (long)d.B * d.C * d.nz * d.mx;
-#define XF(NX_, T_, ...) k_xfwd<NX_, T_><<<blocks_for(rows, 4 * (32 / T_)), 128, 0, s>>>(in, ws.T1, rows, d.mx, ws.twx)
+#define XF(NX_, T_, ...) (void)launch_pdl(k_xfwd<NX_, T_>, dim3(blocks_for(rows, 4 * (32 / T_))), dim3(128), 0, s, in, ws.T1, rows, d.mx, ws.twx)
   LAT_CASES(XF, d.nx, 0);
 #undef XF
-#define YF(NY_, T_, ...) k_yfwd<NY_, T_><<<blocks_for(ycols, 4 * (32 / T_)), 128, 0, s>>>(ws.T1, V, d, ws.twy)
+#define YF(NY_, T_, ...) (void)launch_pdl(k_yfwd<NY_, T_>, dim3(blocks_for(ycols, 4 * (32 / T_))), dim3(128), 0, s, ws.T1, V, d, ws.twy)
   LAT_CASES(YF, d.ny, 0);
 #undef YF
   return !bad;
@@ -793,10 +809,10 @@ static bool xy_analysis(const Dims& d, const FnoWs& ws, const float* in, cf* V, 
 static bool xy_synthesis(const Dims& d, const FnoWs& ws, const cf* U, float* out, float scale, cudaStream_t s) {
   bool bad = false;
   const long rows = (long)d.B * d.C * d.nz * d.ny, ycols = (long)d.B * d.C * d.nz * d.mx;
-#define YI(NY_, T_, ...) k_yinv<NY_, T_><<<blocks_for(ycols, 4 * (32 / T_)), 128, 0, s>>>(U, ws.T2, d, ws.twy)
+#define YI(NY_, T_, ...) (void)launch_pdl(k_yinv<NY_, T_>, dim3(blocks_for(ycols, 4 * (32 / T_))), dim3(128), 0, s, U, ws.T2, d, ws.twy)
   LAT_CASES(YI, d.ny, 0);
 #undef YI
-#define XI(NX_, T_, ...) k_xinv<NX_, T_><<<blocks_for(rows, 4 * (32 / T_)), 128, 0, s>>>(ws.T2, out, rows, d.mx, scale, ws.twx)
+#define XI(NX_, T_, ...) (void)launch_pdl(k_xinv<NX_, T_>, dim3(blocks_for(rows, 4 * (32 / T_))), dim3(128), 0, s, ws.T2, out, rows, d.mx, scale, ws.twx)
   LAT_CASES(XI, d.nx, 0);
 #undef XI
   return !bad;
@@ -804,7 +820,7 @@ static bool xy_synthesis(const Dims& d, const FnoWs& ws, const cf* U, float* out
 static bool z_analysis(const Dims& d, const FnoWs& ws, const float* in, cf* W, cudaStream_t s) {
   bool bad = false;
   const long zcols = (long)d.B * d.C * d.nx * d.ny;
-#define ZF(NZ_, T_, ...) k_zfwd<NZ_, T_><<<blocks_for(zcols, 4 * (32 / T_)), 128, 0, s>>>(in, W, d, ws.twz)
+#define ZF(NZ_, T_, ...) (void)launch_pdl(k_zfwd<NZ_, T_>, dim3(blocks_for(zcols, 4 * (32 / T_))), dim3(128), 0, s, in, W, d, ws.twz)
   COL_CASES(ZF, d.nz, 0);
 #undef ZF
   return !bad;
@@ -812,7 +828,7 @@ static bool z_analysis(const Dims& d, const FnoWs& ws, const float* in, cf* W, c
 static bool z_synthesis(const Dims& d, const FnoWs& ws, const cf* U, float* out, float scale, cudaStream_t s) {
   bool bad = false;
   const long zcols = (long)d.B * d.C * d.nx * d.ny;
-#define ZI(NZ_, T_, ...) k_zinv<NZ_, T_><<<blocks_for(zcols, 4 * (32 / T_)), 128, 0, s>>>(U, out, d, scale, ws.twz)
+#define ZI(NZ_, T_, ...) (void)launch_pdl(k_zinv<NZ_, T_>, dim3(blocks_for(zcols, 4 * (32 / T_))), dim3(128), 0, s, U, out, d, scale, ws.twz)
   COL_CASES(ZI, d.nz, 0);
 #undef ZI
   return !bad;
@@ -835,7 +851,7 @@ static void mix_xy(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint,
     return;
   }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)(d.mx * d.my));
-  k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2,
+  (void)launch_pdl(k_mix, dim3(g), dim3(256), mix_smem_bytes(d.C), s, V, U, K, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2,
                                            adjoint, !adjoint && !exact, !exact);
 }
 static void mix_z(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, cudaStream_t s) {
@@ -846,18 +862,18 @@ static void mix_z(const Dims& d, const cf* V, cf* U, const cf* K, bool adjoint, 
     return;
   }
   dim3 g(blocks_for(NB, MIX_TN), (unsigned)d.mz);
-  k_mix<<<g, 256, mix_smem_bytes(d.C), s>>>(V, U, K, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, adjoint, !adjoint && !exact,
+  (void)launch_pdl(k_mix, dim3(g), dim3(256), mix_smem_bytes(d.C), s, V, U, K, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, adjoint, !adjoint && !exact,
                                            !exact);
 }
 static void mixgrad_xy(const Dims& d, const cf* Ubar, const cf* V, cf* dK, float scale, cudaStream_t s) {
   const long NB = (long)d.B * d.nz;
   dim3 g(blocks_for(NB, GRAD_CHUNK), (unsigned)(d.mx * d.my));
-  k_mixgrad<<<g, 256, 0, s>>>(Ubar, V, (float*)dK, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2, scale);
+  (void)launch_pdl(k_mixgrad, dim3(g), dim3(256), 0, s, Ubar, V, (float*)dK, d.C, NB, d.mx, d.MX, (d.MY - d.my) / 2, (d.MX - d.mx) / 2, scale);
 }
 static void mixgrad_z(const Dims& d, const cf* Ubar, const cf* V, cf* dK, float scale, cudaStream_t s) {
   const long NB = (long)d.B * d.nx * d.ny;
   dim3 g(blocks_for(NB, GRAD_CHUNK), (unsigned)d.mz);
-  k_mixgrad<<<g, 256, 0, s>>>(Ubar, V, (float*)dK, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, scale);
+  (void)launch_pdl(k_mixgrad, dim3(g), dim3(256), 0, s, Ubar, V, (float*)dK, d.C, NB, 1, 1, (d.MZ - d.mz) / 2, 0, scale);
 }
 
 static int upload_twiddles(const FnoWs& ws, int nx, int ny, int nz, cudaStream_t s) {
@@ -916,7 +932,7 @@ static int fno_run(const fno_weights_t* w, const float* a, int B, int nx, int ny
   // layer inputs: in checkpoint mode v_l lives in vL[l] (kept), else the layers update ws.v in place
   auto vin = [&](int l) -> float* { return mode == FNO_CHECKPOINT ? ws.vL + l * ws.act : ws.v; };
   const bool tc = fno_mlp_tc_enabled(C, w->dh, w->dq);
-  k_lift<<<blocks_for((long)B * N, 256), 256, 0, s>>>(a, vin(0), w->lift_w, w->lift_b, B, C, nx, ny, nz);
+  (void)launch_pdl(k_lift, dim3(blocks_for((long)B * N, 256)), dim3(256), 0, s, a, vin(0), w->lift_w, w->lift_b, B, C, nx, ny, nz);
   PSFD_CHECK_LAUNCH();
   for (int l = 0; l < L; ++l) {
     const bool st = mode == FNO_STORE;
@@ -933,7 +949,7 @@ static int fno_run(const fno_weights_t* w, const float* a, int B, int nx, int ny
                       w->w2 + (size_t)l * 32 * 64, w->b2 + (size_t)l * 32, N, B, l < L - 1, s);
       if (rc) return rc;
     } else {
-      k_mlp<32, 64><<<blocks_for((long)B * N, 128), 128, 0, s>>>(
+      (void)launch_pdl(k_mlp<32, 64>, dim3(blocks_for((long)B * N, 128)), dim3(128), 0, s,
           vin(l), vout, uxy, uz, w->w1 + (size_t)l * 64 * 32, w->b1 + (size_t)l * 64, w->w2 + (size_t)l * 32 * 64,
           w->b2 + (size_t)l * 32, N, B, l < L - 1);
       PSFD_CHECK_LAUNCH();
@@ -941,7 +957,7 @@ static int fno_run(const fno_weights_t* w, const float* a, int B, int nx, int ny
   }
   if (!ok) { psfd_set_error("fno: unsupported size"); return PSFD_ERR_ARG; }
   if (tc) return fno_proj_tc(ws.v, (cf*)E_out, w->q1, w->qb1, w->q2, w->qb2, N, B, s);
-  k_proj<32, 128><<<blocks_for((long)B * N, 128), 128, 0, s>>>(ws.v, (cf*)E_out, w->q1, w->qb1, w->q2, w->qb2, N, B);
+  (void)launch_pdl(k_proj<32, 128>, dim3(blocks_for((long)B * N, 128)), dim3(128), 0, s, ws.v, (cf*)E_out, w->q1, w->qb1, w->q2, w->qb2, N, B);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -1021,7 +1037,7 @@ extern "C" int fno_backward(const fno_weights_t* w, const fno_grads_t* g, const 
   const float sxy = 1.0f / ((float)nx * (float)ny), sz = 1.0f / (float)nz;
   const unsigned pw_all = blocks_for((long)B * N, BW_TILE);
   const unsigned pw_blocks = pw_all < 4u * 148u ? pw_all : 4u * 148u;
-  k_proj_bwd<32, 128><<<pw_blocks, BW_TILE, proj_bwd_smem<32, 128>(), s>>>(
+  (void)launch_pdl(k_proj_bwd<32, 128>, dim3(pw_blocks), dim3(BW_TILE), proj_bwd_smem<32, 128>(), s,
       ws.v, (const cf*)dE, ws.dv, w->q1, w->qb1, w->q2, g->q1, g->qb1, g->q2, g->qb2, N, B);
   PSFD_CHECK_LAUNCH();
   bool ok = true;
@@ -1041,7 +1057,7 @@ extern "C" int fno_backward(const fno_weights_t* w, const fno_grads_t* g, const 
     cf* dKxy = (cf*)g->kxy + (size_t)l * w->my * w->mx * C * C;
     cf* dKz = (cf*)g->kz + (size_t)l * w->mz * C * C;
     // MLP (Eq. 4): dh = d(loss)/d(uxy + uz); the residual keeps dv as part of d(loss)/d(v_l)
-    k_mlp_bwd<32, 64><<<pw_blocks, BW_TILE, mlp_bwd_smem<32, 64>(), s>>>(
+    (void)launch_pdl(k_mlp_bwd<32, 64>, dim3(pw_blocks), dim3(BW_TILE), mlp_bwd_smem<32, 64>(), s,
         uxy, uz, ws.dv, ws.dh, w->w1 + (size_t)l * 64 * 32, w->b1 + (size_t)l * 64, w->w2 + (size_t)l * 32 * 64,
         w->b2 + (size_t)l * 32, g->w1 + (size_t)l * 64 * 32, g->b1 + (size_t)l * 64, g->w2 + (size_t)l * 32 * 64,
         g->b2 + (size_t)l * 32, N, B, l < w->layers - 1);
@@ -1051,18 +1067,18 @@ extern "C" int fno_backward(const fno_weights_t* w, const fno_grads_t* g, const 
     mixgrad_z(d, ws.Wg, Wm, dKz, sz, s);
     mix_z(d, ws.Wg, ws.Wu, Kz, true, s);
     ok &= z_synthesis(d, ws, ws.Wu, ws.tmp, sz, s);
-    k_axpy_f<<<blocks_for(nact, 256), 256, 0, s>>>(ws.dh, ws.tmp, nact);
+    (void)launch_pdl(k_axpy_f, dim3(blocks_for(nact, 256)), dim3(256), 0, s, ws.dh, ws.tmp, nact);
     PSFD_CHECK_LAUNCH();
     // xy branch adjoint (Eq. 2): dv += XY^T d(uxy); dKxy += (1/(nx ny)) F_xy(d uxy) conj(V)
     ok &= xy_analysis(d, ws, ws.dh, ws.Vg, s);
     mixgrad_xy(d, ws.Vg, Vm, dKxy, sxy, s);
     mix_xy(d, ws.Vg, ws.Um, Kxy, true, s);
     ok &= xy_synthesis(d, ws, ws.Um, ws.tmp, sxy, s);
-    k_axpy_f<<<blocks_for(nact, 256), 256, 0, s>>>(ws.dv, ws.tmp, nact);
+    (void)launch_pdl(k_axpy_f, dim3(blocks_for(nact, 256)), dim3(256), 0, s, ws.dv, ws.tmp, nact);
     PSFD_CHECK_LAUNCH();
   }
   if (!ok) { psfd_set_error("fno_backward: unsupported size"); return PSFD_ERR_ARG; }
-  k_lift_bwd<<<(unsigned)(2 * 148), 256, 0, s>>>(a, ws.dv, g->lift_w, g->lift_b, B, C, nx, ny, nz);
+  (void)launch_pdl(k_lift_bwd, dim3((unsigned)(2 * 148)), dim3(256), 0, s, a, ws.dv, g->lift_w, g->lift_b, B, C, nx, ny, nz);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -1070,6 +1086,7 @@ extern "C" int fno_backward(const fno_weights_t* w, const fno_grads_t* g, const 
 // ---------------------------------------------------------------- spectral upsampling
 __global__ void k_pad_spectrum(const cf* __restrict__ src, cf* __restrict__ dst, int nx0, int ny0, int nz0, int nx,
                                int ny, int nz, long nb, float scale) {
+  pdl_enter();
   const long n0 = (long)nx0 * ny0 * nz0;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb * n0) return;
@@ -1095,7 +1112,7 @@ static int upsample_run(const psfd_c64* src, int nb, int nx0, int ny0, int nz0, 
   if ((rc = launch_cols(ny0, nx0, tmp, (long)nb * nz0 * nx0, true, 1.f, tw + twoff[1], s))) return rc;
   if ((rc = launch_cols(nz0, nx0 * ny0, tmp, (long)nb * nx0 * ny0, true, 1.f, tw + twoff[2], s))) return rc;
   PSFD_CUDA_TRY(cudaMemsetAsync(dst, 0, (size_t)nb * n1 * sizeof(cf), s));
-  k_pad_spectrum<<<blocks_for((long)nb * n0, 256), 256, 0, s>>>(tmp, (cf*)dst, nx0, ny0, nz0, nx, ny, nz, nb,
+  (void)launch_pdl(k_pad_spectrum, dim3(blocks_for((long)nb * n0, 256)), dim3(256), 0, s, tmp, (cf*)dst, nx0, ny0, nz0, nx, ny, nz, nb,
                                                                 1.0f / (float)n0);
   PSFD_CHECK_LAUNCH();
   if ((rc = launch_cols(nz, nx * ny, (cf*)dst, (long)nb * nx * ny, false, 1.f, tw + twoff[5], s))) return rc;

@@ -22,6 +22,7 @@
 #include <cstdlib>
 
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(NT2) k_mlp_tc(const float* vin, float* vout, c
                                                 const float* __restrict__ b1, const float* __restrict__ W2,
                                                 const float* __restrict__ b2, long N, int B, int outer_gelu,
                                                 int* err) {
+  pdl_enter();
   constexpr int HC = MLP_C / 2, HH = MLP_H / 2;   // channels and hidden units per thread
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* Ahi = sm;
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(NT2) k_proj_tc(const float* __restrict__ v, cf
                                                  const float* __restrict__ Q1, const float* __restrict__ qb1,
                                                  const float* __restrict__ Q2, const float* __restrict__ qb2, long N,
                                                  int B, int* err) {
+  pdl_enter();
   constexpr int HC = MLP_C / 2, HQ = PROJ_Q / 2;
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* Ahi = sm;
@@ -404,7 +407,7 @@ int fno_mlp_tc(const float* vin, float* vout, const float* uxy, const float* uz,
   int rc = mlp_err_ptr();
   if (rc) return rc;
   const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 2);
-  k_mlp_tc<<<grid, NT2, MLP_SMEM, s>>>(vin, vout, uxy, uz, W1, b1, W2, b2, N, B, outer_gelu ? 1 : 0, g_mlp_err);
+  (void)launch_pdl(k_mlp_tc, dim3(grid), dim3(NT2), MLP_SMEM, s, vin, vout, uxy, uz, W1, b1, W2, b2, N, B, outer_gelu ? 1 : 0, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -414,7 +417,7 @@ int fno_proj_tc(const float* v, cf* E, const float* Q1, const float* qb1, const 
   int rc = mlp_err_ptr();
   if (rc) return rc;
   const unsigned grid = persistent_grid(((long)B * N + MT - 1) / MT, 2);
-  k_proj_tc<<<grid, NT2, PROJ_SMEM, s>>>(v, E, Q1, qb1, Q2, qb2, N, B, g_mlp_err);
+  (void)launch_pdl(k_proj_tc, dim3(grid), dim3(NT2), PROJ_SMEM, s, v, E, Q1, qb1, Q2, qb2, N, B, g_mlp_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }

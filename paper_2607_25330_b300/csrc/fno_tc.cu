@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -77,6 +78,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __global__ void __launch_bounds__(TC_THREADS) k_mix_tc(const cf* __restrict__ V, cf* __restrict__ U,
                                                        const cf* __restrict__ K, long NB, int mx, int MX, int offy,
                                                        int offx, int* err) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* As = sm;
   unsigned char* Bs = sm + A_BYTES;
@@ -202,7 +204,7 @@ int fno_mix_tc(const cf* V, cf* U, const cf* K, long NB, int modes, int mx, int 
     return PSFD_ERR_CUDA;
   }
   dim3 g((unsigned)((NB + TC_M - 1) / TC_M), (unsigned)modes);
-  k_mix_tc<<<g, TC_THREADS, A_BYTES + B_BYTES, s>>>(V, U, K, NB, mx, MX, offy, offx, g_tc_err);
+  (void)launch_pdl(k_mix_tc, dim3(g), dim3(TC_THREADS), A_BYTES + B_BYTES, s, V, U, K, NB, mx, MX, offy, offx, g_tc_err);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
