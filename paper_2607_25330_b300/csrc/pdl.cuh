@@ -1,4 +1,5 @@
-// Programmatic dependent launch for the kernels of a Krylov iteration.
+// Programmatic dependent launch for the kernels of the solver loops (Krylov iterations, refinement
+// residuals) and of the FNO.
 //
 // A kernel launched with launch_pdl may be scheduled before the kernel ahead of it on the stream
 // has fully retired (the driver overlaps the two launches' set-up).  Its first statement is
