@@ -174,6 +174,7 @@ struct Row64 {
   const zd* tw;
   zd* y;
   int ny, nz, nab, za0;
+  const int* plane_nz;   // nullable (forward transforms): planes flagged 0 are zero and are skipped
 };
 
 template <int NX, int T, int OP, class C>
@@ -187,6 +188,8 @@ __global__ void __launch_bounds__(64) k_rows64(Row64 a) {
   const int p = lane / T, t = lane - p * T;
   const long row = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * P + p;
   const bool act = row < a.nrows;
+  // a zero plane transforms to zero: a warp whose rows all lie in zero planes has nothing to do
+  if (a.plane_nz && __all_sync(0xffffffffu, !act || !a.plane_nz[row / a.ny])) return;
   zd* src = a.buf + (act ? row : 0) * NX;
   const RT scale(a.scale);
   C v[R];
@@ -234,6 +237,7 @@ struct Col64 {
   const zd* pc;   // per-plane contrast; multiplier cs * c[z]
   double cs;
   int nab, za0;
+  const int* plane_nz;   // nullable (forward transforms): planes flagged 0 are zero and are skipped
   long plane_elems;
 };
 
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(64) k_cols64(Col64 a) {
   const bool act = colid < a.ncolumns;
   const long cid = act ? colid : 0;
   const long plane = cid / a.nx;
+  if (a.plane_nz && __all_sync(0xffffffffu, !act || !a.plane_nz[plane])) return;   // zero planes stay zero
   const int ix = (int)(cid - plane * a.nx);
   zd* base = a.buf + plane * a.plane_elems + ix;
   const long sx = a.nx;
@@ -406,6 +411,7 @@ int fp64_prepare(psfd_plan_s* P) {
     std::vector<zd> sinv, twx, twy, twz;
     pml_sinv64(P, sinv);
     host_tw64(P->nx, twx); host_tw64(P->ny, twy); host_tw64(P->nz, twz);
+    PSFD_CUDA_TRY(cudaMalloc((void**)&F.plane_nz, (size_t)P->nrhs * 3 * P->nz * sizeof(int)));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.kx, P->nx * 8));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.ky, P->ny * 8));
     PSFD_CUDA_TRY(cudaMalloc((void**)&F.kz, P->nz * 8));
@@ -446,9 +452,29 @@ int fp64_prepare(psfd_plan_s* P) {
   return PSFD_OK;
 }
 
+// flags[q] = 1 if plane q of a (nplanes planes of ncols complex64 entries) has a nonzero (or NaN)
+// entry, else 0
+__global__ void k_plane_any(const cf* __restrict__ a, long plane_elems, int* flags) {
+  const cf* p = a + (long)blockIdx.x * plane_elems;
+  int any = 0;
+  for (long i = threadIdx.x; i < plane_elems; i += blockDim.x) {
+    const cf v = p[i];
+    any |= (v.x != 0.f) || (v.y != 0.f);
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) flags[blockIdx.x] = any;
+}
+
+int plane_flags(psfd_plan_s* P, const cf* a, long nplanes, int* flags) {
+  k_plane_any<<<(unsigned)nplanes, 256, 0, P->stream>>>(a, P->ncols, flags);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
 void fp64_free(psfd_plan_s* P) {
   Fp64Tables& F = P->F;
-  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.sback, F.twx, F.twy, F.twz, F.G, F.X, F.kz_f, F.sinv_f, F.twx_f, F.twy_f, F.twz_f};
+  void* ptrs[] = {F.kx, F.ky, F.kz, F.sinv, F.sback, F.twx, F.twy, F.twz, F.G, F.X, F.kz_f, F.sinv_f, F.twx_f, F.twy_f, F.twz_f,
+                  F.plane_nz};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   F = Fp64Tables();
@@ -494,14 +520,15 @@ int apply64_hybrid(psfd_plan_s* P, const zd* x, zd* y) {
 }
 
 // real space <-> HYBRID in FP64 over nplanes planes (unitary scale applied once)
-int transform64(psfd_plan_s* P, zd* buf, long nplanes, bool forward, double scale) {
+int transform64(psfd_plan_s* P, zd* buf, long nplanes, bool forward, double scale, const int* plane_nz) {
   StageScope sc(P->stream, ST_TRANSFORM);
   int rc;
   Row64 r{};
   r.buf = buf; r.nrows = nplanes * P->ny; r.tw = P->F.twx; r.twf = reinterpret_cast<const cff*>(P->F.twx_f);
+  r.ny = P->ny; r.plane_nz = forward ? plane_nz : nullptr;
   Col64 c{};
   c.buf = buf; c.ncolumns = nplanes * P->nx; c.nx = P->nx; c.tw = P->F.twy; c.twf = reinterpret_cast<const cff*>(P->F.twy_f);
-  c.plane_elems = P->ncols;
+  c.plane_elems = P->ncols; c.plane_nz = forward ? plane_nz : nullptr;
   if (forward) {
     r.scale = 1.0;
     if ((rc = rows64(P->nx, r, R64_FWD, P->stream))) return rc;

@@ -27,6 +27,7 @@ struct Fp64Tables {
   double2* G = nullptr;
   size_t G_elems = 0;
   double2* X = nullptr;      // [nrhs][3][nz][ny][nx] input copy of the real-space psfd_apply64
+  int* plane_nz = nullptr;   // [nrhs][3][nz] 1 where a plane of the refined solve's b is not zero
   // double-float (hi, lo) copies used by the extended-precision transforms
   float* kz_f = nullptr;
   float* sinv_f = nullptr;
@@ -106,7 +107,9 @@ struct psfd_plan_s {
 int fp64_prepare(psfd_plan_s* P);
 void fp64_free(psfd_plan_s* P);
 int apply64_hybrid(psfd_plan_s* P, const double2* x, double2* y);
-int transform64(psfd_plan_s* P, double2* buf, long nplanes, bool forward, double scale);
+int transform64(psfd_plan_s* P, double2* buf, long nplanes, bool forward, double scale,
+                const int* plane_nz = nullptr);
+int plane_flags(psfd_plan_s* P, const cf* a, long nplanes, int* flags);
 
 // apply.cu
 int launch_axial(psfd_plan_s* P, const cf* x, cf* y, int mode, const int* done, int nrhs_active);

@@ -1264,7 +1264,10 @@ extern "C" int psfd_solve_ex(psfd_plan P, const psfd_c64* b, const psfd_c64* x0,
   // b (complex64, real space) -> FP64 HYBRID
   a64.a32 = (const cf*)b; a64.o64 = b64;
   if ((rc = launch_v64<V64_PROMOTE>(a64, nr, st, nb))) return fail(rc);
-  if ((rc = transform64(P, b64, nplanes, true, us))) return fail(rc);
+  // b usually vanishes outside the absorber planes (it carries the factor delta-eps): the zero
+  // planes, flagged from b itself, are left out of its lateral transform
+  if ((rc = plane_flags(P, (const cf*)b, nplanes, P->F.plane_nz))) return fail(rc);
+  if ((rc = transform64(P, b64, nplanes, true, us, P->F.plane_nz))) return fail(rc);
   a64.a64 = b64;
   if ((rc = launch_v64<V64_NORM>(a64, nr, st, nb))) return fail(rc);
   // ||b||^2 stays in res0 until the first inner solve: it is read with the first residual
